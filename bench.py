@@ -1,0 +1,398 @@
+"""Benchmark: delayed-asynchronous PageRank + Bellman-Ford on RMAT scale 22.
+
+One step = one PageRank solve (d = 0.85, tol 1e-6, delayed) plus eight
+Bellman-Ford solves (fixed sources, uint32 weights in [1, 255], delayed) on the
+RMAT scale-22 graph (a=.57 b=.19 c=.19, edge factor 16, seed 2), all in the
+persistent CUDA kernels behind the C ABI. The metric is GTEPS counted per
+finished solve: (solves * m) / time. With inputs resident in HBM the timed
+region holds K steps between CUDA events; `e2e` repeats the step through the
+public API from pinned host buffers (graph upload, plan, solves, result
+download). The CSR (about 285 MB) and weights are larger than L2, so no flush
+is needed between steps.
+
+--impl reference times the CPU oracle's OpenMP form of the same method (the
+paper's CPU scheme) on the host cores, on a bounded sample of the workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PageRank/SSSP time-to-converge & GTEPS at tol 1e-6; batched & adjoint vs plain"
+SCALE, EF, SEED = 22, 16, 2
+N_SOURCES = 8
+PR_DELTA, SSSP_DELTA = 256, 32
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    mx.append(float(p[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, p[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def build_inputs():
+    from paper_2110_01409_gb300 import inputs as I
+
+    t0 = time.time()
+    g = I.rmat(SCALE, EF, 0.57, 0.19, 0.19, seed=SEED)
+    w = I.weights_u32(g, SEED)
+    srcs = I.sources(g, N_SOURCES, seed=SEED)
+    return g, w, srcs, time.time() - t0
+
+
+def algorithmic_bytes(n, m, kind):
+    """Compulsory bytes of one sweep (gathers of the state vector count as L2
+    hits: the 4n-byte vector fits in L2): rowptr 4(n+1), colidx 4m, own old
+    value 4n + new value 4n, plus per-vertex out-degree 4n (PageRank) or the
+    per-edge weight 4m (Bellman-Ford)."""
+    base = 4 * (n + 1) + 4 * m + 8 * n
+    return base + (4 * n if kind == "pr" else 4 * m)
+
+
+def run_gpu(args):
+    import torch
+
+    from paper_2110_01409_gb300 import build as B
+    from paper_2110_01409_gb300 import dag
+
+    rank, world, local = _dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    g, w, srcs, gen_s = build_inputs()
+    n, m = g.n, g.m
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    rowptr = torch.from_numpy(g.rowptr).to(dev)
+    colidx = torch.from_numpy(g.colidx).to(dev)
+    w_d = torch.from_numpy(w.view(np.int32)).to(dev)
+    plan = dag.Plan(rowptr, colidx)
+    rank_out = torch.empty(n, dtype=torch.float32, device=dev)
+    dist_out = [torch.empty(n, dtype=torch.int32, device=dev) for _ in range(N_SOURCES)]
+
+    # ---- warm-up with statuses (also records per-solve sweeps) ----
+    pr_iters, bf_iters = [], []
+    for _ in range(args.warmup):
+        _, st = dag.pagerank(plan, 0.85, 1e-6, "delayed", PR_DELTA, 1000, out=rank_out)
+        assert st["converged"], st
+        pr_iters.append(st["iters"])
+        its = []
+        for k, s in enumerate(srcs):
+            _, st = dag.sssp(plan, int(s), w_d, "delayed", SSSP_DELTA, n + 1, out=dist_out[k])
+            assert st["converged"], st
+            its.append(st["iters"])
+        bf_iters.append(its)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, device events, per-launch events for the roofline ----
+    K = args.steps
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    pr_ev = [(ev(), ev()) for _ in range(K)]
+    bf_ev = [[(ev(), ev()) for _ in range(N_SOURCES)] for _ in range(K)]
+    t_start, t_end = ev(), ev()
+    clocks = Clocks(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_start.record(stream)
+    for k in range(K):
+        pr_ev[k][0].record(stream)
+        dag.pagerank(plan, 0.85, 1e-6, "delayed", PR_DELTA, 1000, out=rank_out, stats=False)
+        pr_ev[k][1].record(stream)
+        for j, s in enumerate(srcs):
+            bf_ev[k][j][0].record(stream)
+            dag.sssp(plan, int(s), w_d, "delayed", SSSP_DELTA, n + 1, out=dist_out[j], stats=False)
+            bf_ev[k][j][1].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms_total = t_start.elapsed_time(t_end)
+    if world > 1:
+        tt = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_total = float(tt.item())
+        dist.barrier()
+    ms_step = ms_total / K
+    solves = 1 + N_SOURCES
+    value = world * solves * m * K / (ms_total * 1e-3) / 1e9
+
+    # statuses of the timed solves: one more checked step (results must match the warm-up)
+    _, st_pr = dag.pagerank(plan, 0.85, 1e-6, "delayed", PR_DELTA, 1000, out=rank_out)
+    assert st_pr["converged"]
+    pr_ms = statistics.mean(a.elapsed_time(b) for a, b in pr_ev)
+    bf_ms = statistics.mean(a.elapsed_time(b) for row in bf_ev for a, b in row)
+    pr_sweeps = statistics.mean(pr_iters + [st_pr["iters"]])
+    bf_sweeps = statistics.mean(x for row in bf_iters for x in row)
+    pr_bytes = algorithmic_bytes(n, m, "pr") * pr_sweeps
+    bf_bytes = algorithmic_bytes(n, m, "bf") * bf_sweeps
+    peak, peak_kind = _peaks()
+    # dominant kernel by total time in the step
+    if bf_ms * N_SOURCES >= pr_ms:
+        dom, dom_bytes, dom_ms, dom_sweeps = "sweep_kernel<BF,DELAYED>", bf_bytes, bf_ms, bf_sweeps
+    else:
+        dom, dom_bytes, dom_ms, dom_sweeps = "sweep_kernel<PR,DELAYED>", pr_bytes, pr_ms, pr_sweeps
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    traffic = _recorded_traffic(dom, dom_sweeps)
+
+    # ---- e2e through the public API from pinned host buffers ----
+    e2e = run_e2e(args, g, w, srcs, dev, dag, torch) if args.e2e else None
+
+    detail = {}
+    if args.detail and rank == 0:
+        detail = run_detail(g, w, srcs, plan, w_d, dag, torch, args)
+
+    out = {
+        "metric": METRIC,
+        "value": round(value, 3),
+        "unit": "GTEPS",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_step, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32/u32",
+        "data": "synthetic (seeded RMAT stand-in for the GAP Kron graph)",
+        "config": {"workload": f"rmat{SCALE}: pagerank d=0.85 tol=1e-6 delayed delta={PR_DELTA} + "
+                               f"sssp x{N_SOURCES} sources delayed delta={SSSP_DELTA}",
+                   "n": n, "m": m, "sources": [int(s) for s in srcs], "workers": st_pr["workers"],
+                   "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (CSR+weights ~0.55 GB)",
+                   "graph_gen_s": round(gen_s, 2)},
+        "per_solve": {"pagerank_ms": round(pr_ms, 3), "pagerank_sweeps": pr_sweeps,
+                      "sssp_ms": round(bf_ms, 3), "sssp_sweeps": bf_sweeps,
+                      "gteps_work_rate": round(((pr_sweeps + N_SOURCES * bf_sweeps) * m) / (ms_step * 1e-3) / 1e9, 3)},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "bytes_per_launch": int(dom_bytes), "traffic": traffic},
+        "clocks": clk,
+        "gpu_launches": K * solves,
+        "e2e": e2e,
+    }
+    if rank == 0 and args.cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(g, w, srcs)
+    if detail:
+        out["detail"] = detail
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _recorded_traffic(kernel, sweeps):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (hash match); else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        src = open(os.path.join(ROOT, "paper_2110_01409_gb300", "csrc", "sweep.cu"), "rb").read()
+        if rec.get("sweep_cu_sha256") != hashlib.sha256(src).hexdigest():
+            return None
+        per_sweep = rec["kernels"][kernel]["dram_bytes_per_sweep"]
+        return int(per_sweep * sweeps)
+    except Exception:
+        return None
+
+
+def run_e2e(args, g, w, srcs, dev, dag, torch):
+    """Same step through the public API from pinned host memory, copies inside the timed region."""
+    rp_h = torch.from_numpy(g.rowptr).pin_memory()
+    ci_h = torch.from_numpy(g.colidx).pin_memory()
+    w_h = torch.from_numpy(w.view(np.int32)).pin_memory()
+    res_pr = torch.empty(g.n, dtype=torch.float32).pin_memory()
+    res_bf = torch.empty((N_SOURCES, g.n), dtype=torch.int32).pin_memory()
+    h2d = rp_h.numel() * 4 + ci_h.numel() * 4 + w_h.numel() * 4
+    d2h = res_pr.numel() * 4 + res_bf.numel() * 4
+    K = max(1, min(args.steps, 3))
+
+    def step():
+        rp = rp_h.to(dev, non_blocking=True)
+        ci = ci_h.to(dev, non_blocking=True)
+        wd = w_h.to(dev, non_blocking=True)
+        plan = dag.Plan(rp, ci)
+        r, _ = dag.pagerank(plan, 0.85, 1e-6, "delayed", PR_DELTA, 1000, stats=False)
+        res_pr.copy_(r, non_blocking=True)
+        for j, s in enumerate(srcs):
+            d, _ = dag.sssp(plan, int(s), wd, "delayed", SSSP_DELTA, g.n + 1, stats=False)
+            res_bf[j].copy_(d, non_blocking=True)
+        torch.cuda.synchronize()
+        plan.close()
+
+    step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        step()
+    t = (time.perf_counter() - t0) / K
+    return {"value": round((1 + N_SOURCES) * g.m / t / 1e9, 3), "unit": "GTEPS", "ms_per_step": round(t * 1e3, 3),
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+
+def run_detail(g, w, srcs, plan, w_d, dag, torch, args):
+    """Per-variant sweeps and times (3 trials) on the same graph; paper's variants table."""
+    res = {}
+    trials = 3
+    for name, var, dl in [("sync", "sync", 0), ("async", "async", 0), ("delayed32", "delayed", 32),
+                          ("delayed256", "delayed", 256), ("delayed4096", "delayed", 4096)]:
+        pr_it, pr_ms, bf_it, bf_ms = [], [], [], []
+        for _ in range(trials):
+            _, st = dag.pagerank(plan, 0.85, 1e-6, var, dl, 1000)
+            pr_it.append(st["iters"])
+            pr_ms.append(st["ms"])
+            _, st = dag.sssp(plan, int(srcs[0]), w_d, var, dl, g.n + 1)
+            bf_it.append(st["iters"])
+            bf_ms.append(st["ms"])
+        res[name] = {"pr_sweeps": pr_it, "pr_ms_median": round(statistics.median(pr_ms), 3),
+                     "sssp_sweeps": bf_it, "sssp_ms_median": round(statistics.median(bf_ms), 3)}
+    return res
+
+
+def cpu_baseline(g, w, srcs):
+    """The oracle's OpenMP form (paper's CPU scheme) on all host cores: one
+    delayed PageRank and one delayed Bellman-Ford solve of the same graph."""
+    import oracle
+
+    cores = os.cpu_count() or 1
+    _, it_pr, s_pr, ok1 = oracle.pagerank_threads(g, oracle.DELAYED, tol=1e-6, threads=cores, delta=PR_DELTA)
+    _, it_bf, s_bf, ok2 = oracle.sssp_threads(g, w, int(srcs[0]), oracle.DELAYED, threads=cores, delta=SSSP_DELTA)
+    secs = s_pr + s_bf
+    return {"value": round(2 * g.m / secs / 1e9, 4), "unit": "GTEPS", "cores": cores, "kind": "oracle",
+            "sample": f"1 pagerank (delta {PR_DELTA}, {it_pr} sweeps, {s_pr:.2f}s) + 1 sssp from source {int(srcs[0])} "
+                      f"(delta {SSSP_DELTA}, {it_bf} sweeps, {s_bf:.2f}s) of the 1+{N_SOURCES}-solve step",
+            "converged": bool(ok1 and ok2)}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle's paper-scheme form, timed on the host cores."""
+    rank, world, _ = _dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    g, w, srcs, _ = build_inputs()
+    cores = os.cpu_count() or 1
+
+    def step():
+        _, _, s1, _ = oracle.pagerank_threads(g, oracle.DELAYED, tol=1e-6, threads=cores, delta=PR_DELTA)
+        _, _, s2, _ = oracle.sssp_threads(g, w, int(srcs[0]), oracle.DELAYED, threads=cores, delta=SSSP_DELTA)
+        return s1 + s2
+
+    for _ in range(args.warmup):
+        step()
+    t = sum(step() for _ in range(args.steps))
+    value = 2 * g.m * args.steps / t / 1e9
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GTEPS", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t / args.steps * 1e3, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/u32",
+           "data": "synthetic (seeded RMAT stand-in for the GAP Kron graph)",
+           "config": {"workload": f"rmat{SCALE}: pagerank d=0.85 tol=1e-6 delayed delta={PR_DELTA} + "
+                                  f"sssp x{N_SOURCES} sources delayed delta={SSSP_DELTA}", "n": g.n, "m": g.m},
+           "cpu_baseline": {"value": round(value, 4), "unit": "GTEPS", "cores": cores, "kind": "oracle",
+                            "sample": "each step: 1 pagerank + 1 sssp (source 0 of 8) of the 1+8-solve step"},
+           "e2e": {"value": round(value, 4), "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="dag", choices=["dag", "reference"])
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--detail", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,213 @@
+/*
+ * dag.h -- C ABI of libdag.so: delayed-asynchronous pull PageRank and
+ * Bellman-Ford SSSP on one GB300 GPU (sm_103a).
+ *
+ * Method: Blanco, McMillan, Low, "Delayed Asynchronous Iterative Graph
+ * Algorithms", HPEC 2021. Each worker (here: a CTA) owns a contiguous block of
+ * vertices balanced by in-neighbour count (Sec. III-A), computes its vertices
+ * with a pull over their in-edges, and either writes each new value straight
+ * into the global array (asynchronous, Sec. I), or to a separate array read
+ * only in the next iteration (synchronous, Sec. I), or to a private buffer of
+ * delta values that it copies to the global array when full and at the end of
+ * its block (delayed asynchronous, Sec. III and III-B). One barrier separates
+ * iterations (Sec. I).
+ *
+ * Conventions for every entry point:
+ *  - Graphs are in-edge CSR: colidx[rowptr[v] .. rowptr[v+1]) are the sources u
+ *    of the edges u -> v. rowptr/colidx are int32 (m < 2^31).
+ *  - Pointers named d_* are DEVICE pointers on the current CUDA device; h_*
+ *    are HOST pointers. All arrays belong to the caller; the library keeps no
+ *    pointer to them after the call returns, except that a plan keeps the CSR
+ *    pointers it was created with (the caller keeps them alive and unchanged
+ *    until dag_plan_destroy).
+ *  - stream is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream). Work is enqueued on it. When a host stats pointer is given, the
+ *    call waits for the stream before returning.
+ *  - Return value: DAG_OK (0) or a negative DAG_ERR_* code; dag_strerror()
+ *    names it and dag_last_error_message() adds detail. Arguments are checked
+ *    on the host before anything is enqueued; a rejected call changes nothing.
+ *  - A solve that reaches max_iters without meeting its stopping rule returns
+ *    DAG_ERR_NOT_CONVERGED and still writes its last iterate.
+ *  - Every device-side wait (the grid barrier between iterations) has a time
+ *    limit; when it runs out the kernel stops, the call returns
+ *    DAG_ERR_BARRIER_TIMEOUT and the CUDA context stays usable.
+ */
+#ifndef DAG_H
+#define DAG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DAG_OK 0
+#define DAG_ERR_INVALID (-1)          /* bad argument: shape, range, null, delta < 0 ... */
+#define DAG_ERR_NOT_CONVERGED (-2)    /* max_iters reached; outputs hold the last iterate */
+#define DAG_ERR_BARRIER_TIMEOUT (-3)  /* a grid barrier wait ran out of time */
+#define DAG_ERR_CUDA (-4)             /* a CUDA runtime call failed */
+#define DAG_ERR_NOMEM (-5)            /* device allocation failed */
+
+/* Update order (Sec. I and III-B). DAG_DELAYED with delta = 0 is DAG_ASYNC. */
+typedef enum { DAG_SYNC = 0, DAG_ASYNC = 1, DAG_DELAYED = 2 } dag_variant;
+
+/* In-edge CSR, device arrays. */
+typedef struct {
+    int32_t n;              /* vertices, >= 1 */
+    int64_t m;              /* edges, 0 <= m < 2^31 */
+    const int32_t* d_rowptr; /* [n+1], rowptr[0] = 0, nondecreasing, rowptr[n] = m */
+    const int32_t* d_colidx; /* [m], each in [0, n) */
+} dag_csr;
+
+/* Result of one solve (host struct). */
+typedef struct {
+    int32_t iters;           /* sweeps run, the one that met the stopping rule included */
+    int32_t err;             /* DAG_OK, DAG_ERR_NOT_CONVERGED or DAG_ERR_BARRIER_TIMEOUT */
+    double residual;         /* last sweep: L1 change (PageRank) or vertices updated (SSSP) */
+    float ms;                /* device time of the solve, CUDA events around it */
+    int32_t workers;         /* CTAs that held a vertex block (the paper's thread count) */
+    int32_t delta;           /* buffer size used (0 for sync/async) */
+    int64_t flushes;         /* buffer flushes over the whole solve (delayed only) */
+    int64_t edges_processed; /* m * iters */
+} dag_stats;
+
+typedef struct dag_plan dag_plan; /* opaque */
+
+/*
+ * Plan: out-degrees, per-vertex data and workspace for one graph (the
+ * untimed setup step: Sec. III-A's static partition is computed per launch
+ * shape and cached here). d_colidx entries are checked against [0, n) on the
+ * device. The plan owns its workspace and frees it in dag_plan_destroy.
+ * barrier_timeout_ms <= 0 selects the default (2000 ms).
+ */
+int dag_plan_create(const dag_csr* csr, int32_t barrier_timeout_ms, dag_plan** out);
+int dag_plan_destroy(dag_plan* plan);
+
+/* Copies the plan's out-degree array (int32 [n]) into d_outdeg (device). */
+int dag_plan_out_degree(const dag_plan* plan, int32_t* d_outdeg, void* stream);
+
+/*
+ * The static partition the sweep kernels use for `workers` CTAs (Sec. III-A):
+ * h_start[p] (host, workers+1 values) is the first vertex of block p, chosen
+ * so that every block carries about (n + m)/workers of the weight
+ * (in-degree + 1) per vertex: h_start[p] = min { v : v + rowptr[v] >=
+ * ceil(p (n+m) / workers) }. Synchronous (waits for the result).
+ */
+int dag_partition(dag_plan* plan, int32_t workers, int32_t* h_start);
+
+/* Largest number of CTAs the persistent kernel of this (variant, delta) runs with. */
+int dag_workers(dag_plan* plan, dag_variant variant, int32_t delta, int32_t* out_workers);
+
+#define DAG_PR_WARM_START 1 /* flags: start from d_rank instead of the teleport vector */
+
+/*
+ * PageRank (Sec. IV-A; stopping rule Sec. IV):
+ *   r'_v = (1-d) t_v + d ( sum_{u in in(v)} M_vu r_u + D/n ),
+ * M_vu = 1/outdeg(u) when d_val is NULL, else d_val[e] (P_vu per in-edge e,
+ * e.g. from dag_normalize_weights). t = d_teleport (device, n, sum 1) or 1/n
+ * when NULL. D is the dangling mass, formed as T - N (T = sum t, N = mass on
+ * vertices with out-edges) from the global array as each tile of rows is
+ * computed. Stops after the first sweep whose sum_v |r'_v - r_v| <= tol.
+ * d in (0,1), tol > 0, max_iters >= 1, delta >= 0 (counted in 32-bit vertex
+ * values, Sec. III-B; delta >= rows per CTA flushes once per sweep). d_rank
+ * (device, float [n]) receives r; with DAG_PR_WARM_START it also gives r^0.
+ * Without it r^0 = t. FP32 values, FP64 residual and dangling sums.
+ */
+int dag_pagerank(dag_plan* plan, float d, double tol, dag_variant variant, int32_t delta,
+                 int32_t max_iters, const float* d_teleport, const float* d_val, float* d_rank,
+                 int32_t flags, dag_stats* h_stats, void* stream);
+
+/*
+ * Bellman-Ford SSSP (Sec. IV): dist'_v = min(dist_v, min over in-edges with
+ * dist_u finite of dist_u + w_uv), every value stored every sweep (Sec. IV,
+ * "unconditionally storing updates"); stops after a sweep that lowered no
+ * value. d_w: uint32 weight per in-edge (device, [m]); d_dist (device,
+ * uint32 [n]) receives the distances, 0xFFFFFFFF for unreachable vertices.
+ */
+int dag_sssp(dag_plan* plan, uint32_t src, dag_variant variant, int32_t delta, int32_t max_iters,
+             const uint32_t* d_w, uint32_t* d_dist, dag_stats* h_stats, void* stream);
+
+/* Result of a batched solve (host struct). */
+typedef struct {
+    int32_t sweeps;          /* sweeps the launch ran (the slowest column's) */
+    int32_t err;             /* DAG_OK, DAG_ERR_NOT_CONVERGED or DAG_ERR_BARRIER_TIMEOUT */
+    float ms;                /* device time */
+    int32_t workers;
+    int32_t delta;
+    int64_t column_sweeps;   /* sum over columns of the sweeps each ran */
+} dag_batch_stats;
+
+/*
+ * Batched personalized PageRank: B teleport columns in one persistent launch
+ * (no counterpart in the paper; each column is the PageRank of dag_pagerank
+ * with its own teleport). d_V: row-major float [n][B] (column c = teleport of
+ * problem c, sum 1). d_R: row-major float [n][B], receives the ranks (r^0 = V).
+ * Each column stops on its own at its first sweep with L1 change <= tol and
+ * is frozen from then on. d_iters (device int32 [B]) receives each column's
+ * sweep count. B in [1, 1024]. delta as in dag_pagerank (rows per CTA).
+ */
+int dag_ppr_batched(dag_plan* plan, float d, double tol, dag_variant variant, int32_t delta,
+                    int32_t max_iters, int32_t B, const float* d_V, float* d_R, int32_t* d_iters,
+                    dag_batch_stats* h_stats, void* stream);
+
+/*
+ * Batched Bellman-Ford: B sources in one persistent launch; d_src (device
+ * uint32 [B]); d_D row-major uint32 [n][B] receives the distances; d_iters
+ * (device int32 [B]) each column's sweep count (a column stops after a sweep
+ * that lowered none of its values). B in [1, 1024].
+ */
+int dag_sssp_batched(dag_plan* plan, dag_variant variant, int32_t delta, int32_t max_iters, int32_t B,
+                     const uint32_t* d_src, const uint32_t* d_w, uint32_t* d_D, int32_t* d_iters,
+                     dag_batch_stats* h_stats, void* stream);
+
+/*
+ * Out-edge CSR of the plan's graph (for the adjoint pull). d_out_rowptr
+ * (device int32 [n+1]), d_out_colidx (device int32 [m]: targets v of u's
+ * out-edges, ascending), d_perm (device int32 [m]): in-edge index of each
+ * out-edge, so that out-edge k is in-edge d_perm[k].
+ */
+int dag_transpose(dag_plan* plan, int32_t* d_out_rowptr, int32_t* d_out_colidx, int32_t* d_perm,
+                  void* stream);
+
+/*
+ * Row normalisation of raw edge weights into the transition matrix: d_s[u] =
+ * sum of d_w over u's out-edges (device float [n]), d_val[e] = d_w[e] /
+ * d_s[src(e)] (device float [m], in-edge order). d_w > 0 expected. (M_vu of
+ * dag_pagerank; no counterpart in the paper.)
+ */
+int dag_normalize_weights(dag_plan* plan, const float* d_w, float* d_val, float* d_s, void* stream);
+
+/*
+ * PageRank adjoint (no counterpart in the paper): for a loss with dL/dr = c,
+ * solves lambda = c + d M^T lambda + d g (sum_v lambda_v)/n (g: vertices with
+ * no out-edges) by the same sweep (variant, delta) pulled over the out-edge
+ * CSR held by out_plan (a plan created on dag_transpose's output), with
+ * d_val_out[k] = P of out-edge k. Stops at L1 change <= tol * ||c||_1. Then
+ * (with d_rank the forward result, d_s the normaliser, d_val the in-edge P):
+ *   d_grad_w[e] = d r_u (lambda_v - (M^T lambda)_u) / s_u  for in-edge e = (u -> v),
+ *   d_grad_t[v] = (1 - d) lambda_v.
+ * d_lambda (device float [n], nullable) receives lambda.
+ */
+int dag_pagerank_adjoint(dag_plan* in_plan, dag_plan* out_plan, float d, double tol, dag_variant variant,
+                         int32_t delta, int32_t max_iters, const float* d_val, const float* d_val_out,
+                         const float* d_s, const float* d_rank, const float* d_c, float* d_grad_w,
+                         float* d_grad_t, float* d_lambda, dag_stats* h_stats, void* stream);
+
+/* Names an error code. Never NULL. */
+const char* dag_strerror(int code);
+/* Detail of the last error raised on the calling host thread ("" if none). */
+const char* dag_last_error_message(void);
+
+/*
+ * Test hook for the failure path: when nonzero, the next solve on this plan
+ * makes CTA 0 leave before its first grid barrier, so the others' bounded
+ * waits run out (after timeout_ms) and the call returns
+ * DAG_ERR_BARRIER_TIMEOUT. Resets itself after one solve.
+ */
+int dag_debug_skip_barrier_once(dag_plan* plan, int32_t timeout_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DAG_H */

@@ -1,0 +1,275 @@
+// C ABI entry points of libdag.so (declared in include/dag.h): argument
+// checks, launch of the persistent sweep, timing and status read-back.
+#include <cmath>
+#include <cstdio>
+#include <string>
+
+#include "dag_internal.cuh"
+
+namespace dag {
+
+static thread_local std::string g_last_error;
+
+int set_error(int code, const std::string& msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_check(cudaError_t e, const char* what)
+{
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return DAG_ERR_NOMEM;
+    return DAG_ERR_CUDA;
+}
+
+namespace {
+
+struct Timer {
+    cudaEvent_t a = nullptr, b = nullptr;
+    bool on = false;
+    void start(cudaStream_t s, bool want)
+    {
+        on = want;
+        if (!on) return;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        cudaEventRecord(a, s);
+    }
+    void stop(cudaStream_t s)
+    {
+        if (on) cudaEventRecord(b, s);
+    }
+    float ms()
+    {
+        float x = 0.0f;
+        if (on) cudaEventElapsedTime(&x, a, b);
+        return x;
+    }
+    ~Timer()
+    {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
+
+// Reads the device status of a finished solve into h (waits for the stream).
+int finish_solve(dag_plan* plan, int nblocks, int delta, Timer& tm, cudaStream_t s, dag_stats* h)
+{
+    SyncBlock sb;
+    DAG_CUDA(cudaMemcpyAsync(&sb, plan->sync, sizeof(SyncBlock), cudaMemcpyDeviceToHost, s));
+    DAG_CUDA(cudaStreamSynchronize(s));
+    DAG_CUDA(cudaGetLastError());
+    int rc = DAG_OK;
+    if (sb.err) rc = sb.err;
+    else if (!sb.converged) rc = DAG_ERR_NOT_CONVERGED;
+    if (h) {
+        h->iters = sb.iters;
+        h->err = rc;
+        h->residual = sb.residual;
+        h->ms = tm.ms();
+        h->workers = nblocks;
+        h->delta = delta;
+        h->flushes = sb.flushes;
+        h->edges_processed = (long long)sb.iters * plan->m;
+    }
+    if (rc == DAG_ERR_BARRIER_TIMEOUT) set_error(rc, "grid barrier wait ran out of time");
+    else if (rc == DAG_ERR_NOT_CONVERGED) set_error(rc, "max_iters reached before the stopping rule");
+    return rc;
+}
+
+int check_variant(int variant, int delta, int max_iters)
+{
+    if (variant < DAG_SYNC || variant > DAG_DELAYED) return set_error(DAG_ERR_INVALID, "unknown variant");
+    if (delta < 0) return set_error(DAG_ERR_INVALID, "delta must be >= 0");
+    if (max_iters < 1) return set_error(DAG_ERR_INVALID, "max_iters must be >= 1");
+    return DAG_OK;
+}
+
+}  // namespace
+}  // namespace dag
+
+using namespace dag;
+
+extern "C" const char* dag_strerror(int code)
+{
+    switch (code) {
+    case DAG_OK: return "ok";
+    case DAG_ERR_INVALID: return "invalid argument";
+    case DAG_ERR_NOT_CONVERGED: return "not converged within max_iters";
+    case DAG_ERR_BARRIER_TIMEOUT: return "grid barrier timeout";
+    case DAG_ERR_CUDA: return "CUDA error";
+    case DAG_ERR_NOMEM: return "out of device memory";
+    default: return "unknown error";
+    }
+}
+
+extern "C" const char* dag_last_error_message(void) { return g_last_error.c_str(); }
+
+extern "C" int dag_workers(dag_plan* plan, dag_variant variant, int32_t delta, int32_t* out_workers)
+{
+    if (!plan || !out_workers) return set_error(DAG_ERR_INVALID, "null argument");
+    int rc = check_variant(variant, delta, 1);
+    if (rc) return rc;
+    if (variant == DAG_DELAYED && delta == 0) variant = DAG_ASYNC;
+    int cap = 0;
+    if (variant == DAG_DELAYED) sweep_buffer_cap(plan, delta, &cap);
+    return max_workers(plan, MODE_PR, variant, cap, out_workers);
+}
+
+extern "C" int dag_pagerank(dag_plan* plan, float d, double tol, dag_variant variant, int32_t delta,
+                            int32_t max_iters, const float* d_teleport, const float* d_val, float* d_rank,
+                            int32_t flags, dag_stats* h_stats, void* stream)
+{
+    if (!plan || !d_rank) return set_error(DAG_ERR_INVALID, "null argument");
+    if (!(d > 0.0f && d < 1.0f)) return set_error(DAG_ERR_INVALID, "d must lie in (0, 1)");
+    if (!(tol > 0.0) || std::isnan(tol)) return set_error(DAG_ERR_INVALID, "tol must be > 0");
+    int rc = check_variant(variant, delta, max_iters);
+    if (rc) return rc;
+    int var = variant;
+    if (var == DAG_DELAYED && delta == 0) var = DAG_ASYNC;
+    cudaStream_t s = (cudaStream_t)stream;
+    SweepParams p{};
+    p.n = plan->n;
+    p.rowptr = plan->rowptr;
+    p.colidx = plan->colidx;
+    p.val = d_val;
+    p.degf = plan->degf;
+    p.base = d_teleport;
+    p.base_scale = 1.0f - d;
+    p.uniform_base = (1.0f - d) / (float)plan->n;
+    p.d = d;
+    p.g_coef = d / (float)plan->n;
+    p.tol = tol;
+    p.max_iters = max_iters;
+    p.x0 = plan->x0;
+    p.x1 = plan->x1;
+    p.init = (flags & DAG_PR_WARM_START) ? d_rank : nullptr;
+    p.out = d_rank;
+    Timer tm;
+    tm.start(s, h_stats != nullptr);
+    int nb = 0;
+    rc = launch_sweep(plan, d_val ? MODE_PRW : MODE_PR, var, delta, p, s, &nb);
+    if (rc) return rc;
+    tm.stop(s);
+    if (!h_stats) return DAG_OK;
+    return finish_solve(plan, nb, var == DAG_DELAYED ? delta : 0, tm, s, h_stats);
+}
+
+extern "C" int dag_sssp(dag_plan* plan, uint32_t src, dag_variant variant, int32_t delta, int32_t max_iters,
+                        const uint32_t* d_w, uint32_t* d_dist, dag_stats* h_stats, void* stream)
+{
+    if (!plan || !d_dist || (plan->m > 0 && !d_w)) return set_error(DAG_ERR_INVALID, "null argument");
+    if (src >= (uint32_t)plan->n) return set_error(DAG_ERR_INVALID, "source outside [0, n)");
+    int rc = check_variant(variant, delta, max_iters);
+    if (rc) return rc;
+    int var = variant;
+    if (var == DAG_DELAYED && delta == 0) var = DAG_ASYNC;
+    cudaStream_t s = (cudaStream_t)stream;
+    SweepParams p{};
+    p.n = plan->n;
+    p.rowptr = plan->rowptr;
+    p.colidx = plan->colidx;
+    p.w = d_w;
+    p.degf = plan->degf;
+    p.tol = 0.0;
+    p.max_iters = max_iters;
+    p.src = src;
+    p.x0 = plan->x0;
+    p.x1 = plan->x1;
+    p.out = d_dist;
+    Timer tm;
+    tm.start(s, h_stats != nullptr);
+    int nb = 0;
+    rc = launch_sweep(plan, MODE_BF, var, delta, p, s, &nb);
+    if (rc) return rc;
+    tm.stop(s);
+    if (!h_stats) return DAG_OK;
+    return finish_solve(plan, nb, var == DAG_DELAYED ? delta : 0, tm, s, h_stats);
+}
+
+extern "C" int dag_pagerank_adjoint(dag_plan* in_plan, dag_plan* out_plan, float d, double tol,
+                                    dag_variant variant, int32_t delta, int32_t max_iters, const float* d_val,
+                                    const float* d_val_out, const float* d_s, const float* d_rank,
+                                    const float* d_c, float* d_grad_w, float* d_grad_t, float* d_lambda,
+                                    dag_stats* h_stats, void* stream)
+{
+    if (!in_plan || !out_plan || !d_c || !d_rank || !d_s) return set_error(DAG_ERR_INVALID, "null argument");
+    if (in_plan->n != out_plan->n || in_plan->m != out_plan->m)
+        return set_error(DAG_ERR_INVALID, "in_plan and out_plan describe different graphs");
+    if (in_plan->m > 0 && (!d_val_out || (d_grad_w && !d_val)))
+        return set_error(DAG_ERR_INVALID, "null edge values");
+    if (!(d > 0.0f && d < 1.0f)) return set_error(DAG_ERR_INVALID, "d must lie in (0, 1)");
+    if (!(tol > 0.0)) return set_error(DAG_ERR_INVALID, "tol must be > 0");
+    int rc = check_variant(variant, delta, max_iters);
+    if (rc) return rc;
+    int var = variant;
+    if (var == DAG_DELAYED && delta == 0) var = DAG_ASYNC;
+    cudaStream_t s = (cudaStream_t)stream;
+    float* lam = d_lambda;
+    float* lam_tmp = nullptr;
+    if (!lam) {
+        DAG_CUDA(cudaMalloc(&lam_tmp, (size_t)in_plan->n * sizeof(float)));
+        lam = lam_tmp;
+    }
+    SweepParams p{};
+    p.n = out_plan->n;
+    p.rowptr = out_plan->rowptr;
+    p.colidx = out_plan->colidx;
+    p.val = d_val_out;
+    p.degf = in_plan->degf;  // forward out-degree = out-CSR row length: dangling test
+    p.base = d_c;
+    p.base_scale = 1.0f;
+    p.d = d;
+    p.g_coef = d / (float)out_plan->n;
+    p.tol = tol;
+    p.max_iters = max_iters;
+    p.x0 = out_plan->x0;
+    p.x1 = out_plan->x1;
+    p.out = lam;
+    p.aux_out = in_plan->scratch_f;  // (M^T lambda)_u of the last sweep
+    Timer tm;
+    tm.start(s, true);
+    int nb = 0;
+    rc = launch_sweep(out_plan, MODE_ADJ, var, delta, p, s, &nb);
+    if (rc) {
+        if (lam_tmp) cudaFree(lam_tmp);
+        return rc;
+    }
+    rc = launch_edge_grad(in_plan, d, d_val, d_s, d_rank, lam, in_plan->scratch_f, d_grad_w, d_grad_t, s);
+    tm.stop(s);
+    int rc2 = finish_solve(out_plan, nb, var == DAG_DELAYED ? delta : 0, tm, s, h_stats);
+    if (lam_tmp) cudaFree(lam_tmp);
+    return rc ? rc : rc2;
+}
+
+extern "C" int dag_ppr_batched(dag_plan* plan, float d, double tol, dag_variant variant, int32_t delta,
+                               int32_t max_iters, int32_t B, const float* d_V, float* d_R, int32_t* d_iters,
+                               dag_batch_stats* h_stats, void* stream)
+{
+    if (!plan || !d_V || !d_R || !d_iters) return set_error(DAG_ERR_INVALID, "null argument");
+    if (B < 1 || B > 1024) return set_error(DAG_ERR_INVALID, "B must lie in [1, 1024]");
+    if (!(d > 0.0f && d < 1.0f)) return set_error(DAG_ERR_INVALID, "d must lie in (0, 1)");
+    if (!(tol > 0.0)) return set_error(DAG_ERR_INVALID, "tol must be > 0");
+    int rc = check_variant(variant, delta, max_iters);
+    if (rc) return rc;
+    int var = variant;
+    if (var == DAG_DELAYED && delta == 0) var = DAG_ASYNC;
+    return launch_batched(plan, 0, var, delta, max_iters, B, d, tol, d_V, nullptr, d_R, d_iters, h_stats,
+                          (cudaStream_t)stream);
+}
+
+extern "C" int dag_sssp_batched(dag_plan* plan, dag_variant variant, int32_t delta, int32_t max_iters, int32_t B,
+                                const uint32_t* d_src, const uint32_t* d_w, uint32_t* d_D, int32_t* d_iters,
+                                dag_batch_stats* h_stats, void* stream)
+{
+    if (!plan || !d_src || !d_D || !d_iters || (plan->m > 0 && !d_w))
+        return set_error(DAG_ERR_INVALID, "null argument");
+    if (B < 1 || B > 1024) return set_error(DAG_ERR_INVALID, "B must lie in [1, 1024]");
+    int rc = check_variant(variant, delta, max_iters);
+    if (rc) return rc;
+    int var = variant;
+    if (var == DAG_DELAYED && delta == 0) var = DAG_ASYNC;
+    return launch_batched(plan, 1, var, delta, max_iters, B, 0.0f, 0.0, d_src, d_w, d_D, d_iters, h_stats,
+                          (cudaStream_t)stream);
+}

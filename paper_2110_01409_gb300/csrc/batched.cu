@@ -1,0 +1,429 @@
+// Batched personalized PageRank and batched Bellman-Ford in one persistent
+// launch (no counterpart in the paper: each column is an independent problem
+// solved with the paper's sweep, Sec. III; columns stop on their own).
+//
+// State X is row-major [n][B]: the B values of a vertex are contiguous, so an
+// in-edge gathers one contiguous slice of B values. A CTA owns a vertex block
+// (Sec. III-A partition) and holds one warp per 32-column chunk; every warp
+// walks the CTA's merge-path tiles in vertex order, one lane per column. A
+// column that met its stopping rule is frozen (not read, not written) for the
+// rest of the launch, and a warp whose 32 columns are all frozen skips the
+// tile. In the delayed form the "worker" of Sec. III-B is a (CTA, column
+// chunk) pair: each warp buffers delta rows of its 32 columns in shared
+// memory and copies them out when the buffer is full or its block is done.
+#include <climits>
+
+#include "dag_internal.cuh"
+
+namespace dag {
+
+struct BatchParams {
+    int n;
+    int B;
+    int nblocks;
+    const int* rowptr;
+    const int* colidx;
+    const uint32_t* w;
+    const float* degf;
+    const float* V;        // PPR teleports [n][B]
+    const uint32_t* src;   // BF sources [B]
+    float d;
+    float g_coef;
+    double tol;
+    int max_iters;
+    int delta;             // rows per warp buffer (delayed)
+    uint32_t* X0;          // [n][B] (the caller's output array)
+    uint32_t* X1;          // [n][B] workspace (sync)
+    const int* cta_row;
+    const int* cta_tile;
+    const int* tile_row;
+    const int* tile_nz;
+    SyncBlock* sb;
+    double* acc_res;       // [3][B]
+    double* acc_g;         // [3][B]
+    double* gl;            // [B] live non-dangling mass (async / delayed PPR)
+    double* T;             // [B] teleport totals
+    int* iters;            // [B] sweeps of each column (output)
+    long long timeout_ns;
+};
+
+constexpr int BU = 8;  // edges gathered per warp before accumulating
+
+template <bool BF>
+__device__ __forceinline__ uint32_t b_ident()
+{
+    return BF ? INF : 0u;
+}
+
+template <bool BF>
+__device__ __forceinline__ uint32_t b_comb(uint32_t a, uint32_t b)
+{
+    if constexpr (BF) return a < b ? a : b;
+    else return __float_as_uint(__uint_as_float(a) + __uint_as_float(b));
+}
+
+__device__ __forceinline__ uint32_t b_relax(uint32_t du, uint32_t w)
+{
+    if (du == INF) return INF;
+    uint32_t s = du + w;
+    return (s < du || s == INF) ? INF - 1u : s;
+}
+
+template <bool BF, int VAR>
+__global__ void batched_kernel(const BatchParams p)
+{
+    constexpr bool SYNC = VAR == DAG_SYNC;
+    constexpr bool DELAYED = VAR == DAG_DELAYED;
+    constexpr bool LIVE = !SYNC && !BF;
+    extern __shared__ __align__(16) uint32_t smem[];
+    int* s_col = (int*)smem;
+    int* s_end = s_col + TILE;
+    uint32_t* s_w = (uint32_t*)(s_end + TILE + 1);
+    uint32_t* s_buf = s_w + (BF ? TILE : 0);  // per warp: delta rows x 32 columns
+
+    const int B = p.B;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int col = warp * 32 + lane;
+    const bool colok = col < B;
+    const int cb = blockIdx.x;
+    const int row_lo = p.cta_row[cb], row_hi = p.cta_row[cb + 1];
+    const int tile_lo = p.cta_tile[cb], tile_hi = p.cta_tile[cb + 1];
+    unsigned long long bar = 0;
+    uint32_t* mybuf = s_buf + (size_t)warp * (DELAYED ? p.delta : 0) * 32;
+
+    // ---------------- initial values ----------------
+    {
+        double gpart = 0.0, tpart = 0.0;
+        uint32_t s0 = BF && colok ? p.src[col] : 0u;
+        for (int v = row_lo; v < row_hi; ++v) {
+            if (!colok) continue;
+            const size_t k = (size_t)v * B + col;
+            if constexpr (BF) {
+                p.X0[k] = ((uint32_t)v == s0) ? 0u : INF;
+            } else {
+                const float t = p.V[k];
+                const float dg = p.degf[v];
+                p.X0[k] = __float_as_uint(dg > 0.0f ? t / dg : t);
+                if (dg > 0.0f) gpart += (double)t;
+                tpart += (double)t;
+            }
+        }
+        if (!BF && colok) {
+            if (tpart != 0.0) atomicAdd(&p.T[col], tpart);
+            if (gpart != 0.0) {
+                atomicAdd(&p.acc_g[2 * B + col], gpart);
+                if (LIVE) atomicAdd(&p.gl[col], gpart);
+            }
+        }
+    }
+    if (!grid_barrier(p.sb, p.nblocks, bar, p.timeout_ns)) return;
+    double Tc = 0.0, gprev = 0.0;
+    if (!BF && colok) {
+        Tc = ld_relaxed_f64(&p.T[col]);
+        gprev = ld_relaxed_f64(&p.acc_g[2 * B + col]);
+    }
+    bool active = colok;
+    int last_it = 0;  // sweeps this column ran (same value in every CTA)
+    int it = 0;
+    for (; it < p.max_iters; ++it) {
+        const int slot = it % 3;
+        const uint32_t* xin = SYNC ? ((it & 1) ? p.X1 : p.X0) : p.X0;
+        uint32_t* xout = SYNC ? ((it & 1) ? p.X0 : p.X1) : p.X0;
+        double res = 0.0, gsum = 0.0, dg_acc = 0.0;
+        uint32_t carry = b_ident<BF>();
+        int buf_first = row_lo, buf_cnt = 0;
+        const bool warp_active = __any_sync(0xffffffffu, active);
+        float gt = 0.0f;
+        if (SYNC && !BF) gt = (float)((double)p.g_coef * (Tc - gprev));
+
+        for (int t = tile_lo; t < tile_hi; ++t) {
+            const int a0 = p.tile_row[t], b0 = p.tile_nz[t];
+            const int NA = p.tile_row[t + 1] - a0, NB = p.tile_nz[t + 1] - b0;
+            __syncthreads();  // previous tile's staging no longer read
+            for (int i = threadIdx.x; i < NA; i += blockDim.x) s_end[i] = ld_stream_i32(p.rowptr + a0 + i + 1) - b0;
+            if (threadIdx.x == 0) s_end[NA] = INT_MAX;
+            for (int j = threadIdx.x; j < NB; j += blockDim.x) {
+                s_col[j] = ld_stream_i32(p.colidx + b0 + j);
+                if constexpr (BF) s_w[j] = ld_stream_u32(p.w + b0 + j);
+            }
+            __syncthreads();
+            if (!warp_active) continue;
+            if constexpr (LIVE) {
+                if (active) gt = (float)((double)p.g_coef * (Tc - ld_relaxed_f64(&p.gl[col])));
+            }
+            uint32_t acc = carry;
+            int i = 0;
+            int re = s_end[0];
+            auto finish_row = [&](int r, uint32_t sum) {
+                const int v = a0 + r;
+                if (!active) return;
+                const size_t k = (size_t)v * B + col;
+                uint32_t xnew;
+                if constexpr (BF) {
+                    const uint32_t old = SYNC ? ld_weak_b32(xin + k) : ld_relaxed_b32(xin + k);
+                    xnew = sum < old ? sum : old;
+                    if (xnew < old) res += 1.0;
+                } else {
+                    const float xo = __uint_as_float(SYNC ? ld_weak_b32(xin + k) : ld_relaxed_b32(xin + k));
+                    const float dg = p.degf[v];
+                    const float rold = dg > 0.0f ? xo * dg : xo;
+                    const float rnew = (1.0f - p.d) * ld_stream_f32(p.V + k) + p.d * __uint_as_float(sum) + gt;
+                    res += fabs((double)rnew - (double)rold);
+                    if (dg > 0.0f) {
+                        gsum += (double)rnew;
+                        dg_acc += (double)rnew - (double)rold;
+                    }
+                    xnew = __float_as_uint(dg > 0.0f ? rnew / dg : rnew);
+                }
+                if constexpr (SYNC) st_weak_b32(xout + k, xnew);
+                else if constexpr (DELAYED) mybuf[(v - buf_first) * 32 + lane] = xnew;
+                else st_relaxed_b32(xout + k, xnew);
+            };
+            auto maybe_flush = [&](bool force) {
+                if constexpr (DELAYED) {
+                    if (buf_cnt > 0 && (buf_cnt >= p.delta || force)) {
+                        __syncwarp();
+                        if (active)
+                            for (int q = 0; q < buf_cnt; ++q)
+                                st_relaxed_b32(p.X0 + (size_t)(buf_first + q) * B + col, mybuf[q * 32 + lane]);
+                        if (LIVE && active && dg_acc != 0.0) {
+                            atomicAdd(&p.gl[col], dg_acc);
+                            dg_acc = 0.0;
+                        }
+                        buf_first += buf_cnt;
+                        buf_cnt = 0;
+                        __syncwarp();
+                        if (LIVE && active) gt = (float)((double)p.g_coef * (Tc - ld_relaxed_f64(&p.gl[col])));
+                    }
+                }
+            };
+            for (int j0 = 0; j0 < NB; j0 += BU) {
+                uint32_t xv[BU];
+#pragma unroll
+                for (int u = 0; u < BU; ++u) {
+                    const int j = j0 + u;
+                    xv[u] = 0u;
+                    if (j < NB && active) {
+                        const size_t k = (size_t)s_col[j] * B + col;
+                        xv[u] = SYNC ? ld_weak_b32(xin + k) : ld_relaxed_b32(xin + k);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < BU; ++u) {
+                    const int j = j0 + u;
+                    if (j < NB) {
+                        while (re <= j) {
+                            finish_row(i, acc);
+                            if constexpr (DELAYED) { ++buf_cnt; maybe_flush(false); }
+                            acc = b_ident<BF>();
+                            ++i;
+                            re = s_end[i];
+                        }
+                        uint32_t term;
+                        if constexpr (BF) term = b_relax(xv[u], s_w[j]);
+                        else term = xv[u];
+                        acc = b_comb<BF>(acc, term);
+                    }
+                }
+            }
+            while (i < NA) {
+                finish_row(i, acc);
+                if constexpr (DELAYED) { ++buf_cnt; maybe_flush(false); }
+                acc = b_ident<BF>();
+                ++i;
+            }
+            carry = acc;
+            if constexpr (DELAYED) maybe_flush(t == tile_hi - 1);
+            if constexpr (VAR == DAG_ASYNC && !BF) {
+                if (active && dg_acc != 0.0) {
+                    atomicAdd(&p.gl[col], dg_acc);
+                    dg_acc = 0.0;
+                }
+            }
+        }
+        // ---- end of sweep ----
+        if (active) {
+            if (res != 0.0) atomicAdd(&p.acc_res[slot * B + col], res);
+            if (SYNC && !BF && gsum != 0.0) atomicAdd(&p.acc_g[slot * B + col], gsum);
+        }
+        if (!grid_barrier(p.sb, p.nblocks, bar, p.timeout_ns)) return;
+        int still = 0;
+        if (active) {
+            const double r = ld_relaxed_f64(&p.acc_res[slot * B + col]);
+            if (SYNC && !BF) gprev = ld_relaxed_f64(&p.acc_g[slot * B + col]);
+            if (r <= p.tol) {
+                active = false;
+                last_it = it + 1;
+                if (cb == 0) p.iters[col] = it + 1;
+            } else {
+                still = 1;
+            }
+        }
+        if (cb == 0 && colok) {
+            const int dead = (it + 2) % 3;
+            p.acc_res[dead * B + col] = 0.0;
+            p.acc_g[dead * B + col] = 0.0;
+        }
+        if (!__syncthreads_or(still)) { ++it; break; }
+    }
+    if (cb == 0 && active) p.iters[col] = it;  // not converged: ran them all
+    if (active) last_it = it;
+    {
+        // every CTA holds all B columns and reads the same sums, so CTA 0 sees the outcome
+        const int any_active = __syncthreads_or(active ? 1 : 0);
+        if (cb == 0 && threadIdx.x == 0) {
+            p.sb->iters = it;
+            p.sb->converged = any_active ? 0 : 1;
+        }
+    }
+
+    // ---------------- output: r = x * outdeg, from the buffer of each column's last sweep ----------------
+    if (!colok) return;
+    for (int v = row_lo; v < row_hi; ++v) {
+        const size_t k = (size_t)v * B + col;
+        uint32_t x;
+        if constexpr (SYNC) x = (last_it & 1) ? ld_relaxed_b32(p.X1 + k) : ld_relaxed_b32(p.X0 + k);
+        else x = ld_relaxed_b32(p.X0 + k);
+        if constexpr (BF) {
+            p.X0[k] = x;
+        } else {
+            const float dg = p.degf[v];
+            p.X0[k] = __float_as_uint(dg > 0.0f ? __uint_as_float(x) * dg : __uint_as_float(x));
+        }
+    }
+}
+
+using BKernel = void (*)(const BatchParams);
+
+static BKernel bkernel_for(int is_bf, int variant)
+{
+    static const BKernel table[2][3] = {
+        {batched_kernel<false, DAG_SYNC>, batched_kernel<false, DAG_ASYNC>, batched_kernel<false, DAG_DELAYED>},
+        {batched_kernel<true, DAG_SYNC>, batched_kernel<true, DAG_ASYNC>, batched_kernel<true, DAG_DELAYED>},
+    };
+    return table[is_bf][variant];
+}
+
+int launch_batched(dag_plan* plan, int is_bf, int variant, int delta, int max_iters, int B, float d, double tol,
+                   const void* V_or_src, const uint32_t* w, void* out, int* iters, dag_batch_stats* st,
+                   cudaStream_t s)
+{
+    const int n = plan->n;
+    const int W = (B + 31) / 32;
+    const int threads = W * 32;
+    if (is_bf) {
+        // sources must be vertices of the graph
+        std::vector<uint32_t> hs(B);
+        DAG_CUDA(cudaMemcpyAsync(hs.data(), V_or_src, (size_t)B * 4, cudaMemcpyDeviceToHost, s));
+        DAG_CUDA(cudaStreamSynchronize(s));
+        for (int c = 0; c < B; ++c)
+            if (hs[c] >= (uint32_t)n) return set_error(DAG_ERR_INVALID, "source outside [0, n)");
+    }
+    const int dl = (variant == DAG_DELAYED) ? delta : 0;
+    size_t dyn = (size_t)(2 * TILE + 1 + (is_bf ? TILE : 0)) * 4 + (size_t)W * dl * 32 * 4;
+    BKernel k = bkernel_for(is_bf, variant);
+    int max_dyn = 0;
+    DAG_CUDA(cudaDeviceGetAttribute(&max_dyn, cudaDevAttrMaxSharedMemoryPerBlockOptin, plan->device));
+    if (dyn > (size_t)max_dyn)
+        return set_error(DAG_ERR_INVALID, "delta too large for the batched delay buffers in shared memory");
+    DAG_CUDA(cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    int per_sm = 0;
+    DAG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k, threads, dyn));
+    if (per_sm < 1) return set_error(DAG_ERR_INVALID, "batched kernel cannot be resident");
+    const int nb = per_sm * plan->num_sms;
+    Partition* part = nullptr;
+    int rc = get_partition(plan, nb, &part, s);
+    if (rc) return rc;
+    // workspace: X1 (sync) and the per-column control block
+    size_t xbytes = (variant == DAG_SYNC) ? (size_t)n * B * 4 : 0;
+    if (xbytes > plan->bx_bytes) {
+        cudaFree(plan->bx);
+        plan->bx = nullptr;
+        plan->bx_bytes = 0;
+        if (cudaMalloc(&plan->bx, xbytes) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(DAG_ERR_NOMEM, "batched workspace allocation failed");
+        }
+        plan->bx_bytes = xbytes;
+    }
+    size_t cbytes = sizeof(SyncBlock) + (size_t)B * (3 + 3 + 1 + 1) * sizeof(double);
+    if (cbytes > plan->bsync_bytes) {
+        cudaFree(plan->bsync);
+        plan->bsync = nullptr;
+        plan->bsync_bytes = 0;
+        if (cudaMalloc(&plan->bsync, cbytes) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(DAG_ERR_NOMEM, "batched control allocation failed");
+        }
+        plan->bsync_bytes = cbytes;
+    }
+    DAG_CUDA(cudaMemsetAsync(plan->bsync, 0, cbytes, s));
+    BatchParams p{};
+    p.n = n;
+    p.B = B;
+    p.nblocks = nb;
+    p.rowptr = plan->rowptr;
+    p.colidx = plan->colidx;
+    p.w = w;
+    p.degf = plan->degf;
+    p.V = is_bf ? nullptr : (const float*)V_or_src;
+    p.src = is_bf ? (const uint32_t*)V_or_src : nullptr;
+    p.d = d;
+    p.g_coef = d / (float)n;
+    p.tol = is_bf ? 0.0 : tol;
+    p.max_iters = max_iters;
+    p.delta = dl;
+    p.X0 = (uint32_t*)out;
+    p.X1 = (uint32_t*)plan->bx;
+    p.cta_row = part->cta_row;
+    p.cta_tile = part->cta_tile;
+    p.tile_row = part->tile_row;
+    p.tile_nz = part->tile_nz;
+    p.sb = (SyncBlock*)plan->bsync;
+    double* base = (double*)((char*)plan->bsync + sizeof(SyncBlock));
+    p.acc_res = base;
+    p.acc_g = base + 3 * B;
+    p.gl = base + 6 * B;
+    p.T = base + 7 * B;
+    p.iters = iters;
+    p.timeout_ns = plan->timeout_ns;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (st) {
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, s);
+    }
+    void* args[] = {(void*)&p};
+    cudaError_t le = cudaLaunchCooperativeKernel((const void*)k, dim3(nb), dim3(threads), args, dyn, s);
+    if (le != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        return cuda_check(le, "batched cooperative launch");
+    }
+    if (!st) return DAG_OK;
+    cudaEventRecord(e1, s);
+    SyncBlock sb;
+    DAG_CUDA(cudaMemcpyAsync(&sb, plan->bsync, sizeof(SyncBlock), cudaMemcpyDeviceToHost, s));
+    std::vector<int> hit(B);
+    DAG_CUDA(cudaMemcpyAsync(hit.data(), iters, (size_t)B * sizeof(int), cudaMemcpyDeviceToHost, s));
+    DAG_CUDA(cudaStreamSynchronize(s));
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int rc2 = DAG_OK;
+    if (sb.err) rc2 = sb.err;
+    else if (!sb.converged) rc2 = DAG_ERR_NOT_CONVERGED;
+    long long colsw = 0;
+    for (int c = 0; c < B; ++c) colsw += hit[c];
+    st->sweeps = sb.iters;
+    st->err = rc2;
+    st->ms = ms;
+    st->workers = nb;
+    st->delta = dl;
+    st->column_sweeps = colsw;
+    if (rc2 == DAG_ERR_BARRIER_TIMEOUT) set_error(rc2, "grid barrier wait ran out of time");
+    return rc2;
+}
+
+}  // namespace dag

@@ -1,0 +1,275 @@
+// Internal declarations shared by the libdag.so translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/dag.h"
+
+namespace dag {
+
+// ---------------------------------------------------------------------------
+// Launch shape of the persistent sweep kernels.
+// A CTA walks its vertex block in merge-path tiles of TILE items, where an item
+// is either one in-edge or one row end (Merrill & Garland, "Merge-based
+// parallel sparse matrix-vector multiplication", SC 2016). Tiles follow vertex
+// order, so the rows a tile completes are contiguous and a delay buffer of
+// consecutive rows can be flushed with coalesced stores.
+// ---------------------------------------------------------------------------
+constexpr int NT = 256;           // threads per CTA
+constexpr int IPT = 7;            // items per thread per tile (odd: fewer bank conflicts in the walk)
+constexpr int TILE = NT * IPT;    // items per tile
+constexpr int NWARP = NT / 32;
+constexpr int GSTRIPES = 32;      // stripes of the live dangling/global-sum accumulator
+constexpr int GSTRIDE = 4;        // doubles between stripes (32 bytes)
+
+enum Mode { MODE_PR = 0, MODE_PRW = 1, MODE_ADJ = 2, MODE_BF = 3 };
+
+constexpr uint32_t INF = 0xFFFFFFFFu;
+
+// Device-side control block of one solve (lives in the plan's workspace,
+// zeroed before each launch).
+struct __align__(128) SyncBlock {
+    unsigned long long arrive;   // grid-barrier arrivals, monotone within a launch
+    int err;                     // first error (DAG_ERR_*), 0 while fine
+    int iters;                   // sweeps run
+    double residual;             // last sweep's residual
+    long long flushes;           // delay-buffer flushes
+    int converged;
+    int pad0;
+    double T;                    // teleport total (PageRank)
+    double acc_res[3];           // per-sweep residual sums, slot = sweep % 3 (init = slot 2)
+    double acc_g[3];             // per-sweep global sums (N for PageRank, sum lambda for the adjoint)
+    double pad1[4];
+    double stripe[GSTRIPES * GSTRIDE]; // live global sum (async / delayed)
+};
+
+// Parameters of one sweep launch.
+struct SweepParams {
+    int n;
+    int nblocks;
+    const int* rowptr;
+    const int* colidx;
+    const float* val;       // per-edge P (PRW, ADJ)
+    const uint32_t* w;      // per-edge weight (BF)
+    const float* degf;      // out-degree as float (PR, PRW: dangling when 0; ADJ: row length of out-CSR)
+    const float* base;      // per-row base vector: teleport (PR/PRW) or c (ADJ); NULL = uniform
+    float base_scale;       // (1-d) for PageRank, 1 for the adjoint
+    float uniform_base;     // base when `base` is NULL: (1-d)/n
+    float d;
+    float g_coef;           // d/n: weight of the global term per row
+    double tol;
+    int max_iters;
+    int delta;              // delayed buffer size (rows); 0 for sync/async
+    int buf_cap;            // delay buffer capacity (elements of dynamic shared memory)
+    uint32_t src;           // BF source
+    // state (two buffers for sync)
+    void* x0;
+    void* x1;
+    // partition
+    const int* cta_row;     // [nblocks+1]
+    const int* cta_tile;    // [nblocks+1]
+    const int* tile_row;    // [tiles+1]
+    const int* tile_nz;     // [tiles+1]
+    // control
+    SyncBlock* sync;
+    long long timeout_ns;
+    int skip_barrier_cta0;  // test hook
+    // init / output
+    const float* init;      // warm start (PR) or nullptr
+    void* out;              // float r / lambda, or uint32 dist
+    float* aux_out;         // ADJ: (M^T lambda)_u of the last sweep, nullable
+};
+
+// Partition of one launch shape, cached per plan.
+struct Partition {
+    int nblocks = 0;
+    int tiles = 0;
+    int max_rows = 0;
+    int* cta_row = nullptr;   // device [nblocks+1]
+    int* cta_tile = nullptr;  // device [nblocks+1]
+    int* tile_row = nullptr;  // device [tiles+1]
+    int* tile_nz = nullptr;   // device [tiles+1]
+};
+
+}  // namespace dag
+
+struct dag_plan {
+    int n = 0;
+    long long m = 0;
+    const int* rowptr = nullptr;
+    const int* colidx = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    long long timeout_ns = 2000000000LL;
+    int skip_barrier_once = 0;
+    long long skip_timeout_ns = 0;
+    // per-vertex data
+    int* outdeg = nullptr;    // [n]
+    float* degf = nullptr;    // [n]
+    // workspace
+    void* x0 = nullptr;       // [n] 4-byte values
+    void* x1 = nullptr;       // [n]
+    dag::SyncBlock* sync = nullptr;
+    float* scratch_f = nullptr; // [n] float scratch (adjoint aux)
+    std::map<int, dag::Partition> parts;
+    // batched workspace (grown on demand)
+    void* bx = nullptr;
+    size_t bx_bytes = 0;
+    void* bsync = nullptr;
+    size_t bsync_bytes = 0;
+};
+
+namespace dag {
+
+// error plumbing (api.cu)
+int set_error(int code, const std::string& msg);
+int cuda_check(cudaError_t e, const char* what);
+#define DAG_CUDA(call)                                            \
+    do {                                                          \
+        cudaError_t e__ = (call);                                 \
+        if (e__ != cudaSuccess) return ::dag::cuda_check(e__, #call); \
+    } while (0)
+
+// plan.cu
+int get_partition(dag_plan* plan, int nblocks, Partition** out, cudaStream_t s);
+int max_workers(dag_plan* plan, int mode, int variant, int buf_cap_elems, int* out);
+
+// sweep.cu
+int launch_sweep(dag_plan* plan, int mode, int variant, int delta, SweepParams& p, cudaStream_t s,
+                 int* out_nblocks);
+int sweep_buffer_cap(dag_plan* plan, int delta, int* cap);
+
+// batched.cu
+int launch_batched(dag_plan* plan, int is_bf, int variant, int delta, int max_iters, int B, float d,
+                   double tol, const void* V_or_src, const uint32_t* w, void* out, int* iters,
+                   dag_batch_stats* st, cudaStream_t s);
+
+// adjoint.cu
+int launch_edge_grad(dag_plan* in_plan, float d, const float* val, const float* s_norm, const float* rank,
+                     const float* lambda, const float* mt, float* grad_w, float* grad_t, cudaStream_t st);
+int launch_transpose(dag_plan* plan, int* out_rowptr, int* out_colidx, int* perm, cudaStream_t s);
+int launch_normalize(dag_plan* plan, const float* w, float* val, float* s_out, cudaStream_t s);
+
+}  // namespace dag
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+namespace dag {
+
+__device__ __forceinline__ int ld_stream_i32(const int* p)
+{
+    int v;
+    asm volatile("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float ld_stream_f32(const float* p)
+{
+    float v;
+    asm volatile("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_stream_u32(const uint32_t* p)
+{
+    uint32_t v;
+    asm volatile("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+// Weak load: may hit in L1. Used for data no other CTA writes during this
+// sweep (the previous iterate in the synchronous form).
+__device__ __forceinline__ uint32_t ld_weak_b32(const void* p)
+{
+    uint32_t v;
+    asm volatile("ld.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+// Relaxed gpu-scope load: served by L2, the point of coherence, so it sees
+// other CTAs' latest stores. Used by the in-place (async / delayed) forms.
+__device__ __forceinline__ uint32_t ld_relaxed_b32(const void* p)
+{
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_b32(void* p, uint32_t v)
+{
+    asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_weak_b32(void* p, uint32_t v)
+{
+    asm volatile("st.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ double ld_relaxed_f64(const double* p)
+{
+    double v;
+    asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_relaxed_i32(const int* p)
+{
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long globaltimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier for a co-resident (cooperative) grid. Arrivals count up
+// monotonically; after its k-th barrier a CTA waits for k * nblocks arrivals.
+// The wait is bounded: past timeout_ns, or when another CTA has already
+// recorded an error, it records DAG_ERR_BARRIER_TIMEOUT (first error wins) and
+// returns false. Every thread of the CTA gets the same answer.
+__device__ __forceinline__ bool grid_barrier(SyncBlock* sb, unsigned nblocks, unsigned long long& target,
+                                             long long timeout_ns)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        target += nblocks;
+        __threadfence();
+        atomicAdd(&sb->arrive, 1ULL);
+        int ok = 1;
+        unsigned long long t0 = globaltimer_ns();
+        unsigned spins = 0;
+        while (ld_acquire_u64(&sb->arrive) < target) {
+            if (ld_relaxed_i32(&sb->err) != 0) { ok = 0; break; }
+            if ((++spins & 31u) == 0 && (long long)(globaltimer_ns() - t0) > timeout_ns) {
+                atomicCAS(&sb->err, 0, DAG_ERR_BARRIER_TIMEOUT);
+                ok = 0;
+                break;
+            }
+            __nanosleep(100);
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace dag
+#endif

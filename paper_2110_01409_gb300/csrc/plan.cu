@@ -1,0 +1,356 @@
+// Plan setup (untimed): CSR checks, out-degrees, the static vertex partition
+// of Sec. III-A per launch shape, the out-edge CSR and weight normalisation.
+#include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_scan.cuh>
+
+#include <algorithm>
+
+#include "dag_internal.cuh"
+
+namespace dag {
+
+// ---------------------------------------------------------------------------
+// CSR checks and per-vertex data
+// ---------------------------------------------------------------------------
+__global__ void k_check_rowptr(const int* rowptr, int n, long long m, int* bad)
+{
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v > n) return;
+    int x = rowptr[v];
+    if (v == 0 && x != 0) atomicOr(bad, 1);
+    if (v == n && (long long)x != m) atomicOr(bad, 1);
+    if (v < n && rowptr[v + 1] < x) atomicOr(bad, 1);
+}
+
+__global__ void k_out_degree(const int* colidx, long long m, int n, int* outdeg, int* bad)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < m;
+         e += (long long)gridDim.x * blockDim.x) {
+        int u = colidx[e];
+        if (u < 0 || u >= n) { atomicOr(bad, 2); continue; }
+        atomicAdd(&outdeg[u], 1);
+    }
+}
+
+__global__ void k_degf(const int* outdeg, float* degf, int n)
+{
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) degf[v] = (float)outdeg[v];
+}
+
+// ---------------------------------------------------------------------------
+// Partition: block p starts at min { v : v + rowptr[v] >= ceil(p (n+m) / P) }
+// (every vertex weighs in-degree + 1), then each block is cut into merge-path
+// tiles of TILE items; a tile's start is (rows ended before it, edges before it).
+// ---------------------------------------------------------------------------
+__global__ void k_cta_rows(const int* rowptr, int n, long long total, int P, int* cta_row)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p > P) return;
+    if (p == 0) { cta_row[0] = 0; return; }
+    if (p == P) { cta_row[P] = n; return; }
+    long long target = ((long long)p * total + P - 1) / P;
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if ((long long)mid + rowptr[mid] >= target) hi = mid;
+        else lo = mid + 1;
+    }
+    cta_row[p] = lo;
+}
+
+// Tile counts and their exclusive prefix, one thread (P is at most a few thousand).
+__global__ void k_cta_tiles(const int* rowptr, const int* cta_row, int P, int* cta_tile, int* max_rows)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    int acc = 0, mr = 0;
+    for (int p = 0; p < P; ++p) {
+        cta_tile[p] = acc;
+        int r0 = cta_row[p], r1 = cta_row[p + 1];
+        long long items = (long long)(r1 - r0) + (rowptr[r1] - rowptr[r0]);
+        acc += (int)((items + TILE - 1) / TILE);
+        mr = max(mr, r1 - r0);
+    }
+    cta_tile[P] = acc;
+    *max_rows = mr;
+}
+
+__global__ void k_tile_coords(const int* rowptr, int n, long long m, const int* cta_row, const int* cta_tile,
+                              int P, int tiles, int* tile_row, int* tile_nz)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > tiles) return;
+    if (k == tiles) { tile_row[k] = n; tile_nz[k] = (int)m; return; }
+    int lo = 0, hi = P - 1;  // owning block: last p with cta_tile[p] <= k
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (cta_tile[mid] <= k) lo = mid;
+        else hi = mid - 1;
+    }
+    int p = lo;
+    long long diag = (long long)cta_row[p] + rowptr[cta_row[p]] + (long long)(k - cta_tile[p]) * TILE;
+    // rows whose end item lies before diag: first v with v + rowptr[v+1] >= diag
+    int a = cta_row[p], b = cta_row[p + 1];
+    while (a < b) {
+        int mid = (a + b) >> 1;
+        if ((long long)mid + rowptr[mid + 1] >= diag) b = mid;
+        else a = mid + 1;
+    }
+    tile_row[k] = a;
+    tile_nz[k] = (int)(diag - a);
+}
+
+int get_partition(dag_plan* plan, int P, Partition** out, cudaStream_t s)
+{
+    auto it = plan->parts.find(P);
+    if (it != plan->parts.end()) { *out = &it->second; return DAG_OK; }
+    Partition part;
+    part.nblocks = P;
+    int* mr_dev = nullptr;
+    DAG_CUDA(cudaMalloc(&part.cta_row, (P + 1) * sizeof(int)));
+    DAG_CUDA(cudaMalloc(&part.cta_tile, (P + 1) * sizeof(int)));
+    DAG_CUDA(cudaMalloc(&mr_dev, sizeof(int)));
+    long long total = (long long)plan->n + plan->m;
+    k_cta_rows<<<(P + 1 + 255) / 256, 256, 0, s>>>(plan->rowptr, plan->n, total, P, part.cta_row);
+    k_cta_tiles<<<1, 1, 0, s>>>(plan->rowptr, part.cta_row, P, part.cta_tile, mr_dev);
+    int tiles = 0;
+    DAG_CUDA(cudaMemcpyAsync(&tiles, part.cta_tile + P, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DAG_CUDA(cudaMemcpyAsync(&part.max_rows, mr_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DAG_CUDA(cudaStreamSynchronize(s));
+    cudaFree(mr_dev);
+    part.tiles = tiles;
+    DAG_CUDA(cudaMalloc(&part.tile_row, (tiles + 1) * sizeof(int)));
+    DAG_CUDA(cudaMalloc(&part.tile_nz, (tiles + 1) * sizeof(int)));
+    k_tile_coords<<<(tiles + 1 + 255) / 256, 256, 0, s>>>(plan->rowptr, plan->n, plan->m, part.cta_row,
+                                                           part.cta_tile, P, tiles, part.tile_row, part.tile_nz);
+    DAG_CUDA(cudaGetLastError());
+    auto ins = plan->parts.emplace(P, part);
+    *out = &ins.first->second;
+    return DAG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Out-edge CSR: a stable radix sort of the in-edges by source keeps, within
+// each source, the in-CSR order, i.e. ascending targets.
+// ---------------------------------------------------------------------------
+__global__ void k_edge_dst(const int* rowptr, int n, int* dst)
+{
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    for (int e = rowptr[v]; e < rowptr[v + 1]; ++e) dst[e] = v;
+}
+__global__ void k_iota(int* a, long long m)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < m; e += (long long)gridDim.x * blockDim.x)
+        a[e] = (int)e;
+}
+__global__ void k_gather_i32(const int* src, const int* idx, int* out, long long m)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < m; e += (long long)gridDim.x * blockDim.x)
+        out[e] = src[idx[e]];
+}
+
+static int bits_for(int n)
+{
+    int b = 1;
+    while (b < 31 && (1LL << b) < n) ++b;
+    return b;
+}
+
+int launch_transpose(dag_plan* plan, int* out_rowptr, int* out_colidx, int* perm, cudaStream_t s)
+{
+    const int n = plan->n;
+    const long long m = plan->m;
+    // out_rowptr = exclusive prefix of out-degree, with the total at [n]
+    // scan over n+1 entries (the last one 0) so that out_rowptr[n] = m
+    void* tmp = nullptr;
+    int* padded = nullptr;
+    size_t tmp_bytes = 0;
+    DAG_CUDA(cudaMalloc(&padded, (size_t)(n + 1) * sizeof(int)));
+    DAG_CUDA(cudaMemsetAsync(padded + n, 0, sizeof(int), s));
+    DAG_CUDA(cudaMemcpyAsync(padded, plan->outdeg, (size_t)n * sizeof(int), cudaMemcpyDeviceToDevice, s));
+    DAG_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp_bytes, padded, out_rowptr, n + 1, s));
+    DAG_CUDA(cudaMalloc(&tmp, tmp_bytes));
+    DAG_CUDA(cub::DeviceScan::ExclusiveSum(tmp, tmp_bytes, padded, out_rowptr, n + 1, s));
+    DAG_CUDA(cudaStreamSynchronize(s));
+    cudaFree(tmp);
+    cudaFree(padded);
+    if (m == 0) return DAG_OK;
+    int *keys_out = nullptr, *vals_in = nullptr, *dst = nullptr;
+    DAG_CUDA(cudaMalloc(&keys_out, (size_t)m * sizeof(int)));
+    DAG_CUDA(cudaMalloc(&vals_in, (size_t)m * sizeof(int)));
+    DAG_CUDA(cudaMalloc(&dst, (size_t)m * sizeof(int)));
+    k_iota<<<1024, 256, 0, s>>>(vals_in, m);
+    k_edge_dst<<<(n + 255) / 256, 256, 0, s>>>(plan->rowptr, n, dst);
+    tmp_bytes = 0;
+    DAG_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, plan->colidx, keys_out, vals_in, perm, (int)m, 0,
+                                             bits_for(n), s));
+    DAG_CUDA(cudaMalloc(&tmp, tmp_bytes));
+    DAG_CUDA(cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, plan->colidx, keys_out, vals_in, perm, (int)m, 0,
+                                             bits_for(n), s));
+    k_gather_i32<<<1024, 256, 0, s>>>(dst, perm, out_colidx, m);
+    DAG_CUDA(cudaGetLastError());
+    DAG_CUDA(cudaStreamSynchronize(s));
+    cudaFree(tmp);
+    cudaFree(keys_out);
+    cudaFree(vals_in);
+    cudaFree(dst);
+    return DAG_OK;
+}
+
+// s[u] = sum of w over u's out-edges (one thread per source over the
+// out-CSR, fixed order); val[e] = w[e] / s[colidx[e]].
+__global__ void k_out_sum(const int* orow, const int* perm, const float* w, int n, float* s)
+{
+    int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    float acc = 0.0f;
+    for (int k = orow[u]; k < orow[u + 1]; ++k) acc += w[perm[k]];
+    s[u] = acc;
+}
+__global__ void k_div(const int* colidx, const float* w, const float* s, float* val, long long m)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < m; e += (long long)gridDim.x * blockDim.x)
+        val[e] = w[e] / s[colidx[e]];
+}
+
+int launch_normalize(dag_plan* plan, const float* w, float* val, float* s_out, cudaStream_t s)
+{
+    const int n = plan->n;
+    const long long m = plan->m;
+    int *orow = nullptr, *ocol = nullptr, *perm = nullptr;
+    DAG_CUDA(cudaMalloc(&orow, (size_t)(n + 1) * sizeof(int)));
+    DAG_CUDA(cudaMalloc(&ocol, (size_t)std::max(m, 1LL) * sizeof(int)));
+    DAG_CUDA(cudaMalloc(&perm, (size_t)std::max(m, 1LL) * sizeof(int)));
+    int rc = launch_transpose(plan, orow, ocol, perm, s);
+    if (rc) return rc;
+    k_out_sum<<<(n + 255) / 256, 256, 0, s>>>(orow, perm, w, n, s_out);
+    if (m) k_div<<<2048, 256, 0, s>>>(plan->colidx, w, s_out, val, m);
+    DAG_CUDA(cudaGetLastError());
+    DAG_CUDA(cudaStreamSynchronize(s));
+    cudaFree(orow);
+    cudaFree(ocol);
+    cudaFree(perm);
+    return DAG_OK;
+}
+
+}  // namespace dag
+
+// ---------------------------------------------------------------------------
+// Plan life cycle (C ABI)
+// ---------------------------------------------------------------------------
+using namespace dag;
+
+extern "C" int dag_plan_create(const dag_csr* csr, int32_t barrier_timeout_ms, dag_plan** out)
+{
+    if (!csr || !out) return set_error(DAG_ERR_INVALID, "null argument");
+    *out = nullptr;
+    if (csr->n < 1 || csr->m < 0 || csr->m >= (1LL << 31))
+        return set_error(DAG_ERR_INVALID, "need n >= 1 and 0 <= m < 2^31");
+    if (!csr->d_rowptr || (csr->m > 0 && !csr->d_colidx))
+        return set_error(DAG_ERR_INVALID, "null CSR array");
+    dag_plan* p = new dag_plan();
+    p->n = csr->n;
+    p->m = csr->m;
+    p->rowptr = csr->d_rowptr;
+    p->colidx = csr->d_colidx;
+    if (barrier_timeout_ms > 0) p->timeout_ns = (long long)barrier_timeout_ms * 1000000LL;
+    auto fail = [&](int rc) { dag_plan_destroy(p); return rc; };
+    if (cudaGetDevice(&p->device) != cudaSuccess) return fail(cuda_check(cudaGetLastError(), "cudaGetDevice"));
+    cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
+    const int n = p->n;
+    int* bad = nullptr;
+    if (cudaMalloc(&p->outdeg, (size_t)n * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&p->degf, (size_t)n * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&p->x0, (size_t)n * 4) != cudaSuccess || cudaMalloc(&p->x1, (size_t)n * 4) != cudaSuccess ||
+        cudaMalloc(&p->scratch_f, (size_t)n * 4) != cudaSuccess ||
+        cudaMalloc(&p->sync, sizeof(SyncBlock)) != cudaSuccess || cudaMalloc(&bad, sizeof(int)) != cudaSuccess) {
+        cudaFree(bad);
+        cudaGetLastError();
+        return fail(set_error(DAG_ERR_NOMEM, "plan workspace allocation failed"));
+    }
+    cudaStream_t s = 0;
+    cudaMemsetAsync(bad, 0, sizeof(int), s);
+    cudaMemsetAsync(p->outdeg, 0, (size_t)n * sizeof(int), s);
+    k_check_rowptr<<<(n + 1 + 255) / 256, 256, 0, s>>>(p->rowptr, n, p->m, bad);
+    int hbad = 0;
+    cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaFree(bad);
+        return fail(cuda_check(cudaGetLastError(), "rowptr check"));
+    }
+    if (hbad) {
+        cudaFree(bad);
+        return fail(set_error(DAG_ERR_INVALID, "rowptr must start at 0, not decrease and end at m"));
+    }
+    if (p->m > 0) k_out_degree<<<2048, 256, 0, s>>>(p->colidx, p->m, n, p->outdeg, bad);
+    k_degf<<<(n + 255) / 256, 256, 0, s>>>(p->outdeg, p->degf, n);
+    cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    cudaFree(bad);
+    if (e != cudaSuccess) return fail(cuda_check(e, "out-degree"));
+    if (hbad) return fail(set_error(DAG_ERR_INVALID, "colidx entry outside [0, n)"));
+    *out = p;
+    return DAG_OK;
+}
+
+extern "C" int dag_plan_destroy(dag_plan* p)
+{
+    if (!p) return DAG_OK;
+    cudaFree(p->outdeg);
+    cudaFree(p->degf);
+    cudaFree(p->x0);
+    cudaFree(p->x1);
+    cudaFree(p->scratch_f);
+    cudaFree(p->sync);
+    cudaFree(p->bx);
+    cudaFree(p->bsync);
+    for (auto& kv : p->parts) {
+        cudaFree(kv.second.cta_row);
+        cudaFree(kv.second.cta_tile);
+        cudaFree(kv.second.tile_row);
+        cudaFree(kv.second.tile_nz);
+    }
+    delete p;
+    return DAG_OK;
+}
+
+extern "C" int dag_plan_out_degree(const dag_plan* p, int32_t* d_outdeg, void* stream)
+{
+    if (!p || !d_outdeg) return set_error(DAG_ERR_INVALID, "null argument");
+    DAG_CUDA(cudaMemcpyAsync(d_outdeg, p->outdeg, (size_t)p->n * sizeof(int), cudaMemcpyDeviceToDevice,
+                             (cudaStream_t)stream));
+    return DAG_OK;
+}
+
+extern "C" int dag_partition(dag_plan* p, int32_t workers, int32_t* h_start)
+{
+    if (!p || !h_start || workers < 1) return set_error(DAG_ERR_INVALID, "bad argument");
+    Partition* part = nullptr;
+    int rc = get_partition(p, workers, &part, 0);
+    if (rc) return rc;
+    DAG_CUDA(cudaMemcpy(h_start, part->cta_row, (size_t)(workers + 1) * sizeof(int), cudaMemcpyDeviceToHost));
+    return DAG_OK;
+}
+
+extern "C" int dag_transpose(dag_plan* p, int32_t* d_out_rowptr, int32_t* d_out_colidx, int32_t* d_perm,
+                             void* stream)
+{
+    if (!p || !d_out_rowptr || (p->m > 0 && (!d_out_colidx || !d_perm)))
+        return set_error(DAG_ERR_INVALID, "null argument");
+    return launch_transpose(p, d_out_rowptr, d_out_colidx, d_perm, (cudaStream_t)stream);
+}
+
+extern "C" int dag_normalize_weights(dag_plan* p, const float* d_w, float* d_val, float* d_s, void* stream)
+{
+    if (!p || !d_s || (p->m > 0 && (!d_w || !d_val))) return set_error(DAG_ERR_INVALID, "null argument");
+    return launch_normalize(p, d_w, d_val, d_s, (cudaStream_t)stream);
+}
+
+extern "C" int dag_debug_skip_barrier_once(dag_plan* p, int32_t timeout_ms)
+{
+    if (!p || timeout_ms < 1) return set_error(DAG_ERR_INVALID, "bad argument");
+    p->skip_barrier_once = 1;
+    p->skip_timeout_ns = (long long)timeout_ms * 1000000LL;
+    return DAG_OK;
+}

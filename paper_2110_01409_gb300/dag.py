@@ -1,0 +1,324 @@
+"""Python binding of libdag.so (ctypes): argument marshalling only.
+
+Every step of a solve runs in the CUDA library; this module turns torch CUDA
+tensors into device pointers, passes the current torch stream, and turns
+status codes into exceptions. Loading fails loudly when libdag.so is missing
+(build it with ``paper_2110_01409_gb300.build.build()``): there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdag.so")
+
+OK, ERR_INVALID, ERR_NOT_CONVERGED, ERR_BARRIER_TIMEOUT, ERR_CUDA, ERR_NOMEM = 0, -1, -2, -3, -4, -5
+SYNC, ASYNC, DELAYED = 0, 1, 2
+VARIANTS = {"sync": SYNC, "async": ASYNC, "delayed": DELAYED}
+WARM_START = 1
+
+EXPORTS = (
+    "dag_plan_create", "dag_plan_destroy", "dag_plan_out_degree", "dag_partition", "dag_workers",
+    "dag_pagerank", "dag_sssp", "dag_ppr_batched", "dag_sssp_batched", "dag_transpose",
+    "dag_normalize_weights", "dag_pagerank_adjoint", "dag_strerror", "dag_last_error_message",
+    "dag_debug_skip_barrier_once",
+)
+
+
+class DagError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+class _Csr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("m", ctypes.c_int64), ("d_rowptr", ctypes.c_void_p),
+                ("d_colidx", ctypes.c_void_p)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("err", ctypes.c_int32), ("residual", ctypes.c_double),
+                ("ms", ctypes.c_float), ("workers", ctypes.c_int32), ("delta", ctypes.c_int32),
+                ("flushes", ctypes.c_int64), ("edges_processed", ctypes.c_int64)]
+
+
+class _BStats(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int32), ("err", ctypes.c_int32), ("ms", ctypes.c_float),
+                ("workers", ctypes.c_int32), ("delta", ctypes.c_int32), ("column_sweeps", ctypes.c_int64)]
+
+
+_lib = None
+_lock = threading.Lock()
+_vp, _i32, _f32, _f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_float, ctypes.c_double
+
+
+def lib():
+    """The loaded libdag.so. Raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"libdag.so not found at {LIB_PATH}; run paper_2110_01409_gb300.build.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            L.dag_plan_create.argtypes = [ctypes.POINTER(_Csr), _i32, ctypes.POINTER(_vp)]
+            L.dag_plan_destroy.argtypes = [_vp]
+            L.dag_plan_out_degree.argtypes = [_vp, _vp, _vp]
+            L.dag_partition.argtypes = [_vp, _i32, _vp]
+            L.dag_workers.argtypes = [_vp, _i32, _i32, ctypes.POINTER(_i32)]
+            L.dag_pagerank.argtypes = [_vp, _f32, _f64, _i32, _i32, _i32, _vp, _vp, _vp, _i32,
+                                       ctypes.POINTER(_Stats), _vp]
+            L.dag_sssp.argtypes = [_vp, ctypes.c_uint32, _i32, _i32, _i32, _vp, _vp, ctypes.POINTER(_Stats), _vp]
+            L.dag_ppr_batched.argtypes = [_vp, _f32, _f64, _i32, _i32, _i32, _i32, _vp, _vp, _vp,
+                                          ctypes.POINTER(_BStats), _vp]
+            L.dag_sssp_batched.argtypes = [_vp, _i32, _i32, _i32, _i32, _vp, _vp, _vp, _vp,
+                                           ctypes.POINTER(_BStats), _vp]
+            L.dag_transpose.argtypes = [_vp, _vp, _vp, _vp, _vp]
+            L.dag_normalize_weights.argtypes = [_vp, _vp, _vp, _vp, _vp]
+            L.dag_pagerank_adjoint.argtypes = [_vp, _vp, _f32, _f64, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp,
+                                               _vp, _vp, _vp, ctypes.POINTER(_Stats), _vp]
+            L.dag_strerror.argtypes = [_i32]
+            L.dag_strerror.restype = ctypes.c_char_p
+            L.dag_last_error_message.argtypes = []
+            L.dag_last_error_message.restype = ctypes.c_char_p
+            L.dag_debug_skip_barrier_once.argtypes = [_vp, _i32]
+            for f in EXPORTS:
+                if f not in ("dag_strerror", "dag_last_error_message"):
+                    getattr(L, f).restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _raise(rc: int, allow_not_converged: bool = True):
+    if rc == OK or (allow_not_converged and rc == ERR_NOT_CONVERGED):
+        return
+    L = lib()
+    raise DagError(rc, f"{L.dag_strerror(rc).decode()}: {L.dag_last_error_message().decode()}")
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t, dtype, n, name):
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == dtype and t.is_contiguous() and t.numel() == n):
+        raise ValueError(f"{name}: need a contiguous CUDA {dtype} tensor of {n} elements")
+    return t
+
+
+def _variant(v):
+    return VARIANTS[v] if isinstance(v, str) else int(v)
+
+
+def _stats(st: _Stats, m: int) -> dict:
+    return dict(iters=st.iters, err=st.err, converged=st.err == OK, residual=st.residual, ms=st.ms,
+                workers=st.workers, delta=st.delta, flushes=st.flushes, edges_processed=st.edges_processed)
+
+
+class Plan:
+    """Per-graph plan over device CSR tensors (kept alive by the plan)."""
+
+    def __init__(self, rowptr: torch.Tensor, colidx: torch.Tensor, barrier_timeout_ms: int = 0):
+        n = rowptr.numel() - 1
+        m = colidx.numel()
+        _dev(rowptr, torch.int32, n + 1, "rowptr")
+        if m:
+            _dev(colidx, torch.int32, m, "colidx")
+        self.rowptr, self.colidx, self.n, self.m = rowptr, colidx, n, m
+        csr = _Csr(n, m, rowptr.data_ptr(), colidx.data_ptr() if m else 0)
+        h = ctypes.c_void_p()
+        _raise(lib().dag_plan_create(ctypes.byref(csr), barrier_timeout_ms, ctypes.byref(h)), False)
+        self.h = h
+
+    @classmethod
+    def from_graph(cls, g, device="cuda", **kw):
+        rp = torch.from_numpy(g.rowptr).to(device)
+        ci = torch.from_numpy(g.colidx).to(device) if g.m else torch.zeros(1, dtype=torch.int32, device=device)[:0]
+        return cls(rp, ci, **kw)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().dag_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def out_degree(self) -> torch.Tensor:
+        out = torch.empty(self.n, dtype=torch.int32, device=self.rowptr.device)
+        _raise(lib().dag_plan_out_degree(self.h, _ptr(out), _stream()), False)
+        return out
+
+    def partition(self, workers: int):
+        import numpy as np
+        start = np.empty(workers + 1, dtype=np.int32)
+        _raise(lib().dag_partition(self.h, workers, start.ctypes.data), False)
+        return start
+
+    def workers(self, variant="delayed", delta=256) -> int:
+        w = _i32(0)
+        _raise(lib().dag_workers(self.h, _variant(variant), delta, ctypes.byref(w)), False)
+        return w.value
+
+    def debug_skip_barrier_once(self, timeout_ms: int):
+        _raise(lib().dag_debug_skip_barrier_once(self.h, timeout_ms), False)
+
+
+def pagerank(plan: Plan, d=0.85, tol=1e-6, variant="delayed", delta=256, max_iters=1000, teleport=None,
+             val=None, out=None, warm_start=False, stream=None, stats=True):
+    """PageRank through dag_pagerank. Returns (rank float32 tensor, stats dict or None)."""
+    dev = plan.rowptr.device
+    out = out if out is not None else torch.empty(plan.n, dtype=torch.float32, device=dev)
+    _dev(out, torch.float32, plan.n, "out")
+    _dev(teleport, torch.float32, plan.n, "teleport")
+    _dev(val, torch.float32, plan.m, "val")
+    st = _Stats()
+    rc = lib().dag_pagerank(plan.h, d, tol, _variant(variant), delta, max_iters, _ptr(teleport), _ptr(val),
+                            _ptr(out), WARM_START if warm_start else 0, ctypes.byref(st) if stats else None,
+                            _stream(stream))
+    _raise(rc)
+    return out, (_stats(st, plan.m) if stats else None)
+
+
+def sssp(plan: Plan, src: int, w, variant="delayed", delta=32, max_iters=None, out=None, stream=None,
+         stats=True):
+    """Bellman-Ford through dag_sssp. Returns (dist int64-view-free uint32 as int32 tensor, stats)."""
+    dev = plan.rowptr.device
+    out = out if out is not None else torch.empty(plan.n, dtype=torch.int32, device=dev)
+    _dev(out, torch.int32, plan.n, "out")
+    if plan.m:
+        _dev(w, torch.int32, plan.m, "w")
+    max_iters = plan.n + 1 if max_iters is None else max_iters
+    st = _Stats()
+    rc = lib().dag_sssp(plan.h, src, _variant(variant), delta, max_iters, _ptr(w) if plan.m else None, _ptr(out),
+                        ctypes.byref(st) if stats else None, _stream(stream))
+    _raise(rc)
+    return out, (_stats(st, plan.m) if stats else None)
+
+
+def _bstats(st: _BStats) -> dict:
+    return dict(sweeps=st.sweeps, err=st.err, converged=st.err == OK, ms=st.ms, workers=st.workers,
+                delta=st.delta, column_sweeps=st.column_sweeps)
+
+
+def ppr_batched(plan: Plan, V: torch.Tensor, d=0.85, tol=1e-6, variant="async", delta=0, max_iters=1000,
+                out=None, stream=None, stats=True):
+    """B personalized PageRanks; V row-major [n, B]. Returns (R [n, B], iters [B], stats)."""
+    n, B = V.shape
+    _dev(V, torch.float32, n * B, "V")
+    out = out if out is not None else torch.empty_like(V)
+    iters = torch.empty(B, dtype=torch.int32, device=V.device)
+    st = _BStats()
+    rc = lib().dag_ppr_batched(plan.h, d, tol, _variant(variant), delta, max_iters, B, _ptr(V), _ptr(out),
+                               _ptr(iters), ctypes.byref(st) if stats else None, _stream(stream))
+    _raise(rc)
+    return out, iters, (_bstats(st) if stats else None)
+
+
+def sssp_batched(plan: Plan, srcs: torch.Tensor, w, variant="async", delta=0, max_iters=None, out=None,
+                 stream=None, stats=True):
+    """B Bellman-Ford solves; srcs int32 [B]. Returns (D int32 [n, B] holding uint32 bits, iters, stats)."""
+    B = srcs.numel()
+    _dev(srcs, torch.int32, B, "srcs")
+    if plan.m:
+        _dev(w, torch.int32, plan.m, "w")
+    out = out if out is not None else torch.empty((plan.n, B), dtype=torch.int32, device=srcs.device)
+    iters = torch.empty(B, dtype=torch.int32, device=srcs.device)
+    max_iters = plan.n + 1 if max_iters is None else max_iters
+    st = _BStats()
+    rc = lib().dag_sssp_batched(plan.h, _variant(variant), delta, max_iters, B, _ptr(srcs),
+                                _ptr(w) if plan.m else None, _ptr(out), _ptr(iters),
+                                ctypes.byref(st) if stats else None, _stream(stream))
+    _raise(rc)
+    return out, iters, (_bstats(st) if stats else None)
+
+
+def transpose(plan: Plan):
+    """Out-edge CSR (rowptr, colidx) and perm: out-edge k is in-edge perm[k]."""
+    dev = plan.rowptr.device
+    orow = torch.empty(plan.n + 1, dtype=torch.int32, device=dev)
+    ocol = torch.empty(max(plan.m, 1), dtype=torch.int32, device=dev)
+    perm = torch.empty(max(plan.m, 1), dtype=torch.int32, device=dev)
+    _raise(lib().dag_transpose(plan.h, _ptr(orow), _ptr(ocol), _ptr(perm), _stream()), False)
+    return orow, ocol[: plan.m], perm[: plan.m]
+
+
+def normalize_weights(plan: Plan, w: torch.Tensor):
+    """(val per in-edge, s per vertex) with val[e] = w[e] / s[src(e)]."""
+    _dev(w, torch.float32, plan.m, "w")
+    val = torch.empty_like(w)
+    s = torch.empty(plan.n, dtype=torch.float32, device=w.device)
+    _raise(lib().dag_normalize_weights(plan.h, _ptr(w), _ptr(val), _ptr(s), _stream()), False)
+    return val, s
+
+
+def pagerank_adjoint(in_plan: Plan, out_plan: Plan, val, val_out, s, rank, c, d=0.85, tol=1e-6,
+                     variant="delayed", delta=256, max_iters=10000, want_lambda=False, stream=None):
+    """Adjoint solve + gradients. Returns (grad_w [m], grad_t [n], lambda or None, stats)."""
+    dev = rank.device
+    gw = torch.empty(in_plan.m, dtype=torch.float32, device=dev)
+    gt = torch.empty(in_plan.n, dtype=torch.float32, device=dev)
+    lam = torch.empty(in_plan.n, dtype=torch.float32, device=dev) if want_lambda else None
+    st = _Stats()
+    rc = lib().dag_pagerank_adjoint(in_plan.h, out_plan.h, d, tol, _variant(variant), delta, max_iters,
+                                    _ptr(val), _ptr(val_out), _ptr(s), _ptr(rank), _ptr(c), _ptr(gw), _ptr(gt),
+                                    _ptr(lam), ctypes.byref(st), _stream(stream))
+    _raise(rc)
+    return gw, gt, lam, _stats(st, in_plan.m)
+
+
+class WeightedPageRank:
+    """Forward/backward of weighted PageRank over one graph: holds the in-edge
+    plan, the out-edge CSR and its plan, and the in->out edge permutation."""
+
+    def __init__(self, plan: Plan, d=0.85, tol=1e-6, variant="delayed", delta=256, max_iters=10000):
+        self.plan, self.d, self.tol, self.variant, self.delta, self.max_iters = plan, d, tol, variant, delta, max_iters
+        orow, ocol, perm = transpose(plan)
+        self.perm = perm.long()
+        self.out_plan = Plan(orow, ocol)
+
+    def forward(self, w: torch.Tensor, teleport: torch.Tensor | None = None):
+        val, s = normalize_weights(self.plan, w)
+        r, st = pagerank(self.plan, self.d, self.tol, self.variant, self.delta, self.max_iters, teleport=teleport,
+                         val=val)
+        return r, val, s, st
+
+    def backward(self, val, s, r, c):
+        val_out = val[self.perm].contiguous()
+        return pagerank_adjoint(self.plan, self.out_plan, val, val_out, s, r, c.contiguous(), self.d, self.tol,
+                                self.variant, self.delta, self.max_iters)
+
+
+class PageRankFn(torch.autograd.Function):
+    """r = PageRank(row-normalised w, teleport t); gradients w.r.t. w and t by
+    the adjoint sweep (no iterates stored)."""
+
+    @staticmethod
+    def forward(ctx, w, t, model: WeightedPageRank):
+        r, val, s, st = model.forward(w.detach().contiguous(), None if t is None else t.detach().contiguous())
+        ctx.model = model
+        ctx.has_t = t is not None
+        ctx.save_for_backward(val, s, r)
+        ctx.stats = st
+        return r
+
+    @staticmethod
+    def backward(ctx, grad_r):
+        val, s, r = ctx.saved_tensors
+        gw, gt, _, st = ctx.model.backward(val, s, r, grad_r.contiguous().float())
+        ctx.backward_stats = st
+        return gw, (gt if ctx.has_t else None), None
