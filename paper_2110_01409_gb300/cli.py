@@ -1,0 +1,60 @@
+"""Run one solve on a generated graph and print its statistics as JSON.
+
+    python -m paper_2110_01409_gb300.cli --graph rmat --scale 20 --algo sssp --variant delayed --delta 32
+
+Used for single-kernel profiling captures (a small case of the benchmark's
+kernels) and for quick experiments from the shell.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import numpy as np
+import torch
+
+from . import build as B
+from . import dag
+from . import inputs as I
+
+
+def make_graph(kind: str, scale: int, seed: int):
+    if kind == "rmat":
+        return I.rmat(scale, 16, 0.57, 0.19, 0.19, seed=seed)
+    if kind == "er":
+        return I.erdos_renyi(1 << scale, 16, seed=seed)
+    if kind == "banded":
+        return I.banded(1 << scale, 15, 1024, 1, seed=seed)
+    raise ValueError(kind)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--graph", default="rmat", choices=["rmat", "er", "banded"])
+    ap.add_argument("--scale", type=int, default=20)
+    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--algo", default="pagerank", choices=["pagerank", "sssp"])
+    ap.add_argument("--variant", default="delayed", choices=list(dag.VARIANTS))
+    ap.add_argument("--delta", type=int, default=256)
+    ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--tol", type=float, default=1e-6)
+    args = ap.parse_args()
+    B.build()
+    g = make_graph(args.graph, args.scale, args.seed)
+    plan = dag.Plan.from_graph(g, "cuda")
+    out = []
+    for _ in range(args.repeat):
+        if args.algo == "pagerank":
+            _, st = dag.pagerank(plan, 0.85, args.tol, args.variant, args.delta)
+        else:
+            w = torch.from_numpy(I.weights_u32(g, args.seed).view(np.int32)).cuda()
+            src = int(I.sources(g, 1, seed=args.seed)[0])
+            _, st = dag.sssp(plan, src, w, args.variant, args.delta)
+        out.append(st)
+    torch.cuda.synchronize()
+    print(json.dumps({"graph": args.graph, "scale": args.scale, "n": g.n, "m": g.m, "algo": args.algo,
+                      "variant": args.variant, "delta": args.delta, "runs": out}))
+
+
+if __name__ == "__main__":
+    main()

@@ -112,9 +112,12 @@ extern "C" int dag_workers(dag_plan* plan, dag_variant variant, int32_t delta, i
     int rc = check_variant(variant, delta, 1);
     if (rc) return rc;
     if (variant == DAG_DELAYED && delta == 0) variant = DAG_ASYNC;
-    int cap = 0;
-    if (variant == DAG_DELAYED) sweep_buffer_cap(plan, delta, &cap);
-    return max_workers(plan, MODE_PR, variant, cap, out_workers);
+    int nb = 0, cap = 0;
+    Partition* part = nullptr;
+    rc = sweep_shape(plan, MODE_PR, variant, delta, &nb, &cap, &part, 0);
+    if (rc) return rc;
+    *out_workers = nb;
+    return DAG_OK;
 }
 
 extern "C" int dag_pagerank(dag_plan* plan, float d, double tol, dag_variant variant, int32_t delta,

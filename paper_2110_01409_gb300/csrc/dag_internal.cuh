@@ -20,8 +20,18 @@ namespace dag {
 // order, so the rows a tile completes are contiguous and a delay buffer of
 // consecutive rows can be flushed with coalesced stores.
 // ---------------------------------------------------------------------------
-constexpr int NT = 256;           // threads per CTA
-constexpr int IPT = 7;            // items per thread per tile (odd: fewer bank conflicts in the walk)
+#ifndef DAG_NT
+#define DAG_NT 256
+#endif
+#ifndef DAG_IPT
+#define DAG_IPT 7
+#endif
+#ifndef DAG_MINBLOCKS
+#define DAG_MINBLOCKS 4
+#endif
+constexpr int NT = DAG_NT;        // threads per CTA
+constexpr int IPT = DAG_IPT;      // items per thread per tile (odd: fewer bank conflicts in the walk)
+constexpr int MINBLOCKS = DAG_MINBLOCKS;  // CTAs per SM the register budget is sized for
 constexpr int TILE = NT * IPT;    // items per tile
 constexpr int NWARP = NT / 32;
 constexpr int GSTRIPES = 32;      // stripes of the live dangling/global-sum accumulator
@@ -142,7 +152,8 @@ int max_workers(dag_plan* plan, int mode, int variant, int buf_cap_elems, int* o
 // sweep.cu
 int launch_sweep(dag_plan* plan, int mode, int variant, int delta, SweepParams& p, cudaStream_t s,
                  int* out_nblocks);
-int sweep_buffer_cap(dag_plan* plan, int delta, int* cap);
+int sweep_shape(dag_plan* plan, int mode, int variant, int delta, int* nb_out, int* cap_out, Partition** part_out,
+                cudaStream_t s);
 
 // batched.cu
 int launch_batched(dag_plan* plan, int is_bf, int variant, int delta, int max_iters, int B, float d,
@@ -181,8 +192,10 @@ __device__ __forceinline__ uint32_t ld_stream_u32(const uint32_t* p)
     asm volatile("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(v) : "l"(p));
     return v;
 }
-// Weak load: may hit in L1. Used for data no other CTA writes during this
-// sweep (the previous iterate in the synchronous form).
+// Weak load: may hit in L1. Used for the previous iterate in the synchronous
+// form (no CTA writes it during the sweep) and for the delayed form's view of
+// the live array, which may lag other CTAs' flushes until this SM's next
+// acquire (a flush or the grid barrier).
 __device__ __forceinline__ uint32_t ld_weak_b32(const void* p)
 {
     uint32_t v;

@@ -14,11 +14,24 @@
 //    array (the "global read" form, Sec. III-C);
 //  * one grid barrier per iteration (Sec. I) and the stopping rules of Sec. IV.
 //
-// GPU specifics: in-place forms read the shared state with relaxed gpu-scope
-// loads (served by L2, where all CTAs' stores meet), the synchronous form
-// with ordinary loads that may hit in L1; the edge stream (colidx, weights)
-// bypasses L1. Rows completed by a tile are contiguous, so flushes are
-// coalesced stores of consecutive values.
+// GPU specifics. The synchronous form reads the previous iterate with
+// ordinary loads, which may hit in L1 (no CTA writes that array during the
+// sweep). The asynchronous form reads the live array with relaxed gpu-scope
+// loads, served by L2 where all CTAs' stores meet, so every value is the
+// latest written. The delayed form reads with ordinary loads too: a CTA's
+// view of other blocks may then lag until its next flush, where an acquire
+// fence refreshes it. The delay delta thus sets both how often a worker
+// publishes its values and how often it takes in everyone else's; between
+// refreshes the gathers keep their L1 hits, which in-place coherent reads
+// give up. The edge stream (colidx, weights) bypasses L1. Rows completed by a
+// tile are contiguous, so flushes are coalesced stores of consecutive values.
+//
+// Per tile: all loads (edge stream, gathers, row ends, the rows' old values)
+// are issued in one staging phase; after barrier (A) each thread walks its
+// IPT items of the merge path; after barrier (B) each thread takes the carry
+// of a row begun by earlier threads from a block segmented prefix over the
+// warps' run totals and finishes the rows it ends. A delayed flush is copied
+// out between (A) and (B) of the following tile, so it costs no barrier.
 #include <climits>
 #include <type_traits>
 
@@ -55,25 +68,25 @@ __device__ __forceinline__ uint32_t relax(uint32_t du, uint32_t w)
     return (s < du || s == INF) ? INF - 1u : s;
 }
 
+template <int MODE>
 struct SweepShared {
     uint32_t val[TILE];        // gathered edge terms of the tile
     int rowend[TILE + 1];      // tile-relative row end offsets (+ sentinel)
     uint32_t rowsum[TILE];     // per-row reduction of the tile
-    uint32_t scan[NT];         // per-thread inclusive segmented scan of carries
-    int wkey[NWARP];
-    uint32_t wval[NWARP];
-    uint32_t wscan[NWARP];
+    int wkey[NWARP];           // row in progress after each warp's last lane
+    int wfirst[NWARP];         // row in progress after each warp's first lane
+    uint32_t wval[NWARP];      // warp-local inclusive run total at the last lane
     double red0[NWARP];
     double red1[NWARP];
-    double dgw[NWARP];
-    double G;                  // live global sum read at the tile start
+    double G;                  // live global sum read during the tile's staging
     double res;                // broadcast of the sweep residual
     double gprev;              // broadcast of the previous sweep's global sum
     double T;                  // broadcast of the teleport total / ||c||_1
 };
 
 // Block sum of two doubles; the result is valid in thread 0.
-__device__ __forceinline__ void block_sum2(SweepShared& sh, double& a, double& b)
+template <class SH>
+__device__ __forceinline__ void block_sum2(SH& sh, double& a, double& b)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     a = warp_sum(a);
@@ -87,8 +100,80 @@ __device__ __forceinline__ void block_sum2(SweepShared& sh, double& a, double& b
     __syncthreads();
 }
 
+constexpr int RP = 2;  // epilogue rows per thread whose inputs are loaded with the tile
+
+// Registers of a tile being loaded ahead of use.
+template <int MODE>
+struct Stage {
+    int a0, b0, NA, NB;
+    int col[IPT];        // edge stream (source ids)
+    uint32_t aux[IPT];   // per-edge weight / value
+    uint32_t term[IPT];  // gathered edge terms
+    int rend[IPT];       // tile-relative row ends
+    uint32_t pfx[RP];    // old values of the first RP * NT rows
+    float pfd[RP];       // their out-degrees
+    double gs;           // one stripe of the live global sum (warp 0)
+};
+
+// Issues the coalesced loads of tile t (everything except the gathers).
+template <int MODE, bool WEAK>
+__device__ __forceinline__ void stage_issue(Stage<MODE>& st, const SweepParams& p, const uint32_t* xin, int t, int tid)
+{
+    constexpr bool BF = MODE == MODE_BF;
+    st.a0 = p.tile_row[t];
+    st.b0 = p.tile_nz[t];
+    st.NA = p.tile_row[t + 1] - st.a0;
+    st.NB = p.tile_nz[t + 1] - st.b0;
+#pragma unroll
+    for (int q = 0; q < IPT; ++q) {
+        const int j = tid + q * NT;
+        st.col[q] = 0;
+        st.aux[q] = 0;
+        if (j < st.NB) {
+            st.col[q] = ld_stream_i32(p.colidx + st.b0 + j);
+            if constexpr (BF) st.aux[q] = ld_stream_u32(p.w + st.b0 + j);
+            if constexpr (MODE == MODE_PRW || MODE == MODE_ADJ)
+                st.aux[q] = __float_as_uint(ld_stream_f32(p.val + st.b0 + j));
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < IPT; ++q) {
+        const int i = tid + q * NT;
+        st.rend[q] = (i < st.NA) ? ld_stream_i32(p.rowptr + st.a0 + i + 1) - st.b0 : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < RP; ++k) {
+        const int r = tid + k * NT;
+        st.pfx[k] = 0u;
+        st.pfd[k] = 0.0f;
+        if (r < st.NA) {
+            st.pfx[k] = WEAK ? ld_weak_b32(xin + st.a0 + r) : ld_relaxed_b32(xin + st.a0 + r);
+            if constexpr (!BF) st.pfd[k] = ld_stream_f32(p.degf + st.a0 + r);
+        }
+    }
+}
+
+// Issues tile t's gathers of the state vector (sync: previous iterate; delayed:
+// this SM's view of the live array; async: the live array in L2).
+template <int MODE, bool WEAK>
+__device__ __forceinline__ void stage_gather(Stage<MODE>& st, const uint32_t* xin, int tid)
+{
+#pragma unroll
+    for (int q = 0; q < IPT; ++q) {
+        const int j = tid + q * NT;
+        uint32_t term = 0u;
+        if (j < st.NB) {
+            const uint32_t xv = WEAK ? ld_weak_b32(xin + st.col[q]) : ld_relaxed_b32(xin + st.col[q]);
+            if constexpr (MODE == MODE_BF) term = relax(xv, st.aux[q]);
+            else if constexpr (MODE == MODE_PR) term = xv;
+            else term = __float_as_uint(__uint_as_float(st.aux[q]) * __uint_as_float(xv));
+        }
+        st.term[q] = term;
+    }
+}
+
 template <int MODE, int VAR>
-__global__ void __launch_bounds__(NT) sweep_kernel(const SweepParams p)
+__global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams p)
 {
     using O = Op<MODE>;
     constexpr bool BF = MODE == MODE_BF;
@@ -96,7 +181,7 @@ __global__ void __launch_bounds__(NT) sweep_kernel(const SweepParams p)
     constexpr bool DELAYED = VAR == DAG_DELAYED;
     constexpr bool LIVE_G = !SYNC && !BF;  // async/delayed PageRank-type: live global sum
 
-    __shared__ SweepShared sh;
+    __shared__ SweepShared<MODE> sh;
     extern __shared__ uint32_t s_buf[];  // delay buffer (DELAYED)
 
     const int c = blockIdx.x;
@@ -166,68 +251,87 @@ __global__ void __launch_bounds__(NT) sweep_kernel(const SweepParams p)
         const int slot = it % 3;
         const uint32_t* xin = SYNC ? ((it & 1) ? X1 : X0) : X0;
         uint32_t* xout = SYNC ? ((it & 1) ? X0 : X1) : X0;
-        double res_part = 0.0, g_part = 0.0, dg_part = 0.0;
-        uint32_t carry = O::identity();  // partial of the row that continues into the next tile
-        bool publish = false;            // async: a tile's change of G waits in sh.dgw
-        // global term of this sweep (sync) or of this tile (async/delayed)
+        // per-thread partial sums in FP32 (few rows each); FP64 from the block reduction on
+        float res_part = 0.0f, g_part = 0.0f, dg_part = 0.0f;
+        uint32_t carry = O::identity();  // thread 0: partial of the row continuing into the next tile
+        bool flush_pending = false;      // delayed: the buffer is copied out during the next tile's walk
         float gterm = 0.0f;
         if constexpr (SYNC && !BF) {
             gterm = (MODE == MODE_ADJ) ? (float)((double)p.g_coef * gprev)
                                        : (float)((double)p.g_coef * (T - gprev));
         }
 
-        for (int t = tile_lo; t < tile_hi; ++t) {
-            const int a0 = p.tile_row[t], b0 = p.tile_nz[t];
-            const int NA = p.tile_row[t + 1] - a0, NB = p.tile_nz[t + 1] - b0;
-            const int L = NA + NB;
-
+        // Software pipeline: while tile t is walked, tile t+1's edge stream,
+        // row ends and old values are in flight (issued after barrier A of t)
+        // and its gathers too (issued before barrier C of t).
+        Stage<MODE> nx;
+        if (tile_lo < tile_hi) {
+            stage_issue<MODE, SYNC || DELAYED>(nx, p, xin, tile_lo, tid);
+            stage_gather<MODE, SYNC || DELAYED>(nx, xin, tid);
             if constexpr (LIVE_G) {
-                if (warp == 0) {
-                    double gs = ld_relaxed_f64(&sb->stripe[lane * GSTRIDE]);
-                    gs = warp_sum(gs);
-                    if (lane == 0) sh.G = gs;
-                }
+                if (warp == 0) nx.gs = ld_relaxed_f64(&sb->stripe[lane * GSTRIDE]);
             }
-            // -------- stage the tile: row ends, then gathered edge terms --------
-            for (int i = tid; i < NA; i += NT) sh.rowend[i] = ld_stream_i32(p.rowptr + a0 + i + 1) - b0;
-            if (tid == 0) sh.rowend[NA] = INT_MAX;
-            {
-                int col[IPT];
-                uint32_t aux[IPT];
-#pragma unroll
-                for (int q = 0; q < IPT; ++q) {
-                    const int j = tid + q * NT;
-                    col[q] = 0;
-                    aux[q] = 0;
-                    if (j < NB) {
-                        col[q] = ld_stream_i32(p.colidx + b0 + j);
-                        if constexpr (BF) aux[q] = ld_stream_u32(p.w + b0 + j);
-                        if constexpr (MODE == MODE_PRW || MODE == MODE_ADJ)
-                            aux[q] = __float_as_uint(ld_stream_f32(p.val + b0 + j));
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < IPT; ++q) {
-                    const int j = tid + q * NT;
-                    if (j < NB) {
-                        uint32_t xv = SYNC ? ld_weak_b32(xin + col[q]) : ld_relaxed_b32(xin + col[q]);
-                        uint32_t term;
-                        if constexpr (BF) term = relax(xv, aux[q]);
-                        else if constexpr (MODE == MODE_PR) term = xv;
-                        else term = __float_as_uint(__uint_as_float(aux[q]) * __uint_as_float(xv));
-                        sh.val[j] = term;
-                    }
-                }
-            }
-            __syncthreads();  // (A) tile staged
+        }
 
-            if constexpr (VAR == DAG_ASYNC && !BF) {
-                if (publish && tid == 0) {
-                    double s = 0.0;
-                    for (int k = 0; k < NWARP; ++k) s += sh.dgw[k];
-                    atomicAdd(&sb->stripe[(c % GSTRIPES) * GSTRIDE], s);
+        for (int t = tile_lo; t <= tile_hi; ++t) {
+            // One pass per tile, plus one extra pass (t == tile_hi) that only completes a pending flush.
+            const bool real = t < tile_hi;
+            const int a0 = real ? nx.a0 : 0, b0 = real ? nx.b0 : 0;
+            const int NA = real ? nx.NA : 0, NB = real ? nx.NB : 0;
+            const int L = NA + NB;
+            uint32_t pf_x[RP];
+            float pf_d[RP];
+            // -------- tile t into shared memory --------
+            if (real) {
+#pragma unroll
+                for (int q = 0; q < IPT; ++q) {
+                    const int jj = tid + q * NT;
+                    if (jj < NB) sh.val[jj] = nx.term[q];
+                    if (jj < NA) sh.rowend[jj] = nx.rend[q];
                 }
-                publish = false;
+#pragma unroll
+                for (int k = 0; k < RP; ++k) { pf_x[k] = nx.pfx[k]; pf_d[k] = nx.pfd[k]; }
+                if constexpr (LIVE_G) {
+                    if (warp == 0) {
+                        const double gs = warp_sum(nx.gs);
+                        if (lane == 0) sh.G = gs;
+                    }
+                }
+            }
+            if (tid == 0) sh.rowend[NA] = INT_MAX;
+            __syncthreads();  // (A) tile staged; every thread is done with the previous tile
+
+            // -------- delayed: copy out the buffer filled by the previous tiles --------
+            if constexpr (DELAYED) {
+                if (flush_pending) {
+                    for (int k = tid; k < buf_cnt; k += NT) st_relaxed_b32(X0 + buf_first + k, s_buf[k]);
+                    if constexpr (!BF) {
+                        const float s = warp_sum(dg_part);
+                        dg_part = 0.0f;
+                        __syncwarp();
+                        if (lane == 0 && s != 0.0f) {
+                            __threadfence();  // this warp's flushed values before its share of N
+                            atomicAdd(&sb->stripe[(c % GSTRIPES) * GSTRIDE], (double)s);
+                        }
+                    }
+                    if (tid == 0) {
+                        // refresh this SM's view: later ordinary loads see what other CTAs published
+                        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+                        ++flushes;
+                    }
+                    buf_first += buf_cnt;  // every thread keeps the same copy of the buffer state
+                    buf_cnt = 0;
+                    flush_pending = false;
+                }
+            }
+            if (!real) break;
+            const bool more = t + 1 < tile_hi;
+            if (more) stage_issue<MODE, SYNC || DELAYED>(nx, p, xin, t + 1, tid);
+            float gt = gterm;
+            if constexpr (LIVE_G) {
+                const double G = sh.G;
+                gt = (MODE == MODE_ADJ) ? (float)((double)p.g_coef * G) : (float)((double)p.g_coef * (T - G));
+                if (warp == 0 && more) nx.gs = ld_relaxed_f64(&sb->stripe[lane * GSTRIDE]);
             }
 
             // -------- merge-path walk over this thread's IPT items --------
@@ -258,7 +362,7 @@ __global__ void __launch_bounds__(NT) sweep_kernel(const SweepParams p)
                     }
                 }
             }
-            // -------- block segmented scan of (row in progress, partial) --------
+            // -------- segmented scan of (row in progress, partial) --------
             const int key = i;
             uint32_t sv = acc;
 #pragma unroll
@@ -268,117 +372,106 @@ __global__ void __launch_bounds__(NT) sweep_kernel(const SweepParams p)
                 if (lane >= o && ok == key) sv = O::combine(sv, ov);
             }
             if (lane == 31) { sh.wkey[warp] = key; sh.wval[warp] = sv; }
-            __syncthreads();  // (B)
-            if (warp == 0) {
-                const int wk = lane < NWARP ? sh.wkey[lane] : INT_MAX - lane;
-                uint32_t wv = lane < NWARP ? sh.wval[lane] : O::identity();
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t ov = __shfl_up_sync(0xffffffffu, wv, o);
-                    const int ok = __shfl_up_sync(0xffffffffu, wk, o);
-                    if (lane >= o && ok == wk) wv = O::combine(wv, ov);
-                }
-                if (lane < NWARP) sh.wscan[lane] = wv;
-            }
-            __syncthreads();  // (C)
+            if (lane == 0) sh.wfirst[warp] = key;
+            __syncthreads();  // (B) warp run totals visible
+
+            // E_w: run total ending at warp w's last lane, over all earlier warps
+            // (segmented scan over the NWARP warp summaries, in every warp).
+            uint32_t E;
             {
-                const int k_first = __shfl_sync(0xffffffffu, key, 0);
-                if (warp > 0 && key == k_first && sh.wkey[warp - 1] == key)
-                    sv = O::combine(sv, sh.wscan[warp - 1]);
+                const int wl = lane < NWARP ? lane : NWARP - 1;
+                const int wk = sh.wkey[wl];
+                const bool head = lane == 0 || sh.wfirst[wl] != wk || sh.wkey[wl > 0 ? wl - 1 : 0] != wk;
+                E = sh.wval[wl];
+                int hd = head ? 1 : 0;
+#pragma unroll
+                for (int o = 1; o < NWARP; o <<= 1) {
+                    const uint32_t oe = __shfl_up_sync(0xffffffffu, E, o);
+                    const int oh = __shfl_up_sync(0xffffffffu, hd, o);
+                    if (lane >= o && !hd) E = O::combine(E, oe);
+                    if (lane >= o) hd |= oh;
+                }
             }
-            sh.scan[tid] = sv;
-            __syncthreads();  // (D)
-            if (tid > 0 && emitted) sh.rowsum[i_start] = O::combine(sh.rowsum[i_start], sh.scan[tid - 1]);
-            if (tid == 0) carry = sh.scan[NT - 1];
-            __syncthreads();  // (E) row sums final
+            const uint32_t E_prev = __shfl_sync(0xffffffffu, E, warp > 0 ? warp - 1 : 0);
+            const int key_prev = warp > 0 ? sh.wkey[warp - 1] : -1;
+            const int k_first = __shfl_sync(0xffffffffu, key, 0);
+            const uint32_t pre = (warp > 0 && key_prev == k_first) ? E_prev : O::identity();
+            const uint32_t S = (key == k_first) ? O::combine(sv, pre) : sv;
+            uint32_t cin = __shfl_up_sync(0xffffffffu, S, 1);
+            if (lane == 0) cin = (warp > 0) ? E_prev : O::identity();
+            if (tid > 0 && emitted) sh.rowsum[i_start] = O::combine(sh.rowsum[i_start], cin);
+            const uint32_t E_last = __shfl_sync(0xffffffffu, E, NWARP - 1);  // whole warp takes part
+            if (tid == 0) carry = E_last;  // partial of row NA for the next tile
+            if (more) stage_gather<MODE, SYNC || DELAYED>(nx, xin, tid);
+            __syncthreads();  // (C) row sums final
 
             // -------- epilogue: new values of the rows this tile completed --------
-            float gt = gterm;
-            if constexpr (LIVE_G) {
-                gt = (MODE == MODE_ADJ) ? (float)((double)p.g_coef * sh.G)
-                                        : (float)((double)p.g_coef * (T - sh.G));
-            }
-            for (int r = tid; r < NA; r += NT) {
+#pragma unroll
+            for (int k = 0; k < IPT; ++k) {
+                const int r = tid + k * NT;
+                if (r >= NA) break;
                 const int v = a0 + r;
                 const uint32_t sum = sh.rowsum[r];
+                uint32_t xo_bits;
+                float dg = 0.0f;
+                if (k < RP) {
+                    xo_bits = pf_x[k < RP ? k : 0];
+                    dg = pf_d[k < RP ? k : 0];
+                } else {
+                    xo_bits = SYNC || DELAYED ? ld_weak_b32(xin + v) : ld_relaxed_b32(xin + v);
+                    if constexpr (!BF) dg = ld_stream_f32(p.degf + v);
+                }
                 uint32_t xnew;
                 if constexpr (BF) {
-                    const uint32_t old = SYNC ? ld_weak_b32(xin + v) : ld_relaxed_b32(xin + v);
-                    xnew = sum < old ? sum : old;
-                    if (xnew < old) res_part += 1.0;
+                    xnew = sum < xo_bits ? sum : xo_bits;
+                    if (xnew < xo_bits) res_part += 1.0f;
                 } else {
-                    const float xo = __uint_as_float(SYNC ? ld_weak_b32(xin + v) : ld_relaxed_b32(xin + v));
-                    const float dg = ld_stream_f32(p.degf + v);
-                    float rnew;
-                    float rold;
+                    const float xo = __uint_as_float(xo_bits);
+                    float rnew, rold;
                     if constexpr (MODE == MODE_ADJ) {
                         rold = xo;
                         rnew = ld_stream_f32(p.base + v) + p.d * __uint_as_float(sum) + (dg == 0.0f ? gt : 0.0f);
-                        g_part += (double)rnew;
-                        dg_part += (double)rnew - (double)rold;
+                        g_part += rnew;
+                        dg_part += rnew - rold;
                         if (p.aux_out) p.aux_out[v] = __uint_as_float(sum);
                     } else {
                         rold = (MODE == MODE_PR && dg > 0.0f) ? xo * dg : xo;
                         const float bv = p.base ? p.base_scale * ld_stream_f32(p.base + v) : p.uniform_base;
                         rnew = bv + p.d * __uint_as_float(sum) + gt;
                         if (dg > 0.0f) {
-                            g_part += (double)rnew;
-                            dg_part += (double)rnew - (double)rold;
+                            g_part += rnew;
+                            dg_part += rnew - rold;
                         }
                     }
-                    res_part += fabs((double)rnew - (double)rold);
+                    res_part += fabsf(rnew - rold);
                     xnew = __float_as_uint((MODE == MODE_PR && dg > 0.0f) ? rnew / dg : rnew);
                 }
                 if constexpr (SYNC) st_weak_b32(xout + v, xnew);
                 else if constexpr (DELAYED) s_buf[v - buf_first] = xnew;
                 else st_relaxed_b32(xout + v, xnew);
             }
-
             if constexpr (VAR == DAG_ASYNC && !BF) {
-                const double s = warp_sum(dg_part);
-                dg_part = 0.0;
-                if (lane == 0) sh.dgw[warp] = s;
-                publish = true;  // summed by thread 0 after the next barrier point
+                const float s = warp_sum(dg_part);
+                dg_part = 0.0f;
+                if (lane == 0 && s != 0.0f) atomicAdd(&sb->stripe[(c % GSTRIPES) * GSTRIDE], (double)s);
             }
             if constexpr (DELAYED) {
                 buf_cnt += NA;
-                if (buf_cnt >= p.delta || t == tile_hi - 1) {
-                    double s = 0.0;
-                    if constexpr (!BF) s = warp_sum(dg_part);
-                    dg_part = 0.0;
-                    if (lane == 0) sh.dgw[warp] = s;
-                    __syncthreads();  // buffer complete
-                    for (int k = tid; k < buf_cnt; k += NT) st_relaxed_b32(X0 + buf_first + k, s_buf[k]);
-                    if constexpr (!BF) {
-                        if (tid == 0) {
-                            double tot = 0.0;
-                            for (int k = 0; k < NWARP; ++k) tot += sh.dgw[k];
-                            atomicAdd(&sb->stripe[(c % GSTRIPES) * GSTRIDE], tot);
-                        }
-                    }
-                    buf_first += buf_cnt;
-                    buf_cnt = 0;
-                    ++flushes;
-                    __syncthreads();  // buffer free again
-                }
+                if (buf_cnt >= p.delta || t == tile_hi - 1) flush_pending = true;
             }
         }  // tiles
 
-        if constexpr (VAR == DAG_ASYNC && !BF) {
-            __syncthreads();
-            if (publish && tid == 0) {
-                double s = 0.0;
-                for (int k = 0; k < NWARP; ++k) s += sh.dgw[k];
-                atomicAdd(&sb->stripe[(c % GSTRIPES) * GSTRIDE], s);
-            }
+        if constexpr (DELAYED) {
+            buf_first = row_lo;
+            buf_cnt = 0;
         }
-        if constexpr (DELAYED) buf_first = row_lo;
 
         // -------- end of sweep: residual, barrier, stopping rule --------
-        block_sum2(sh, res_part, g_part);
+        double res_d = (double)res_part, g_d = (double)g_part;
+        block_sum2(sh, res_d, g_d);
         if (tid == 0) {
-            if (res_part != 0.0) atomicAdd(&sb->acc_res[slot], res_part);
-            if (SYNC && !BF && g_part != 0.0) atomicAdd(&sb->acc_g[slot], g_part);
+            if (res_d != 0.0) atomicAdd(&sb->acc_res[slot], res_d);
+            if (SYNC && !BF && g_d != 0.0) atomicAdd(&sb->acc_g[slot], g_d);
         }
         if (!grid_barrier(sb, p.nblocks, bar_target, p.timeout_ns)) return;
         if (tid == 0) {
@@ -436,24 +529,15 @@ static KernelFn kernel_for(int mode, int variant)
     return table[mode][variant];
 }
 
-// Elements of dynamic shared memory a delayed sweep needs for buffer size
-// delta: up to delta - 1 buffered rows plus one tile's rows.
-int sweep_buffer_cap(dag_plan* plan, int delta, int* cap)
-{
-    long long c = (long long)delta - 1 + TILE;
-    if (c > plan->n) c = plan->n;
-    if (c < 1) c = 1;
-    *cap = (int)c;
-    return DAG_OK;
-}
-
 int max_workers(dag_plan* plan, int mode, int variant, int buf_cap_elems, int* out)
 {
     KernelFn k = kernel_for(mode, variant);
     size_t dyn = (variant == DAG_DELAYED) ? (size_t)buf_cap_elems * 4 : 0;
     int max_dyn = 0;
     DAG_CUDA(cudaDeviceGetAttribute(&max_dyn, cudaDevAttrMaxSharedMemoryPerBlockOptin, plan->device));
-    if (dyn + sizeof(SweepShared) > (size_t)max_dyn)
+    cudaFuncAttributes fa;
+    DAG_CUDA(cudaFuncGetAttributes(&fa, (const void*)k));
+    if (dyn + fa.sharedSizeBytes > (size_t)max_dyn)
         return set_error(DAG_ERR_INVALID, "delta too large: the delay buffer does not fit in shared memory");
     DAG_CUDA(cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     int per_sm = 0;
@@ -463,18 +547,44 @@ int max_workers(dag_plan* plan, int mode, int variant, int buf_cap_elems, int* o
     return DAG_OK;
 }
 
+// Launch shape of a sweep: CTA count, delay-buffer capacity and partition.
+// A delayed sweep's buffer holds at most min(delta - 1 + TILE, rows of the
+// CTA) values (a flush empties it once it reaches delta after a tile). Fewer
+// CTAs mean longer blocks, so the shape is settled by a short fixed-point loop.
+int sweep_shape(dag_plan* plan, int mode, int variant, int delta, int* nb_out, int* cap_out, Partition** part_out,
+                cudaStream_t s)
+{
+    int nb = 0;
+    int rc = max_workers(plan, mode, variant, 0, &nb);
+    if (rc) return rc;
+    int cap = 0;
+    Partition* part = nullptr;
+    for (int iter = 0; iter < 6; ++iter) {
+        rc = get_partition(plan, nb, &part, s);
+        if (rc) return rc;
+        if (variant != DAG_DELAYED) break;
+        long long need = (long long)delta - 1 + TILE;
+        if (need > part->max_rows) need = part->max_rows;
+        cap = (int)(need < 1 ? 1 : need);
+        int nb2 = 0;
+        rc = max_workers(plan, mode, variant, cap, &nb2);
+        if (rc) return rc;
+        if (nb2 >= nb) break;
+        nb = nb2;
+    }
+    *nb_out = nb;
+    *cap_out = cap;
+    *part_out = part;
+    return DAG_OK;
+}
+
 int launch_sweep(dag_plan* plan, int mode, int variant, int delta, SweepParams& p, cudaStream_t s,
                  int* out_nblocks)
 {
-    int cap = 0;
-    if (variant == DAG_DELAYED) sweep_buffer_cap(plan, delta, &cap);
-    int nb = 0;
-    int rc = max_workers(plan, mode, variant, cap, &nb);
-    if (rc) return rc;
+    int nb = 0, cap = 0;
     Partition* part = nullptr;
-    rc = get_partition(plan, nb, &part, s);
+    int rc = sweep_shape(plan, mode, variant, delta, &nb, &cap, &part, s);
     if (rc) return rc;
-    if (variant == DAG_DELAYED && cap > part->max_rows + TILE) cap = part->max_rows + TILE;
     p.nblocks = nb;
     p.delta = (variant == DAG_DELAYED) ? delta : 0;
     p.buf_cap = cap;
@@ -494,6 +604,7 @@ int launch_sweep(dag_plan* plan, int mode, int variant, int delta, SweepParams& 
     KernelFn k = kernel_for(mode, variant);
     void* args[] = {(void*)&p};
     size_t dyn = (variant == DAG_DELAYED) ? (size_t)cap * 4 : 0;
+    DAG_CUDA(cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     DAG_CUDA(cudaLaunchCooperativeKernel((const void*)k, dim3(nb), dim3(NT), args, dyn, s));
     *out_nblocks = nb;
     return DAG_OK;
