@@ -178,6 +178,13 @@ int dag_transpose(dag_plan* plan, int32_t* d_out_rowptr, int32_t* d_out_colidx, 
 int dag_normalize_weights(dag_plan* plan, const float* d_w, float* d_val, float* d_s, void* stream);
 
 /*
+ * d_out[k] = d_src[d_idx[k]] for k < m (device arrays; d_idx in range is the
+ * caller's duty). Puts per-edge values into out-edge order with
+ * dag_transpose's d_perm, e.g. d_val_out for dag_pagerank_adjoint.
+ */
+int dag_gather_f32(const float* d_src, const int32_t* d_idx, int64_t m, float* d_out, void* stream);
+
+/*
  * PageRank adjoint (no counterpart in the paper): for a loss with dL/dr = c,
  * solves lambda = c + d M^T lambda + d g (sum_v lambda_v)/n (g: vertices with
  * no out-edges) by the same sweep (variant, delta) pulled over the out-edge

@@ -214,6 +214,12 @@ __global__ void k_div(const int* colidx, const float* w, const float* s, float* 
         val[e] = w[e] / s[colidx[e]];
 }
 
+__global__ void k_gather_f32(const float* src, const int* idx, float* out, long long m)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < m; e += (long long)gridDim.x * blockDim.x)
+        out[e] = src[idx[e]];
+}
+
 int launch_normalize(dag_plan* plan, const float* w, float* val, float* s_out, cudaStream_t s)
 {
     const int n = plan->n;
@@ -345,6 +351,15 @@ extern "C" int dag_normalize_weights(dag_plan* p, const float* d_w, float* d_val
 {
     if (!p || !d_s || (p->m > 0 && (!d_w || !d_val))) return set_error(DAG_ERR_INVALID, "null argument");
     return launch_normalize(p, d_w, d_val, d_s, (cudaStream_t)stream);
+}
+
+extern "C" int dag_gather_f32(const float* d_src, const int32_t* d_idx, int64_t m, float* d_out, void* stream)
+{
+    if (m < 0 || (m > 0 && (!d_src || !d_idx || !d_out))) return set_error(DAG_ERR_INVALID, "bad argument");
+    if (m == 0) return DAG_OK;
+    k_gather_f32<<<2048, 256, 0, (cudaStream_t)stream>>>(d_src, d_idx, d_out, m);
+    DAG_CUDA(cudaGetLastError());
+    return DAG_OK;
 }
 
 extern "C" int dag_debug_skip_barrier_once(dag_plan* p, int32_t timeout_ms)

@@ -26,7 +26,7 @@ EXPORTS = (
     "dag_plan_create", "dag_plan_destroy", "dag_plan_out_degree", "dag_partition", "dag_workers",
     "dag_pagerank", "dag_sssp", "dag_ppr_batched", "dag_sssp_batched", "dag_transpose",
     "dag_normalize_weights", "dag_pagerank_adjoint", "dag_strerror", "dag_last_error_message",
-    "dag_debug_skip_barrier_once",
+    "dag_debug_skip_barrier_once", "dag_gather_f32",
 )
 
 
@@ -86,6 +86,7 @@ def lib():
             L.dag_last_error_message.argtypes = []
             L.dag_last_error_message.restype = ctypes.c_char_p
             L.dag_debug_skip_barrier_once.argtypes = [_vp, _i32]
+            L.dag_gather_f32.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp]
             for f in EXPORTS:
                 if f not in ("dag_strerror", "dag_last_error_message"):
                     getattr(L, f).restype = ctypes.c_int
@@ -288,7 +289,7 @@ class WeightedPageRank:
     def __init__(self, plan: Plan, d=0.85, tol=1e-6, variant="delayed", delta=256, max_iters=10000):
         self.plan, self.d, self.tol, self.variant, self.delta, self.max_iters = plan, d, tol, variant, delta, max_iters
         orow, ocol, perm = transpose(plan)
-        self.perm = perm.long()
+        self.perm = perm
         self.out_plan = Plan(orow, ocol)
 
     def forward(self, w: torch.Tensor, teleport: torch.Tensor | None = None):
@@ -298,7 +299,8 @@ class WeightedPageRank:
         return r, val, s, st
 
     def backward(self, val, s, r, c):
-        val_out = val[self.perm].contiguous()
+        val_out = torch.empty_like(val)
+        _raise(lib().dag_gather_f32(_ptr(val), _ptr(self.perm), self.plan.m, _ptr(val_out), _stream()), False)
         return pagerank_adjoint(self.plan, self.out_plan, val, val_out, s, r, c.contiguous(), self.d, self.tol,
                                 self.variant, self.delta, self.max_iters)
 
