@@ -200,6 +200,32 @@ int dag_pagerank_adjoint(dag_plan* in_plan, dag_plan* out_plan, float d, double 
                          const float* d_s, const float* d_rank, const float* d_c, float* d_grad_w,
                          float* d_grad_t, float* d_lambda, dag_stats* h_stats, void* stream);
 
+/*
+ * PageRank with no device allocation. This is an interface convenience with
+ * no counterpart in the paper. It is for callers that cannot call cudaMalloc
+ * at solve time, for instance an application whose device memory is owned by
+ * its own pool allocator, or a latency-bound service that cannot accept
+ * cudaMalloc's implicit device synchronisation. It computes what dag_pagerank
+ * computes for the in-edge CSR *csr (same arguments; val is not supported),
+ * without a plan. Its scratch (out-degrees, state buffers, control block,
+ * partition) lives in one fixed device array of about 17 MiB inside the
+ * library, which every GPU that loads the library keeps until exit.
+ *  - Limits: n <= DAG_NOALLOC_MAX_N and m <= DAG_NOALLOC_MAX_M; a larger
+ *    graph returns DAG_ERR_INVALID and changes nothing.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current. Make that first call
+ *    before any stream capture.
+ *  - All calls share the array, and it keeps the previous call's contents
+ *    (each call clears what it needs zeroed). Calls whose GPU work overlaps,
+ *    for instance on two streams, race on it: serialise them.
+ *  - The call waits for `stream`; h_stats->ms is left 0.
+ */
+#define DAG_NOALLOC_MAX_N (1 << 20)
+#define DAG_NOALLOC_MAX_M (1 << 24)
+int dag_pagerank_noalloc(const dag_csr* csr, float d, double tol, dag_variant variant, int32_t delta,
+                         int32_t max_iters, const float* d_teleport, float* d_rank, dag_stats* h_stats,
+                         void* stream);
+
 /* Names an error code. Never NULL. */
 const char* dag_strerror(int code);
 /* Detail of the last error raised on the calling host thread ("" if none). */

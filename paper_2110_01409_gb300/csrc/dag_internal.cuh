@@ -155,6 +155,17 @@ int launch_sweep(dag_plan* plan, int mode, int variant, int delta, SweepParams& 
 int sweep_shape(dag_plan* plan, int mode, int variant, int delta, int* nb_out, int* cap_out, Partition** part_out,
                 cudaStream_t s);
 
+const void* sweep_kernel_ptr(int mode, int variant);
+
+// plan.cu kernels reused by the allocation-free entry point (noalloc.cu)
+__global__ void k_check_rowptr(const int* rowptr, int n, long long m, int* bad);
+__global__ void k_out_degree(const int* colidx, long long m, int n, int* outdeg, int* bad);
+__global__ void k_degf(const int* outdeg, float* degf, int n);
+__global__ void k_cta_rows(const int* rowptr, int n, long long total, int P, int* cta_row);
+__global__ void k_cta_tiles(const int* rowptr, const int* cta_row, int P, int* cta_tile, int* max_rows);
+__global__ void k_tile_coords(const int* rowptr, int n, long long m, const int* cta_row, const int* cta_tile,
+                              int P, int tiles, int* tile_row, int* tile_nz);
+
 // batched.cu
 int launch_batched(dag_plan* plan, int is_bf, int variant, int delta, int max_iters, int B, float d,
                    double tol, const void* V_or_src, const uint32_t* w, void* out, int* iters,

@@ -529,6 +529,10 @@ static KernelFn kernel_for(int mode, int variant)
     return table[mode][variant];
 }
 
+// The sweep kernel of (mode, variant), for launches that build their own
+// parameters (the allocation-free entry point).
+const void* sweep_kernel_ptr(int mode, int variant) { return (const void*)kernel_for(mode, variant); }
+
 int max_workers(dag_plan* plan, int mode, int variant, int buf_cap_elems, int* out)
 {
     KernelFn k = kernel_for(mode, variant);

@@ -26,7 +26,7 @@ EXPORTS = (
     "dag_plan_create", "dag_plan_destroy", "dag_plan_out_degree", "dag_partition", "dag_workers",
     "dag_pagerank", "dag_sssp", "dag_ppr_batched", "dag_sssp_batched", "dag_transpose",
     "dag_normalize_weights", "dag_pagerank_adjoint", "dag_strerror", "dag_last_error_message",
-    "dag_debug_skip_barrier_once", "dag_gather_f32",
+    "dag_debug_skip_barrier_once", "dag_pagerank_noalloc", "dag_gather_f32",
 )
 
 
@@ -87,6 +87,8 @@ def lib():
             L.dag_last_error_message.restype = ctypes.c_char_p
             L.dag_debug_skip_barrier_once.argtypes = [_vp, _i32]
             L.dag_gather_f32.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp]
+            L.dag_pagerank_noalloc.argtypes = [ctypes.POINTER(_Csr), _f32, _f64, _i32, _i32, _i32, _vp, _vp,
+                                               ctypes.POINTER(_Stats), _vp]
             for f in EXPORTS:
                 if f not in ("dag_strerror", "dag_last_error_message"):
                     getattr(L, f).restype = ctypes.c_int
@@ -280,6 +282,23 @@ def pagerank_adjoint(in_plan: Plan, out_plan: Plan, val, val_out, s, rank, c, d=
                                     _ptr(lam), ctypes.byref(st), _stream(stream))
     _raise(rc)
     return gw, gt, lam, _stats(st, in_plan.m)
+
+
+def pagerank_noalloc(rowptr: torch.Tensor, colidx: torch.Tensor, d=0.85, tol=1e-6, variant="delayed", delta=256,
+                     max_iters=1000, teleport=None, out=None, stream=None):
+    """PageRank through dag_pagerank_noalloc: no plan and no device allocation
+    inside the library (n <= 2^20, m <= 2^24). Returns (rank, stats)."""
+    n, m = rowptr.numel() - 1, colidx.numel()
+    _dev(rowptr, torch.int32, n + 1, "rowptr")
+    out = out if out is not None else torch.empty(n, dtype=torch.float32, device=rowptr.device)
+    _dev(out, torch.float32, n, "out")
+    _dev(teleport, torch.float32, n, "teleport")
+    csr = _Csr(n, m, rowptr.data_ptr(), colidx.data_ptr() if m else 0)
+    st = _Stats()
+    rc = lib().dag_pagerank_noalloc(ctypes.byref(csr), d, tol, _variant(variant), delta, max_iters, _ptr(teleport),
+                                    _ptr(out), ctypes.byref(st), _stream(stream))
+    _raise(rc)
+    return out, _stats(st, m)
 
 
 class WeightedPageRank:
