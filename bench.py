@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 METRIC = "PageRank/SSSP time-to-converge & GTEPS at tol 1e-6; batched & adjoint vs plain"
 SCALE, EF, SEED = 22, 16, 2
 N_SOURCES = 8
-PR_DELTA, SSSP_DELTA = 256, 32
+PR_DELTA, SSSP_DELTA = 32, 32
 
 
 def _peaks():
@@ -219,8 +219,10 @@ def run_gpu(args):
     e2e = run_e2e(args, g, w, srcs, dev, dag, torch) if args.e2e else None
 
     detail = {}
-    if args.detail and rank == 0:
-        detail = run_detail(g, w, srcs, plan, w_d, dag, torch, args)
+    if args.extras and rank == 0:
+        detail["variants"] = run_detail(g, w, srcs, plan, w_d, dag, torch, args)
+        detail["adjoint"] = run_adjoint(g, plan, dag, torch)
+        detail["batched"] = run_batched(dag, torch)
 
     out = {
         "metric": METRIC,
@@ -329,19 +331,28 @@ def run_detail(g, w, srcs, plan, w_d, dag, torch, args):
     return res
 
 
-def cpu_baseline(g, w, srcs):
-    """The oracle's OpenMP form (paper's CPU scheme) on all host cores: one
-    delayed PageRank and one delayed Bellman-Ford solve of the same graph."""
+def cpu_step(g, w, srcs, cores):
+    """One step on the CPU oracle's OpenMP form (the paper's thread scheme):
+    1 delayed PageRank + the 8 delayed Bellman-Ford solves. Returns seconds and sweeps."""
     import oracle
 
+    _, it_pr, s_pr, ok = oracle.pagerank_threads(g, oracle.DELAYED, tol=1e-6, threads=cores, delta=PR_DELTA)
+    secs, sweeps = s_pr, [it_pr]
+    for s in srcs:
+        _, it, sec, ok2 = oracle.sssp_threads(g, w, int(s), oracle.DELAYED, threads=cores, delta=SSSP_DELTA)
+        secs += sec
+        sweeps.append(it)
+        ok = ok and ok2
+    return secs, sweeps, ok
+
+
+def cpu_baseline(g, w, srcs):
+    """The oracle's OpenMP form on all host cores, on the whole step (bounded: a few seconds)."""
     cores = os.cpu_count() or 1
-    _, it_pr, s_pr, ok1 = oracle.pagerank_threads(g, oracle.DELAYED, tol=1e-6, threads=cores, delta=PR_DELTA)
-    _, it_bf, s_bf, ok2 = oracle.sssp_threads(g, w, int(srcs[0]), oracle.DELAYED, threads=cores, delta=SSSP_DELTA)
-    secs = s_pr + s_bf
-    return {"value": round(2 * g.m / secs / 1e9, 4), "unit": "GTEPS", "cores": cores, "kind": "oracle",
-            "sample": f"1 pagerank (delta {PR_DELTA}, {it_pr} sweeps, {s_pr:.2f}s) + 1 sssp from source {int(srcs[0])} "
-                      f"(delta {SSSP_DELTA}, {it_bf} sweeps, {s_bf:.2f}s) of the 1+{N_SOURCES}-solve step",
-            "converged": bool(ok1 and ok2)}
+    secs, sweeps, ok = cpu_step(g, w, srcs, cores)
+    return {"value": round((1 + N_SOURCES) * g.m / secs / 1e9, 4), "unit": "GTEPS", "cores": cores, "kind": "oracle",
+            "sample": f"one full step (1 pagerank + {N_SOURCES} sssp, delta {PR_DELTA}/{SSSP_DELTA}, sweeps {sweeps}) "
+                      f"in {secs:.2f} s", "converged": bool(ok)}
 
 
 def run_reference(args):
@@ -354,16 +365,13 @@ def run_reference(args):
     oracle.build()
     g, w, srcs, _ = build_inputs()
     cores = os.cpu_count() or 1
-
-    def step():
-        _, _, s1, _ = oracle.pagerank_threads(g, oracle.DELAYED, tol=1e-6, threads=cores, delta=PR_DELTA)
-        _, _, s2, _ = oracle.sssp_threads(g, w, int(srcs[0]), oracle.DELAYED, threads=cores, delta=SSSP_DELTA)
-        return s1 + s2
-
     for _ in range(args.warmup):
-        step()
-    t = sum(step() for _ in range(args.steps))
-    value = 2 * g.m * args.steps / t / 1e9
+        cpu_step(g, w, srcs, cores)
+    t = 0.0
+    for _ in range(args.steps):
+        secs, _, _ = cpu_step(g, w, srcs, cores)
+        t += secs
+    value = (1 + N_SOURCES) * g.m * args.steps / t / 1e9
     out = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GTEPS", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t / args.steps * 1e3, 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/u32",
@@ -371,9 +379,77 @@ def run_reference(args):
            "config": {"workload": f"rmat{SCALE}: pagerank d=0.85 tol=1e-6 delayed delta={PR_DELTA} + "
                                   f"sssp x{N_SOURCES} sources delayed delta={SSSP_DELTA}", "n": g.n, "m": g.m},
            "cpu_baseline": {"value": round(value, 4), "unit": "GTEPS", "cores": cores, "kind": "oracle",
-                            "sample": "each step: 1 pagerank + 1 sssp (source 0 of 8) of the 1+8-solve step"},
+                            "sample": "each step: the full step (1 pagerank + 8 sssp) on the oracle's OpenMP form"},
            "e2e": {"value": round(value, 4), "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
+
+
+def run_batched(dag, torch):
+    """Batched form (RMAT scale 20, seed 4): 256 PPR columns + 64 SSSP sources, one
+    persistent launch each, against the plain single-vector sweep on the same graph."""
+    from paper_2110_01409_gb300 import autotune
+    from paper_2110_01409_gb300 import inputs as I
+
+    g = I.rmat(20, 16, 0.57, 0.19, 0.19, seed=4)
+    plan = dag.Plan.from_graph(g, "cuda")
+    sets = I.ppr_seed_sets(g.n, 256, seed=4)
+    V = torch.from_numpy(I.teleport_matrix(g.n, sets)).cuda()
+    w = torch.from_numpy(I.weights_u32(g, 4).view(np.int32)).cuda()
+    srcs = torch.from_numpy(I.sources(g, 64, seed=4).view(np.int32)).cuda()
+    tuned_ppr = autotune.tune(plan, "ppr_batched", cache=None, trials=1, V=V)
+    R, it, st = dag.ppr_batched(plan, V, 0.85, 1e-6, tuned_ppr["variant"], tuned_ppr["delta"])
+    tuned_bf = autotune.tune(plan, "sssp_batched", cache=None, trials=1, srcs=srcs, w=w)
+    D, it2, st2 = dag.sssp_batched(plan, srcs, w, tuned_bf["variant"], tuned_bf["delta"])
+    plan.set_worker_cap(0)
+    # plain single-vector solves of a few columns with the same choice, for the per-column comparison
+    one_ppr, one_bf = [], []
+    Vc = V[:, :8].t().contiguous()
+    for c in range(8):
+        _, s1 = dag.pagerank(plan, 0.85, 1e-6, "async", 0, teleport=Vc[c].contiguous())
+        one_ppr.append(s1["ms"])
+        _, s2 = dag.sssp(plan, int(srcs[c]), w, "async", 0)
+        one_bf.append(s2["ms"])
+    m = g.m
+    return {"graph": {"n": g.n, "m": m, "seed": 4},
+            "ppr": {"B": 256, "choice": {k: tuned_ppr[k] for k in ("variant", "delta", "workers")},
+                    "ms": round(st["ms"], 3), "sweeps": st["sweeps"], "column_sweeps": st["column_sweeps"],
+                    "gteps_solve_rate": round(256 * m / (st["ms"] * 1e-3) / 1e9, 2),
+                    "single_vector_ms_per_column": round(float(np.median(one_ppr)), 3),
+                    "speedup_vs_single": round(256 * float(np.median(one_ppr)) / st["ms"], 2),
+                    "converged": st["converged"]},
+            "sssp": {"B": 64, "choice": {k: tuned_bf[k] for k in ("variant", "delta", "workers")},
+                     "ms": round(st2["ms"], 3), "sweeps": st2["sweeps"], "column_sweeps": st2["column_sweeps"],
+                     "gteps_solve_rate": round(64 * m / (st2["ms"] * 1e-3) / 1e9, 2),
+                     "single_vector_ms_per_source": round(float(np.median(one_bf)), 3),
+                     "speedup_vs_single": round(64 * float(np.median(one_bf)) / st2["ms"], 2),
+                     "converged": st2["converged"]}}
+
+
+def run_adjoint(g, plan, dag, torch):
+    """Adjoint form (RMAT scale 22, FP32 weights in (0,1], 4096 targets, w_i ~ N(0,1)):
+    forward weighted PageRank and its backward pass, beside the plain sweep."""
+    from paper_2110_01409_gb300 import inputs as I
+
+    w = torch.from_numpy(I.weights_f32(g, SEED)).cuda()
+    targets, wt = I.adjoint_targets(g.n, 4096, seed=5)
+    c = torch.zeros(g.n, dtype=torch.float32, device="cuda")
+    c[torch.from_numpy(targets).cuda()] = torch.from_numpy(wt.astype(np.float32)).cuda()
+    model = dag.WeightedPageRank(plan, d=0.85, tol=1e-6, variant="delayed", delta=PR_DELTA)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    out = {}
+    for rep in range(2):
+        e0, e1, e2 = ev(), ev(), ev()
+        e0.record()
+        r, val, s, st_f = model.forward(w)
+        e1.record()
+        gw, gt, _, st_b = model.backward(val, s, r, c)
+        e2.record()
+        torch.cuda.synchronize()
+        out = {"forward_ms": round(e0.elapsed_time(e1), 3), "forward_sweeps": st_f["iters"],
+               "backward_ms": round(e1.elapsed_time(e2), 3), "adjoint_sweeps": st_b["iters"],
+               "adjoint_solve_ms": round(st_b["ms"], 3), "targets": 4096,
+               "converged": bool(st_f["converged"] and st_b["converged"])}
+    return out
 
 
 def main():
@@ -384,7 +460,8 @@ def main():
     ap.add_argument("--impl", default="dag", choices=["dag", "reference"])
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
-    ap.add_argument("--detail", action="store_true")
+    ap.add_argument("--quick", dest="extras", action="store_false",
+                    help="skip the variant table, the adjoint and the batched measurements")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

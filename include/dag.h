@@ -95,10 +95,29 @@ int dag_plan_out_degree(const dag_plan* plan, int32_t* d_outdeg, void* stream);
  */
 int dag_partition(dag_plan* plan, int32_t workers, int32_t* h_start);
 
-/* Largest number of CTAs the persistent kernel of this (variant, delta) runs with. */
+/* Number of CTAs the persistent kernel of this (variant, delta) runs with. */
 int dag_workers(dag_plan* plan, dag_variant variant, int32_t delta, int32_t* out_workers);
 
-#define DAG_PR_WARM_START 1 /* flags: start from d_rank instead of the teleport vector */
+/*
+ * Caps the CTAs (workers, Sec. III-A blocks) of later solves on this plan at
+ * max_workers (0 = as many as can be resident). Fewer workers mean longer
+ * blocks, i.e. more rows per CTA; the autotuner varies it.
+ */
+int dag_plan_set_worker_cap(dag_plan* plan, int32_t max_workers);
+
+/* Flags of dag_pagerank / dag_sssp. */
+#define DAG_PR_WARM_START 1 /* start from d_rank instead of the teleport vector (PageRank) */
+/*
+ * How a delayed sweep reads the global array (Sec. III-C's "global reads").
+ * Default: ordinary loads, which may be served from the SM's L1, with the
+ * CTA's view refreshed (an acquire fence) at each of its flushes, so delta
+ * sets both how often a worker publishes and how often it takes in others'
+ * values. DAG_READ_COHERENT: every read goes to L2, the point where all CTAs'
+ * stores meet (as fresh as the asynchronous form). DAG_READ_CACHED: ordinary
+ * loads refreshed only by the grid barrier between sweeps.
+ */
+#define DAG_READ_COHERENT 2
+#define DAG_READ_CACHED 4
 
 /*
  * PageRank (Sec. IV-A; stopping rule Sec. IV):
@@ -112,6 +131,7 @@ int dag_workers(dag_plan* plan, dag_variant variant, int32_t delta, int32_t* out
  * values, Sec. III-B; delta >= rows per CTA flushes once per sweep). d_rank
  * (device, float [n]) receives r; with DAG_PR_WARM_START it also gives r^0.
  * Without it r^0 = t. FP32 values, FP64 residual and dangling sums.
+ * flags: DAG_PR_WARM_START | one DAG_READ_* (delayed form only).
  */
 int dag_pagerank(dag_plan* plan, float d, double tol, dag_variant variant, int32_t delta,
                  int32_t max_iters, const float* d_teleport, const float* d_val, float* d_rank,
@@ -123,9 +143,10 @@ int dag_pagerank(dag_plan* plan, float d, double tol, dag_variant variant, int32
  * "unconditionally storing updates"); stops after a sweep that lowered no
  * value. d_w: uint32 weight per in-edge (device, [m]); d_dist (device,
  * uint32 [n]) receives the distances, 0xFFFFFFFF for unreachable vertices.
+ * flags: DAG_READ_* (delayed form only).
  */
 int dag_sssp(dag_plan* plan, uint32_t src, dag_variant variant, int32_t delta, int32_t max_iters,
-             const uint32_t* d_w, uint32_t* d_dist, dag_stats* h_stats, void* stream);
+             const uint32_t* d_w, uint32_t* d_dist, int32_t flags, dag_stats* h_stats, void* stream);
 
 /* Result of a batched solve (host struct). */
 typedef struct {

@@ -78,6 +78,13 @@ int finish_solve(dag_plan* plan, int nblocks, int delta, Timer& tm, cudaStream_t
     return rc;
 }
 
+int read_mode_of(int flags)
+{
+    if (flags & DAG_READ_COHERENT) return READ_COHERENT;
+    if (flags & DAG_READ_CACHED) return READ_CACHED;
+    return READ_CACHED_REFRESH;
+}
+
 int check_variant(int variant, int delta, int max_iters)
 {
     if (variant < DAG_SYNC || variant > DAG_DELAYED) return set_error(DAG_ERR_INVALID, "unknown variant");
@@ -149,6 +156,7 @@ extern "C" int dag_pagerank(dag_plan* plan, float d, double tol, dag_variant var
     p.x1 = plan->x1;
     p.init = (flags & DAG_PR_WARM_START) ? d_rank : nullptr;
     p.out = d_rank;
+    p.read_mode = read_mode_of(flags);
     Timer tm;
     tm.start(s, h_stats != nullptr);
     int nb = 0;
@@ -160,7 +168,7 @@ extern "C" int dag_pagerank(dag_plan* plan, float d, double tol, dag_variant var
 }
 
 extern "C" int dag_sssp(dag_plan* plan, uint32_t src, dag_variant variant, int32_t delta, int32_t max_iters,
-                        const uint32_t* d_w, uint32_t* d_dist, dag_stats* h_stats, void* stream)
+                        const uint32_t* d_w, uint32_t* d_dist, int32_t flags, dag_stats* h_stats, void* stream)
 {
     if (!plan || !d_dist || (plan->m > 0 && !d_w)) return set_error(DAG_ERR_INVALID, "null argument");
     if (src >= (uint32_t)plan->n) return set_error(DAG_ERR_INVALID, "source outside [0, n)");
@@ -181,6 +189,7 @@ extern "C" int dag_sssp(dag_plan* plan, uint32_t src, dag_variant variant, int32
     p.x0 = plan->x0;
     p.x1 = plan->x1;
     p.out = d_dist;
+    p.read_mode = read_mode_of(flags);
     Timer tm;
     tm.start(s, h_stats != nullptr);
     int nb = 0;

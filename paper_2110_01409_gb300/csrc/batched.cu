@@ -93,7 +93,7 @@ __global__ void batched_kernel(const BatchParams p)
 
     // ---------------- initial values ----------------
     {
-        double gpart = 0.0, tpart = 0.0;
+        float gpart = 0.0f, tpart = 0.0f;  // per-lane partials over the block; FP64 in the atomics
         uint32_t s0 = BF && colok ? p.src[col] : 0u;
         for (int v = row_lo; v < row_hi; ++v) {
             if (!colok) continue;
@@ -104,15 +104,15 @@ __global__ void batched_kernel(const BatchParams p)
                 const float t = p.V[k];
                 const float dg = p.degf[v];
                 p.X0[k] = __float_as_uint(dg > 0.0f ? t / dg : t);
-                if (dg > 0.0f) gpart += (double)t;
-                tpart += (double)t;
+                if (dg > 0.0f) gpart += t;
+                tpart += t;
             }
         }
         if (!BF && colok) {
-            if (tpart != 0.0) atomicAdd(&p.T[col], tpart);
-            if (gpart != 0.0) {
-                atomicAdd(&p.acc_g[2 * B + col], gpart);
-                if (LIVE) atomicAdd(&p.gl[col], gpart);
+            if (tpart != 0.0f) atomicAdd(&p.T[col], (double)tpart);
+            if (gpart != 0.0f) {
+                atomicAdd(&p.acc_g[2 * B + col], (double)gpart);
+                if (LIVE) atomicAdd(&p.gl[col], (double)gpart);
             }
         }
     }
@@ -129,7 +129,7 @@ __global__ void batched_kernel(const BatchParams p)
         const int slot = it % 3;
         const uint32_t* xin = SYNC ? ((it & 1) ? p.X1 : p.X0) : p.X0;
         uint32_t* xout = SYNC ? ((it & 1) ? p.X0 : p.X1) : p.X0;
-        double res = 0.0, gsum = 0.0, dg_acc = 0.0;
+        float res = 0.0f, gsum = 0.0f, dg_acc = 0.0f;  // per-lane partials; FP64 in the atomics
         uint32_t carry = b_ident<BF>();
         int buf_first = row_lo, buf_cnt = 0;
         const bool warp_active = __any_sync(0xffffffffu, active);
@@ -162,16 +162,16 @@ __global__ void batched_kernel(const BatchParams p)
                 if constexpr (BF) {
                     const uint32_t old = SYNC ? ld_weak_b32(xin + k) : ld_relaxed_b32(xin + k);
                     xnew = sum < old ? sum : old;
-                    if (xnew < old) res += 1.0;
+                    if (xnew < old) res += 1.0f;
                 } else {
                     const float xo = __uint_as_float(SYNC ? ld_weak_b32(xin + k) : ld_relaxed_b32(xin + k));
                     const float dg = p.degf[v];
                     const float rold = dg > 0.0f ? xo * dg : xo;
                     const float rnew = (1.0f - p.d) * ld_stream_f32(p.V + k) + p.d * __uint_as_float(sum) + gt;
-                    res += fabs((double)rnew - (double)rold);
+                    res += fabsf(rnew - rold);
                     if (dg > 0.0f) {
-                        gsum += (double)rnew;
-                        dg_acc += (double)rnew - (double)rold;
+                        gsum += rnew;
+                        dg_acc += rnew - rold;
                     }
                     xnew = __float_as_uint(dg > 0.0f ? rnew / dg : rnew);
                 }
@@ -186,9 +186,9 @@ __global__ void batched_kernel(const BatchParams p)
                         if (active)
                             for (int q = 0; q < buf_cnt; ++q)
                                 st_relaxed_b32(p.X0 + (size_t)(buf_first + q) * B + col, mybuf[q * 32 + lane]);
-                        if (LIVE && active && dg_acc != 0.0) {
-                            atomicAdd(&p.gl[col], dg_acc);
-                            dg_acc = 0.0;
+                        if (LIVE && active && dg_acc != 0.0f) {
+                            atomicAdd(&p.gl[col], (double)dg_acc);
+                            dg_acc = 0.0f;
                         }
                         buf_first += buf_cnt;
                         buf_cnt = 0;
@@ -235,16 +235,16 @@ __global__ void batched_kernel(const BatchParams p)
             carry = acc;
             if constexpr (DELAYED) maybe_flush(t == tile_hi - 1);
             if constexpr (VAR == DAG_ASYNC && !BF) {
-                if (active && dg_acc != 0.0) {
-                    atomicAdd(&p.gl[col], dg_acc);
-                    dg_acc = 0.0;
+                if (active && dg_acc != 0.0f) {
+                    atomicAdd(&p.gl[col], (double)dg_acc);
+                    dg_acc = 0.0f;
                 }
             }
         }
         // ---- end of sweep ----
         if (active) {
-            if (res != 0.0) atomicAdd(&p.acc_res[slot * B + col], res);
-            if (SYNC && !BF && gsum != 0.0) atomicAdd(&p.acc_g[slot * B + col], gsum);
+            if (res != 0.0f) atomicAdd(&p.acc_res[slot * B + col], (double)res);
+            if (SYNC && !BF && gsum != 0.0f) atomicAdd(&p.acc_g[slot * B + col], (double)gsum);
         }
         if (!grid_barrier(p.sb, p.nblocks, bar, p.timeout_ns)) return;
         int still = 0;
@@ -330,7 +330,8 @@ int launch_batched(dag_plan* plan, int is_bf, int variant, int delta, int max_it
     int per_sm = 0;
     DAG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k, threads, dyn));
     if (per_sm < 1) return set_error(DAG_ERR_INVALID, "batched kernel cannot be resident");
-    const int nb = per_sm * plan->num_sms;
+    int nb = per_sm * plan->num_sms;
+    if (plan->worker_cap > 0 && nb > plan->worker_cap) nb = plan->worker_cap;
     Partition* part = nullptr;
     int rc = get_partition(plan, nb, &part, s);
     if (rc) return rc;

@@ -39,6 +39,9 @@ constexpr int GSTRIDE = 4;        // doubles between stripes (32 bytes)
 
 enum Mode { MODE_PR = 0, MODE_PRW = 1, MODE_ADJ = 2, MODE_BF = 3 };
 
+// How the delayed form reads other blocks' values (see dag.h, DAG_READ_*).
+enum ReadMode { READ_CACHED_REFRESH = 0, READ_COHERENT = 1, READ_CACHED = 2 };
+
 constexpr uint32_t INF = 0xFFFFFFFFu;
 
 // Device-side control block of one solve (lives in the plan's workspace,
@@ -76,6 +79,7 @@ struct SweepParams {
     int max_iters;
     int delta;              // delayed buffer size (rows); 0 for sync/async
     int buf_cap;            // delay buffer capacity (elements of dynamic shared memory)
+    int buf_clamped;        // 1: capacity below delta - 1 + TILE (shared memory limit): flush when full
     uint32_t src;           // BF source
     // state (two buffers for sync)
     void* x0;
@@ -89,6 +93,7 @@ struct SweepParams {
     SyncBlock* sync;
     long long timeout_ns;
     int skip_barrier_cta0;  // test hook
+    int read_mode;          // ReadMode (delayed form)
     // init / output
     const float* init;      // warm start (PR) or nullptr
     void* out;              // float r / lambda, or uint32 dist
@@ -118,6 +123,7 @@ struct dag_plan {
     long long timeout_ns = 2000000000LL;
     int skip_barrier_once = 0;
     long long skip_timeout_ns = 0;
+    int worker_cap = 0;       // > 0: at most this many CTAs per solve (more rows per CTA)
     // per-vertex data
     int* outdeg = nullptr;    // [n]
     float* degf = nullptr;    // [n]

@@ -18,6 +18,7 @@
 // contents, so each call clears what must start at zero; two calls whose work
 // overlaps on the GPU (for example on two streams) race on it. The paper has
 // no counterpart of this entry point: it is an interface convenience.
+#include <algorithm>
 #include <mutex>
 
 #include "dag_internal.cuh"
@@ -131,6 +132,15 @@ extern "C" int dag_pagerank_noalloc(const dag_csr* csr, float d, double tol, dag
     if (nb > NA_MAX_CTAS) nb = NA_MAX_CTAS;
     int host_flags[4] = {0, 0, 0, 0};
     int cap = 0;
+    bool clamped = false;
+    long long max_cap = 0;
+    {
+        int max_dyn = 0;
+        cudaFuncAttributes fa;
+        DAG_CUDA(cudaDeviceGetAttribute(&max_dyn, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+        DAG_CUDA(cudaFuncGetAttributes(&fa, sweep_kernel_ptr(MODE_PR, var)));
+        max_cap = ((long long)max_dyn - (long long)fa.sharedSizeBytes) / 4;
+    }
     for (int iter = 0; iter < 6; ++iter) {
         k_cta_rows<<<(nb + 1 + 255) / 256, 256, 0, s>>>(rowptr, n, (long long)n + m, nb, cta_row);
         k_cta_tiles<<<1, 1, 0, s>>>(rowptr, cta_row, nb, cta_tile, flags + 2);
@@ -141,6 +151,8 @@ extern "C" int dag_pagerank_noalloc(const dag_csr* csr, float d, double tol, dag
         if (var != DAG_DELAYED) break;
         long long need = (long long)delta - 1 + TILE;
         if (need > host_flags[2]) need = host_flags[2];
+        if (need > max_cap) need = max_cap;
+        clamped = need < std::min((long long)delta - 1 + TILE, (long long)host_flags[2]);
         cap = (int)(need < 1 ? 1 : need);
         int nb2 = 0;
         rc = max_workers(&shape, MODE_PR, var, cap, &nb2);
@@ -169,6 +181,7 @@ extern "C" int dag_pagerank_noalloc(const dag_csr* csr, float d, double tol, dag
     p.max_iters = max_iters;
     p.delta = (var == DAG_DELAYED) ? delta : 0;
     p.buf_cap = cap;
+    p.buf_clamped = clamped ? 1 : 0;
     p.x0 = base + OFF_X0;
     p.x1 = base + OFF_X1;
     p.cta_row = cta_row;

@@ -353,6 +353,13 @@ extern "C" int dag_normalize_weights(dag_plan* p, const float* d_w, float* d_val
     return launch_normalize(p, d_w, d_val, d_s, (cudaStream_t)stream);
 }
 
+extern "C" int dag_plan_set_worker_cap(dag_plan* p, int32_t max_workers)
+{
+    if (!p || max_workers < 0) return set_error(DAG_ERR_INVALID, "bad argument");
+    p->worker_cap = max_workers;
+    return DAG_OK;
+}
+
 extern "C" int dag_gather_f32(const float* d_src, const int32_t* d_idx, int64_t m, float* d_out, void* stream)
 {
     if (m < 0 || (m > 0 && (!d_src || !d_idx || !d_out))) return set_error(DAG_ERR_INVALID, "bad argument");

@@ -32,6 +32,7 @@
 // of a row begun by earlier threads from a block segmented prefix over the
 // warps' run totals and finishes the rows it ends. A delayed flush is copied
 // out between (A) and (B) of the following tile, so it costs no barrier.
+#include <algorithm>
 #include <climits>
 #include <type_traits>
 
@@ -78,7 +79,7 @@ struct SweepShared {
     uint32_t wval[NWARP];      // warp-local inclusive run total at the last lane
     double red0[NWARP];
     double red1[NWARP];
-    double G;                  // live global sum read during the tile's staging
+    float gt;                  // the tile's global (dangling) term from the live sum
     double res;                // broadcast of the sweep residual
     double gprev;              // broadcast of the previous sweep's global sum
     double T;                  // broadcast of the teleport total / ||c||_1
@@ -116,8 +117,9 @@ struct Stage {
 };
 
 // Issues the coalesced loads of tile t (everything except the gathers).
-template <int MODE, bool WEAK>
-__device__ __forceinline__ void stage_issue(Stage<MODE>& st, const SweepParams& p, const uint32_t* xin, int t, int tid)
+template <int MODE>
+__device__ __forceinline__ void stage_issue(Stage<MODE>& st, const SweepParams& p, const uint32_t* xin, int t, int tid,
+                                            bool weak)
 {
     constexpr bool BF = MODE == MODE_BF;
     st.a0 = p.tile_row[t];
@@ -147,7 +149,7 @@ __device__ __forceinline__ void stage_issue(Stage<MODE>& st, const SweepParams& 
         st.pfx[k] = 0u;
         st.pfd[k] = 0.0f;
         if (r < st.NA) {
-            st.pfx[k] = WEAK ? ld_weak_b32(xin + st.a0 + r) : ld_relaxed_b32(xin + st.a0 + r);
+            st.pfx[k] = weak ? ld_weak_b32(xin + st.a0 + r) : ld_relaxed_b32(xin + st.a0 + r);
             if constexpr (!BF) st.pfd[k] = ld_stream_f32(p.degf + st.a0 + r);
         }
     }
@@ -155,15 +157,15 @@ __device__ __forceinline__ void stage_issue(Stage<MODE>& st, const SweepParams& 
 
 // Issues tile t's gathers of the state vector (sync: previous iterate; delayed:
 // this SM's view of the live array; async: the live array in L2).
-template <int MODE, bool WEAK>
-__device__ __forceinline__ void stage_gather(Stage<MODE>& st, const uint32_t* xin, int tid)
+template <int MODE>
+__device__ __forceinline__ void stage_gather(Stage<MODE>& st, const uint32_t* xin, int tid, bool weak)
 {
 #pragma unroll
     for (int q = 0; q < IPT; ++q) {
         const int j = tid + q * NT;
         uint32_t term = 0u;
         if (j < st.NB) {
-            const uint32_t xv = WEAK ? ld_weak_b32(xin + st.col[q]) : ld_relaxed_b32(xin + st.col[q]);
+            const uint32_t xv = weak ? ld_weak_b32(xin + st.col[q]) : ld_relaxed_b32(xin + st.col[q]);
             if constexpr (MODE == MODE_BF) term = relax(xv, st.aux[q]);
             else if constexpr (MODE == MODE_PR) term = xv;
             else term = __float_as_uint(__uint_as_float(st.aux[q]) * __uint_as_float(xv));
@@ -241,6 +243,9 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
     double gprev = BF ? 0.0 : sh.gprev;
     const double tol = (MODE == MODE_ADJ) ? p.tol * T : p.tol;
 
+    // sync reads the previous iterate with ordinary loads; async reads the live
+    // array coherently (L2); delayed follows p.read_mode
+    const bool weak = SYNC || (DELAYED && p.read_mode != READ_COHERENT);
     int buf_first = row_lo, buf_cnt = 0;
     long long flushes = 0;
     int it = 0;
@@ -266,8 +271,8 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
         // and its gathers too (issued before barrier C of t).
         Stage<MODE> nx;
         if (tile_lo < tile_hi) {
-            stage_issue<MODE, SYNC || DELAYED>(nx, p, xin, tile_lo, tid);
-            stage_gather<MODE, SYNC || DELAYED>(nx, xin, tid);
+            stage_issue<MODE>(nx, p, xin, tile_lo, tid, weak);
+            stage_gather<MODE>(nx, xin, tid, weak);
             if constexpr (LIVE_G) {
                 if (warp == 0) nx.gs = ld_relaxed_f64(&sb->stripe[lane * GSTRIDE]);
             }
@@ -293,8 +298,11 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
                 for (int k = 0; k < RP; ++k) { pf_x[k] = nx.pfx[k]; pf_d[k] = nx.pfd[k]; }
                 if constexpr (LIVE_G) {
                     if (warp == 0) {
-                        const double gs = warp_sum(nx.gs);
-                        if (lane == 0) sh.G = gs;
+                        // the tile's global term, formed once (FP64 is scarce on this part)
+                        const double G = warp_sum(nx.gs);
+                        if (lane == 0)
+                            sh.gt = (MODE == MODE_ADJ) ? (float)((double)p.g_coef * G)
+                                                       : (float)((double)p.g_coef * (T - G));
                     }
                 }
             }
@@ -316,7 +324,7 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
                     }
                     if (tid == 0) {
                         // refresh this SM's view: later ordinary loads see what other CTAs published
-                        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+                        if (p.read_mode == READ_CACHED_REFRESH) asm volatile("fence.acq_rel.gpu;" ::: "memory");
                         ++flushes;
                     }
                     buf_first += buf_cnt;  // every thread keeps the same copy of the buffer state
@@ -326,11 +334,10 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
             }
             if (!real) break;
             const bool more = t + 1 < tile_hi;
-            if (more) stage_issue<MODE, SYNC || DELAYED>(nx, p, xin, t + 1, tid);
+            if (more) stage_issue<MODE>(nx, p, xin, t + 1, tid, weak);
             float gt = gterm;
             if constexpr (LIVE_G) {
-                const double G = sh.G;
-                gt = (MODE == MODE_ADJ) ? (float)((double)p.g_coef * G) : (float)((double)p.g_coef * (T - G));
+                gt = sh.gt;
                 if (warp == 0 && more) nx.gs = ld_relaxed_f64(&sb->stripe[lane * GSTRIDE]);
             }
 
@@ -402,7 +409,7 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
             if (tid > 0 && emitted) sh.rowsum[i_start] = O::combine(sh.rowsum[i_start], cin);
             const uint32_t E_last = __shfl_sync(0xffffffffu, E, NWARP - 1);  // whole warp takes part
             if (tid == 0) carry = E_last;  // partial of row NA for the next tile
-            if (more) stage_gather<MODE, SYNC || DELAYED>(nx, xin, tid);
+            if (more) stage_gather<MODE>(nx, xin, tid, weak);
             __syncthreads();  // (C) row sums final
 
             // -------- epilogue: new values of the rows this tile completed --------
@@ -418,7 +425,7 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
                     xo_bits = pf_x[k < RP ? k : 0];
                     dg = pf_d[k < RP ? k : 0];
                 } else {
-                    xo_bits = SYNC || DELAYED ? ld_weak_b32(xin + v) : ld_relaxed_b32(xin + v);
+                    xo_bits = weak ? ld_weak_b32(xin + v) : ld_relaxed_b32(xin + v);
                     if constexpr (!BF) dg = ld_stream_f32(p.degf + v);
                 }
                 uint32_t xnew;
@@ -457,7 +464,9 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
             }
             if constexpr (DELAYED) {
                 buf_cnt += NA;
-                if (buf_cnt >= p.delta || t == tile_hi - 1) flush_pending = true;
+                // flush at delta, at the block end, or (buffer clamped to what fits) when the next tile might not fit
+                if (buf_cnt >= p.delta || t == tile_hi - 1 || (p.buf_clamped && buf_cnt > p.buf_cap - TILE))
+                    flush_pending = true;
             }
         }  // tiles
 
@@ -561,14 +570,24 @@ int sweep_shape(dag_plan* plan, int mode, int variant, int delta, int* nb_out, i
     int nb = 0;
     int rc = max_workers(plan, mode, variant, 0, &nb);
     if (rc) return rc;
+    if (plan->worker_cap > 0 && nb > plan->worker_cap) nb = plan->worker_cap;
     int cap = 0;
     Partition* part = nullptr;
+    long long max_cap = 0;  // largest buffer (values) one CTA can hold beside its static shared memory
+    {
+        int max_dyn = 0;
+        cudaFuncAttributes fa;
+        DAG_CUDA(cudaDeviceGetAttribute(&max_dyn, cudaDevAttrMaxSharedMemoryPerBlockOptin, plan->device));
+        DAG_CUDA(cudaFuncGetAttributes(&fa, sweep_kernel_ptr(mode, variant)));
+        max_cap = ((long long)max_dyn - (long long)fa.sharedSizeBytes) / 4;
+    }
     for (int iter = 0; iter < 6; ++iter) {
         rc = get_partition(plan, nb, &part, s);
         if (rc) return rc;
         if (variant != DAG_DELAYED) break;
         long long need = (long long)delta - 1 + TILE;
         if (need > part->max_rows) need = part->max_rows;
+        if (need > max_cap) need = max_cap;  // a larger buffer does not fit: it flushes when full
         cap = (int)(need < 1 ? 1 : need);
         int nb2 = 0;
         rc = max_workers(plan, mode, variant, cap, &nb2);
@@ -592,6 +611,8 @@ int launch_sweep(dag_plan* plan, int mode, int variant, int delta, SweepParams& 
     p.nblocks = nb;
     p.delta = (variant == DAG_DELAYED) ? delta : 0;
     p.buf_cap = cap;
+    p.buf_clamped = (variant == DAG_DELAYED && (long long)cap < std::min((long long)delta - 1 + TILE,
+                                                                          (long long)part->max_rows)) ? 1 : 0;
     p.cta_row = part->cta_row;
     p.cta_tile = part->cta_tile;
     p.tile_row = part->tile_row;

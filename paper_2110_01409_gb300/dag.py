@@ -21,12 +21,13 @@ OK, ERR_INVALID, ERR_NOT_CONVERGED, ERR_BARRIER_TIMEOUT, ERR_CUDA, ERR_NOMEM = 0
 SYNC, ASYNC, DELAYED = 0, 1, 2
 VARIANTS = {"sync": SYNC, "async": ASYNC, "delayed": DELAYED}
 WARM_START = 1
+READ_MODES = {"refresh": 0, "coherent": 2, "cached": 4}  # delayed form's reads (DAG_READ_*)
 
 EXPORTS = (
     "dag_plan_create", "dag_plan_destroy", "dag_plan_out_degree", "dag_partition", "dag_workers",
     "dag_pagerank", "dag_sssp", "dag_ppr_batched", "dag_sssp_batched", "dag_transpose",
     "dag_normalize_weights", "dag_pagerank_adjoint", "dag_strerror", "dag_last_error_message",
-    "dag_debug_skip_barrier_once", "dag_pagerank_noalloc", "dag_gather_f32",
+    "dag_debug_skip_barrier_once", "dag_pagerank_noalloc", "dag_gather_f32", "dag_plan_set_worker_cap",
 )
 
 
@@ -72,7 +73,8 @@ def lib():
             L.dag_workers.argtypes = [_vp, _i32, _i32, ctypes.POINTER(_i32)]
             L.dag_pagerank.argtypes = [_vp, _f32, _f64, _i32, _i32, _i32, _vp, _vp, _vp, _i32,
                                        ctypes.POINTER(_Stats), _vp]
-            L.dag_sssp.argtypes = [_vp, ctypes.c_uint32, _i32, _i32, _i32, _vp, _vp, ctypes.POINTER(_Stats), _vp]
+            L.dag_sssp.argtypes = [_vp, ctypes.c_uint32, _i32, _i32, _i32, _vp, _vp, _i32, ctypes.POINTER(_Stats),
+                                   _vp]
             L.dag_ppr_batched.argtypes = [_vp, _f32, _f64, _i32, _i32, _i32, _i32, _vp, _vp, _vp,
                                           ctypes.POINTER(_BStats), _vp]
             L.dag_sssp_batched.argtypes = [_vp, _i32, _i32, _i32, _i32, _vp, _vp, _vp, _vp,
@@ -87,6 +89,7 @@ def lib():
             L.dag_last_error_message.restype = ctypes.c_char_p
             L.dag_debug_skip_barrier_once.argtypes = [_vp, _i32]
             L.dag_gather_f32.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp]
+            L.dag_plan_set_worker_cap.argtypes = [_vp, _i32]
             L.dag_pagerank_noalloc.argtypes = [ctypes.POINTER(_Csr), _f32, _f64, _i32, _i32, _i32, _vp, _vp,
                                                ctypes.POINTER(_Stats), _vp]
             for f in EXPORTS:
@@ -177,12 +180,16 @@ class Plan:
         _raise(lib().dag_workers(self.h, _variant(variant), delta, ctypes.byref(w)), False)
         return w.value
 
+    def set_worker_cap(self, max_workers: int):
+        """At most max_workers CTAs per solve (0: as many as fit)."""
+        _raise(lib().dag_plan_set_worker_cap(self.h, max_workers), False)
+
     def debug_skip_barrier_once(self, timeout_ms: int):
         _raise(lib().dag_debug_skip_barrier_once(self.h, timeout_ms), False)
 
 
 def pagerank(plan: Plan, d=0.85, tol=1e-6, variant="delayed", delta=256, max_iters=1000, teleport=None,
-             val=None, out=None, warm_start=False, stream=None, stats=True):
+             val=None, out=None, warm_start=False, stream=None, stats=True, reads="refresh"):
     """PageRank through dag_pagerank. Returns (rank float32 tensor, stats dict or None)."""
     dev = plan.rowptr.device
     out = out if out is not None else torch.empty(plan.n, dtype=torch.float32, device=dev)
@@ -191,14 +198,15 @@ def pagerank(plan: Plan, d=0.85, tol=1e-6, variant="delayed", delta=256, max_ite
     _dev(val, torch.float32, plan.m, "val")
     st = _Stats()
     rc = lib().dag_pagerank(plan.h, d, tol, _variant(variant), delta, max_iters, _ptr(teleport), _ptr(val),
-                            _ptr(out), WARM_START if warm_start else 0, ctypes.byref(st) if stats else None,
+                            _ptr(out), (WARM_START if warm_start else 0) | READ_MODES[reads],
+                            ctypes.byref(st) if stats else None,
                             _stream(stream))
     _raise(rc)
     return out, (_stats(st, plan.m) if stats else None)
 
 
 def sssp(plan: Plan, src: int, w, variant="delayed", delta=32, max_iters=None, out=None, stream=None,
-         stats=True):
+         stats=True, reads="refresh"):
     """Bellman-Ford through dag_sssp. Returns (dist int64-view-free uint32 as int32 tensor, stats)."""
     dev = plan.rowptr.device
     out = out if out is not None else torch.empty(plan.n, dtype=torch.int32, device=dev)
@@ -208,7 +216,7 @@ def sssp(plan: Plan, src: int, w, variant="delayed", delta=32, max_iters=None, o
     max_iters = plan.n + 1 if max_iters is None else max_iters
     st = _Stats()
     rc = lib().dag_sssp(plan.h, src, _variant(variant), delta, max_iters, _ptr(w) if plan.m else None, _ptr(out),
-                        ctypes.byref(st) if stats else None, _stream(stream))
+                        READ_MODES[reads], ctypes.byref(st) if stats else None, _stream(stream))
     _raise(rc)
     return out, (_stats(st, plan.m) if stats else None)
 
