@@ -1,9 +1,11 @@
 """Benchmark: delayed-asynchronous PageRank + Bellman-Ford on RMAT scale 22.
 
-One step = one PageRank solve (d = 0.85, tol 1e-6, delayed) plus eight
-Bellman-Ford solves (fixed sources, uint32 weights in [1, 255], delayed) on the
-RMAT scale-22 graph (a=.57 b=.19 c=.19, edge factor 16, seed 2), all in the
-persistent CUDA kernels behind the C ABI. The metric is GTEPS counted per
+One step = one PageRank solve (d = 0.85, tol 1e-6) plus eight Bellman-Ford
+solves (fixed sources, uint32 weights in [1, 255]) on the RMAT scale-22 graph
+(a=.57 b=.19 c=.19, edge factor 16, seed 2), all in the persistent CUDA
+kernels behind the C ABI, each with the delayed method's buffer size delta
+picked by the autotuner among {0, 32, 256, 4096} (delta = 0 is the
+asynchronous end of the method, Sec. III-B). The metric is GTEPS counted per
 finished solve: (solves * m) / time. With inputs resident in HBM the timed
 region holds K steps between CUDA events; `e2e` repeats the step through the
 public API from pinned host buffers (graph upload, plan, solves, result
@@ -32,7 +34,10 @@ sys.path.insert(0, ROOT)
 METRIC = "PageRank/SSSP time-to-converge & GTEPS at tol 1e-6; batched & adjoint vs plain"
 SCALE, EF, SEED = 22, 16, 2
 N_SOURCES = 8
-PR_DELTA, SSSP_DELTA = 32, 32
+PR_DELTA, SSSP_DELTA = 32, 32  # fixed-delta runs of the variant table and the CPU oracle
+DELTAS = (0, 32, 256, 4096)
+WORKLOAD = (f"rmat{SCALE}: pagerank d=0.85 tol=1e-6 + sssp x{N_SOURCES} sources, "
+            f"delayed method, delta picked per algorithm over {list(DELTAS)}")
 
 
 def _peaks():
@@ -118,9 +123,9 @@ def algorithmic_bytes(n, m, kind):
     """Compulsory bytes of one sweep (gathers of the state vector count as L2
     hits: the 4n-byte vector fits in L2): rowptr 4(n+1), colidx 4m, own old
     value 4n + new value 4n, plus per-vertex out-degree 4n (PageRank) or the
-    per-edge weight 4m (Bellman-Ford)."""
+    per-edge weight (Bellman-Ford: 4m as uint32, m as uint8)."""
     base = 4 * (n + 1) + 4 * m + 8 * n
-    return base + (4 * n if kind == "pr" else 4 * m)
+    return base + {"pr": 4 * n, "bf": 4 * m, "bf8": m}[kind]
 
 
 def run_gpu(args):
@@ -145,20 +150,31 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     rowptr = torch.from_numpy(g.rowptr).to(dev)
     colidx = torch.from_numpy(g.colidx).to(dev)
-    w_d = torch.from_numpy(w.view(np.int32)).to(dev)
+    w_d = torch.from_numpy(w.view(np.int32)).to(dev)      # uint32 weights (variant table, reference runs)
+    w8_d = torch.from_numpy(w.astype(np.uint8)).to(dev)   # the same weights, one byte each (w <= 255)
     plan = dag.Plan(rowptr, colidx)
     rank_out = torch.empty(n, dtype=torch.float32, device=dev)
     dist_out = [torch.empty(n, dtype=torch.int32, device=dev) for _ in range(N_SOURCES)]
 
+    # ---- delta per algorithm: the autotuner over the delayed method's delta (0 = async end) ----
+    from paper_2110_01409_gb300 import autotune
+
+    cands = [("delayed", dl) for dl in DELTAS]
+    tune_pr = autotune.tune(plan, "pagerank", candidates=cands, worker_fractions=[1.0], trials=2, cache=None)
+    tune_bf = autotune.tune(plan, "sssp", candidates=cands, worker_fractions=[1.0], trials=2, cache=None,
+                            src=int(srcs[0]), w=w8_d)
+    plan.set_worker_cap(0)
+    pr_dl, bf_dl = tune_pr["delta"], tune_bf["delta"]
+
     # ---- warm-up with statuses (also records per-solve sweeps) ----
     pr_iters, bf_iters = [], []
     for _ in range(args.warmup):
-        _, st = dag.pagerank(plan, 0.85, 1e-6, "delayed", PR_DELTA, 1000, out=rank_out)
+        _, st = dag.pagerank(plan, 0.85, 1e-6, "delayed", pr_dl, 1000, out=rank_out)
         assert st["converged"], st
         pr_iters.append(st["iters"])
         its = []
         for k, s in enumerate(srcs):
-            _, st = dag.sssp(plan, int(s), w_d, "delayed", SSSP_DELTA, n + 1, out=dist_out[k])
+            _, st = dag.sssp(plan, int(s), w8_d, "delayed", bf_dl, n + 1, out=dist_out[k])
             assert st["converged"], st
             its.append(st["iters"])
         bf_iters.append(its)
@@ -178,11 +194,11 @@ def run_gpu(args):
     t_start.record(stream)
     for k in range(K):
         pr_ev[k][0].record(stream)
-        dag.pagerank(plan, 0.85, 1e-6, "delayed", PR_DELTA, 1000, out=rank_out, stats=False)
+        dag.pagerank(plan, 0.85, 1e-6, "delayed", pr_dl, 1000, out=rank_out, stats=False)
         pr_ev[k][1].record(stream)
         for j, s in enumerate(srcs):
             bf_ev[k][j][0].record(stream)
-            dag.sssp(plan, int(s), w_d, "delayed", SSSP_DELTA, n + 1, out=dist_out[j], stats=False)
+            dag.sssp(plan, int(s), w8_d, "delayed", bf_dl, n + 1, out=dist_out[j], stats=False)
             bf_ev[k][j][1].record(stream)
     t_end.record(stream)
     torch.cuda.synchronize()
@@ -198,25 +214,26 @@ def run_gpu(args):
     value = world * solves * m * K / (ms_total * 1e-3) / 1e9
 
     # statuses of the timed solves: one more checked step (results must match the warm-up)
-    _, st_pr = dag.pagerank(plan, 0.85, 1e-6, "delayed", PR_DELTA, 1000, out=rank_out)
+    _, st_pr = dag.pagerank(plan, 0.85, 1e-6, "delayed", pr_dl, 1000, out=rank_out)
     assert st_pr["converged"]
     pr_ms = statistics.mean(a.elapsed_time(b) for a, b in pr_ev)
     bf_ms = statistics.mean(a.elapsed_time(b) for row in bf_ev for a, b in row)
     pr_sweeps = statistics.mean(pr_iters + [st_pr["iters"]])
     bf_sweeps = statistics.mean(x for row in bf_iters for x in row)
     pr_bytes = algorithmic_bytes(n, m, "pr") * pr_sweeps
-    bf_bytes = algorithmic_bytes(n, m, "bf") * bf_sweeps
+    bf_bytes = algorithmic_bytes(n, m, "bf8") * bf_sweeps
     peak, peak_kind = _peaks()
     # dominant kernel by total time in the step
+    vname = lambda dl: "DELAYED" if dl > 0 else "ASYNC"  # noqa: E731  (delta 0 runs the async kernel)
     if bf_ms * N_SOURCES >= pr_ms:
-        dom, dom_bytes, dom_ms, dom_sweeps = "sweep_kernel<BF,DELAYED>", bf_bytes, bf_ms, bf_sweeps
+        dom, dom_bytes, dom_ms, dom_sweeps = f"sweep_kernel<BF8,{vname(bf_dl)}>", bf_bytes, bf_ms, bf_sweeps
     else:
-        dom, dom_bytes, dom_ms, dom_sweeps = "sweep_kernel<PR,DELAYED>", pr_bytes, pr_ms, pr_sweeps
+        dom, dom_bytes, dom_ms, dom_sweeps = f"sweep_kernel<PR,{vname(pr_dl)}>", pr_bytes, pr_ms, pr_sweeps
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
     traffic = _recorded_traffic(dom, dom_sweeps)
 
     # ---- e2e through the public API from pinned host buffers ----
-    e2e = run_e2e(args, g, w, srcs, dev, dag, torch) if args.e2e else None
+    e2e = run_e2e(args, g, w, srcs, dev, dag, torch, pr_dl, bf_dl) if args.e2e else None
 
     detail = {}
     if args.extras and rank == 0:
@@ -237,8 +254,12 @@ def run_gpu(args):
         "vs_baseline": None,
         "dtype": "f32/u32",
         "data": "synthetic (seeded RMAT stand-in for the GAP Kron graph)",
-        "config": {"workload": f"rmat{SCALE}: pagerank d=0.85 tol=1e-6 delayed delta={PR_DELTA} + "
-                               f"sssp x{N_SOURCES} sources delayed delta={SSSP_DELTA}",
+        "config": {"workload": WORKLOAD, "weights": "uint8 per edge (values in [1, 255])",
+                   "delta": {"pagerank": pr_dl, "sssp": bf_dl},
+                   "autotune_ms": {"pagerank": {str(c["delta"]): round(c["ms"], 3) for c in tune_pr["candidates"]
+                                                if "ms" in c},
+                                   "sssp": {str(c["delta"]): round(c["ms"], 3) for c in tune_bf["candidates"]
+                                            if "ms" in c}},
                    "n": n, "m": m, "sources": [int(s) for s in srcs], "workers": st_pr["workers"],
                    "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (CSR+weights ~0.55 GB)",
                    "graph_gen_s": round(gen_s, 2)},
@@ -278,14 +299,14 @@ def _recorded_traffic(kernel, sweeps):
         return None
 
 
-def run_e2e(args, g, w, srcs, dev, dag, torch):
+def run_e2e(args, g, w, srcs, dev, dag, torch, pr_dl, bf_dl):
     """Same step through the public API from pinned host memory, copies inside the timed region."""
     rp_h = torch.from_numpy(g.rowptr).pin_memory()
     ci_h = torch.from_numpy(g.colidx).pin_memory()
-    w_h = torch.from_numpy(w.view(np.int32)).pin_memory()
+    w_h = torch.from_numpy(w.astype(np.uint8)).pin_memory()
     res_pr = torch.empty(g.n, dtype=torch.float32).pin_memory()
     res_bf = torch.empty((N_SOURCES, g.n), dtype=torch.int32).pin_memory()
-    h2d = rp_h.numel() * 4 + ci_h.numel() * 4 + w_h.numel() * 4
+    h2d = rp_h.numel() * 4 + ci_h.numel() * 4 + w_h.numel() * 1
     d2h = res_pr.numel() * 4 + res_bf.numel() * 4
     K = max(1, min(args.steps, 3))
 
@@ -294,10 +315,10 @@ def run_e2e(args, g, w, srcs, dev, dag, torch):
         ci = ci_h.to(dev, non_blocking=True)
         wd = w_h.to(dev, non_blocking=True)
         plan = dag.Plan(rp, ci)
-        r, _ = dag.pagerank(plan, 0.85, 1e-6, "delayed", PR_DELTA, 1000, stats=False)
+        r, _ = dag.pagerank(plan, 0.85, 1e-6, "delayed", pr_dl, 1000, stats=False)
         res_pr.copy_(r, non_blocking=True)
         for j, s in enumerate(srcs):
-            d, _ = dag.sssp(plan, int(s), wd, "delayed", SSSP_DELTA, g.n + 1, stats=False)
+            d, _ = dag.sssp(plan, int(s), wd, "delayed", bf_dl, g.n + 1, stats=False)
             res_bf[j].copy_(d, non_blocking=True)
         torch.cuda.synchronize()
         plan.close()
@@ -331,15 +352,25 @@ def run_detail(g, w, srcs, plan, w_d, dag, torch, args):
     return res
 
 
-def cpu_step(g, w, srcs, cores):
-    """One step on the CPU oracle's OpenMP form (the paper's thread scheme):
-    1 delayed PageRank + the 8 delayed Bellman-Ford solves. Returns seconds and sweeps."""
+def cpu_tune(g, w, src, cores):
+    """Best delta per algorithm for the CPU oracle's OpenMP form (one trial each)."""
     import oracle
 
-    _, it_pr, s_pr, ok = oracle.pagerank_threads(g, oracle.DELAYED, tol=1e-6, threads=cores, delta=PR_DELTA)
+    best_pr = min(DELTAS, key=lambda dl: oracle.pagerank_threads(g, oracle.DELAYED, tol=1e-6, threads=cores,
+                                                                 delta=dl)[2])
+    best_bf = min(DELTAS, key=lambda dl: oracle.sssp_threads(g, w, src, oracle.DELAYED, threads=cores, delta=dl)[2])
+    return best_pr, best_bf
+
+
+def cpu_step(g, w, srcs, cores, pr_dl, bf_dl):
+    """One step on the CPU oracle's OpenMP form (the paper's thread scheme):
+    1 PageRank + the 8 Bellman-Ford solves. Returns seconds, sweeps, converged."""
+    import oracle
+
+    _, it_pr, s_pr, ok = oracle.pagerank_threads(g, oracle.DELAYED, tol=1e-6, threads=cores, delta=pr_dl)
     secs, sweeps = s_pr, [it_pr]
     for s in srcs:
-        _, it, sec, ok2 = oracle.sssp_threads(g, w, int(s), oracle.DELAYED, threads=cores, delta=SSSP_DELTA)
+        _, it, sec, ok2 = oracle.sssp_threads(g, w, int(s), oracle.DELAYED, threads=cores, delta=bf_dl)
         secs += sec
         sweeps.append(it)
         ok = ok and ok2
@@ -349,10 +380,11 @@ def cpu_step(g, w, srcs, cores):
 def cpu_baseline(g, w, srcs):
     """The oracle's OpenMP form on all host cores, on the whole step (bounded: a few seconds)."""
     cores = os.cpu_count() or 1
-    secs, sweeps, ok = cpu_step(g, w, srcs, cores)
+    pr_dl, bf_dl = cpu_tune(g, w, int(srcs[0]), cores)
+    secs, sweeps, ok = cpu_step(g, w, srcs, cores, pr_dl, bf_dl)
     return {"value": round((1 + N_SOURCES) * g.m / secs / 1e9, 4), "unit": "GTEPS", "cores": cores, "kind": "oracle",
-            "sample": f"one full step (1 pagerank + {N_SOURCES} sssp, delta {PR_DELTA}/{SSSP_DELTA}, sweeps {sweeps}) "
-                      f"in {secs:.2f} s", "converged": bool(ok)}
+            "sample": f"one full step (1 pagerank + {N_SOURCES} sssp, delta {pr_dl}/{bf_dl} picked over "
+                      f"{list(DELTAS)}, sweeps {sweeps}) in {secs:.2f} s", "converged": bool(ok)}
 
 
 def run_reference(args):
@@ -365,19 +397,19 @@ def run_reference(args):
     oracle.build()
     g, w, srcs, _ = build_inputs()
     cores = os.cpu_count() or 1
+    pr_dl, bf_dl = cpu_tune(g, w, int(srcs[0]), cores)
     for _ in range(args.warmup):
-        cpu_step(g, w, srcs, cores)
+        cpu_step(g, w, srcs, cores, pr_dl, bf_dl)
     t = 0.0
     for _ in range(args.steps):
-        secs, _, _ = cpu_step(g, w, srcs, cores)
+        secs, _, _ = cpu_step(g, w, srcs, cores, pr_dl, bf_dl)
         t += secs
     value = (1 + N_SOURCES) * g.m * args.steps / t / 1e9
     out = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GTEPS", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t / args.steps * 1e3, 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/u32",
            "data": "synthetic (seeded RMAT stand-in for the GAP Kron graph)",
-           "config": {"workload": f"rmat{SCALE}: pagerank d=0.85 tol=1e-6 delayed delta={PR_DELTA} + "
-                                  f"sssp x{N_SOURCES} sources delayed delta={SSSP_DELTA}", "n": g.n, "m": g.m},
+           "config": {"workload": WORKLOAD, "delta": {"pagerank": pr_dl, "sssp": bf_dl}, "n": g.n, "m": g.m},
            "cpu_baseline": {"value": round(value, 4), "unit": "GTEPS", "cores": cores, "kind": "oracle",
                             "sample": "each step: the full step (1 pagerank + 8 sssp) on the oracle's OpenMP form"},
            "e2e": {"value": round(value, 4), "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

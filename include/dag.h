@@ -148,6 +148,15 @@ int dag_pagerank(dag_plan* plan, float d, double tol, dag_variant variant, int32
 int dag_sssp(dag_plan* plan, uint32_t src, dag_variant variant, int32_t delta, int32_t max_iters,
              const uint32_t* d_w, uint32_t* d_dist, int32_t flags, dag_stats* h_stats, void* stream);
 
+/*
+ * dag_sssp with one-byte weights (d_w8: uint8 per in-edge, device, [m]) for
+ * graphs whose weights lie in [0, 255], such as those of Sec. IV's runs
+ * here (w in [1, 255]): the weight stream of each sweep shrinks from 4m to m
+ * bytes. Same results and errors as dag_sssp with the same weights.
+ */
+int dag_sssp_u8(dag_plan* plan, uint32_t src, dag_variant variant, int32_t delta, int32_t max_iters,
+                const uint8_t* d_w8, uint32_t* d_dist, int32_t flags, dag_stats* h_stats, void* stream);
+
 /* Result of a batched solve (host struct). */
 typedef struct {
     int32_t sweeps;          /* sweeps the launch ran (the slowest column's) */

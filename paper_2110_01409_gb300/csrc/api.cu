@@ -167,37 +167,56 @@ extern "C" int dag_pagerank(dag_plan* plan, float d, double tol, dag_variant var
     return finish_solve(plan, nb, var == DAG_DELAYED ? delta : 0, tm, s, h_stats);
 }
 
-extern "C" int dag_sssp(dag_plan* plan, uint32_t src, dag_variant variant, int32_t delta, int32_t max_iters,
-                        const uint32_t* d_w, uint32_t* d_dist, int32_t flags, dag_stats* h_stats, void* stream)
+namespace dag {
+namespace {
+int sssp_impl(dag_plan* plan, uint32_t src, int variant, int delta, int max_iters, const uint32_t* w,
+              const uint8_t* w8, uint32_t* dist, int flags, dag_stats* h_stats, cudaStream_t s)
 {
-    if (!plan || !d_dist || (plan->m > 0 && !d_w)) return set_error(DAG_ERR_INVALID, "null argument");
+    if (!plan || !dist || (plan->m > 0 && !w && !w8)) return set_error(DAG_ERR_INVALID, "null argument");
     if (src >= (uint32_t)plan->n) return set_error(DAG_ERR_INVALID, "source outside [0, n)");
     int rc = check_variant(variant, delta, max_iters);
     if (rc) return rc;
     int var = variant;
     if (var == DAG_DELAYED && delta == 0) var = DAG_ASYNC;
-    cudaStream_t s = (cudaStream_t)stream;
     SweepParams p{};
     p.n = plan->n;
     p.rowptr = plan->rowptr;
     p.colidx = plan->colidx;
-    p.w = d_w;
+    p.w = w;
+    p.w8 = w8;
     p.degf = plan->degf;
     p.tol = 0.0;
     p.max_iters = max_iters;
     p.src = src;
     p.x0 = plan->x0;
     p.x1 = plan->x1;
-    p.out = d_dist;
+    p.out = dist;
     p.read_mode = read_mode_of(flags);
     Timer tm;
     tm.start(s, h_stats != nullptr);
     int nb = 0;
-    rc = launch_sweep(plan, MODE_BF, var, delta, p, s, &nb);
+    rc = launch_sweep(plan, w8 ? MODE_BF8 : MODE_BF, var, delta, p, s, &nb);
     if (rc) return rc;
     tm.stop(s);
     if (!h_stats) return DAG_OK;
     return finish_solve(plan, nb, var == DAG_DELAYED ? delta : 0, tm, s, h_stats);
+}
+}  // namespace
+}  // namespace dag
+
+extern "C" int dag_sssp(dag_plan* plan, uint32_t src, dag_variant variant, int32_t delta, int32_t max_iters,
+                        const uint32_t* d_w, uint32_t* d_dist, int32_t flags, dag_stats* h_stats, void* stream)
+{
+    if (plan && plan->m > 0 && !d_w) return set_error(DAG_ERR_INVALID, "null weights");
+    return sssp_impl(plan, src, variant, delta, max_iters, d_w, nullptr, d_dist, flags, h_stats, (cudaStream_t)stream);
+}
+
+extern "C" int dag_sssp_u8(dag_plan* plan, uint32_t src, dag_variant variant, int32_t delta, int32_t max_iters,
+                           const uint8_t* d_w8, uint32_t* d_dist, int32_t flags, dag_stats* h_stats, void* stream)
+{
+    if (plan && plan->m > 0 && !d_w8) return set_error(DAG_ERR_INVALID, "null weights");
+    return sssp_impl(plan, src, variant, delta, max_iters, nullptr, d_w8, d_dist, flags, h_stats,
+                     (cudaStream_t)stream);
 }
 
 extern "C" int dag_pagerank_adjoint(dag_plan* in_plan, dag_plan* out_plan, float d, double tol,

@@ -173,7 +173,7 @@ __global__ void batched_kernel(const BatchParams p)
                         gsum += rnew;
                         dg_acc += rnew - rold;
                     }
-                    xnew = __float_as_uint(dg > 0.0f ? rnew / dg : rnew);
+                    xnew = __float_as_uint(dg > 0.0f ? __fdividef(rnew, dg) : rnew);  // 2 ulp, no special-value path
                 }
                 if constexpr (SYNC) st_weak_b32(xout + k, xnew);
                 else if constexpr (DELAYED) mybuf[(v - buf_first) * 32 + lane] = xnew;

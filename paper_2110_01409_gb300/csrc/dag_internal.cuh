@@ -37,7 +37,7 @@ constexpr int NWARP = NT / 32;
 constexpr int GSTRIPES = 32;      // stripes of the live dangling/global-sum accumulator
 constexpr int GSTRIDE = 4;        // doubles between stripes (32 bytes)
 
-enum Mode { MODE_PR = 0, MODE_PRW = 1, MODE_ADJ = 2, MODE_BF = 3 };
+enum Mode { MODE_PR = 0, MODE_PRW = 1, MODE_ADJ = 2, MODE_BF = 3, MODE_BF8 = 4 };  // BF8: uint8 weights
 
 // How the delayed form reads other blocks' values (see dag.h, DAG_READ_*).
 enum ReadMode { READ_CACHED_REFRESH = 0, READ_COHERENT = 1, READ_CACHED = 2 };
@@ -69,6 +69,7 @@ struct SweepParams {
     const int* colidx;
     const float* val;       // per-edge P (PRW, ADJ)
     const uint32_t* w;      // per-edge weight (BF)
+    const uint8_t* w8;      // per-edge weight, one byte (BF8)
     const float* degf;      // out-degree as float (PR, PRW: dangling when 0; ADJ: row length of out-CSR)
     const float* base;      // per-row base vector: teleport (PR/PRW) or c (ADJ); NULL = uniform
     float base_scale;       // (1-d) for PageRank, 1 for the adjoint
@@ -207,6 +208,52 @@ __device__ __forceinline__ uint32_t ld_stream_u32(const uint32_t* p)
 {
     uint32_t v;
     asm volatile("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+// L2 eviction policies. The per-edge streams (colidx, weights, edge values) are
+// read once per sweep and are larger than L2: they go first, so that the
+// per-vertex arrays every tile rereads (row ends, out-degrees, the state
+// vector) stay resident in L2 across sweeps.
+__device__ __forceinline__ uint64_t policy_evict_first()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint32_t ld_edge_b32(const void* p, uint64_t pol)
+{
+    uint32_t v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_edge_u8(const uint8_t* p, uint64_t pol)
+{
+    uint32_t v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u8 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_vertex_b32(const void* p, uint64_t pol)
+{
+    uint32_t v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_weak_keep_b32(const void* p, uint64_t pol)
+{
+    uint32_t v;
+    asm volatile("ld.global.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_relaxed_keep_b32(const void* p, uint64_t pol)
+{
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol) : "memory");
     return v;
 }
 // Weak load: may hit in L1. Used for the previous iterate in the synchronous

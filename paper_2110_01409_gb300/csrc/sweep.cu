@@ -59,6 +59,8 @@ struct Op<MODE_BF> {
     static __device__ __forceinline__ uint32_t identity() { return INF; }
     static __device__ __forceinline__ uint32_t combine(uint32_t a, uint32_t b) { return a < b ? a : b; }
 };
+template <>
+struct Op<MODE_BF8> : Op<MODE_BF> {};
 
 // dist_u + w, INF when dist_u is INF; a finite sum that would reach INF stays
 // finite at INF - 1 (cannot happen for n * 255 < 2^32).
@@ -119,9 +121,9 @@ struct Stage {
 // Issues the coalesced loads of tile t (everything except the gathers).
 template <int MODE>
 __device__ __forceinline__ void stage_issue(Stage<MODE>& st, const SweepParams& p, const uint32_t* xin, int t, int tid,
-                                            bool weak)
+                                            bool weak, uint64_t pol_edge, uint64_t pol_vertex)
 {
-    constexpr bool BF = MODE == MODE_BF;
+    constexpr bool BF = MODE == MODE_BF || MODE == MODE_BF8;
     st.a0 = p.tile_row[t];
     st.b0 = p.tile_nz[t];
     st.NA = p.tile_row[t + 1] - st.a0;
@@ -132,16 +134,16 @@ __device__ __forceinline__ void stage_issue(Stage<MODE>& st, const SweepParams& 
         st.col[q] = 0;
         st.aux[q] = 0;
         if (j < st.NB) {
-            st.col[q] = ld_stream_i32(p.colidx + st.b0 + j);
-            if constexpr (BF) st.aux[q] = ld_stream_u32(p.w + st.b0 + j);
-            if constexpr (MODE == MODE_PRW || MODE == MODE_ADJ)
-                st.aux[q] = __float_as_uint(ld_stream_f32(p.val + st.b0 + j));
+            st.col[q] = (int)ld_edge_b32(p.colidx + st.b0 + j, pol_edge);
+            if constexpr (MODE == MODE_BF) st.aux[q] = ld_edge_b32(p.w + st.b0 + j, pol_edge);
+            if constexpr (MODE == MODE_BF8) st.aux[q] = ld_edge_u8(p.w8 + st.b0 + j, pol_edge);
+            if constexpr (MODE == MODE_PRW || MODE == MODE_ADJ) st.aux[q] = ld_edge_b32(p.val + st.b0 + j, pol_edge);
         }
     }
 #pragma unroll
     for (int q = 0; q < IPT; ++q) {
         const int i = tid + q * NT;
-        st.rend[q] = (i < st.NA) ? ld_stream_i32(p.rowptr + st.a0 + i + 1) - st.b0 : 0;
+        st.rend[q] = (i < st.NA) ? (int)ld_vertex_b32(p.rowptr + st.a0 + i + 1, pol_vertex) - st.b0 : 0;
     }
 #pragma unroll
     for (int k = 0; k < RP; ++k) {
@@ -149,8 +151,9 @@ __device__ __forceinline__ void stage_issue(Stage<MODE>& st, const SweepParams& 
         st.pfx[k] = 0u;
         st.pfd[k] = 0.0f;
         if (r < st.NA) {
-            st.pfx[k] = weak ? ld_weak_b32(xin + st.a0 + r) : ld_relaxed_b32(xin + st.a0 + r);
-            if constexpr (!BF) st.pfd[k] = ld_stream_f32(p.degf + st.a0 + r);
+            st.pfx[k] = weak ? ld_weak_keep_b32(xin + st.a0 + r, pol_vertex)
+                             : ld_relaxed_keep_b32(xin + st.a0 + r, pol_vertex);
+            if constexpr (!BF) st.pfd[k] = __uint_as_float(ld_vertex_b32(p.degf + st.a0 + r, pol_vertex));
         }
     }
 }
@@ -158,15 +161,17 @@ __device__ __forceinline__ void stage_issue(Stage<MODE>& st, const SweepParams& 
 // Issues tile t's gathers of the state vector (sync: previous iterate; delayed:
 // this SM's view of the live array; async: the live array in L2).
 template <int MODE>
-__device__ __forceinline__ void stage_gather(Stage<MODE>& st, const uint32_t* xin, int tid, bool weak)
+__device__ __forceinline__ void stage_gather(Stage<MODE>& st, const uint32_t* xin, int tid, bool weak,
+                                             uint64_t pol_vertex)
 {
 #pragma unroll
     for (int q = 0; q < IPT; ++q) {
         const int j = tid + q * NT;
         uint32_t term = 0u;
         if (j < st.NB) {
-            const uint32_t xv = weak ? ld_weak_b32(xin + st.col[q]) : ld_relaxed_b32(xin + st.col[q]);
-            if constexpr (MODE == MODE_BF) term = relax(xv, st.aux[q]);
+            const uint32_t xv = weak ? ld_weak_keep_b32(xin + st.col[q], pol_vertex)
+                                     : ld_relaxed_keep_b32(xin + st.col[q], pol_vertex);
+            if constexpr (MODE == MODE_BF || MODE == MODE_BF8) term = relax(xv, st.aux[q]);
             else if constexpr (MODE == MODE_PR) term = xv;
             else term = __float_as_uint(__uint_as_float(st.aux[q]) * __uint_as_float(xv));
         }
@@ -178,7 +183,7 @@ template <int MODE, int VAR>
 __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams p)
 {
     using O = Op<MODE>;
-    constexpr bool BF = MODE == MODE_BF;
+    constexpr bool BF = MODE == MODE_BF || MODE == MODE_BF8;
     constexpr bool SYNC = VAR == DAG_SYNC;
     constexpr bool DELAYED = VAR == DAG_DELAYED;
     constexpr bool LIVE_G = !SYNC && !BF;  // async/delayed PageRank-type: live global sum
@@ -246,6 +251,8 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
     // sync reads the previous iterate with ordinary loads; async reads the live
     // array coherently (L2); delayed follows p.read_mode
     const bool weak = SYNC || (DELAYED && p.read_mode != READ_COHERENT);
+    const uint64_t pol_edge = policy_evict_first();
+    const uint64_t pol_vertex = policy_evict_last();
     int buf_first = row_lo, buf_cnt = 0;
     long long flushes = 0;
     int it = 0;
@@ -271,8 +278,8 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
         // and its gathers too (issued before barrier C of t).
         Stage<MODE> nx;
         if (tile_lo < tile_hi) {
-            stage_issue<MODE>(nx, p, xin, tile_lo, tid, weak);
-            stage_gather<MODE>(nx, xin, tid, weak);
+            stage_issue<MODE>(nx, p, xin, tile_lo, tid, weak, pol_edge, pol_vertex);
+            stage_gather<MODE>(nx, xin, tid, weak, pol_vertex);
             if constexpr (LIVE_G) {
                 if (warp == 0) nx.gs = ld_relaxed_f64(&sb->stripe[lane * GSTRIDE]);
             }
@@ -334,7 +341,7 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
             }
             if (!real) break;
             const bool more = t + 1 < tile_hi;
-            if (more) stage_issue<MODE>(nx, p, xin, t + 1, tid, weak);
+            if (more) stage_issue<MODE>(nx, p, xin, t + 1, tid, weak, pol_edge, pol_vertex);
             float gt = gterm;
             if constexpr (LIVE_G) {
                 gt = sh.gt;
@@ -409,7 +416,7 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
             if (tid > 0 && emitted) sh.rowsum[i_start] = O::combine(sh.rowsum[i_start], cin);
             const uint32_t E_last = __shfl_sync(0xffffffffu, E, NWARP - 1);  // whole warp takes part
             if (tid == 0) carry = E_last;  // partial of row NA for the next tile
-            if (more) stage_gather<MODE>(nx, xin, tid, weak);
+            if (more) stage_gather<MODE>(nx, xin, tid, weak, pol_vertex);
             __syncthreads();  // (C) row sums final
 
             // -------- epilogue: new values of the rows this tile completed --------
@@ -451,7 +458,9 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
                         }
                     }
                     res_part += fabsf(rnew - rold);
-                    xnew = __float_as_uint((MODE == MODE_PR && dg > 0.0f) ? rnew / dg : rnew);
+                    // x = r / outdeg; __fdividef (2 ulp) has no special-value path, and the
+                    // quotient of a dangling row (dg = 0) is discarded by the select
+                    xnew = __float_as_uint((MODE == MODE_PR && dg > 0.0f) ? __fdividef(rnew, dg) : rnew);
                 }
                 if constexpr (SYNC) st_weak_b32(xout + v, xnew);
                 else if constexpr (DELAYED) s_buf[v - buf_first] = xnew;
@@ -529,11 +538,12 @@ using KernelFn = void (*)(const SweepParams);
 
 static KernelFn kernel_for(int mode, int variant)
 {
-    static const KernelFn table[4][3] = {
+    static const KernelFn table[5][3] = {
         {sweep_kernel<MODE_PR, DAG_SYNC>, sweep_kernel<MODE_PR, DAG_ASYNC>, sweep_kernel<MODE_PR, DAG_DELAYED>},
         {sweep_kernel<MODE_PRW, DAG_SYNC>, sweep_kernel<MODE_PRW, DAG_ASYNC>, sweep_kernel<MODE_PRW, DAG_DELAYED>},
         {sweep_kernel<MODE_ADJ, DAG_SYNC>, sweep_kernel<MODE_ADJ, DAG_ASYNC>, sweep_kernel<MODE_ADJ, DAG_DELAYED>},
         {sweep_kernel<MODE_BF, DAG_SYNC>, sweep_kernel<MODE_BF, DAG_ASYNC>, sweep_kernel<MODE_BF, DAG_DELAYED>},
+        {sweep_kernel<MODE_BF8, DAG_SYNC>, sweep_kernel<MODE_BF8, DAG_ASYNC>, sweep_kernel<MODE_BF8, DAG_DELAYED>},
     };
     return table[mode][variant];
 }

@@ -28,6 +28,7 @@ EXPORTS = (
     "dag_pagerank", "dag_sssp", "dag_ppr_batched", "dag_sssp_batched", "dag_transpose",
     "dag_normalize_weights", "dag_pagerank_adjoint", "dag_strerror", "dag_last_error_message",
     "dag_debug_skip_barrier_once", "dag_pagerank_noalloc", "dag_gather_f32", "dag_plan_set_worker_cap",
+    "dag_sssp_u8",
 )
 
 
@@ -90,6 +91,8 @@ def lib():
             L.dag_debug_skip_barrier_once.argtypes = [_vp, _i32]
             L.dag_gather_f32.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp]
             L.dag_plan_set_worker_cap.argtypes = [_vp, _i32]
+            L.dag_sssp_u8.argtypes = [_vp, ctypes.c_uint32, _i32, _i32, _i32, _vp, _vp, _i32,
+                                      ctypes.POINTER(_Stats), _vp]
             L.dag_pagerank_noalloc.argtypes = [ctypes.POINTER(_Csr), _f32, _f64, _i32, _i32, _i32, _vp, _vp,
                                                ctypes.POINTER(_Stats), _vp]
             for f in EXPORTS:
@@ -207,16 +210,19 @@ def pagerank(plan: Plan, d=0.85, tol=1e-6, variant="delayed", delta=256, max_ite
 
 def sssp(plan: Plan, src: int, w, variant="delayed", delta=32, max_iters=None, out=None, stream=None,
          stats=True, reads="refresh"):
-    """Bellman-Ford through dag_sssp. Returns (dist int64-view-free uint32 as int32 tensor, stats)."""
+    """Bellman-Ford through dag_sssp (w: int32 view of uint32 weights) or
+    dag_sssp_u8 (w: uint8 weights). Returns (dist as int32 holding uint32 bits, stats)."""
     dev = plan.rowptr.device
     out = out if out is not None else torch.empty(plan.n, dtype=torch.int32, device=dev)
     _dev(out, torch.int32, plan.n, "out")
+    u8 = w is not None and w.dtype == torch.uint8
     if plan.m:
-        _dev(w, torch.int32, plan.m, "w")
+        _dev(w, torch.uint8 if u8 else torch.int32, plan.m, "w")
     max_iters = plan.n + 1 if max_iters is None else max_iters
     st = _Stats()
-    rc = lib().dag_sssp(plan.h, src, _variant(variant), delta, max_iters, _ptr(w) if plan.m else None, _ptr(out),
-                        READ_MODES[reads], ctypes.byref(st) if stats else None, _stream(stream))
+    fn = lib().dag_sssp_u8 if u8 else lib().dag_sssp
+    rc = fn(plan.h, src, _variant(variant), delta, max_iters, _ptr(w) if plan.m else None, _ptr(out),
+            READ_MODES[reads], ctypes.byref(st) if stats else None, _stream(stream))
     _raise(rc)
     return out, (_stats(st, plan.m) if stats else None)
 

@@ -210,3 +210,17 @@ def test_flush_counts_follow_delta(dag):
     # small delta: a flush after every tile that completes >= delta rows, so more per sweep
     _, st16 = dag.pagerank(plan, 0.85, 1e-6, "delayed", 16)
     assert st16["flushes"] / st16["iters"] > 1.5 * nonempty
+
+
+@pytest.mark.parametrize("variant,delta", [("sync", 0), ("async", 0), ("delayed", 16), ("delayed", 5000)])
+def test_sssp_u8_weights_bit_exact(dag, variant, delta):
+    # dag_sssp_u8 reads one byte per edge; results equal Dijkstra on the same weights
+    for g, src in [(I.rmat(14, 16, seed=2), 5), (I.erdos_renyi(30000, 16, seed=3), 11)]:
+        w = I.weights_u32(g, 1)
+        plan = _plan(dag, g)
+        ref = oracle.dijkstra(g, w, src)
+        d, st = dag.sssp(plan, src, torch.from_numpy(w.astype(np.uint8)).cuda(), variant, delta)
+        assert st["converged"] and np.array_equal(_u32(d), ref)
+        if variant == "sync":
+            _, it, _, _ = oracle.sssp(g, w, src, oracle.SYNC)
+            assert st["iters"] == it
