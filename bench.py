@@ -232,6 +232,14 @@ def run_gpu(args):
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
     traffic = _recorded_traffic(dom, dom_sweeps)
 
+    # ---- the sweep's real ceiling: one streamed gather pass over the same colidx (dag_probe_gather) ----
+    coherent = bf_dl == 0  # the async sweep gathers with relaxed gpu-scope loads
+    probe_ms = dag.probe_gather(plan, rank_out, coherent=coherent, repeats=5)
+    bf_sweep_ms = bf_ms / bf_sweeps
+    gather_floor = {"probe_ms_per_pass": round(probe_ms, 4), "loads": "relaxed (L2)" if coherent else "ordinary",
+                    "sweep_ms": round(bf_sweep_ms, 4), "frac": round(probe_ms / bf_sweep_ms, 3),
+                    "kernel": dom if dom.startswith("sweep_kernel<BF8") else f"sweep_kernel<BF8,{vname(bf_dl)}>"}
+
     # ---- e2e through the public API from pinned host buffers ----
     e2e = run_e2e(args, g, w, srcs, dev, dag, torch, pr_dl, bf_dl) if args.e2e else None
 
@@ -269,6 +277,7 @@ def run_gpu(args):
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "bytes_per_launch": int(dom_bytes), "traffic": traffic},
+        "gather_floor": gather_floor,
         "clocks": clk,
         "gpu_launches": K * solves,
         "e2e": e2e,
@@ -283,17 +292,31 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def sweep_source_hash():
+    """sha256 of the sweep kernel's sources: a recorded ncu traffic figure is
+    used only while it still describes the kernel that runs."""
+    h = hashlib.sha256()
+    for f in ("sweep.cu", "dag_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2110_01409_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def _recorded_traffic(kernel, sweeps):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source (hash match); else None."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes per launch (read + write) from profiles/sweep_traffic.txt, a
+    summary of an ncu capture of the same kernel on the same workload, scaled
+    by the launch's sweeps; None when the kernel source changed since."""
+    path = os.path.join(ROOT, "profiles", "sweep_traffic.txt")
     try:
+        rec = {}
         with open(path) as f:
-            rec = json.load(f)
-        src = open(os.path.join(ROOT, "paper_2110_01409_gb300", "csrc", "sweep.cu"), "rb").read()
-        if rec.get("sweep_cu_sha256") != hashlib.sha256(src).hexdigest():
+            for line in f:
+                if line.strip() and not line.startswith("#") and ":" in line:
+                    k, v = line.split(":", 1)
+                    rec[k.strip()] = v.strip()
+        if rec.get("sweep_source_sha256") != sweep_source_hash():
             return None
-        per_sweep = rec["kernels"][kernel]["dram_bytes_per_sweep"]
+        per_sweep = float(rec[f"{kernel} rmat{SCALE} dram_bytes_per_sweep"])
         return int(per_sweep * sweeps)
     except Exception:
         return None

@@ -256,6 +256,18 @@ int dag_pagerank_noalloc(const dag_csr* csr, float d, double tol, dag_variant va
                          int32_t max_iters, const float* d_teleport, float* d_rank, dag_stats* h_stats,
                          void* stream);
 
+/*
+ * Measurement aid (no counterpart in the paper): the time of one pass that
+ * streams d_idx[0..m) and gathers d_x[d_idx[e]] (device arrays; every index
+ * must lie in [0, n), which the caller guarantees, e.g. a plan's colidx),
+ * four gathers in flight per thread, nothing else. coherent != 0 gathers with
+ * gpu-scope relaxed loads (as the asynchronous sweep), else with ordinary
+ * loads (as the synchronous and delayed sweeps). *h_ms receives the mean over
+ * `repeats` passes. This is the ceiling a sweep's gathers cannot beat.
+ */
+int dag_probe_gather(const int32_t* d_idx, int64_t m, const float* d_x, int32_t n, int32_t coherent,
+                     int32_t repeats, float* h_ms, void* stream);
+
 /* Names an error code. Never NULL. */
 const char* dag_strerror(int code);
 /* Detail of the last error raised on the calling host thread ("" if none). */

@@ -33,7 +33,8 @@ def main():
     ap.add_argument("--graph", default="rmat", choices=["rmat", "er", "banded"])
     ap.add_argument("--scale", type=int, default=20)
     ap.add_argument("--seed", type=int, default=2)
-    ap.add_argument("--algo", default="pagerank", choices=["pagerank", "sssp"])
+    ap.add_argument("--algo", default="pagerank", choices=["pagerank", "sssp", "sssp8"],
+                    help="sssp8: Bellman-Ford with one-byte weights (dag_sssp_u8)")
     ap.add_argument("--variant", default="delayed", choices=list(dag.VARIANTS))
     ap.add_argument("--delta", type=int, default=256)
     ap.add_argument("--repeat", type=int, default=1)
@@ -47,7 +48,8 @@ def main():
         if args.algo == "pagerank":
             _, st = dag.pagerank(plan, 0.85, args.tol, args.variant, args.delta)
         else:
-            w = torch.from_numpy(I.weights_u32(g, args.seed).view(np.int32)).cuda()
+            w32 = I.weights_u32(g, args.seed)
+            w = torch.from_numpy(w32.astype(np.uint8) if args.algo == "sssp8" else w32.view(np.int32)).cuda()
             src = int(I.sources(g, 1, seed=args.seed)[0])
             _, st = dag.sssp(plan, src, w, args.variant, args.delta)
         out.append(st)

@@ -28,7 +28,7 @@ EXPORTS = (
     "dag_pagerank", "dag_sssp", "dag_ppr_batched", "dag_sssp_batched", "dag_transpose",
     "dag_normalize_weights", "dag_pagerank_adjoint", "dag_strerror", "dag_last_error_message",
     "dag_debug_skip_barrier_once", "dag_pagerank_noalloc", "dag_gather_f32", "dag_plan_set_worker_cap",
-    "dag_sssp_u8",
+    "dag_sssp_u8", "dag_probe_gather",
 )
 
 
@@ -91,6 +91,7 @@ def lib():
             L.dag_debug_skip_barrier_once.argtypes = [_vp, _i32]
             L.dag_gather_f32.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp]
             L.dag_plan_set_worker_cap.argtypes = [_vp, _i32]
+            L.dag_probe_gather.argtypes = [_vp, ctypes.c_int64, _vp, _i32, _i32, _i32, ctypes.POINTER(_f32), _vp]
             L.dag_sssp_u8.argtypes = [_vp, ctypes.c_uint32, _i32, _i32, _i32, _vp, _vp, _i32,
                                       ctypes.POINTER(_Stats), _vp]
             L.dag_pagerank_noalloc.argtypes = [ctypes.POINTER(_Csr), _f32, _f64, _i32, _i32, _i32, _vp, _vp,
@@ -313,6 +314,15 @@ def pagerank_noalloc(rowptr: torch.Tensor, colidx: torch.Tensor, d=0.85, tol=1e-
                                     _ptr(out), ctypes.byref(st), _stream(stream))
     _raise(rc)
     return out, _stats(st, m)
+
+
+def probe_gather(plan: Plan, x: torch.Tensor, coherent=True, repeats=5, stream=None) -> float:
+    """ms of one streamed gather pass x[colidx[e]] over the plan's graph (dag_probe_gather)."""
+    _dev(x, torch.float32, plan.n, "x")
+    ms = _f32(0)
+    _raise(lib().dag_probe_gather(_ptr(plan.colidx), plan.m, _ptr(x), plan.n, 1 if coherent else 0, repeats,
+                                  ctypes.byref(ms), _stream(stream)), False)
+    return ms.value
 
 
 class WeightedPageRank:

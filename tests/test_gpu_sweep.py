@@ -224,3 +224,12 @@ def test_sssp_u8_weights_bit_exact(dag, variant, delta):
         if variant == "sync":
             _, it, _, _ = oracle.sssp(g, w, src, oracle.SYNC)
             assert st["iters"] == it
+
+
+def test_gather_probe_runs(dag):
+    g = I.rmat(14, 16, seed=2)
+    plan = _plan(dag, g)
+    x = torch.ones(g.n, device="cuda")
+    for coherent in (True, False):
+        ms = dag.probe_gather(plan, x, coherent=coherent, repeats=2)
+        assert 0.0 < ms < 1000.0
