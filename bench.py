@@ -37,7 +37,8 @@ N_SOURCES = 8
 PR_DELTA, SSSP_DELTA = 32, 32  # fixed-delta runs of the variant table and the CPU oracle
 DELTAS = (0, 32, 256, 4096)
 WORKLOAD = (f"rmat{SCALE}: pagerank d=0.85 tol=1e-6 + sssp x{N_SOURCES} sources, "
-            f"delayed method, delta picked per algorithm over {list(DELTAS)}")
+            f"delayed method, delta picked per algorithm over {list(DELTAS)} "
+            f"(delta 0 also with own-block L1 reads)")
 
 
 def _peaks():
@@ -119,6 +120,10 @@ def build_inputs():
     return g, w, srcs, time.time() - t0
 
 
+def _cand(c):
+    return str(c["delta"]) + ("" if c["reads"] == "refresh" else "+" + c["reads"])
+
+
 def algorithmic_bytes(n, m, kind):
     """Compulsory bytes of one sweep (gathers of the state vector count as L2
     hits: the 4n-byte vector fits in L2): rowptr 4(n+1), colidx 4m, own old
@@ -159,22 +164,23 @@ def run_gpu(args):
     # ---- delta per algorithm: the autotuner over the delayed method's delta (0 = async end) ----
     from paper_2110_01409_gb300 import autotune
 
-    cands = [("delayed", dl) for dl in DELTAS]
+    cands = [("delayed", dl) for dl in DELTAS] + [("delayed", 0, "own_l1")]
     tune_pr = autotune.tune(plan, "pagerank", candidates=cands, worker_fractions=[1.0], trials=2, cache=None)
     tune_bf = autotune.tune(plan, "sssp", candidates=cands, worker_fractions=[1.0], trials=2, cache=None,
                             src=int(srcs[0]), w=w8_d)
     plan.set_worker_cap(0)
     pr_dl, bf_dl = tune_pr["delta"], tune_bf["delta"]
+    pr_rd, bf_rd = tune_pr["reads"], tune_bf["reads"]
 
     # ---- warm-up with statuses (also records per-solve sweeps) ----
     pr_iters, bf_iters = [], []
     for _ in range(args.warmup):
-        _, st = dag.pagerank(plan, 0.85, 1e-6, "delayed", pr_dl, 1000, out=rank_out)
+        _, st = dag.pagerank(plan, 0.85, 1e-6, "delayed", pr_dl, 1000, out=rank_out, reads=pr_rd)
         assert st["converged"], st
         pr_iters.append(st["iters"])
         its = []
         for k, s in enumerate(srcs):
-            _, st = dag.sssp(plan, int(s), w8_d, "delayed", bf_dl, n + 1, out=dist_out[k])
+            _, st = dag.sssp(plan, int(s), w8_d, "delayed", bf_dl, n + 1, out=dist_out[k], reads=bf_rd)
             assert st["converged"], st
             its.append(st["iters"])
         bf_iters.append(its)
@@ -194,11 +200,11 @@ def run_gpu(args):
     t_start.record(stream)
     for k in range(K):
         pr_ev[k][0].record(stream)
-        dag.pagerank(plan, 0.85, 1e-6, "delayed", pr_dl, 1000, out=rank_out, stats=False)
+        dag.pagerank(plan, 0.85, 1e-6, "delayed", pr_dl, 1000, out=rank_out, stats=False, reads=pr_rd)
         pr_ev[k][1].record(stream)
         for j, s in enumerate(srcs):
             bf_ev[k][j][0].record(stream)
-            dag.sssp(plan, int(s), w8_d, "delayed", bf_dl, n + 1, out=dist_out[j], stats=False)
+            dag.sssp(plan, int(s), w8_d, "delayed", bf_dl, n + 1, out=dist_out[j], stats=False, reads=bf_rd)
             bf_ev[k][j][1].record(stream)
     t_end.record(stream)
     torch.cuda.synchronize()
@@ -214,7 +220,7 @@ def run_gpu(args):
     value = world * solves * m * K / (ms_total * 1e-3) / 1e9
 
     # statuses of the timed solves: one more checked step (results must match the warm-up)
-    _, st_pr = dag.pagerank(plan, 0.85, 1e-6, "delayed", pr_dl, 1000, out=rank_out)
+    _, st_pr = dag.pagerank(plan, 0.85, 1e-6, "delayed", pr_dl, 1000, out=rank_out, reads=pr_rd)
     assert st_pr["converged"]
     pr_ms = statistics.mean(a.elapsed_time(b) for a, b in pr_ev)
     bf_ms = statistics.mean(a.elapsed_time(b) for row in bf_ev for a, b in row)
@@ -241,13 +247,14 @@ def run_gpu(args):
                     "kernel": dom if dom.startswith("sweep_kernel<BF8") else f"sweep_kernel<BF8,{vname(bf_dl)}>"}
 
     # ---- e2e through the public API from pinned host buffers ----
-    e2e = run_e2e(args, g, w, srcs, dev, dag, torch, pr_dl, bf_dl) if args.e2e else None
+    e2e = run_e2e(args, g, w, srcs, dev, dag, torch, (pr_dl, pr_rd), (bf_dl, bf_rd)) if args.e2e else None
 
     detail = {}
     if args.extras and rank == 0:
         detail["variants"] = run_detail(g, w, srcs, plan, w_d, dag, torch, args)
         detail["adjoint"] = run_adjoint(g, plan, dag, torch)
         detail["batched"] = run_batched(dag, torch)
+        detail["access"] = run_access(g, plan, dag, torch)
 
     out = {
         "metric": METRIC,
@@ -264,9 +271,10 @@ def run_gpu(args):
         "data": "synthetic (seeded RMAT stand-in for the GAP Kron graph)",
         "config": {"workload": WORKLOAD, "weights": "uint8 per edge (values in [1, 255])",
                    "delta": {"pagerank": pr_dl, "sssp": bf_dl},
-                   "autotune_ms": {"pagerank": {str(c["delta"]): round(c["ms"], 3) for c in tune_pr["candidates"]
+                   "reads": {"pagerank": pr_rd, "sssp": bf_rd},
+                   "autotune_ms": {"pagerank": {_cand(c): round(c["ms"], 3) for c in tune_pr["candidates"]
                                                 if "ms" in c},
-                                   "sssp": {str(c["delta"]): round(c["ms"], 3) for c in tune_bf["candidates"]
+                                   "sssp": {_cand(c): round(c["ms"], 3) for c in tune_bf["candidates"]
                                             if "ms" in c}},
                    "n": n, "m": m, "sources": [int(s) for s in srcs], "workers": st_pr["workers"],
                    "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (CSR+weights ~0.55 GB)",
@@ -322,7 +330,7 @@ def _recorded_traffic(kernel, sweeps):
         return None
 
 
-def run_e2e(args, g, w, srcs, dev, dag, torch, pr_dl, bf_dl):
+def run_e2e(args, g, w, srcs, dev, dag, torch, pr_choice, bf_choice):
     """Same step through the public API from pinned host memory, copies inside the timed region."""
     rp_h = torch.from_numpy(g.rowptr).pin_memory()
     ci_h = torch.from_numpy(g.colidx).pin_memory()
@@ -338,10 +346,10 @@ def run_e2e(args, g, w, srcs, dev, dag, torch, pr_dl, bf_dl):
         ci = ci_h.to(dev, non_blocking=True)
         wd = w_h.to(dev, non_blocking=True)
         plan = dag.Plan(rp, ci)
-        r, _ = dag.pagerank(plan, 0.85, 1e-6, "delayed", pr_dl, 1000, stats=False)
+        r, _ = dag.pagerank(plan, 0.85, 1e-6, "delayed", pr_choice[0], 1000, stats=False, reads=pr_choice[1])
         res_pr.copy_(r, non_blocking=True)
         for j, s in enumerate(srcs):
-            d, _ = dag.sssp(plan, int(s), wd, "delayed", bf_dl, g.n + 1, stats=False)
+            d, _ = dag.sssp(plan, int(s), wd, "delayed", bf_choice[0], g.n + 1, stats=False, reads=bf_choice[1])
             res_bf[j].copy_(d, non_blocking=True)
         torch.cuda.synchronize()
         plan.close()
@@ -360,19 +368,55 @@ def run_detail(g, w, srcs, plan, w_d, dag, torch, args):
     """Per-variant sweeps and times (3 trials) on the same graph; paper's variants table."""
     res = {}
     trials = 3
-    for name, var, dl in [("sync", "sync", 0), ("async", "async", 0), ("delayed32", "delayed", 32),
-                          ("delayed256", "delayed", 256), ("delayed4096", "delayed", 4096)]:
+    for name, var, dl, rd in [("sync", "sync", 0, "refresh"), ("async", "async", 0, "refresh"),
+                              ("async_own_l1", "async", 0, "own_l1"), ("delayed32", "delayed", 32, "refresh"), ("delayed256", "delayed", 256, "refresh"),
+                              ("delayed4096", "delayed", 4096, "refresh"),
+                              ("delayed4096_local", "delayed", 4096, "local")]:
         pr_it, pr_ms, bf_it, bf_ms = [], [], [], []
         for _ in range(trials):
-            _, st = dag.pagerank(plan, 0.85, 1e-6, var, dl, 1000)
+            _, st = dag.pagerank(plan, 0.85, 1e-6, var, dl, 1000, reads=rd)
             pr_it.append(st["iters"])
             pr_ms.append(st["ms"])
-            _, st = dag.sssp(plan, int(srcs[0]), w_d, var, dl, g.n + 1)
+            _, st = dag.sssp(plan, int(srcs[0]), w_d, var, dl, g.n + 1, reads=rd)
             bf_it.append(st["iters"])
             bf_ms.append(st["ms"])
         res[name] = {"pr_sweeps": pr_it, "pr_ms_median": round(statistics.median(pr_ms), 3),
                      "sssp_sweeps": bf_it, "sssp_ms_median": round(statistics.median(bf_ms), 3)}
     return res
+
+
+def run_access(g, plan, dag, torch):
+    """Fig. 5: reads by each worker of every worker's block, for the benchmark's RMAT
+    graph and a banded graph of the same size (local clustering), at 32 workers
+    (the paper's thread count) and at the sweep's CTA count."""
+    import paper_2110_01409_gb300.inputs as I
+
+    out = {}
+    banded = I.banded(g.n, 15, 1024, 1, seed=SEED)
+    bplan = dag.Plan.from_graph(banded, "cuda")
+    for name, pl in (("rmat", plan), ("banded", bplan)):
+        for P in (32, pl.workers("async", 0)):
+            st = dag.locality(dag.access_matrix(pl, P))
+            out[f"{name}_P{P}"] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in st.items()}
+    # global vs local reads (Sec. III-C) where a worker reads mostly its own block
+    wb = torch.from_numpy(I.weights_u32(banded, SEED).astype(np.uint8)).cuda()
+    src = int(I.sources(banded, 1, seed=SEED)[0])
+    tab = {}
+    for name, var, dl, rd in [("sync", "sync", 0, "refresh"), ("async", "async", 0, "refresh"),
+                              ("async_own_l1", "async", 0, "own_l1"), ("delayed4096", "delayed", 4096, "refresh"),
+                              ("delayed4096_local", "delayed", 4096, "local")]:
+        pr_ms, bf_ms = [], []
+        for _ in range(3):
+            _, st_pr = dag.pagerank(bplan, 0.85, 1e-6, var, dl, 1000, reads=rd)
+            _, st_bf = dag.sssp(bplan, src, wb, var, dl, banded.n + 1, reads=rd)
+            pr_ms.append(st_pr["ms"])
+            bf_ms.append(st_bf["ms"])
+        tab[name] = {"pr_sweeps": st_pr["iters"], "pr_ms_median": round(statistics.median(pr_ms), 3),
+                     "sssp_sweeps": st_bf["iters"], "sssp_ms_median": round(statistics.median(bf_ms), 3)}
+    out["banded_variants"] = tab
+    bplan.close()
+    torch.cuda.synchronize()
+    return out
 
 
 def cpu_tune(g, w, src, cores):

@@ -118,6 +118,23 @@ int dag_plan_set_worker_cap(dag_plan* plan, int32_t max_workers);
  */
 #define DAG_READ_COHERENT 2
 #define DAG_READ_CACHED 4
+/*
+ * Local reads (Sec. III-C): a delayed sweep's CTA reads its own values that
+ * are still in its buffer from the buffer, so they reach its later rows before
+ * the flush. Combines with one DAG_READ_* policy for everything else.
+ */
+#define DAG_READ_LOCAL 8
+/*
+ * Own-block reads through L1 (asynchronous form only): the CTA reads values
+ * of its own vertex block with ordinary loads, which may hit the SM's L1, and
+ * other blocks' values through L2. Only the owning CTA writes its block and
+ * its barriers order those stores before its later loads, so every value read
+ * is as fresh as in the default form; results differ only by the order in
+ * which concurrent CTAs' writes are seen. Helps when workers read mostly
+ * their own block (a clustered graph, Sec. IV-C); the choice is left to the
+ * caller (or to a tuner).
+ */
+#define DAG_READ_OWN_L1 16
 
 /*
  * PageRank (Sec. IV-A; stopping rule Sec. IV):
@@ -131,7 +148,7 @@ int dag_plan_set_worker_cap(dag_plan* plan, int32_t max_workers);
  * values, Sec. III-B; delta >= rows per CTA flushes once per sweep). d_rank
  * (device, float [n]) receives r; with DAG_PR_WARM_START it also gives r^0.
  * Without it r^0 = t. FP32 values, FP64 residual and dangling sums.
- * flags: DAG_PR_WARM_START | one DAG_READ_* (delayed form only).
+ * flags: DAG_PR_WARM_START | one DAG_READ_* (delayed form only) | DAG_READ_OWN_L1 (async form only).
  */
 int dag_pagerank(dag_plan* plan, float d, double tol, dag_variant variant, int32_t delta,
                  int32_t max_iters, const float* d_teleport, const float* d_val, float* d_rank,
@@ -143,7 +160,7 @@ int dag_pagerank(dag_plan* plan, float d, double tol, dag_variant variant, int32
  * "unconditionally storing updates"); stops after a sweep that lowered no
  * value. d_w: uint32 weight per in-edge (device, [m]); d_dist (device,
  * uint32 [n]) receives the distances, 0xFFFFFFFF for unreachable vertices.
- * flags: DAG_READ_* (delayed form only).
+ * flags: DAG_READ_* (delayed form only) | DAG_READ_OWN_L1 (async form only).
  */
 int dag_sssp(dag_plan* plan, uint32_t src, dag_variant variant, int32_t delta, int32_t max_iters,
              const uint32_t* d_w, uint32_t* d_dist, int32_t flags, dag_stats* h_stats, void* stream);
@@ -267,6 +284,15 @@ int dag_pagerank_noalloc(const dag_csr* csr, float d, double tol, dag_variant va
  */
 int dag_probe_gather(const int32_t* d_idx, int64_t m, const float* d_x, int32_t n, int32_t coherent,
                      int32_t repeats, float* h_ms, void* stream);
+
+/*
+ * Access matrix of the static partition into `workers` blocks (Sec. IV-C,
+ * Fig. 5): d_counts[i * workers + j] (device uint64 [workers^2]) = number of
+ * in-edge reads made while computing block i's vertices of vertices owned by
+ * block j, i.e. edges u -> v with v in block i and u in block j. The diagonal
+ * counts a block's reads of its own values. 1 <= workers <= 4096.
+ */
+int dag_access_matrix(dag_plan* plan, int32_t workers, uint64_t* d_counts, void* stream);
 
 /* Names an error code. Never NULL. */
 const char* dag_strerror(int code);

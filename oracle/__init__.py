@@ -52,7 +52,8 @@ def _load():
         if _lib is None:
             build()
             _lib = ctypes.CDLL(_SO)
-            for f in ("orc_pagerank_sync", "orc_pagerank_delayed", "orc_sssp_sync", "orc_sssp_delayed",
+            for f in ("orc_pagerank_sync", "orc_pagerank_delayed", "orc_pagerank_delayed_view", "orc_sssp_sync",
+                      "orc_sssp_delayed", "orc_sssp_delayed_view",
                       "orc_dijkstra", "orc_pagerank_adjoint", "orc_pagerank_threads", "orc_sssp_threads"):
                 getattr(_lib, f).restype = ctypes.c_int
     return _lib
@@ -84,11 +85,12 @@ def partition(g, P: int) -> np.ndarray:
 
 
 def pagerank(g, variant=SYNC, d=0.85, tol=1e-6, max_iters=10000, P=1, delta=0, tele=None, val=None,
-             r0=None):
+             r0=None, local_read=False):
     """fp64 PageRank trajectory. Returns (r, iters, residual history, converged).
 
     variant SYNC: Jacobi; ASYNC: delayed with delta = 0; DELAYED: P round-robin
     workers with buffer delta (delta = 0 is async). r0 defaults to ``tele`` or 1/n.
+    local_read: a worker reads its own unflushed values (Sec. III-C).
     """
     rowptr, colidx = _i32(g.rowptr), _i32(g.colidx)
     tele, val = _f64(tele), _f64(val)
@@ -105,9 +107,11 @@ def pagerank(g, variant=SYNC, d=0.85, tol=1e-6, max_iters=10000, P=1, delta=0, t
                                    ctypes.byref(iters), _p(hist))
     else:
         dl = 0 if variant == ASYNC else delta
-        rc = lib.orc_pagerank_delayed(ctypes.c_int32(g.n), _p(rowptr), _p(colidx), _p(val), ctypes.c_double(d),
-                                      _p(tele), ctypes.c_double(tol), ctypes.c_int32(max_iters),
-                                      ctypes.c_int32(P), ctypes.c_int32(dl), _p(r), ctypes.byref(iters), _p(hist))
+        rc = lib.orc_pagerank_delayed_view(ctypes.c_int32(g.n), _p(rowptr), _p(colidx), _p(val),
+                                           ctypes.c_double(d), _p(tele), ctypes.c_double(tol),
+                                           ctypes.c_int32(max_iters), ctypes.c_int32(P), ctypes.c_int32(dl),
+                                           ctypes.c_int32(1 if local_read else 0), _p(r), ctypes.byref(iters),
+                                           _p(hist))
     if rc < 0:
         raise RuntimeError(f"oracle pagerank failed ({rc})")
     return r, int(iters.value), hist[: iters.value], rc == 0
@@ -121,7 +125,7 @@ def pagerank_fixed_point(g, d=0.85, tele=None, val=None, tol=1e-13, max_iters=10
     return r
 
 
-def sssp(g, w, src, variant=SYNC, P=1, delta=0, max_iters=None):
+def sssp(g, w, src, variant=SYNC, P=1, delta=0, max_iters=None, local_read=False):
     """Bellman-Ford trajectory. Returns (dist uint32, iters, updates per sweep, converged)."""
     rowptr, colidx = _i32(g.rowptr), _i32(g.colidx)
     w = np.ascontiguousarray(w, dtype=np.uint32)
@@ -135,9 +139,10 @@ def sssp(g, w, src, variant=SYNC, P=1, delta=0, max_iters=None):
                                ctypes.c_int32(max_iters), _p(dist), ctypes.byref(iters), _p(upd))
     else:
         dl = 0 if variant == ASYNC else delta
-        rc = lib.orc_sssp_delayed(ctypes.c_int32(g.n), _p(rowptr), _p(colidx), _p(w), ctypes.c_uint32(src),
-                                  ctypes.c_int32(max_iters), ctypes.c_int32(P), ctypes.c_int32(dl), _p(dist),
-                                  ctypes.byref(iters), _p(upd))
+        rc = lib.orc_sssp_delayed_view(ctypes.c_int32(g.n), _p(rowptr), _p(colidx), _p(w), ctypes.c_uint32(src),
+                                       ctypes.c_int32(max_iters), ctypes.c_int32(P), ctypes.c_int32(dl),
+                                       ctypes.c_int32(1 if local_read else 0), _p(dist), ctypes.byref(iters),
+                                       _p(upd))
     if rc < 0:
         raise RuntimeError(f"oracle sssp failed ({rc})")
     return dist, int(iters.value), upd[: iters.value], rc == 0

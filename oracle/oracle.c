@@ -100,6 +100,21 @@ typedef struct {
     double T;             /* sum of tele (1 when uniform) */
 } pr_problem;
 
+/* One row of the PageRank map, reading r; in-neighbours u in [lo, hi) are read
+ * from buf instead (a worker's own unflushed values, Sec. III-C local reads). */
+static double pr_row_view(const pr_problem* q, const double* r, const double* buf, int32_t lo, int32_t hi,
+                          double D, int32_t v)
+{
+    double s = 0.0;
+    for (int32_t e = q->rowptr[v]; e < q->rowptr[v + 1]; ++e) {
+        int32_t u = q->colidx[e];
+        double m_vu = q->val ? q->val[e] : 1.0 / (double)q->outdeg[u];
+        s += m_vu * ((u >= lo && u < hi) ? buf[u] : r[u]);
+    }
+    double t = q->tele ? q->tele[v] : 1.0 / (double)q->n;
+    return (1.0 - q->d) * t + q->d * (s + D / (double)q->n);
+}
+
 /* One row of the PageRank map, reading r. */
 static double pr_row(const pr_problem* q, const double* r, double D, int32_t v)
 {
@@ -164,6 +179,11 @@ int orc_pagerank_sync(int32_t n, const int32_t* rowptr, const int32_t* colidx, c
     return rc;
 }
 
+int orc_pagerank_delayed_view(int32_t n, const int32_t* rowptr, const int32_t* colidx, const double* val,
+                              double d, const double* tele, double tol, int32_t max_iters,
+                              int32_t P, int32_t delta, int32_t local_read, double* r, int32_t* iters,
+                              double* res_hist);
+
 /*
  * Delayed-asynchronous PageRank with P round-robin workers and buffer delta
  * (delta = 0: asynchronous). Same arguments and return codes as the sync form.
@@ -171,6 +191,21 @@ int orc_pagerank_sync(int32_t n, const int32_t* rowptr, const int32_t* colidx, c
 int orc_pagerank_delayed(int32_t n, const int32_t* rowptr, const int32_t* colidx, const double* val,
                          double d, const double* tele, double tol, int32_t max_iters,
                          int32_t P, int32_t delta, double* r, int32_t* iters, double* res_hist)
+{
+    return orc_pagerank_delayed_view(n, rowptr, colidx, val, d, tele, tol, max_iters, P, delta, 0, r, iters,
+                                     res_hist);
+}
+
+/*
+ * As orc_pagerank_delayed; with local_read != 0 a worker reads its own
+ * unflushed values from its buffer (the "local read" form, Sec. III-C) instead
+ * of the global array. Everything else (the dangling term, other workers'
+ * values) still comes from the global array.
+ */
+int orc_pagerank_delayed_view(int32_t n, const int32_t* rowptr, const int32_t* colidx, const double* val,
+                              double d, const double* tele, double tol, int32_t max_iters,
+                              int32_t P, int32_t delta, int32_t local_read, double* r, int32_t* iters,
+                              double* res_hist)
 {
     if (P < 1 || delta < 0) return -2;
     if (P > n) P = n;
@@ -204,7 +239,8 @@ int orc_pagerank_delayed(int32_t n, const int32_t* rowptr, const int32_t* colidx
             for (int32_t p = 0; p < P; ++p) {
                 if (pos[p] >= start[p + 1]) continue;
                 int32_t v = pos[p];
-                double x = pr_row(&q, r, q.T - N, v);
+                double x = local_read ? pr_row_view(&q, r, buf, first[p], first[p] + cnt[p], q.T - N, v)
+                                      : pr_row(&q, r, q.T - N, v);
                 res += fabs(x - r[v]);
                 tick_val[p] = x;
             }
@@ -244,6 +280,22 @@ int orc_pagerank_delayed(int32_t n, const int32_t* rowptr, const int32_t* colidx
 /* ------------------------------------------------------------------------- */
 /* Bellman-Ford SSSP                                                          */
 /* ------------------------------------------------------------------------- */
+
+/* Bellman-Ford row; in-neighbours in [lo, hi) are read from buf (local reads, Sec. III-C). */
+static uint32_t bf_row_view(const int32_t* rowptr, const int32_t* colidx, const uint32_t* w,
+                            const uint32_t* dist, const uint32_t* buf, int32_t lo, int32_t hi, int32_t v)
+{
+    uint32_t best = dist[v];
+    for (int32_t e = rowptr[v]; e < rowptr[v + 1]; ++e) {
+        int32_t u = colidx[e];
+        uint32_t du = (u >= lo && u < hi) ? buf[u] : dist[u];
+        if (du == ORC_INF) continue;
+        uint64_t cand = (uint64_t)du + w[e];
+        if (cand >= ORC_INF) cand = ORC_INF - 1u;
+        if (cand < best) best = (uint32_t)cand;
+    }
+    return best;
+}
 
 static uint32_t bf_row(const int32_t* rowptr, const int32_t* colidx, const uint32_t* w,
                        const uint32_t* dist, int32_t v)
@@ -291,9 +343,21 @@ int orc_sssp_sync(int32_t n, const int32_t* rowptr, const int32_t* colidx, const
 }
 
 /* Delayed-asynchronous Bellman-Ford (delta = 0: asynchronous), P round-robin workers. */
+int orc_sssp_delayed_view(int32_t n, const int32_t* rowptr, const int32_t* colidx, const uint32_t* w,
+                          uint32_t src, int32_t max_iters, int32_t P, int32_t delta, int32_t local_read,
+                          uint32_t* dist, int32_t* iters, int64_t* updates);
+
 int orc_sssp_delayed(int32_t n, const int32_t* rowptr, const int32_t* colidx, const uint32_t* w,
                      uint32_t src, int32_t max_iters, int32_t P, int32_t delta,
                      uint32_t* dist, int32_t* iters, int64_t* updates)
+{
+    return orc_sssp_delayed_view(n, rowptr, colidx, w, src, max_iters, P, delta, 0, dist, iters, updates);
+}
+
+/* As orc_sssp_delayed; local_read != 0: a worker reads its own unflushed values (Sec. III-C). */
+int orc_sssp_delayed_view(int32_t n, const int32_t* rowptr, const int32_t* colidx, const uint32_t* w,
+                          uint32_t src, int32_t max_iters, int32_t P, int32_t delta, int32_t local_read,
+                          uint32_t* dist, int32_t* iters, int64_t* updates)
 {
     if (P < 1 || delta < 0) return -2;
     if (P > n) P = n;
@@ -323,7 +387,8 @@ int orc_sssp_delayed(int32_t n, const int32_t* rowptr, const int32_t* colidx, co
             for (int32_t p = 0; p < P; ++p) {
                 if (pos[p] >= start[p + 1]) continue;
                 int32_t v = pos[p];
-                uint32_t x = bf_row(rowptr, colidx, w, dist, v);
+                uint32_t x = local_read ? bf_row_view(rowptr, colidx, w, dist, buf, first[p], first[p] + cnt[p], v)
+                                        : bf_row(rowptr, colidx, w, dist, v);
                 if (x < dist[v]) ++changed;
                 tick_val[p] = x;
             }

@@ -25,7 +25,9 @@ from . import dag
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "dag_autotune.json")
 _lock = threading.Lock()
 
-SINGLE_CANDIDATES = [("sync", 0), ("async", 0), ("delayed", 32), ("delayed", 256), ("delayed", 4096)]
+# (variant, delta[, reads]); reads defaults to "refresh" (see dag.READ_MODES)
+SINGLE_CANDIDATES = [("sync", 0), ("async", 0), ("async", 0, "own_l1"), ("delayed", 32), ("delayed", 256),
+                     ("delayed", 4096), ("delayed", 4096, "local")]
 BATCH_CANDIDATES = [("sync", 0), ("async", 0), ("delayed", 4), ("delayed", 16)]
 WORKER_FRACTIONS = [1.0, 0.5]
 
@@ -58,13 +60,20 @@ def _store(path, key, value):
         os.replace(tmp, path)
 
 
-def _run(plan, algo, variant, delta, kw):
+def _norm(c):
+    """(variant, delta, reads) from a 2- or 3-tuple candidate."""
+    return (c[0], int(c[1]), c[2] if len(c) > 2 else "refresh")
+
+
+def _run(plan, algo, variant, delta, reads, kw):
     if algo == "pagerank":
-        _, st = dag.pagerank(plan, variant=variant, delta=delta, **kw)
+        _, st = dag.pagerank(plan, variant=variant, delta=delta, reads=reads, **kw)
         return st["ms"], st
     if algo == "sssp":
-        _, st = dag.sssp(plan, kw["src"], kw["w"], variant=variant, delta=delta)
+        _, st = dag.sssp(plan, kw["src"], kw["w"], variant=variant, delta=delta, reads=reads)
         return st["ms"], st
+    if reads != "refresh":
+        raise ValueError("the batched forms take no read mode")
     if algo == "ppr_batched":
         _, _, st = dag.ppr_batched(plan, kw["V"], variant=variant, delta=delta, tol=kw.get("tol", 1e-6))
         return st["ms"], st
@@ -75,15 +84,22 @@ def _run(plan, algo, variant, delta, kw):
 
 
 def tune(plan: dag.Plan, algo: str, candidates=None, worker_fractions=None, trials: int = 2,
-         cache: str | None = DEFAULT_CACHE, **kw) -> dict:
+         cache: str | None = DEFAULT_CACHE, locality_cutoff: float | None = None, **kw) -> dict:
     """Fastest (variant, delta, workers) for `algo` on this plan's graph.
 
     algo: "pagerank" (kw: tol, teleport, ...), "sssp" (kw: src, w), "ppr_batched"
     (kw: V), "sssp_batched" (kw: srcs, w). Returns a dict with the choice and the
     measured candidates; leaves the plan's worker cap at the chosen value.
+
+    locality_cutoff: the precomputed-topology signal of Sec. V. The access
+    matrix of the full launch's partition is counted first; when the share of
+    reads a worker makes of its own block reaches the cutoff, the buffered
+    (delayed) candidates are not timed, since buffering does not relieve
+    contention on a graph whose updates are read mostly by their writer
+    (Sec. IV-C).
     """
     batched = algo.endswith("batched")
-    cands = candidates or (BATCH_CANDIDATES if batched else SINGLE_CANDIDATES)
+    cands = [_norm(c) for c in (candidates or (BATCH_CANDIDATES if batched else SINGLE_CANDIDATES))]
     fracs = worker_fractions or WORKER_FRACTIONS
     B = int(kw["V"].shape[1]) if algo == "ppr_batched" else (int(kw["srcs"].numel()) if algo == "sssp_batched" else 1)
     key = f"{fingerprint(plan)}|{algo}|B{B}"
@@ -94,27 +110,34 @@ def tune(plan: dag.Plan, algo: str, candidates=None, worker_fractions=None, tria
             return hit
     plan.set_worker_cap(0)
     full = plan.workers("async", 0)
+    signal = None
+    if locality_cutoff is not None:
+        signal = dag.locality(dag.access_matrix(plan, full))
+        if signal["diag_share"] >= locality_cutoff:
+            cands = [c for c in cands if c[0] != "delayed"] or cands
     results = []
     for frac in fracs:
         cap = max(1, int(full * frac))
         plan.set_worker_cap(0 if frac >= 1.0 else cap)
-        for variant, delta in cands:
+        for variant, delta, reads in cands:
             times, sweeps = [], []
             try:
                 for _ in range(trials):
-                    ms, st = _run(plan, algo, variant, delta, kw)
+                    ms, st = _run(plan, algo, variant, delta, reads, kw)
                     times.append(ms)
                     sweeps.append(st.get("iters", st.get("sweeps")))
             except dag.DagError as e:  # e.g. a delta whose buffer cannot be resident
-                results.append(dict(variant=variant, delta=delta, workers=0 if frac >= 1.0 else cap,
+                results.append(dict(variant=variant, delta=delta, reads=reads, workers=0 if frac >= 1.0 else cap,
                                     error=str(e)))
                 continue
-            results.append(dict(variant=variant, delta=delta, workers=0 if frac >= 1.0 else cap,
+            results.append(dict(variant=variant, delta=delta, reads=reads, workers=0 if frac >= 1.0 else cap,
                                 ms=float(np.median(times)), sweeps=sweeps))
     ok = [r for r in results if "ms" in r]
     best = min(ok, key=lambda r: r["ms"])
-    choice = dict(variant=best["variant"], delta=best["delta"], workers=best["workers"], ms=best["ms"],
-                  candidates=results)
+    choice = dict(variant=best["variant"], delta=best["delta"], reads=best["reads"], workers=best["workers"],
+                  ms=best["ms"], candidates=results)
+    if signal is not None:
+        choice["locality"] = signal
     plan.set_worker_cap(best["workers"])
     if cache:
         _store(cache, key, choice)

@@ -37,6 +37,7 @@ def main():
                     help="sssp8: Bellman-Ford with one-byte weights (dag_sssp_u8)")
     ap.add_argument("--variant", default="delayed", choices=list(dag.VARIANTS))
     ap.add_argument("--delta", type=int, default=256)
+    ap.add_argument("--reads", default="refresh", choices=list(dag.READ_MODES))
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--tol", type=float, default=1e-6)
     args = ap.parse_args()
@@ -46,16 +47,16 @@ def main():
     out = []
     for _ in range(args.repeat):
         if args.algo == "pagerank":
-            _, st = dag.pagerank(plan, 0.85, args.tol, args.variant, args.delta)
+            _, st = dag.pagerank(plan, 0.85, args.tol, args.variant, args.delta, reads=args.reads)
         else:
             w32 = I.weights_u32(g, args.seed)
             w = torch.from_numpy(w32.astype(np.uint8) if args.algo == "sssp8" else w32.view(np.int32)).cuda()
             src = int(I.sources(g, 1, seed=args.seed)[0])
-            _, st = dag.sssp(plan, src, w, args.variant, args.delta)
+            _, st = dag.sssp(plan, src, w, args.variant, args.delta, reads=args.reads)
         out.append(st)
     torch.cuda.synchronize()
     print(json.dumps({"graph": args.graph, "scale": args.scale, "n": g.n, "m": g.m, "algo": args.algo,
-                      "variant": args.variant, "delta": args.delta, "runs": out}))
+                      "variant": args.variant, "delta": args.delta, "reads": args.reads, "runs": out}))
 
 
 if __name__ == "__main__":

@@ -157,6 +157,8 @@ extern "C" int dag_pagerank(dag_plan* plan, float d, double tol, dag_variant var
     p.init = (flags & DAG_PR_WARM_START) ? d_rank : nullptr;
     p.out = d_rank;
     p.read_mode = read_mode_of(flags);
+    p.local_read = (flags & DAG_READ_LOCAL) ? 1 : 0;
+    p.own_l1 = (flags & DAG_READ_OWN_L1) ? 1 : 0;
     Timer tm;
     tm.start(s, h_stats != nullptr);
     int nb = 0;
@@ -192,6 +194,8 @@ int sssp_impl(dag_plan* plan, uint32_t src, int variant, int delta, int max_iter
     p.x1 = plan->x1;
     p.out = dist;
     p.read_mode = read_mode_of(flags);
+    p.local_read = (flags & DAG_READ_LOCAL) ? 1 : 0;
+    p.own_l1 = (flags & DAG_READ_OWN_L1) ? 1 : 0;
     Timer tm;
     tm.start(s, h_stats != nullptr);
     int nb = 0;

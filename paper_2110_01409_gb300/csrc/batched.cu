@@ -328,8 +328,15 @@ int launch_batched(dag_plan* plan, int is_bf, int variant, int delta, int max_it
         return set_error(DAG_ERR_INVALID, "delta too large for the batched delay buffers in shared memory");
     DAG_CUDA(cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     int per_sm = 0;
+    DAG_CUDA(cudaFuncSetAttribute((const void*)k, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     DAG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k, threads, dyn));
     if (per_sm < 1) return set_error(DAG_ERR_INVALID, "batched kernel cannot be resident");
+    {
+        cudaFuncAttributes fa;
+        DAG_CUDA(cudaFuncGetAttributes(&fa, (const void*)k));
+        const int rc = set_l1_carveout((const void*)k, plan->device, threads, fa.sharedSizeBytes, dyn, per_sm);
+        if (rc) return rc;
+    }
     int nb = per_sm * plan->num_sms;
     if (plan->worker_cap > 0 && nb > plan->worker_cap) nb = plan->worker_cap;
     Partition* part = nullptr;

@@ -95,6 +95,8 @@ struct SweepParams {
     long long timeout_ns;
     int skip_barrier_cta0;  // test hook
     int read_mode;          // ReadMode (delayed form)
+    int local_read;         // delayed form: read own unflushed rows from the buffer (Sec. III-C)
+    int own_l1;             // async form: own block through L1, other blocks through L2
     // init / output
     const float* init;      // warm start (PR) or nullptr
     void* out;              // float r / lambda, or uint32 dist
@@ -163,6 +165,9 @@ int sweep_shape(dag_plan* plan, int mode, int variant, int delta, int* nb_out, i
                 cudaStream_t s);
 
 const void* sweep_kernel_ptr(int mode, int variant);
+// Smallest shared-memory carveout of kernel k that keeps per_sm CTAs of
+// (static_smem + dyn) bytes resident; the rest of the SM's array is L1.
+int set_l1_carveout(const void* k, int device, int threads, size_t static_smem, size_t dyn, int per_sm);
 
 // plan.cu kernels reused by the allocation-free entry point (noalloc.cu)
 __global__ void k_check_rowptr(const int* rowptr, int n, long long m, int* bad);

@@ -141,7 +141,9 @@ extern "C" int dag_pagerank_noalloc(const dag_csr* csr, float d, double tol, dag
         DAG_CUDA(cudaFuncGetAttributes(&fa, sweep_kernel_ptr(MODE_PR, var)));
         max_cap = ((long long)max_dyn - (long long)fa.sharedSizeBytes) / 4;
     }
-    for (int iter = 0; iter < 6; ++iter) {
+    bool settled = false;  // CTAs per SM only fall (4, 3, 2, 1), so a few passes settle the shape
+    for (int iter = 0; iter < 6 && !settled; ++iter) {
+        settled = true;
         k_cta_rows<<<(nb + 1 + 255) / 256, 256, 0, s>>>(rowptr, n, (long long)n + m, nb, cta_row);
         k_cta_tiles<<<1, 1, 0, s>>>(rowptr, cta_row, nb, cta_tile, flags + 2);
         DAG_CUDA(cudaMemcpyAsync(flags + 1, cta_tile + nb, sizeof(int), cudaMemcpyDeviceToDevice, s));
@@ -157,9 +159,12 @@ extern "C" int dag_pagerank_noalloc(const dag_csr* csr, float d, double tol, dag
         int nb2 = 0;
         rc = max_workers(&shape, MODE_PR, var, cap, &nb2);
         if (rc) return rc;
-        if (nb2 >= nb) break;
-        nb = nb2;
+        if (nb2 < nb) {
+            nb = nb2;
+            settled = false;
+        }
     }
+    if (!settled) return set_error(DAG_ERR_INVALID, "launch shape did not settle");
     const int tiles = host_flags[1];
     if (tiles > NA_MAX_TILES) return set_error(DAG_ERR_INVALID, "partition exceeds the no-alloc scratch");
     k_tile_coords<<<(tiles + 1 + 255) / 256, 256, 0, s>>>(rowptr, n, m, cta_row, cta_tile, nb, tiles, tile_row,

@@ -160,17 +160,29 @@ __device__ __forceinline__ void stage_issue(Stage<MODE>& st, const SweepParams& 
 
 // Issues tile t's gathers of the state vector (sync: previous iterate; delayed:
 // this SM's view of the live array; async: the live array in L2).
+// lbuf/lbase/lcnt: the CTA's own unflushed rows [lbase, lbase + lcnt), read from
+// shared memory instead of the global array (local reads, Sec. III-C); lcnt = 0
+// reads everything from the global array.
+// own_lo/own_n: the CTA's own vertex block. Only this CTA writes those values, and
+// its barriers order its own stores before its later loads, so an ordinary
+// (L1-cacheable) load of them is as fresh as a gpu-scope load: the async form
+// may read its own block that way and other blocks through L2 (own_n = 0: all
+// through L2).
 template <int MODE>
 __device__ __forceinline__ void stage_gather(Stage<MODE>& st, const uint32_t* xin, int tid, bool weak,
-                                             uint64_t pol_vertex)
+                                             uint64_t pol_vertex, const uint32_t* lbuf, int lbase, int lcnt,
+                                             int own_lo, int own_n)
 {
 #pragma unroll
     for (int q = 0; q < IPT; ++q) {
         const int j = tid + q * NT;
         uint32_t term = 0u;
         if (j < st.NB) {
-            const uint32_t xv = weak ? ld_weak_keep_b32(xin + st.col[q], pol_vertex)
-                                     : ld_relaxed_keep_b32(xin + st.col[q], pol_vertex);
+            const unsigned off = (unsigned)(st.col[q] - lbase);
+            const bool l1 = weak || (unsigned)(st.col[q] - own_lo) < (unsigned)own_n;
+            const uint32_t xv = off < (unsigned)lcnt ? lbuf[off]
+                              : l1 ? ld_weak_keep_b32(xin + st.col[q], pol_vertex)
+                                   : ld_relaxed_keep_b32(xin + st.col[q], pol_vertex);
             if constexpr (MODE == MODE_BF || MODE == MODE_BF8) term = relax(xv, st.aux[q]);
             else if constexpr (MODE == MODE_PR) term = xv;
             else term = __float_as_uint(__uint_as_float(st.aux[q]) * __uint_as_float(xv));
@@ -251,6 +263,7 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
     // sync reads the previous iterate with ordinary loads; async reads the live
     // array coherently (L2); delayed follows p.read_mode
     const bool weak = SYNC || (DELAYED && p.read_mode != READ_COHERENT);
+    const int own_lo = row_lo, own_n = (VAR == DAG_ASYNC && p.own_l1) ? row_hi - row_lo : 0;
     const uint64_t pol_edge = policy_evict_first();
     const uint64_t pol_vertex = policy_evict_last();
     int buf_first = row_lo, buf_cnt = 0;
@@ -279,7 +292,7 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
         Stage<MODE> nx;
         if (tile_lo < tile_hi) {
             stage_issue<MODE>(nx, p, xin, tile_lo, tid, weak, pol_edge, pol_vertex);
-            stage_gather<MODE>(nx, xin, tid, weak, pol_vertex);
+            stage_gather<MODE>(nx, xin, tid, weak, pol_vertex, s_buf, 0, 0, own_lo, own_n);
             if constexpr (LIVE_G) {
                 if (warp == 0) nx.gs = ld_relaxed_f64(&sb->stripe[lane * GSTRIDE]);
             }
@@ -416,7 +429,9 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
             if (tid > 0 && emitted) sh.rowsum[i_start] = O::combine(sh.rowsum[i_start], cin);
             const uint32_t E_last = __shfl_sync(0xffffffffu, E, NWARP - 1);  // whole warp takes part
             if (tid == 0) carry = E_last;  // partial of row NA for the next tile
-            if (more) stage_gather<MODE>(nx, xin, tid, weak, pol_vertex);
+            if (more)
+                stage_gather<MODE>(nx, xin, tid, weak, pol_vertex, s_buf, buf_first,
+                                   (DELAYED && p.local_read) ? buf_cnt : 0, own_lo, own_n);
             __syncthreads();  // (C) row sums final
 
             // -------- epilogue: new values of the rows this tile completed --------
@@ -552,6 +567,24 @@ static KernelFn kernel_for(int mode, int variant)
 // parameters (the allocation-free entry point).
 const void* sweep_kernel_ptr(int mode, int variant) { return (const void*)kernel_for(mode, variant); }
 
+// Without a preference the driver may keep whatever L1/shared split an earlier
+// kernel needed (up to the largest shared share), which leaves L1 small and
+// makes a sweep's speed depend on what ran before it.
+int set_l1_carveout(const void* k, int device, int threads, size_t static_smem, size_t dyn, int per_sm)
+{
+    int max_sm = 0, reserved = 0;
+    DAG_CUDA(cudaDeviceGetAttribute(&max_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device));
+    DAG_CUDA(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, device));
+    const size_t need = (size_t)per_sm * (static_smem + dyn + (size_t)reserved);
+    int pct = max_sm > 0 ? (int)((need * 100 + (size_t)max_sm - 1) / (size_t)max_sm) : 100;
+    pct = pct < 1 ? 1 : (pct > 100 ? 100 : pct);
+    DAG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
+    int got = 0;
+    DAG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&got, k, threads, dyn));
+    if (got < per_sm) DAG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    return DAG_OK;
+}
+
 int max_workers(dag_plan* plan, int mode, int variant, int buf_cap_elems, int* out)
 {
     KernelFn k = kernel_for(mode, variant);
@@ -564,8 +597,11 @@ int max_workers(dag_plan* plan, int mode, int variant, int buf_cap_elems, int* o
         return set_error(DAG_ERR_INVALID, "delta too large: the delay buffer does not fit in shared memory");
     DAG_CUDA(cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     int per_sm = 0;
+    DAG_CUDA(cudaFuncSetAttribute((const void*)k, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     DAG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k, NT, dyn));
     if (per_sm < 1) return set_error(DAG_ERR_INVALID, "sweep kernel cannot be resident with this delta");
+    const int rc = set_l1_carveout((const void*)k, plan->device, NT, fa.sharedSizeBytes, dyn, per_sm);
+    if (rc) return rc;
     *out = per_sm * plan->num_sms;
     return DAG_OK;
 }
@@ -591,9 +627,11 @@ int sweep_shape(dag_plan* plan, int mode, int variant, int delta, int* nb_out, i
         DAG_CUDA(cudaFuncGetAttributes(&fa, sweep_kernel_ptr(mode, variant)));
         max_cap = ((long long)max_dyn - (long long)fa.sharedSizeBytes) / 4;
     }
-    for (int iter = 0; iter < 6; ++iter) {
+    bool settled = false;  // CTAs per SM only fall (4, 3, 2, 1), so a few passes settle the shape
+    for (int iter = 0; iter < 6 && !settled; ++iter) {
         rc = get_partition(plan, nb, &part, s);
         if (rc) return rc;
+        settled = true;
         if (variant != DAG_DELAYED) break;
         long long need = (long long)delta - 1 + TILE;
         if (need > part->max_rows) need = part->max_rows;
@@ -602,9 +640,12 @@ int sweep_shape(dag_plan* plan, int mode, int variant, int delta, int* nb_out, i
         int nb2 = 0;
         rc = max_workers(plan, mode, variant, cap, &nb2);
         if (rc) return rc;
-        if (nb2 >= nb) break;
-        nb = nb2;
+        if (nb2 < nb) {
+            nb = nb2;
+            settled = false;
+        }
     }
+    if (!settled) return set_error(DAG_ERR_INVALID, "sweep launch shape did not settle");
     *nb_out = nb;
     *cap_out = cap;
     *part_out = part;

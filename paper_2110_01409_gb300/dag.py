@@ -21,14 +21,16 @@ OK, ERR_INVALID, ERR_NOT_CONVERGED, ERR_BARRIER_TIMEOUT, ERR_CUDA, ERR_NOMEM = 0
 SYNC, ASYNC, DELAYED = 0, 1, 2
 VARIANTS = {"sync": SYNC, "async": ASYNC, "delayed": DELAYED}
 WARM_START = 1
-READ_MODES = {"refresh": 0, "coherent": 2, "cached": 4}  # delayed form's reads (DAG_READ_*)
+READ_MODES = {"refresh": 0, "coherent": 2, "cached": 4,  # delayed form's reads (DAG_READ_*)
+              "local": 8, "local+coherent": 10, "local+cached": 12,
+              "own_l1": 16}  # async form: own block through L1 (DAG_READ_OWN_L1)
 
 EXPORTS = (
     "dag_plan_create", "dag_plan_destroy", "dag_plan_out_degree", "dag_partition", "dag_workers",
     "dag_pagerank", "dag_sssp", "dag_ppr_batched", "dag_sssp_batched", "dag_transpose",
     "dag_normalize_weights", "dag_pagerank_adjoint", "dag_strerror", "dag_last_error_message",
     "dag_debug_skip_barrier_once", "dag_pagerank_noalloc", "dag_gather_f32", "dag_plan_set_worker_cap",
-    "dag_sssp_u8", "dag_probe_gather",
+    "dag_sssp_u8", "dag_probe_gather", "dag_access_matrix",
 )
 
 
@@ -91,6 +93,7 @@ def lib():
             L.dag_debug_skip_barrier_once.argtypes = [_vp, _i32]
             L.dag_gather_f32.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp]
             L.dag_plan_set_worker_cap.argtypes = [_vp, _i32]
+            L.dag_access_matrix.argtypes = [_vp, _i32, _vp, _vp]
             L.dag_probe_gather.argtypes = [_vp, ctypes.c_int64, _vp, _i32, _i32, _i32, ctypes.POINTER(_f32), _vp]
             L.dag_sssp_u8.argtypes = [_vp, ctypes.c_uint32, _i32, _i32, _i32, _vp, _vp, _i32,
                                       ctypes.POINTER(_Stats), _vp]
@@ -314,6 +317,27 @@ def pagerank_noalloc(rowptr: torch.Tensor, colidx: torch.Tensor, d=0.85, tol=1e-
                                     _ptr(out), ctypes.byref(st), _stream(stream))
     _raise(rc)
     return out, _stats(st, m)
+
+
+def access_matrix(plan: Plan, workers: int = 32) -> torch.Tensor:
+    """[workers, workers] int64: reads by block i (row owner) of block j's vertices (Fig. 5)."""
+    out = torch.empty((workers, workers), dtype=torch.int64, device=plan.rowptr.device)
+    _raise(lib().dag_access_matrix(plan.h, workers, _ptr(out), _stream()), False)
+    return out
+
+
+def locality(counts: torch.Tensor) -> dict:
+    """Summary of an access matrix (Fig. 5): the share of all reads that fall on
+    the reader's own block (the diagonal), and the rows whose own share is at
+    least 1/P (the boxes the paper marks)."""
+    c = counts.to(torch.float64)
+    P = c.shape[0]
+    diag = torch.diagonal(c)
+    rows = c.sum(1)
+    own = torch.where(rows > 0, diag / rows.clamp_min(1), torch.zeros_like(diag))
+    total = float(rows.sum())
+    return {"workers": P, "diag_share": float(diag.sum()) / total if total else 0.0,
+            "marked_rows": int((own >= 1.0 / P).sum()), "own_share_median": float(own.median())}
 
 
 def probe_gather(plan: Plan, x: torch.Tensor, coherent=True, repeats=5, stream=None) -> float:

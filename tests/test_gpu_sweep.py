@@ -233,3 +233,76 @@ def test_gather_probe_runs(dag):
     for coherent in (True, False):
         ms = dag.probe_gather(plan, x, coherent=coherent, repeats=2)
         assert 0.0 < ms < 1000.0
+
+
+@pytest.mark.parametrize("delta", [64, 4096, 10 ** 6])
+def test_local_reads_parity(dag, delta):
+    # Sec. III-C local reads: a CTA reads its own unflushed values from its buffer
+    for g in [I.rmat(14, 16, seed=7), I.banded(30011, 15, 1024, 1, seed=3)]:
+        plan = _plan(dag, g)
+        rstar = oracle.pagerank_fixed_point(g, 0.85)
+        r, st = dag.pagerank(plan, 0.85, 1e-6, "delayed", delta, reads="local")
+        assert st["converged"] and _l1(r, rstar) <= 1e-5
+        w = I.weights_u32(g, 1)
+        ref = oracle.dijkstra(g, w, 5)
+        d, st2 = dag.sssp(plan, 5, _w_dev(w), "delayed", delta, reads="local")
+        assert st2["converged"] and np.array_equal(_u32(d), ref)
+        _, it_sync, _, _ = oracle.sssp(g, w, 5, oracle.SYNC)
+        assert st2["iters"] <= it_sync
+
+
+@pytest.mark.parametrize("algo", ["pagerank", "sssp", "sssp8"])
+def test_async_own_block_l1_parity(dag, algo):
+    # async form with the CTA's own block read through L1: same fixed point / exact distances
+    for g in [I.rmat(14, 16, seed=8), I.banded(30011, 15, 1024, 1, seed=4), I.banded(1 << 17, 15, 16, 1, seed=4)]:
+        plan = _plan(dag, g)
+        if algo == "pagerank":
+            r, st = dag.pagerank(plan, 0.85, 1e-6, "async", 0, reads="own_l1")
+            assert st["converged"] and _l1(r, oracle.pagerank_fixed_point(g, 0.85)) <= 1e-5
+            continue
+        w = I.weights_u32(g, 2)
+        ref = oracle.dijkstra(g, w, 3)
+        wd = torch.from_numpy(w.astype(np.uint8)).cuda() if algo == "sssp8" else _w_dev(w)
+        d, st = dag.sssp(plan, 3, wd, "async", 0, reads="own_l1")
+        assert st["converged"] and np.array_equal(_u32(d), ref)
+        _, it_sync, _, _ = oracle.sssp(g, w, 3, oracle.SYNC)
+        assert st["iters"] <= it_sync
+
+
+@pytest.mark.parametrize("P", [1, 32, 152, 700])
+def test_access_matrix_counts_exact(dag, P):
+    # Fig. 5: reads by block i (owner of v) of block j's vertices (owner of u), for edges u -> v
+    for g in [I.rmat(13, 16, seed=3), I.banded(20011, 15, 1024, 1, seed=3)]:
+        plan = _plan(dag, g)
+        got = dag.access_matrix(plan, P).cpu().numpy()
+        start = oracle.partition(g, P)
+        src, dst = g.edges()
+        own = lambda x: np.searchsorted(start, x, side="right") - 1  # noqa: E731
+        want = np.bincount(own(dst) * P + own(src), minlength=P * P).reshape(P, P)
+        assert np.array_equal(got, want)
+        assert got.sum() == g.m
+
+
+def test_access_matrix_locality_rmat_vs_banded(dag):
+    # Sec. IV-C: a clustered graph's reads stay mostly on the diagonal, an RMAT graph's do not
+    rm = dag.locality(dag.access_matrix(_plan(dag, I.rmat(16, 16, seed=5)), 32))
+    bd = dag.locality(dag.access_matrix(_plan(dag, I.banded(1 << 16, 15, 1024, 1, seed=5)), 32))
+    assert bd["diag_share"] > 0.6 and bd["marked_rows"] == 32
+    assert rm["diag_share"] < 0.1
+
+
+def test_autotune_cache_and_locality_cutoff(dag, tmp_path):
+    from paper_2110_01409_gb300 import autotune
+
+    cache = str(tmp_path / "tune.json")
+    plan = _plan(dag, I.banded(1 << 16, 15, 16, 1, seed=6))  # band 16: local even at thousands of blocks
+    c1 = autotune.tune(plan, "pagerank", worker_fractions=[1.0], trials=1, cache=cache, tol=1e-6)
+    want = {autotune._norm(c) for c in autotune.SINGLE_CANDIDATES}
+    assert {(r["variant"], r["delta"], r["reads"]) for r in c1["candidates"]} == want
+    assert (c1["variant"], c1["delta"], c1["reads"]) in want
+    c2 = autotune.tune(plan, "pagerank", worker_fractions=[1.0], trials=1, cache=cache, tol=1e-6)
+    assert c2 == c1  # served from the cache
+    c3 = autotune.tune(plan, "pagerank", worker_fractions=[1.0], trials=1, cache=None, tol=1e-6,
+                       locality_cutoff=0.5)
+    assert c3["locality"]["diag_share"] > 0.5
+    assert all(r["variant"] != "delayed" for r in c3["candidates"])

@@ -131,7 +131,7 @@ def test_hand_worked_one_sweep_on_cycle8():
             r, it, hist, _ = oracle.pagerank(g, oracle.SYNC, d=0.5, tol=0.0, max_iters=1, r0=r0)
         else:
             r, it, hist, _ = oracle.pagerank(g, oracle.DELAYED, d=0.5, tol=0.0, max_iters=1, r0=r0, P=P,
-                                             delta=delta)
+                                             delta=delta, local_read=name.startswith("local"))
         assert it == 1
         assert np.max(np.abs(r - want)) <= 1e-16, name
         assert abs(hist[0] - res) <= 1e-15, name

@@ -103,6 +103,8 @@ def test_bellman_ford_variants_match_dijkstra_and_invariants(seed, src):
         assert ok and np.array_equal(dist, ref), (P, delta)
         # fresher values can only lower distances sooner
         assert it <= it_sync
+        dist, it_l, _, ok = oracle.sssp(g, w, src, oracle.DELAYED, P=P, delta=delta, local_read=True)
+        assert ok and np.array_equal(dist, ref) and it_l <= it_sync
 
 
 def test_hand_worked_path6_traces():
@@ -116,7 +118,8 @@ def test_hand_worked_path6_traces():
         if delta < 0:
             dist, it, u, ok = oracle.sssp(g, w, 0, oracle.SYNC)
         else:
-            dist, it, u, ok = oracle.sssp(g, w, 0, oracle.DELAYED, P=P, delta=delta)
+            dist, it, u, ok = oracle.sssp(g, w, 0, oracle.DELAYED, P=P, delta=delta,
+                                          local_read=name.startswith("local"))
         assert ok, name
         assert list(dist) == [0, 1, 2, 3, 4, 5], name
         assert it == iters and list(u) == want_upd, name
