@@ -35,7 +35,8 @@ constexpr int MINBLOCKS = DAG_MINBLOCKS;  // CTAs per SM the register budget is 
 constexpr int TILE = NT * IPT;    // items per tile
 constexpr int NWARP = NT / 32;
 constexpr int GSTRIPES = 32;      // stripes of the live dangling/global-sum accumulator
-constexpr int GSTRIDE = 4;        // doubles between stripes (32 bytes)
+constexpr int GSTRIDE = 16;       // doubles between stripes: one 128-byte L2 line each, since
+                                  // atomics to stripes sharing a line serialise on it
 
 enum Mode { MODE_PR = 0, MODE_PRW = 1, MODE_ADJ = 2, MODE_BF = 3, MODE_BF8 = 4 };  // BF8: uint8 weights
 
@@ -58,7 +59,7 @@ struct __align__(128) SyncBlock {
     double acc_res[3];           // per-sweep residual sums, slot = sweep % 3 (init = slot 2)
     double acc_g[3];             // per-sweep global sums (N for PageRank, sum lambda for the adjoint)
     double pad1[4];
-    double stripe[GSTRIPES * GSTRIDE]; // live global sum (async / delayed)
+    alignas(128) double stripe[GSTRIPES * GSTRIDE];  // live global sum (async / delayed)
 };
 
 // Parameters of one sweep launch.
