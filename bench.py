@@ -255,6 +255,7 @@ def run_gpu(args):
         detail["adjoint"] = run_adjoint(g, plan, dag, torch)
         detail["batched"] = run_batched(dag, torch)
         detail["access"] = run_access(g, plan, dag, torch)
+        detail["config3"] = run_config3(dag, torch)
 
     out = {
         "metric": METRIC,
@@ -385,6 +386,47 @@ def run_detail(g, w, srcs, plan, w_d, dag, torch, args):
     return res
 
 
+def run_config3(dag, torch):
+    """The clustered and uniform graphs at full size: banded n = 2^24 (15 edges within
+    +-1024 + 1 uniform) and ER n = 2^23 (16 per vertex), seed 3; PageRank and
+    Bellman-Ford (one-byte weights) in every variant; 3 trials each."""
+    import paper_2110_01409_gb300.inputs as I
+
+    out = {}
+    variants = [("sync", "sync", 0, "refresh"), ("async", "async", 0, "refresh"),
+                ("async_own_l1", "async", 0, "own_l1"), ("delayed32", "delayed", 32, "refresh"),
+                ("delayed256", "delayed", 256, "refresh"), ("delayed4096", "delayed", 4096, "refresh"),
+                ("delayed4096_local", "delayed", 4096, "local")]
+    for gname, make in (("banded24", lambda: I.banded(1 << 24, 15, 1024, 1, seed=3)),
+                        ("er23", lambda: I.erdos_renyi(1 << 23, 16, seed=3))):
+        t0 = time.time()
+        g = make()
+        gen_s = time.time() - t0
+        pl = dag.Plan.from_graph(g, "cuda")
+        w8 = torch.from_numpy(I.weights_u32(g, 3).astype(np.uint8)).cuda()
+        src = int(I.sources(g, 1, seed=3)[0])
+        tab = {"n": g.n, "m": g.m, "graph_gen_s": round(gen_s, 1),
+               "locality_P32": round(dag.locality(dag.access_matrix(pl, 32))["diag_share"], 4)}
+        for name, var, dl, rd in variants:
+            pr_ms, pr_it, bf_ms, bf_it = [], [], [], []
+            for _ in range(3):
+                _, st = dag.pagerank(pl, 0.85, 1e-6, var, dl, 1000, reads=rd)
+                assert st["converged"], (gname, name, st)
+                pr_ms.append(st["ms"])
+                pr_it.append(st["iters"])
+                _, st = dag.sssp(pl, src, w8, var, dl, g.n + 1, reads=rd)
+                assert st["converged"], (gname, name, st)
+                bf_ms.append(st["ms"])
+                bf_it.append(st["iters"])
+            tab[name] = {"pr_sweeps": pr_it, "pr_ms_median": round(statistics.median(pr_ms), 3),
+                         "sssp_sweeps": bf_it, "sssp_ms_median": round(statistics.median(bf_ms), 3)}
+        pl.close()
+        del w8
+        out[gname] = tab
+    torch.cuda.synchronize()
+    return out
+
+
 def run_access(g, plan, dag, torch):
     """Fig. 5: reads by each worker of every worker's block, for the benchmark's RMAT
     graph and a banded graph of the same size (local clustering), at 32 workers
@@ -449,9 +491,19 @@ def cpu_baseline(g, w, srcs):
     cores = os.cpu_count() or 1
     pr_dl, bf_dl = cpu_tune(g, w, int(srcs[0]), cores)
     secs, sweeps, ok = cpu_step(g, w, srcs, cores, pr_dl, bf_dl)
+    # one thread, one PageRank solve (the same form; bounded to a couple of seconds)
+    _, it1, s1, _ = oracle_pr_threads(g, pr_dl, 1)
     return {"value": round((1 + N_SOURCES) * g.m / secs / 1e9, 4), "unit": "GTEPS", "cores": cores, "kind": "oracle",
             "sample": f"one full step (1 pagerank + {N_SOURCES} sssp, delta {pr_dl}/{bf_dl} picked over "
-                      f"{list(DELTAS)}, sweeps {sweeps}) in {secs:.2f} s", "converged": bool(ok)}
+                      f"{list(DELTAS)}, sweeps {sweeps}) in {secs:.2f} s", "converged": bool(ok),
+            "single_thread": {"value": round(g.m / s1 / 1e9, 4), "unit": "GTEPS",
+                              "sample": f"one pagerank solve on 1 thread, delta {pr_dl}, {it1} sweeps, {s1:.2f} s"}}
+
+
+def oracle_pr_threads(g, delta, threads):
+    import oracle
+
+    return oracle.pagerank_threads(g, oracle.DELAYED, tol=1e-6, threads=threads, delta=delta)
 
 
 def run_reference(args):
