@@ -15,6 +15,10 @@
  * Conventions for every entry point:
  *  - Graphs are in-edge CSR: colidx[rowptr[v] .. rowptr[v+1]) are the sources u
  *    of the edges u -> v. rowptr/colidx are int32 (m < 2^31).
+ *  - rowptr, colidx and the per-edge weight / value arrays start on a 16-byte
+ *    boundary (any cudaMalloc or fresh torch allocation does); the sweeps copy
+ *    them with TMA bulk copies. A solve given a misaligned array returns
+ *    DAG_ERR_INVALID.
  *  - Pointers named d_* are DEVICE pointers on the current CUDA device; h_*
  *    are HOST pointers. All arrays belong to the caller; the library keeps no
  *    pointer to them after the call returns, except that a plan keeps the CSR
@@ -28,9 +32,10 @@
  *    on the host before anything is enqueued; a rejected call changes nothing.
  *  - A solve that reaches max_iters without meeting its stopping rule returns
  *    DAG_ERR_NOT_CONVERGED and still writes its last iterate.
- *  - Every device-side wait (the grid barrier between iterations) has a time
- *    limit; when it runs out the kernel stops, the call returns
- *    DAG_ERR_BARRIER_TIMEOUT and the CUDA context stays usable.
+ *  - Every device-side wait (the grid barrier between iterations, the wait
+ *    for a tile's staged inputs) has a time limit; when it runs out the kernel
+ *    stops, the call returns DAG_ERR_BARRIER_TIMEOUT and the CUDA context stays
+ *    usable.
  */
 #ifndef DAG_H
 #define DAG_H
@@ -306,6 +311,15 @@ const char* dag_last_error_message(void);
  * DAG_ERR_BARRIER_TIMEOUT. Resets itself after one solve.
  */
 int dag_debug_skip_barrier_once(dag_plan* plan, int32_t timeout_ms);
+
+/*
+ * Test hook for the staging waits of the asynchronous sweep: the next
+ * asynchronous solve on this plan announces 16 more bytes than it copies for
+ * CTA 0's first tile, so that tile's bounded wait runs out (after timeout_ms)
+ * and the call returns DAG_ERR_BARRIER_TIMEOUT. Resets itself after one
+ * asynchronous solve.
+ */
+int dag_debug_stall_staging_once(dag_plan* plan, int32_t timeout_ms);
 
 #ifdef __cplusplus
 }

@@ -34,6 +34,7 @@ constexpr int IPT = DAG_IPT;      // items per thread per tile (odd: fewer bank 
 constexpr int MINBLOCKS = DAG_MINBLOCKS;  // CTAs per SM the register budget is sized for
 constexpr int TILE = NT * IPT;    // items per tile
 constexpr int NWARP = NT / 32;
+constexpr int RING = 3;           // tile staging slots of the sweep kernel (tiles t, t+1, t+2)
 constexpr int GSTRIPES = 32;      // stripes of the live dangling/global-sum accumulator
 constexpr int GSTRIDE = 16;       // doubles between stripes: one 128-byte L2 line each, since
                                   // atomics to stripes sharing a line serialise on it
@@ -95,6 +96,7 @@ struct SweepParams {
     SyncBlock* sync;
     long long timeout_ns;
     int skip_barrier_cta0;  // test hook
+    int stall_fill;         // test hook: CTA 0's first staging wait cannot complete
     int read_mode;          // ReadMode (delayed form)
     int local_read;         // delayed form: read own unflushed rows from the buffer (Sec. III-C)
     int own_l1;             // async form: own block through L1, other blocks through L2
@@ -126,6 +128,7 @@ struct dag_plan {
     int num_sms = 0;
     long long timeout_ns = 2000000000LL;
     int skip_barrier_once = 0;
+    int stall_staging_once = 0;
     long long skip_timeout_ns = 0;
     int worker_cap = 0;       // > 0: at most this many CTAs per solve (more rows per CTA)
     // per-vertex data
@@ -166,6 +169,13 @@ int sweep_shape(dag_plan* plan, int mode, int variant, int delta, int* nb_out, i
                 cudaStream_t s);
 
 const void* sweep_kernel_ptr(int mode, int variant);
+// Dynamic shared memory of a sweep launch in front of the delay buffer: the
+// TMA kernel's tile staging ring (asynchronous form), 0 for the other forms.
+size_t sweep_ring_bytes(int mode, int variant);
+
+// sweep_tma.cu: the asynchronous form's TMA-staged kernel and its ring size.
+const void* sweep_tma_kernel_ptr(int mode);
+size_t sweep_tma_ring_bytes(int mode);
 // Smallest shared-memory carveout of kernel k that keeps per_sm CTAs of
 // (static_smem + dyn) bytes resident; the rest of the SM's array is L1.
 int set_l1_carveout(const void* k, int device, int threads, size_t static_smem, size_t dyn, int per_sm);

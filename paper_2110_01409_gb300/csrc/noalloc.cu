@@ -21,6 +21,8 @@
 #include <algorithm>
 #include <mutex>
 
+#include <cstdint>
+
 #include "dag_internal.cuh"
 
 namespace dag {
@@ -90,6 +92,8 @@ extern "C" int dag_pagerank_noalloc(const dag_csr* csr, float d, double tol, dag
     if (!(tol > 0.0)) return set_error(DAG_ERR_INVALID, "tol must be > 0");
     if (variant < DAG_SYNC || variant > DAG_DELAYED) return set_error(DAG_ERR_INVALID, "unknown variant");
     if (delta < 0 || max_iters < 1) return set_error(DAG_ERR_INVALID, "need delta >= 0 and max_iters >= 1");
+    if ((((uintptr_t)csr->d_rowptr | (uintptr_t)csr->d_colidx) & 15u) != 0)
+        return set_error(DAG_ERR_INVALID, "rowptr and colidx must be 16-byte aligned");
     int var = variant;
     if (var == DAG_DELAYED && delta == 0) var = DAG_ASYNC;
 
@@ -139,7 +143,7 @@ extern "C" int dag_pagerank_noalloc(const dag_csr* csr, float d, double tol, dag
         cudaFuncAttributes fa;
         DAG_CUDA(cudaDeviceGetAttribute(&max_dyn, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
         DAG_CUDA(cudaFuncGetAttributes(&fa, sweep_kernel_ptr(MODE_PR, var)));
-        max_cap = ((long long)max_dyn - (long long)fa.sharedSizeBytes) / 4;
+        max_cap = ((long long)max_dyn - (long long)fa.sharedSizeBytes - (long long)sweep_ring_bytes(MODE_PR, var)) / 4;
     }
     bool settled = false;  // CTAs per SM only fall (4, 3, 2, 1), so a few passes settle the shape
     for (int iter = 0; iter < 6 && !settled; ++iter) {
@@ -198,7 +202,7 @@ extern "C" int dag_pagerank_noalloc(const dag_csr* csr, float d, double tol, dag
     p.out = d_rank;
     DAG_CUDA(cudaMemsetAsync(sync, 0, sizeof(SyncBlock), s));
     const void* k = sweep_kernel_ptr(MODE_PR, var);
-    size_t dyn = (var == DAG_DELAYED) ? (size_t)cap * 4 : 0;
+    size_t dyn = sweep_ring_bytes(MODE_PR, var) + ((var == DAG_DELAYED) ? (size_t)cap * 4 : 0);
     DAG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     void* args[] = {(void*)&p};
     DAG_CUDA(cudaLaunchCooperativeKernel(k, dim3(nb), dim3(NT), args, dyn, s));

@@ -369,6 +369,14 @@ extern "C" int dag_gather_f32(const float* d_src, const int32_t* d_idx, int64_t 
     return DAG_OK;
 }
 
+extern "C" int dag_debug_stall_staging_once(dag_plan* p, int32_t timeout_ms)
+{
+    if (!p || timeout_ms < 1) return set_error(DAG_ERR_INVALID, "bad argument");
+    p->stall_staging_once = 1;
+    p->skip_timeout_ns = (long long)timeout_ms * 1000000LL;
+    return DAG_OK;
+}
+
 extern "C" int dag_debug_skip_barrier_once(dag_plan* p, int32_t timeout_ms)
 {
     if (!p || timeout_ms < 1) return set_error(DAG_ERR_INVALID, "bad argument");

@@ -1,6 +1,8 @@
 // Persistent pull-sweep kernels: PageRank (plain and weighted), the PageRank
 // adjoint, and Bellman-Ford, each in the synchronous, asynchronous and
-// delayed-asynchronous forms.
+// delayed-asynchronous forms. This file holds the register-staged kernel that
+// runs the synchronous and delayed forms, and the launch logic of all three;
+// the asynchronous form runs the TMA-staged kernel of sweep_tma.cu.
 //
 // Paper mapping (Blanco, McMillan, Low, HPEC 2021):
 //  * worker = one CTA owning a contiguous vertex block balanced by in-degree
@@ -27,81 +29,22 @@
 // tile are contiguous, so flushes are coalesced stores of consecutive values.
 //
 // Per tile: all loads (edge stream, gathers, row ends, the rows' old values)
-// are issued in one staging phase; after barrier (A) each thread walks its
-// IPT items of the merge path; after barrier (B) each thread takes the carry
-// of a row begun by earlier threads from a block segmented prefix over the
-// warps' run totals and finishes the rows it ends. A delayed flush is copied
-// out between (A) and (B) of the following tile, so it costs no barrier.
+// are issued in one staging phase into registers; after barrier (A) each
+// thread walks its IPT items of the merge path; after barrier (B) each thread
+// takes the carry of a row begun by earlier threads from a block segmented
+// prefix over the warps' run totals and finishes the rows it ends. A delayed
+// flush is copied out between (A) and (B) of the following tile, so it costs
+// no barrier. This kernel keeps its shared memory small (about 22 KB per CTA
+// plus the delay buffer) because its gathers of the previous iterate or of the
+// SM's view of the live array are ordinary loads that live off L1 hits.
 #include <algorithm>
+#include <cstdint>
 #include <climits>
 #include <type_traits>
 
-#include "dag_internal.cuh"
+#include "sweep_common.cuh"
 
 namespace dag {
-
-template <int MODE>
-struct Op;
-template <>
-struct Op<MODE_PR> {
-    static __device__ __forceinline__ uint32_t identity() { return 0u; }  // +0.0f
-    static __device__ __forceinline__ uint32_t combine(uint32_t a, uint32_t b)
-    {
-        return __float_as_uint(__uint_as_float(a) + __uint_as_float(b));
-    }
-};
-template <>
-struct Op<MODE_PRW> : Op<MODE_PR> {};
-template <>
-struct Op<MODE_ADJ> : Op<MODE_PR> {};
-template <>
-struct Op<MODE_BF> {
-    static __device__ __forceinline__ uint32_t identity() { return INF; }
-    static __device__ __forceinline__ uint32_t combine(uint32_t a, uint32_t b) { return a < b ? a : b; }
-};
-template <>
-struct Op<MODE_BF8> : Op<MODE_BF> {};
-
-// dist_u + w, INF when dist_u is INF; a finite sum that would reach INF stays
-// finite at INF - 1 (cannot happen for n * 255 < 2^32).
-__device__ __forceinline__ uint32_t relax(uint32_t du, uint32_t w)
-{
-    if (du == INF) return INF;
-    uint32_t s = du + w;
-    return (s < du || s == INF) ? INF - 1u : s;
-}
-
-template <int MODE>
-struct SweepShared {
-    uint32_t val[TILE];        // gathered edge terms of the tile
-    int rowend[TILE + 1];      // tile-relative row end offsets (+ sentinel)
-    uint32_t rowsum[TILE];     // per-row reduction of the tile
-    int wkey[NWARP];           // row in progress after each warp's last lane
-    int wfirst[NWARP];         // row in progress after each warp's first lane
-    uint32_t wval[NWARP];      // warp-local inclusive run total at the last lane
-    double red0[NWARP];
-    double red1[NWARP];
-    float gt;                  // the tile's global (dangling) term from the live sum
-    double res;                // broadcast of the sweep residual
-    double gprev;              // broadcast of the previous sweep's global sum
-    double T;                  // broadcast of the teleport total / ||c||_1
-};
-
-// Block sum of two doubles; the result is valid in thread 0.
-template <class SH>
-__device__ __forceinline__ void block_sum2(SH& sh, double& a, double& b)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    a = warp_sum(a);
-    b = warp_sum(b);
-    if (lane == 0) { sh.red0[warp] = a; sh.red1[warp] = b; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        a = 0.0; b = 0.0;
-        for (int k = 0; k < NWARP; ++k) { a += sh.red0[k]; b += sh.red1[k]; }
-    }
-    __syncthreads();
-}
 
 constexpr int RP = 2;  // epilogue rows per thread whose inputs are loaded with the tile
 
@@ -200,7 +143,7 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
     constexpr bool DELAYED = VAR == DAG_DELAYED;
     constexpr bool LIVE_G = !SYNC && !BF;  // async/delayed PageRank-type: live global sum
 
-    __shared__ SweepShared<MODE> sh;
+    __shared__ SweepShared<true> sh;
     extern __shared__ uint32_t s_buf[];  // delay buffer (DELAYED)
 
     const int c = blockIdx.x;
@@ -303,7 +246,6 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
             const bool real = t < tile_hi;
             const int a0 = real ? nx.a0 : 0, b0 = real ? nx.b0 : 0;
             const int NA = real ? nx.NA : 0, NB = real ? nx.NB : 0;
-            const int L = NA + NB;
             uint32_t pf_x[RP];
             float pf_d[RP];
             // -------- tile t into shared memory --------
@@ -361,73 +303,10 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
                 if (warp == 0 && more) nx.gs = ld_relaxed_f64(&sb->stripe[lane * GSTRIDE]);
             }
 
-            // -------- merge-path walk over this thread's IPT items --------
-            const int k0 = min(tid * IPT, L);
-            int lo = max(0, k0 - NB), hi = min(k0, NA);
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (sh.rowend[mid] <= k0 - 1 - mid) lo = mid + 1;
-                else hi = mid;
-            }
-            int i = lo, j = k0 - lo;
-            const int i_start = i;
-            bool emitted = false;
-            uint32_t acc = (tid == 0) ? carry : O::identity();
-            int re = sh.rowend[i];
-#pragma unroll
-            for (int q = 0; q < IPT; ++q) {
-                if (k0 + q < L) {
-                    if (re <= j) {
-                        sh.rowsum[i] = acc;
-                        emitted = true;
-                        acc = O::identity();
-                        ++i;
-                        re = sh.rowend[i];
-                    } else {
-                        acc = O::combine(acc, sh.val[j]);
-                        ++j;
-                    }
-                }
-            }
-            // -------- segmented scan of (row in progress, partial) --------
-            const int key = i;
-            uint32_t sv = acc;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t ov = __shfl_up_sync(0xffffffffu, sv, o);
-                const int ok = __shfl_up_sync(0xffffffffu, key, o);
-                if (lane >= o && ok == key) sv = O::combine(sv, ov);
-            }
-            if (lane == 31) { sh.wkey[warp] = key; sh.wval[warp] = sv; }
-            if (lane == 0) sh.wfirst[warp] = key;
+            // -------- merge-path walk over this thread's IPT items, block segmented scan --------
+            const WalkOut w = walk_tile<MODE, true>(sh, [&](int i) { return sh.rowend[i]; }, NA, NB, carry);
             __syncthreads();  // (B) warp run totals visible
-
-            // E_w: run total ending at warp w's last lane, over all earlier warps
-            // (segmented scan over the NWARP warp summaries, in every warp).
-            uint32_t E;
-            {
-                const int wl = lane < NWARP ? lane : NWARP - 1;
-                const int wk = sh.wkey[wl];
-                const bool head = lane == 0 || sh.wfirst[wl] != wk || sh.wkey[wl > 0 ? wl - 1 : 0] != wk;
-                E = sh.wval[wl];
-                int hd = head ? 1 : 0;
-#pragma unroll
-                for (int o = 1; o < NWARP; o <<= 1) {
-                    const uint32_t oe = __shfl_up_sync(0xffffffffu, E, o);
-                    const int oh = __shfl_up_sync(0xffffffffu, hd, o);
-                    if (lane >= o && !hd) E = O::combine(E, oe);
-                    if (lane >= o) hd |= oh;
-                }
-            }
-            const uint32_t E_prev = __shfl_sync(0xffffffffu, E, warp > 0 ? warp - 1 : 0);
-            const int key_prev = warp > 0 ? sh.wkey[warp - 1] : -1;
-            const int k_first = __shfl_sync(0xffffffffu, key, 0);
-            const uint32_t pre = (warp > 0 && key_prev == k_first) ? E_prev : O::identity();
-            const uint32_t S = (key == k_first) ? O::combine(sv, pre) : sv;
-            uint32_t cin = __shfl_up_sync(0xffffffffu, S, 1);
-            if (lane == 0) cin = (warp > 0) ? E_prev : O::identity();
-            if (tid > 0 && emitted) sh.rowsum[i_start] = O::combine(sh.rowsum[i_start], cin);
-            const uint32_t E_last = __shfl_sync(0xffffffffu, E, NWARP - 1);  // whole warp takes part
+            const uint32_t E_last = finish_scan<MODE>(sh, w);
             if (tid == 0) carry = E_last;  // partial of row NA for the next tile
             if (more)
                 stage_gather<MODE>(nx, xin, tid, weak, pol_vertex, s_buf, buf_first,
@@ -450,33 +329,7 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
                     xo_bits = weak ? ld_weak_b32(xin + v) : ld_relaxed_b32(xin + v);
                     if constexpr (!BF) dg = ld_stream_f32(p.degf + v);
                 }
-                uint32_t xnew;
-                if constexpr (BF) {
-                    xnew = sum < xo_bits ? sum : xo_bits;
-                    if (xnew < xo_bits) res_part += 1.0f;
-                } else {
-                    const float xo = __uint_as_float(xo_bits);
-                    float rnew, rold;
-                    if constexpr (MODE == MODE_ADJ) {
-                        rold = xo;
-                        rnew = ld_stream_f32(p.base + v) + p.d * __uint_as_float(sum) + (dg == 0.0f ? gt : 0.0f);
-                        g_part += rnew;
-                        dg_part += rnew - rold;
-                        if (p.aux_out) p.aux_out[v] = __uint_as_float(sum);
-                    } else {
-                        rold = (MODE == MODE_PR && dg > 0.0f) ? xo * dg : xo;
-                        const float bv = p.base ? p.base_scale * ld_stream_f32(p.base + v) : p.uniform_base;
-                        rnew = bv + p.d * __uint_as_float(sum) + gt;
-                        if (dg > 0.0f) {
-                            g_part += rnew;
-                            dg_part += rnew - rold;
-                        }
-                    }
-                    res_part += fabsf(rnew - rold);
-                    // x = r / outdeg; __fdividef (2 ulp) has no special-value path, and the
-                    // quotient of a dangling row (dg = 0) is discarded by the select
-                    xnew = __float_as_uint((MODE == MODE_PR && dg > 0.0f) ? __fdividef(rnew, dg) : rnew);
-                }
+                const uint32_t xnew = row_update<MODE>(p, v, sum, xo_bits, dg, gt, res_part, g_part, dg_part);
                 if constexpr (SYNC) st_weak_b32(xout + v, xnew);
                 else if constexpr (DELAYED) s_buf[v - buf_first] = xnew;
                 else st_relaxed_b32(xout + v, xnew);
@@ -553,6 +406,7 @@ using KernelFn = void (*)(const SweepParams);
 
 static KernelFn kernel_for(int mode, int variant)
 {
+    if (variant == DAG_ASYNC) return (KernelFn)sweep_tma_kernel_ptr(mode);
     static const KernelFn table[5][3] = {
         {sweep_kernel<MODE_PR, DAG_SYNC>, sweep_kernel<MODE_PR, DAG_ASYNC>, sweep_kernel<MODE_PR, DAG_DELAYED>},
         {sweep_kernel<MODE_PRW, DAG_SYNC>, sweep_kernel<MODE_PRW, DAG_ASYNC>, sweep_kernel<MODE_PRW, DAG_DELAYED>},
@@ -566,6 +420,8 @@ static KernelFn kernel_for(int mode, int variant)
 // The sweep kernel of (mode, variant), for launches that build their own
 // parameters (the allocation-free entry point).
 const void* sweep_kernel_ptr(int mode, int variant) { return (const void*)kernel_for(mode, variant); }
+
+size_t sweep_ring_bytes(int mode, int variant) { return variant == DAG_ASYNC ? sweep_tma_ring_bytes(mode) : 0; }
 
 // Without a preference the driver may keep whatever L1/shared split an earlier
 // kernel needed (up to the largest shared share), which leaves L1 small and
@@ -588,7 +444,7 @@ int set_l1_carveout(const void* k, int device, int threads, size_t static_smem, 
 int max_workers(dag_plan* plan, int mode, int variant, int buf_cap_elems, int* out)
 {
     KernelFn k = kernel_for(mode, variant);
-    size_t dyn = (variant == DAG_DELAYED) ? (size_t)buf_cap_elems * 4 : 0;
+    size_t dyn = sweep_ring_bytes(mode, variant) + ((variant == DAG_DELAYED) ? (size_t)buf_cap_elems * 4 : 0);
     int max_dyn = 0;
     DAG_CUDA(cudaDeviceGetAttribute(&max_dyn, cudaDevAttrMaxSharedMemoryPerBlockOptin, plan->device));
     cudaFuncAttributes fa;
@@ -600,6 +456,19 @@ int max_workers(dag_plan* plan, int mode, int variant, int buf_cap_elems, int* o
     DAG_CUDA(cudaFuncSetAttribute((const void*)k, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     DAG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k, NT, dyn));
     if (per_sm < 1) return set_error(DAG_ERR_INVALID, "sweep kernel cannot be resident with this delta");
+    if (variant == DAG_ASYNC) {
+        // The TMA kernel's streams and coherent gathers bypass L1, but its own-block gathers and
+        // epilogue loads still use it: keep the CTAs' shared memory within the share that leaves
+        // 32 KB of the opt-in maximum to L1 (about 60 KB of L1 on this part), which fits four CTAs
+        // of the one-byte-weight and plain PageRank rings and three of the four-byte ones (with
+        // four of those, L1 drops under 30 KB and the sweep slowed by 25%).
+        int max_sm = 0, reserved = 0;
+        DAG_CUDA(cudaDeviceGetAttribute(&max_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, plan->device));
+        DAG_CUDA(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, plan->device));
+        const size_t per_cta = fa.sharedSizeBytes + dyn + (size_t)reserved;
+        const size_t budget = max_sm > (32 << 10) ? (size_t)max_sm - (32 << 10) : (size_t)max_sm;
+        while (per_sm > 1 && (size_t)per_sm * per_cta > budget) --per_sm;
+    }
     const int rc = set_l1_carveout((const void*)k, plan->device, NT, fa.sharedSizeBytes, dyn, per_sm);
     if (rc) return rc;
     *out = per_sm * plan->num_sms;
@@ -625,7 +494,7 @@ int sweep_shape(dag_plan* plan, int mode, int variant, int delta, int* nb_out, i
         cudaFuncAttributes fa;
         DAG_CUDA(cudaDeviceGetAttribute(&max_dyn, cudaDevAttrMaxSharedMemoryPerBlockOptin, plan->device));
         DAG_CUDA(cudaFuncGetAttributes(&fa, sweep_kernel_ptr(mode, variant)));
-        max_cap = ((long long)max_dyn - (long long)fa.sharedSizeBytes) / 4;
+        max_cap = ((long long)max_dyn - (long long)fa.sharedSizeBytes - (long long)sweep_ring_bytes(mode, variant)) / 4;
     }
     bool settled = false;  // CTAs per SM only fall (4, 3, 2, 1), so a few passes settle the shape
     for (int iter = 0; iter < 6 && !settled; ++iter) {
@@ -671,15 +540,26 @@ int launch_sweep(dag_plan* plan, int mode, int variant, int delta, SweepParams& 
     p.sync = plan->sync;
     p.timeout_ns = plan->timeout_ns;
     p.skip_barrier_cta0 = 0;
+    p.stall_fill = 0;
+    if (plan->stall_staging_once && variant == DAG_ASYNC) {
+        p.stall_fill = 1;
+        p.timeout_ns = plan->skip_timeout_ns;
+        plan->stall_staging_once = 0;
+    }
     if (plan->skip_barrier_once) {
         p.skip_barrier_cta0 = 1;
         p.timeout_ns = plan->skip_timeout_ns;
         plan->skip_barrier_once = 0;
     }
+    // the asynchronous form's tile copies are TMA bulk copies from 16-byte boundaries of these arrays
+    for (const void* a : {(const void*)p.rowptr, (const void*)p.colidx, (const void*)p.w, (const void*)p.w8,
+                          (const void*)p.val, (const void*)p.degf, (const void*)p.x0, (const void*)p.x1})
+        if (((uintptr_t)a & 15u) != 0)
+            return set_error(DAG_ERR_INVALID, "graph, weight and state arrays must be 16-byte aligned");
     DAG_CUDA(cudaMemsetAsync(plan->sync, 0, sizeof(SyncBlock), s));
     KernelFn k = kernel_for(mode, variant);
     void* args[] = {(void*)&p};
-    size_t dyn = (variant == DAG_DELAYED) ? (size_t)cap * 4 : 0;
+    size_t dyn = sweep_ring_bytes(mode, variant) + ((variant == DAG_DELAYED) ? (size_t)cap * 4 : 0);
     DAG_CUDA(cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     DAG_CUDA(cudaLaunchCooperativeKernel((const void*)k, dim3(nb), dim3(NT), args, dyn, s));
     *out_nblocks = nb;

@@ -1,0 +1,217 @@
+// Device pieces shared by the two sweep kernels (sweep.cu: register-staged
+// tiles, used by the synchronous and delayed forms; sweep_tma.cu: TMA-staged
+// tiles, used by the asynchronous form): the per-mode reduction, the
+// Bellman-Ford relaxation, block reductions, the merge-path walk of one tile
+// with its block segmented scan, and the row update of PageRank (Sec. IV-A),
+// its adjoint and Bellman-Ford.
+#pragma once
+
+#include <climits>
+
+#include "dag_internal.cuh"
+
+namespace dag {
+
+template <int MODE>
+struct Op;
+template <>
+struct Op<MODE_PR> {
+    static __device__ __forceinline__ uint32_t identity() { return 0u; }  // +0.0f
+    static __device__ __forceinline__ uint32_t combine(uint32_t a, uint32_t b)
+    {
+        return __float_as_uint(__uint_as_float(a) + __uint_as_float(b));
+    }
+};
+template <>
+struct Op<MODE_PRW> : Op<MODE_PR> {};
+template <>
+struct Op<MODE_ADJ> : Op<MODE_PR> {};
+template <>
+struct Op<MODE_BF> {
+    static __device__ __forceinline__ uint32_t identity() { return INF; }
+    static __device__ __forceinline__ uint32_t combine(uint32_t a, uint32_t b) { return a < b ? a : b; }
+};
+template <>
+struct Op<MODE_BF8> : Op<MODE_BF> {};
+
+// dist_u + w, INF when dist_u is INF; a finite sum that would reach INF stays
+// finite at INF - 1 (cannot happen for n * 255 < 2^32).
+__device__ __forceinline__ uint32_t relax(uint32_t du, uint32_t w)
+{
+    if (du == INF) return INF;
+    uint32_t s = du + w;
+    return (s < du || s == INF) ? INF - 1u : s;
+}
+
+// Shared memory of one sweep CTA. ROWEND: the tile's row ends live here (the
+// register-staged kernel); the TMA kernel reads them from its staging ring.
+template <bool ROWEND>
+struct SweepShared {
+    uint32_t val[TILE];                  // edge terms of the tile
+    int rowend[ROWEND ? TILE + 1 : 1];   // tile-relative row end offsets (+ sentinel)
+    uint32_t rowsum[TILE];               // per-row reduction of the tile
+    int wkey[NWARP];                     // row in progress after each warp's last lane
+    int wfirst[NWARP];                   // row in progress after each warp's first lane
+    uint32_t wval[NWARP];                // warp-local inclusive run total at the last lane
+    double red0[NWARP];
+    double red1[NWARP];
+    float gt;                            // the tile's global (dangling) term from the live sum
+    int abort;                           // a bounded wait of this CTA ran out (TMA kernel)
+    double res;                          // broadcast of the sweep residual
+    double gprev;                        // broadcast of the previous sweep's global sum
+    double T;                            // broadcast of the teleport total / ||c||_1
+    alignas(8) unsigned long long fill_bar[RING];  // staging-ring mbarriers (TMA kernel)
+};
+
+// Block sum of two doubles; the result is valid in thread 0.
+template <class SH>
+__device__ __forceinline__ void block_sum2(SH& sh, double& a, double& b)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if (lane == 0) { sh.red0[warp] = a; sh.red1[warp] = b; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a = 0.0; b = 0.0;
+        for (int k = 0; k < NWARP; ++k) { a += sh.red0[k]; b += sh.red1[k]; }
+    }
+    __syncthreads();
+}
+
+// A thread's part of one tile's merge path (Merrill & Garland): IPT items from
+// diagonal tid * IPT, rows 0..NA-1 and edges 0..NB-1 of the tile, row ends from
+// rowend(i) (tile-relative, i < NA; with SENTINEL, rowend(NA) is INT_MAX too,
+// which saves a compare per step). Rows it ends get their partial in
+// sh.rowsum; the row in progress after its last item is (key, sv) after the
+// warp-level segmented scan, whose warp summaries go to sh.wkey / wval / wfirst.
+// The caller places barrier (B) after this.
+struct WalkOut {
+    int i_start;  // first row this thread touches
+    int key;      // row in progress after its last item
+    uint32_t sv;  // warp-inclusive run total of that row
+    bool emitted; // it ended at least one row
+};
+
+template <int MODE, bool SENTINEL, class SH, class RE>
+__device__ __forceinline__ WalkOut walk_tile(SH& sh, const RE& rowend, int NA, int NB, uint32_t carry)
+{
+    using O = Op<MODE>;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int L = NA + NB;
+    const int k0 = min(tid * IPT, L);
+    int lo = max(0, k0 - NB), hi = min(k0, NA);
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (rowend(mid) <= k0 - 1 - mid) lo = mid + 1;
+        else hi = mid;
+    }
+    WalkOut w;
+    int i = lo, j = k0 - lo;
+    w.i_start = i;
+    w.emitted = false;
+    uint32_t acc = (tid == 0) ? carry : O::identity();
+    int re = (SENTINEL || i < NA) ? rowend(i) : INT_MAX;
+#pragma unroll
+    for (int q = 0; q < IPT; ++q) {
+        if (k0 + q < L) {
+            if (re <= j) {
+                sh.rowsum[i] = acc;
+                w.emitted = true;
+                acc = O::identity();
+                ++i;
+                re = (SENTINEL || i < NA) ? rowend(i) : INT_MAX;
+            } else {
+                acc = O::combine(acc, sh.val[j]);
+                ++j;
+            }
+        }
+    }
+    // segmented scan of (row in progress, partial) within the warp
+    w.key = i;
+    uint32_t sv = acc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t ov = __shfl_up_sync(0xffffffffu, sv, o);
+        const int ok = __shfl_up_sync(0xffffffffu, w.key, o);
+        if (lane >= o && ok == w.key) sv = O::combine(sv, ov);
+    }
+    w.sv = sv;
+    if (lane == 31) { sh.wkey[warp] = w.key; sh.wval[warp] = sv; }
+    if (lane == 0) sh.wfirst[warp] = w.key;
+    return w;
+}
+
+// After barrier (B): the carry of a row begun by earlier threads, from a
+// segmented scan over the warps' run totals (in every warp), added to the
+// first row this thread ended. Returns the partial of the row that continues
+// into the next tile (the same value in every thread).
+template <int MODE, class SH>
+__device__ __forceinline__ uint32_t finish_scan(SH& sh, const WalkOut& w)
+{
+    using O = Op<MODE>;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t E;  // run total ending at warp w's last lane, over all earlier warps
+    {
+        const int wl = lane < NWARP ? lane : NWARP - 1;
+        const int wk = sh.wkey[wl];
+        const bool head = lane == 0 || sh.wfirst[wl] != wk || sh.wkey[wl > 0 ? wl - 1 : 0] != wk;
+        E = sh.wval[wl];
+        int hd = head ? 1 : 0;
+#pragma unroll
+        for (int o = 1; o < NWARP; o <<= 1) {
+            const uint32_t oe = __shfl_up_sync(0xffffffffu, E, o);
+            const int oh = __shfl_up_sync(0xffffffffu, hd, o);
+            if (lane >= o && !hd) E = O::combine(E, oe);
+            if (lane >= o) hd |= oh;
+        }
+    }
+    const uint32_t E_prev = __shfl_sync(0xffffffffu, E, warp > 0 ? warp - 1 : 0);
+    const int key_prev = warp > 0 ? sh.wkey[warp - 1] : -1;
+    const int k_first = __shfl_sync(0xffffffffu, w.key, 0);
+    const uint32_t pre = (warp > 0 && key_prev == k_first) ? E_prev : O::identity();
+    const uint32_t S = (w.key == k_first) ? O::combine(w.sv, pre) : w.sv;
+    uint32_t cin = __shfl_up_sync(0xffffffffu, S, 1);
+    if (lane == 0) cin = (warp > 0) ? E_prev : O::identity();
+    if (tid > 0 && w.emitted) sh.rowsum[w.i_start] = O::combine(sh.rowsum[w.i_start], cin);
+    return __shfl_sync(0xffffffffu, E, NWARP - 1);  // whole warp takes part
+}
+
+// New value of row v from its pull sum and old value (PageRank: x = r/outdeg
+// with dg = outdeg; adjoint: lambda; Bellman-Ford: dist), with the residual
+// and global-sum contributions.
+template <int MODE>
+__device__ __forceinline__ uint32_t row_update(const SweepParams& p, int v, uint32_t sum, uint32_t xo_bits, float dg,
+                                               float gt, float& res_part, float& g_part, float& dg_part)
+{
+    constexpr bool BF = MODE == MODE_BF || MODE == MODE_BF8;
+    if constexpr (BF) {
+        const uint32_t xnew = sum < xo_bits ? sum : xo_bits;
+        if (xnew < xo_bits) res_part += 1.0f;
+        return xnew;
+    } else {
+        const float xo = __uint_as_float(xo_bits);
+        float rnew, rold;
+        if constexpr (MODE == MODE_ADJ) {
+            rold = xo;
+            rnew = ld_stream_f32(p.base + v) + p.d * __uint_as_float(sum) + (dg == 0.0f ? gt : 0.0f);
+            g_part += rnew;
+            dg_part += rnew - rold;
+            if (p.aux_out) p.aux_out[v] = __uint_as_float(sum);
+        } else {
+            rold = (MODE == MODE_PR && dg > 0.0f) ? xo * dg : xo;
+            const float bv = p.base ? p.base_scale * ld_stream_f32(p.base + v) : p.uniform_base;
+            rnew = bv + p.d * __uint_as_float(sum) + gt;
+            if (dg > 0.0f) {
+                g_part += rnew;
+                dg_part += rnew - rold;
+            }
+        }
+        res_part += fabsf(rnew - rold);
+        // x = r / outdeg; __fdividef (2 ulp) has no special-value path, and the
+        // quotient of a dangling row (dg = 0) is discarded by the select
+        return __float_as_uint((MODE == MODE_PR && dg > 0.0f) ? __fdividef(rnew, dg) : rnew);
+    }
+}
+
+}  // namespace dag

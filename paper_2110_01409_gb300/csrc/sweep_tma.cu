@@ -1,0 +1,457 @@
+// Asynchronous pull sweep (Sec. I; delta = 0 of the delayed method, Sec. III-B)
+// of PageRank, weighted PageRank, the PageRank adjoint and Bellman-Ford, with
+// TMA-staged tiles.
+//
+// The asynchronous form reads the live state with relaxed gpu-scope loads,
+// which L2 serves, so its gathers gain nothing from L1; what it needs is
+// gathers in flight long enough to cover L2 latency. So a tile's contiguous
+// inputs (edge stream, row ends, weights or values, the first NT rows' old
+// values and out-degrees) are copied by the TMA engine (cp.async.bulk) two
+// tiles ahead into a three-slot shared-memory ring, completing on one
+// mbarrier per slot, and the tile's gathers are issued a whole tile ahead from
+// the staged edge stream. The walk, scan and row update are those of the
+// register-staged kernel (sweep_common.cuh). Every wait on a ring mbarrier is
+// bounded by the launch's timeout: when one runs out the CTA records
+// DAG_ERR_BARRIER_TIMEOUT, waits (bounded) for its own copies and leaves, and
+// the other CTAs' grid-barrier waits end on the recorded error.
+//
+// Own block through L1 (DAG_READ_OWN_L1): only the owning CTA writes its
+// vertices, and its barriers order its stores before its later loads, so an
+// ordinary load of its own vertices is as fresh as a gpu-scope one; with the
+// flag set those gathers use ordinary loads and may hit in L1.
+#include <cstdint>
+
+#include "sweep_common.cuh"
+
+namespace dag {
+
+// Ring layout (dynamic shared memory). Every copy starts at the 16-byte
+// boundary at or below its first element and ends at the one at or above its
+// last, so it stays inside the 16-byte granules that hold the wanted elements
+// (arrays are 16-byte aligned; the launch checks).
+template <int MODE>
+struct Ring {
+    static constexpr bool BF = MODE == MODE_BF || MODE == MODE_BF8;
+    static constexpr int CR_INTS = TILE + 12;  // edge stream + row ends (a tile's rows + edges <= TILE) + slack
+    static constexpr int OLD_INTS = NT + 8;    // old values of the tile's first NT rows + slack
+    static constexpr int AUX_BYTES = MODE == MODE_PR ? 0 : MODE == MODE_BF8 ? TILE + 32 : (TILE + 8) * 4;
+    static constexpr int DEG_INTS = BF ? 0 : OLD_INTS;
+    static constexpr int OFF_CR = 0;
+    static constexpr int OFF_OLD = OFF_CR + RING * CR_INTS * 4;
+    static constexpr int OFF_DEG = OFF_OLD + RING * OLD_INTS * 4;
+    static constexpr int OFF_AUX = OFF_DEG + RING * DEG_INTS * 4;
+    static constexpr int BYTES = OFF_AUX + 2 * AUX_BYTES;  // weights: two slots, consumed before barrier (A)
+    static_assert(CR_INTS % 4 == 0 && OLD_INTS % 4 == 0 && AUX_BYTES % 16 == 0, "16-byte slot sizes");
+};
+
+// Where tile t's inputs sit inside its slot (element offsets) and how much each
+// copy moves. Every thread derives the same numbers from the tile's
+// merge-path coordinates.
+struct TileGeo {
+    int a0, b0, NA, NB;
+    int c_n;   // edge-stream elements copied (multiple of 4): at most NB + 6
+    int r_n;   // row-end elements copied (multiple of 4): at most NA + 6
+    int nold;  // rows whose old value / out-degree is staged: min(NA, NT)
+    int o_n;   // old-value elements copied (multiple of 4): at most nold + 6
+    __device__ __forceinline__ int col_off() const { return b0 & 3; }
+    __device__ __forceinline__ int rend_off() const { return c_n + ((a0 + 1) & 3); }
+    __device__ __forceinline__ int old_off() const { return a0 & 3; }
+};
+
+__device__ __forceinline__ TileGeo tile_geo(const SweepParams& p, int t)
+{
+    TileGeo g;
+    g.a0 = p.tile_row[t];
+    g.b0 = p.tile_nz[t];
+    g.NA = p.tile_row[t + 1] - g.a0;
+    g.NB = p.tile_nz[t + 1] - g.b0;
+    g.c_n = g.NB ? ((g.b0 + g.NB + 3) & ~3) - (g.b0 & ~3) : 0;
+    g.r_n = g.NA ? ((g.a0 + g.NA + 4) & ~3) - ((g.a0 + 1) & ~3) : 0;
+    g.nold = g.NA < NT ? g.NA : NT;
+    g.o_n = g.nold ? ((g.a0 + g.nold + 3) & ~3) - (g.a0 & ~3) : 0;
+    return g;
+}
+
+template <int MODE>
+__device__ __forceinline__ int aux_off(const TileGeo& g)
+{
+    return MODE == MODE_BF8 ? (g.b0 & 15) : (g.b0 & 3);
+}
+
+template <int MODE>
+__device__ __forceinline__ int aux_bytes(const TileGeo& g)
+{
+    if constexpr (MODE == MODE_PR) return 0;
+    else if constexpr (MODE == MODE_BF8) return g.NB ? ((g.b0 + g.NB + 15) & ~15) - (g.b0 & ~15) : 0;
+    else return 4 * g.c_n;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Waits for the phase of a ring mbarrier with the given parity, bounded by
+// timeout_ns of the global timer.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity, long long timeout_ns)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if ((long long)(globaltimer_ns() - t0) > timeout_ns) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load(void* dst, const void* src, uint32_t bytes, unsigned long long* bar,
+                                         uint64_t pol)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
+        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+        : "memory");
+}
+
+// Thread 0: starts the copies of tile t into the ring slot of fill q.
+template <int MODE>
+__device__ __forceinline__ void issue_fill(unsigned char* ring, unsigned long long* bars, uint32_t q,
+                                           const SweepParams& p, const uint32_t* x, int t, uint64_t pol_edge,
+                                           uint64_t pol_vertex)
+{
+    using R = Ring<MODE>;
+    const TileGeo g = tile_geo(p, t);
+    const int s3 = (int)(q % RING), s2 = (int)(q & 1u);
+    int* cr = (int*)(ring + R::OFF_CR) + s3 * R::CR_INTS;
+    const int ab = aux_bytes<MODE>(g);
+    uint32_t bytes = 4u * (uint32_t)(g.c_n + g.r_n) + (uint32_t)ab + 4u * (uint32_t)g.o_n * (R::BF ? 1u : 2u);
+    if (p.stall_fill && q == 0 && blockIdx.x == 0) bytes += 16u;  // test hook: this phase never completes
+    unsigned long long* bar = &bars[s3];
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier generic accesses of the slot first
+    mbar_expect_tx(bar, bytes);
+    if (g.c_n) tma_load(cr, p.colidx + (g.b0 & ~3), 4u * g.c_n, bar, pol_edge);
+    if (g.r_n) tma_load(cr + g.c_n, p.rowptr + ((g.a0 + 1) & ~3), 4u * g.r_n, bar, pol_vertex);
+    if constexpr (MODE != MODE_PR) {
+        unsigned char* aux = ring + R::OFF_AUX + s2 * R::AUX_BYTES;
+        if (ab) {
+            if constexpr (MODE == MODE_BF8) tma_load(aux, p.w8 + (g.b0 & ~15), (uint32_t)ab, bar, pol_edge);
+            else if constexpr (MODE == MODE_BF) tma_load(aux, p.w + (g.b0 & ~3), (uint32_t)ab, bar, pol_edge);
+            else tma_load(aux, p.val + (g.b0 & ~3), (uint32_t)ab, bar, pol_edge);
+        }
+    }
+    if (g.o_n) {
+        uint32_t* old = (uint32_t*)(ring + R::OFF_OLD) + s3 * R::OLD_INTS;
+        tma_load(old, x + (g.a0 & ~3), 4u * g.o_n, bar, pol_vertex);
+        if constexpr (!R::BF) {
+            uint32_t* deg = (uint32_t*)(ring + R::OFF_DEG) + s3 * R::OLD_INTS;
+            tma_load(deg, p.degf + (g.a0 & ~3), 4u * g.o_n, bar, pol_vertex);
+        }
+    }
+}
+
+// Issues the gathers of a tile's edges from the staged edge stream.
+__device__ __forceinline__ void gather_tile(uint32_t (&term)[IPT], const int* col, int NB, const uint32_t* x, int tid,
+                                            uint64_t pol_vertex, int own_lo, int own_n)
+{
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) {
+        const int j = tid + k * NT;
+        uint32_t xv = 0u;
+        if (j < NB) {
+            const int u = col[j];
+            xv = (unsigned)(u - own_lo) < (unsigned)own_n ? ld_weak_keep_b32(x + u, pol_vertex)
+                                                          : ld_relaxed_keep_b32(x + u, pol_vertex);
+        }
+        term[k] = xv;
+    }
+}
+
+// Edge term of the walk from a gathered value and the edge's weight / value.
+template <int MODE>
+__device__ __forceinline__ uint32_t edge_term(uint32_t xv, const unsigned char* aux, int k)
+{
+    if constexpr (MODE == MODE_BF8) return relax(xv, (uint32_t)aux[k]);
+    else if constexpr (MODE == MODE_BF) return relax(xv, ((const uint32_t*)aux)[k]);
+    else if constexpr (MODE == MODE_PR) return xv;
+    else return __float_as_uint(__uint_as_float(((const uint32_t*)aux)[k]) * __uint_as_float(xv));
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepParams p)
+{
+    using R = Ring<MODE>;
+    constexpr bool BF = MODE == MODE_BF || MODE == MODE_BF8;
+    constexpr bool LIVE_G = !BF;  // PageRank-type: live global sum
+
+    __shared__ SweepShared<false> sh;
+    extern __shared__ __align__(128) unsigned char ring[];  // tile staging ring
+
+    const int c = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    SyncBlock* sb = p.sync;
+    unsigned long long bar_target = 0;
+    uint32_t* X = (uint32_t*)p.x0;
+    const int row_lo = p.cta_row[c], row_hi = p.cta_row[c + 1];
+    const int tile_lo = p.cta_tile[c], tile_hi = p.cta_tile[c + 1];
+    const float inv_n = 1.0f / (float)p.n;
+
+    if (tid == 0) {
+        for (int s = 0; s < RING; ++s) mbar_init(&sh.fill_bar[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        sh.abort = 0;
+    }
+
+    // ---------------- initial values of the owned rows ----------------
+    {
+        double gpart = 0.0, tpart = 0.0;
+        for (int v = row_lo + tid; v < row_hi; v += NT) {
+            if constexpr (BF) {
+                X[v] = (v == (int)p.src) ? 0u : INF;
+            } else if constexpr (MODE == MODE_ADJ) {
+                float cv = p.base[v];
+                float l0 = p.init ? p.init[v] : cv;
+                X[v] = __float_as_uint(l0);
+                gpart += (double)l0;
+                tpart += fabs((double)cv);
+            } else {
+                float t = p.base ? p.base[v] : inv_n;
+                float r0 = p.init ? p.init[v] : t;
+                float dg = p.degf[v];
+                float x = (MODE == MODE_PR && dg > 0.0f) ? r0 / dg : r0;
+                X[v] = __float_as_uint(x);
+                if (dg > 0.0f) gpart += (double)r0;
+                tpart += (double)t;
+            }
+        }
+        if constexpr (!BF) {
+            block_sum2(sh, gpart, tpart);
+            if (tid == 0) {
+                atomicAdd(&sb->acc_g[2], gpart);
+                atomicAdd(&sb->T, tpart);
+                atomicAdd(&sb->stripe[(c % GSTRIPES) * GSTRIDE], gpart);
+            }
+        }
+    }
+    if (p.skip_barrier_cta0 && c == 0) return;  // test hook: the others' waits must run out
+    if (!grid_barrier(sb, p.nblocks, bar_target, p.timeout_ns)) return;
+
+    double T = 1.0;
+    if (tid == 0 && !BF) {
+        sh.T = ld_relaxed_f64(&sb->T);
+        sh.gprev = ld_relaxed_f64(&sb->acc_g[2]);
+    }
+    __syncthreads();
+    if constexpr (!BF) T = (MODE == MODE_ADJ || p.base) ? sh.T : 1.0;  // a uniform teleport sums to 1 exactly
+    const double tol = (MODE == MODE_ADJ) ? p.tol * T : p.tol;
+
+    const int own_lo = row_lo, own_n = p.own_l1 ? row_hi - row_lo : 0;
+    const uint64_t pol_edge = policy_evict_first();
+    const uint64_t pol_vertex = policy_evict_last();
+    int it = 0;
+    bool converged = false;
+    double last_res = 0.0;
+    uint32_t qbase = 0;  // ring fills of earlier sweeps (the fill of tile t is qbase + t - tile_lo)
+
+    for (; it < p.max_iters; ++it) {
+        const int slot = it % 3;
+        // per-thread partial sums in FP32 (few rows each); FP64 from the block reduction on
+        float res_part = 0.0f, g_part = 0.0f, dg_part = 0.0f;
+        uint32_t carry = Op<MODE>::identity();  // thread 0: partial of the row continuing into the next tile
+
+        // Pipeline: tile t+2's inputs are being copied and tile t+1's gathers are in
+        // flight while tile t is walked, scanned and finished.
+        uint32_t term[IPT];  // gathered values of the next tile
+        double gs = 0.0;     // warp 0: one stripe of the live global sum for the next tile
+        if (tid == 0) {
+            if (tile_lo < tile_hi) issue_fill<MODE>(ring, sh.fill_bar, qbase, p, X, tile_lo, pol_edge, pol_vertex);
+            if (tile_lo + 1 < tile_hi)
+                issue_fill<MODE>(ring, sh.fill_bar, qbase + 1, p, X, tile_lo + 1, pol_edge, pol_vertex);
+        }
+        if (tile_lo < tile_hi) {
+            const TileGeo g0 = tile_geo(p, tile_lo);
+            if (mbar_wait(&sh.fill_bar[qbase % RING], (qbase / RING) & 1u, p.timeout_ns)) {
+                const int* cr = (const int*)(ring + R::OFF_CR) + (qbase % RING) * R::CR_INTS;
+                gather_tile(term, cr + g0.col_off(), g0.NB, X, tid, pol_vertex, own_lo, own_n);
+            } else {
+                sh.abort = 1;
+                atomicCAS(&sb->err, 0, DAG_ERR_BARRIER_TIMEOUT);
+#pragma unroll
+                for (int k = 0; k < IPT; ++k) term[k] = 0u;
+            }
+            if constexpr (LIVE_G) {
+                if (warp == 0) gs = ld_relaxed_f64(&sb->stripe[lane * GSTRIDE]);
+            }
+        }
+
+        for (int t = tile_lo; t < tile_hi; ++t) {
+            const uint32_t q = qbase + (uint32_t)(t - tile_lo);
+            const TileGeo g = tile_geo(p, t);
+            const int a0 = g.a0, b0 = g.b0, NA = g.NA, NB = g.NB;
+            const int* rend = (const int*)(ring + R::OFF_CR) + (q % RING) * R::CR_INTS + g.rend_off();
+            // -------- tile t's edge terms into shared memory --------
+            {
+                const unsigned char* aux = ring + R::OFF_AUX + (q & 1u) * R::AUX_BYTES;
+                const int ao = aux_off<MODE>(g);
+#pragma unroll
+                for (int k = 0; k < IPT; ++k) {
+                    const int jj = tid + k * NT;
+                    if (jj < NB) sh.val[jj] = edge_term<MODE>(term[k], aux, ao + jj);
+                }
+                if constexpr (LIVE_G) {
+                    if (warp == 0) {
+                        // the tile's global term, formed once (FP64 is scarce on this part)
+                        const double G = warp_sum(gs);
+                        if (lane == 0)
+                            sh.gt = (MODE == MODE_ADJ) ? (float)((double)p.g_coef * G)
+                                                       : (float)((double)p.g_coef * (T - G));
+                    }
+                }
+            }
+            __syncthreads();  // (A) tile staged; every thread is done with the previous tile
+
+            const bool more = t + 1 < tile_hi;
+            const float gt = LIVE_G ? sh.gt : 0.0f;
+            // -------- tile t+2's copies, tile t+1's gathers --------
+            if (tid == 0 && t + 2 < tile_hi)
+                issue_fill<MODE>(ring, sh.fill_bar, q + 2, p, X, t + 2, pol_edge, pol_vertex);
+            if (more) {
+                const TileGeo g1 = tile_geo(p, t + 1);
+                const uint32_t q1 = q + 1;
+                if (mbar_wait(&sh.fill_bar[q1 % RING], (q1 / RING) & 1u, p.timeout_ns)) {
+                    const int* cr1 = (const int*)(ring + R::OFF_CR) + (q1 % RING) * R::CR_INTS;
+                    gather_tile(term, cr1 + g1.col_off(), g1.NB, X, tid, pol_vertex, own_lo, own_n);
+                } else {
+                    sh.abort = 1;
+                    atomicCAS(&sb->err, 0, DAG_ERR_BARRIER_TIMEOUT);
+#pragma unroll
+                    for (int k = 0; k < IPT; ++k) term[k] = 0u;
+                }
+                if constexpr (LIVE_G) {
+                    if (warp == 0) gs = ld_relaxed_f64(&sb->stripe[lane * GSTRIDE]);
+                }
+            }
+
+            // -------- merge-path walk over this thread's IPT items, block segmented scan --------
+            const WalkOut w = walk_tile<MODE, false>(sh, [&](int i) { return rend[i] - b0; }, NA, NB, carry);
+            __syncthreads();  // (B) warp run totals visible
+            if (sh.abort) {   // a staging wait ran out (error recorded): drain own copies, leave
+                if (tid == 0) {
+                    if (more) (void)mbar_wait(&sh.fill_bar[(q + 1) % RING], ((q + 1) / RING) & 1u, p.timeout_ns);
+                    if (t + 2 < tile_hi)
+                        (void)mbar_wait(&sh.fill_bar[(q + 2) % RING], ((q + 2) / RING) & 1u, p.timeout_ns);
+                }
+                return;  // the other CTAs' barrier waits end on the recorded error
+            }
+            const uint32_t E_last = finish_scan<MODE>(sh, w);
+            if (tid == 0) carry = E_last;  // partial of row NA for the next tile
+            __syncthreads();  // (C) row sums final
+
+            // -------- epilogue: new values of the rows this tile completed --------
+            const uint32_t* old = (const uint32_t*)(ring + R::OFF_OLD) + (q % RING) * R::OLD_INTS + g.old_off();
+            const uint32_t* degs = (const uint32_t*)(ring + R::OFF_DEG) + (q % RING) * R::DEG_INTS + g.old_off();
+#pragma unroll
+            for (int k = 0; k < IPT; ++k) {
+                const int r = tid + k * NT;
+                if (r >= NA) break;
+                const int v = a0 + r;
+                uint32_t xo_bits;
+                float dg = 0.0f;
+                if (k == 0) {  // the first NT rows' inputs came with the tile
+                    xo_bits = old[r];
+                    if constexpr (!BF) dg = __uint_as_float(degs[r]);
+                } else {
+                    xo_bits = ld_relaxed_b32(X + v);
+                    if constexpr (!BF) dg = ld_stream_f32(p.degf + v);
+                }
+                const uint32_t xnew = row_update<MODE>(p, v, sh.rowsum[r], xo_bits, dg, gt, res_part, g_part,
+                                                       dg_part);
+                st_relaxed_b32(X + v, xnew);
+            }
+            if constexpr (LIVE_G) {
+                const float s = warp_sum(dg_part);
+                dg_part = 0.0f;
+                if (lane == 0 && s != 0.0f) atomicAdd(&sb->stripe[(c % GSTRIPES) * GSTRIDE], (double)s);
+            }
+        }  // tiles
+        qbase += (uint32_t)(tile_hi - tile_lo);
+
+        // -------- end of sweep: residual, barrier, stopping rule --------
+        double res_d = (double)res_part, g_d = (double)g_part;
+        block_sum2(sh, res_d, g_d);
+        if (tid == 0 && res_d != 0.0) atomicAdd(&sb->acc_res[slot], res_d);
+        if (!grid_barrier(sb, p.nblocks, bar_target, p.timeout_ns)) return;
+        if (tid == 0) {
+            sh.res = ld_relaxed_f64(&sb->acc_res[slot]);
+            if (c == 0) {
+                const int dead = (it + 2) % 3;  // read by everyone before this barrier
+                sb->acc_res[dead] = 0.0;
+                sb->acc_g[dead] = 0.0;
+            }
+        }
+        __syncthreads();
+        last_res = sh.res;
+        if (last_res <= tol) {
+            converged = true;
+            ++it;
+            break;
+        }
+    }
+
+    // ---------------- output of the owned rows ----------------
+    for (int v = row_lo + tid; v < row_hi; v += NT) {
+        const uint32_t x = ld_relaxed_b32(X + v);
+        if constexpr (BF || MODE == MODE_ADJ || MODE == MODE_PRW) {
+            ((uint32_t*)p.out)[v] = x;
+        } else {
+            const float dg = p.degf[v];
+            ((float*)p.out)[v] = dg > 0.0f ? __uint_as_float(x) * dg : __uint_as_float(x);
+        }
+    }
+    if (tid == 0 && c == 0) {
+        sb->iters = it;
+        sb->residual = last_res;
+        sb->converged = converged ? 1 : 0;
+    }
+}
+
+const void* sweep_tma_kernel_ptr(int mode)
+{
+    switch (mode) {
+    case MODE_PR: return (const void*)sweep_tma_kernel<MODE_PR>;
+    case MODE_PRW: return (const void*)sweep_tma_kernel<MODE_PRW>;
+    case MODE_ADJ: return (const void*)sweep_tma_kernel<MODE_ADJ>;
+    case MODE_BF: return (const void*)sweep_tma_kernel<MODE_BF>;
+    default: return (const void*)sweep_tma_kernel<MODE_BF8>;
+    }
+}
+
+size_t sweep_tma_ring_bytes(int mode)
+{
+    switch (mode) {
+    case MODE_PR: return Ring<MODE_PR>::BYTES;
+    case MODE_PRW: return Ring<MODE_PRW>::BYTES;
+    case MODE_ADJ: return Ring<MODE_ADJ>::BYTES;
+    case MODE_BF: return Ring<MODE_BF>::BYTES;
+    default: return Ring<MODE_BF8>::BYTES;
+    }
+}
+
+}  // namespace dag

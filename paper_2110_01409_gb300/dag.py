@@ -29,7 +29,7 @@ EXPORTS = (
     "dag_plan_create", "dag_plan_destroy", "dag_plan_out_degree", "dag_partition", "dag_workers",
     "dag_pagerank", "dag_sssp", "dag_ppr_batched", "dag_sssp_batched", "dag_transpose",
     "dag_normalize_weights", "dag_pagerank_adjoint", "dag_strerror", "dag_last_error_message",
-    "dag_debug_skip_barrier_once", "dag_pagerank_noalloc", "dag_gather_f32", "dag_plan_set_worker_cap",
+    "dag_debug_skip_barrier_once", "dag_debug_stall_staging_once", "dag_pagerank_noalloc", "dag_gather_f32", "dag_plan_set_worker_cap",
     "dag_sssp_u8", "dag_probe_gather", "dag_access_matrix",
 )
 
@@ -91,6 +91,7 @@ def lib():
             L.dag_last_error_message.argtypes = []
             L.dag_last_error_message.restype = ctypes.c_char_p
             L.dag_debug_skip_barrier_once.argtypes = [_vp, _i32]
+            L.dag_debug_stall_staging_once.argtypes = [_vp, _i32]
             L.dag_gather_f32.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp]
             L.dag_plan_set_worker_cap.argtypes = [_vp, _i32]
             L.dag_access_matrix.argtypes = [_vp, _i32, _vp, _vp]
@@ -193,6 +194,9 @@ class Plan:
 
     def debug_skip_barrier_once(self, timeout_ms: int):
         _raise(lib().dag_debug_skip_barrier_once(self.h, timeout_ms), False)
+
+    def debug_stall_staging_once(self, timeout_ms: int):
+        _raise(lib().dag_debug_stall_staging_once(self.h, timeout_ms), False)
 
 
 def pagerank(plan: Plan, d=0.85, tol=1e-6, variant="delayed", delta=256, max_iters=1000, teleport=None,

@@ -198,6 +198,31 @@ def test_barrier_timeout_is_reported_and_context_survives(dag):
     assert st["converged"] and _l1(r, oracle.dense_pagerank(g)) <= 1e-5
 
 
+@pytest.mark.parametrize("algo", ["pagerank", "sssp8"])
+def test_staging_wait_timeout_is_reported_and_context_survives(dag, algo):
+    # the asynchronous sweep's bounded wait for a tile's TMA copies runs out (its mbarrier phase is
+    # announced 16 bytes short); the call reports it and the next solve on the plan is fine
+    g = I.rmat(12, 16, seed=2)
+    plan = _plan(dag, g)
+    w8 = torch.from_numpy(I.weights_u32(g, 1).astype(np.uint8)).cuda()
+
+    def solve():
+        if algo == "pagerank":
+            return dag.pagerank(plan, 0.85, 1e-6, "async", 0)
+        return dag.sssp(plan, 3, w8, "async", 0)
+
+    plan.debug_stall_staging_once(100)
+    with pytest.raises(dag.DagError) as ei:
+        solve()
+    assert ei.value.code == dag.ERR_BARRIER_TIMEOUT
+    out, st = solve()
+    assert st["converged"]
+    if algo == "pagerank":
+        assert _l1(out, oracle.pagerank_fixed_point(g, 0.85)) <= 1e-5
+    else:
+        assert np.array_equal(_u32(out), oracle.dijkstra(g, I.weights_u32(g, 1), 3))
+
+
 def test_flush_counts_follow_delta(dag):
     g = I.rmat(18, 16, seed=5)  # several tiles per CTA
     plan = _plan(dag, g)
