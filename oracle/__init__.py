@@ -14,6 +14,9 @@ Two parts:
 * ``dense.py``: the plain linear-algebra definitions (numpy, fp64) that pin the
   above on small graphs: the PageRank fixed point as a dense solve, the dense
   adjoint, and central finite differences.
+* ``frontier.py``: synchronous Bellman-Ford with work skipped where no input
+  changed (conditionally processed tiles), counting the edges each sweep
+  touches at the GPU's tile granularity.
 
 Parity is pinned for every function here by the tests under ``tests/`` against
 closed forms, brute force or a dense solve; none is "parity unpinned".

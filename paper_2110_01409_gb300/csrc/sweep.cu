@@ -102,19 +102,13 @@ __device__ __forceinline__ void stage_issue(Stage<MODE>& st, const SweepParams& 
 }
 
 // Issues tile t's gathers of the state vector (sync: previous iterate; delayed:
-// this SM's view of the live array; async: the live array in L2).
+// this SM's view of the live array, or the array in L2 with DAG_READ_COHERENT).
 // lbuf/lbase/lcnt: the CTA's own unflushed rows [lbase, lbase + lcnt), read from
 // shared memory instead of the global array (local reads, Sec. III-C); lcnt = 0
 // reads everything from the global array.
-// own_lo/own_n: the CTA's own vertex block. Only this CTA writes those values, and
-// its barriers order its own stores before its later loads, so an ordinary
-// (L1-cacheable) load of them is as fresh as a gpu-scope load: the async form
-// may read its own block that way and other blocks through L2 (own_n = 0: all
-// through L2).
 template <int MODE>
 __device__ __forceinline__ void stage_gather(Stage<MODE>& st, const uint32_t* xin, int tid, bool weak,
-                                             uint64_t pol_vertex, const uint32_t* lbuf, int lbase, int lcnt,
-                                             int own_lo, int own_n)
+                                             uint64_t pol_vertex, const uint32_t* lbuf, int lbase, int lcnt)
 {
 #pragma unroll
     for (int q = 0; q < IPT; ++q) {
@@ -122,10 +116,9 @@ __device__ __forceinline__ void stage_gather(Stage<MODE>& st, const uint32_t* xi
         uint32_t term = 0u;
         if (j < st.NB) {
             const unsigned off = (unsigned)(st.col[q] - lbase);
-            const bool l1 = weak || (unsigned)(st.col[q] - own_lo) < (unsigned)own_n;
             const uint32_t xv = off < (unsigned)lcnt ? lbuf[off]
-                              : l1 ? ld_weak_keep_b32(xin + st.col[q], pol_vertex)
-                                   : ld_relaxed_keep_b32(xin + st.col[q], pol_vertex);
+                              : weak ? ld_weak_keep_b32(xin + st.col[q], pol_vertex)
+                                     : ld_relaxed_keep_b32(xin + st.col[q], pol_vertex);
             if constexpr (MODE == MODE_BF || MODE == MODE_BF8) term = relax(xv, st.aux[q]);
             else if constexpr (MODE == MODE_PR) term = xv;
             else term = __float_as_uint(__uint_as_float(st.aux[q]) * __uint_as_float(xv));
@@ -206,7 +199,6 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
     // sync reads the previous iterate with ordinary loads; async reads the live
     // array coherently (L2); delayed follows p.read_mode
     const bool weak = SYNC || (DELAYED && p.read_mode != READ_COHERENT);
-    const int own_lo = row_lo, own_n = (VAR == DAG_ASYNC && p.own_l1) ? row_hi - row_lo : 0;
     const uint64_t pol_edge = policy_evict_first();
     const uint64_t pol_vertex = policy_evict_last();
     int buf_first = row_lo, buf_cnt = 0;
@@ -235,7 +227,7 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
         Stage<MODE> nx;
         if (tile_lo < tile_hi) {
             stage_issue<MODE>(nx, p, xin, tile_lo, tid, weak, pol_edge, pol_vertex);
-            stage_gather<MODE>(nx, xin, tid, weak, pol_vertex, s_buf, 0, 0, own_lo, own_n);
+            stage_gather<MODE>(nx, xin, tid, weak, pol_vertex, s_buf, 0, 0);
             if constexpr (LIVE_G) {
                 if (warp == 0) nx.gs = ld_relaxed_f64(&sb->stripe[lane * GSTRIDE]);
             }
@@ -310,7 +302,7 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
             if (tid == 0) carry = E_last;  // partial of row NA for the next tile
             if (more)
                 stage_gather<MODE>(nx, xin, tid, weak, pol_vertex, s_buf, buf_first,
-                                   (DELAYED && p.local_read) ? buf_cnt : 0, own_lo, own_n);
+                                   (DELAYED && p.local_read) ? buf_cnt : 0);
             __syncthreads();  // (C) row sums final
 
             // -------- epilogue: new values of the rows this tile completed --------
@@ -407,14 +399,14 @@ using KernelFn = void (*)(const SweepParams);
 static KernelFn kernel_for(int mode, int variant)
 {
     if (variant == DAG_ASYNC) return (KernelFn)sweep_tma_kernel_ptr(mode);
-    static const KernelFn table[5][3] = {
-        {sweep_kernel<MODE_PR, DAG_SYNC>, sweep_kernel<MODE_PR, DAG_ASYNC>, sweep_kernel<MODE_PR, DAG_DELAYED>},
-        {sweep_kernel<MODE_PRW, DAG_SYNC>, sweep_kernel<MODE_PRW, DAG_ASYNC>, sweep_kernel<MODE_PRW, DAG_DELAYED>},
-        {sweep_kernel<MODE_ADJ, DAG_SYNC>, sweep_kernel<MODE_ADJ, DAG_ASYNC>, sweep_kernel<MODE_ADJ, DAG_DELAYED>},
-        {sweep_kernel<MODE_BF, DAG_SYNC>, sweep_kernel<MODE_BF, DAG_ASYNC>, sweep_kernel<MODE_BF, DAG_DELAYED>},
-        {sweep_kernel<MODE_BF8, DAG_SYNC>, sweep_kernel<MODE_BF8, DAG_ASYNC>, sweep_kernel<MODE_BF8, DAG_DELAYED>},
+    static const KernelFn table[5][2] = {
+        {sweep_kernel<MODE_PR, DAG_SYNC>, sweep_kernel<MODE_PR, DAG_DELAYED>},
+        {sweep_kernel<MODE_PRW, DAG_SYNC>, sweep_kernel<MODE_PRW, DAG_DELAYED>},
+        {sweep_kernel<MODE_ADJ, DAG_SYNC>, sweep_kernel<MODE_ADJ, DAG_DELAYED>},
+        {sweep_kernel<MODE_BF, DAG_SYNC>, sweep_kernel<MODE_BF, DAG_DELAYED>},
+        {sweep_kernel<MODE_BF8, DAG_SYNC>, sweep_kernel<MODE_BF8, DAG_DELAYED>},
     };
-    return table[mode][variant];
+    return table[mode][variant == DAG_DELAYED ? 1 : 0];
 }
 
 // The sweep kernel of (mode, variant), for launches that build their own
