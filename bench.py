@@ -38,7 +38,7 @@ PR_DELTA, SSSP_DELTA = 32, 32  # fixed-delta runs of the variant table and the C
 DELTAS = (0, 32, 256, 4096)
 WORKLOAD = (f"rmat{SCALE}: pagerank d=0.85 tol=1e-6 + sssp x{N_SOURCES} sources, "
             f"delayed method, delta picked per algorithm over {list(DELTAS)} "
-            f"(delta 0 also with own-block L1 reads)")
+            f"(delta 0 also with own-block L1 reads, and for sssp the tile frontier)")
 
 
 def _peaks():
@@ -124,13 +124,19 @@ def _cand(c):
     return str(c["delta"]) + ("" if c["reads"] == "refresh" else "+" + c["reads"])
 
 
-def algorithmic_bytes(n, m, kind):
+def algorithmic_bytes(n, m, kind, edges=None):
     """Compulsory bytes of one sweep (gathers of the state vector count as L2
     hits: the 4n-byte vector fits in L2): rowptr 4(n+1), colidx 4m, own old
     value 4n + new value 4n, plus per-vertex out-degree 4n (PageRank) or the
-    per-edge weight (Bellman-Ford: 4m as uint32, m as uint8)."""
-    base = 4 * (n + 1) + 4 * m + 8 * n
-    return base + {"pr": 4 * n, "bf": 4 * m, "bf8": m}[kind]
+    per-edge weight (Bellman-Ford: 4m as uint32, m as uint8). With `edges`
+    (a frontier launch: the edges it ran over all its sweeps) the result is
+    per launch: the per-edge terms count those edges, the per-vertex ones are
+    left to the caller's sweep count."""
+    per_vertex = 4 * (n + 1) + 8 * n + (4 * n if kind == "pr" else 0)
+    per_edge = 4 + {"pr": 0, "bf": 4, "bf8": 1}[kind]
+    if edges is None:
+        return per_vertex + per_edge * m
+    return per_edge * edges, per_vertex
 
 
 def run_gpu(args):
@@ -165,15 +171,16 @@ def run_gpu(args):
     from paper_2110_01409_gb300 import autotune
 
     cands = [("delayed", dl) for dl in DELTAS] + [("delayed", 0, "own_l1")]
+    cands_bf = cands + [("delayed", 0, "frontier"), ("delayed", 0, "own_l1+frontier")]
     tune_pr = autotune.tune(plan, "pagerank", candidates=cands, worker_fractions=[1.0], trials=2, cache=None)
-    tune_bf = autotune.tune(plan, "sssp", candidates=cands, worker_fractions=[1.0], trials=2, cache=None,
+    tune_bf = autotune.tune(plan, "sssp", candidates=cands_bf, worker_fractions=[1.0], trials=2, cache=None,
                             src=int(srcs[0]), w=w8_d)
     plan.set_worker_cap(0)
     pr_dl, bf_dl = tune_pr["delta"], tune_bf["delta"]
     pr_rd, bf_rd = tune_pr["reads"], tune_bf["reads"]
 
     # ---- warm-up with statuses (also records per-solve sweeps) ----
-    pr_iters, bf_iters = [], []
+    pr_iters, bf_iters, bf_edges = [], [], []
     for _ in range(args.warmup):
         _, st = dag.pagerank(plan, 0.85, 1e-6, "delayed", pr_dl, 1000, out=rank_out, reads=pr_rd)
         assert st["converged"], st
@@ -183,6 +190,7 @@ def run_gpu(args):
             _, st = dag.sssp(plan, int(s), w8_d, "delayed", bf_dl, n + 1, out=dist_out[k], reads=bf_rd)
             assert st["converged"], st
             its.append(st["iters"])
+            bf_edges.append(st["edges_processed"])
         bf_iters.append(its)
     torch.cuda.synchronize()
 
@@ -227,28 +235,38 @@ def run_gpu(args):
     pr_sweeps = statistics.mean(pr_iters + [st_pr["iters"]])
     bf_sweeps = statistics.mean(x for row in bf_iters for x in row)
     pr_bytes = algorithmic_bytes(n, m, "pr") * pr_sweeps
-    bf_bytes = algorithmic_bytes(n, m, "bf8") * bf_sweeps
+    bf_edges_mean = statistics.mean(bf_edges)  # m per sweep, or the frontier's edges per launch
+    e_bytes, v_bytes = algorithmic_bytes(n, m, "bf8", edges=bf_edges_mean)
+    bf_bytes = e_bytes + v_bytes * bf_sweeps
     peak, peak_kind = _peaks()
     # dominant kernel by total time in the step
     # delta 0 runs the asynchronous form's TMA-staged kernel, delta > 0 the register-staged one
-    kname = lambda mode, dl: f"sweep_kernel<{mode},DELAYED>" if dl > 0 else f"sweep_tma_kernel<{mode}>"  # noqa: E731
+    kname = lambda mode, dl, rd="": (f"sweep_kernel<{mode},DELAYED>" if dl > 0 else  # noqa: E731
+                                     f"sweep_tma_kernel<{mode}{',frontier' if 'frontier' in rd else ''}>")
     if bf_ms * N_SOURCES >= pr_ms:
-        dom, dom_bytes, dom_ms, dom_sweeps = kname("BF8", bf_dl), bf_bytes, bf_ms, bf_sweeps
+        dom, dom_bytes, dom_ms, dom_sweeps = kname("BF8", bf_dl, bf_rd), bf_bytes, bf_ms, bf_sweeps
     else:
         dom, dom_bytes, dom_ms, dom_sweeps = kname("PR", pr_dl), pr_bytes, pr_ms, pr_sweeps
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
-    traffic = _recorded_traffic(dom, dom_sweeps)
+    traffic = _recorded_traffic(dom, dom_sweeps, bf_edges_mean if dom.startswith("sweep_tma_kernel<BF8") else None)
 
     # ---- the sweep's real ceiling: one streamed gather pass over the same colidx (dag_probe_gather) ----
     coherent = bf_dl == 0  # the async sweep gathers with relaxed gpu-scope loads
     probe_ms = dag.probe_gather(plan, rank_out, coherent=coherent, repeats=5)
+    # the launch against the probe's time for the edges it ran (sweeps * m, or the frontier's count)
     bf_sweep_ms = bf_ms / bf_sweeps
     gather_floor = {"probe_ms_per_pass": round(probe_ms, 4), "loads": "relaxed (L2)" if coherent else "ordinary",
-                    "sweep_ms": round(bf_sweep_ms, 4), "frac": round(probe_ms / bf_sweep_ms, 3),
-                    "kernel": kname("BF8", bf_dl)}
+                    "sweep_ms": round(bf_sweep_ms, 4), "edges_per_launch_over_m": round(bf_edges_mean / m, 3),
+                    "frac": round(probe_ms * (bf_edges_mean / m) / bf_ms, 3),
+                    "kernel": kname("BF8", bf_dl, bf_rd)}
 
     # ---- e2e through the public API from pinned host buffers ----
-    e2e = run_e2e(args, g, w, srcs, dev, dag, torch, (pr_dl, pr_rd), (bf_dl, bf_rd)) if args.e2e else None
+    # e2e builds a plan per step: the frontier's maps (one out-CSR sort per plan, ~9 ms at this size)
+    # cost more than they save over one step's 8 solves, so e2e runs the same read path without them
+    bf_rd_e2e = bf_rd.replace("+frontier", "").replace("frontier", "refresh")
+    e2e = run_e2e(args, g, w, srcs, dev, dag, torch, (pr_dl, pr_rd), (bf_dl, bf_rd_e2e)) if args.e2e else None
+    if e2e is not None:
+        e2e["sssp_reads"] = bf_rd_e2e
 
     detail = {}
     if args.extras and rank == 0:
@@ -312,10 +330,11 @@ def sweep_source_hash():
     return h.hexdigest()
 
 
-def _recorded_traffic(kernel, sweeps):
+def _recorded_traffic(kernel, sweeps, edges=None):
     """DRAM bytes per launch (read + write) from profiles/sweep_traffic.txt, a
     summary of an ncu capture of the same kernel on the same workload, scaled
-    by the launch's sweeps; None when the kernel source changed since."""
+    by the launch's sweeps (a frontier launch: by the edges it ran); None when
+    the kernel source changed since."""
     path = os.path.join(ROOT, "profiles", "sweep_traffic.txt")
     try:
         rec = {}
@@ -326,6 +345,8 @@ def _recorded_traffic(kernel, sweeps):
                     rec[k.strip()] = v.strip()
         if rec.get("sweep_source_sha256") != sweep_source_hash():
             return None
+        if "frontier" in kernel:
+            return int(float(rec[f"{kernel} rmat{SCALE} dram_bytes_per_edge_run"]) * edges)
         per_sweep = float(rec[f"{kernel} rmat{SCALE} dram_bytes_per_sweep"])
         return int(per_sweep * sweeps)
     except Exception:
@@ -366,25 +387,42 @@ def run_e2e(args, g, w, srcs, dev, dag, torch, pr_choice, bf_choice):
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
 
-def run_detail(g, w, srcs, plan, w_d, dag, torch, args):
-    """Per-variant sweeps and times (3 trials) on the same graph; paper's variants table."""
+def _variant_rows(dag, torch, plan, g, src, w_d, variants, trials=3):
+    """Median time and sweeps of each (name, variant, delta, reads) row for PageRank and
+    Bellman-Ford; frontier rows are Bellman-Ford only. Also the edges the SSSP solves ran."""
     res = {}
-    trials = 3
-    for name, var, dl, rd in [("sync", "sync", 0, "refresh"), ("async", "async", 0, "refresh"),
-                              ("async_own_l1", "async", 0, "own_l1"), ("delayed32", "delayed", 32, "refresh"), ("delayed256", "delayed", 256, "refresh"),
-                              ("delayed4096", "delayed", 4096, "refresh"),
-                              ("delayed4096_local", "delayed", 4096, "local")]:
+    for name, var, dl, rd in variants:
         pr_it, pr_ms, bf_it, bf_ms = [], [], [], []
         for _ in range(trials):
-            _, st = dag.pagerank(plan, 0.85, 1e-6, var, dl, 1000, reads=rd)
-            pr_it.append(st["iters"])
-            pr_ms.append(st["ms"])
-            _, st = dag.sssp(plan, int(srcs[0]), w_d, var, dl, g.n + 1, reads=rd)
+            if "frontier" not in rd:
+                _, st = dag.pagerank(plan, 0.85, 1e-6, var, dl, 1000, reads=rd)
+                assert st["converged"], (name, st)
+                pr_it.append(st["iters"])
+                pr_ms.append(st["ms"])
+            _, st = dag.sssp(plan, src, w_d, var, dl, g.n + 1, reads=rd)
+            assert st["converged"], (name, st)
             bf_it.append(st["iters"])
             bf_ms.append(st["ms"])
-        res[name] = {"pr_sweeps": pr_it, "pr_ms_median": round(statistics.median(pr_ms), 3),
-                     "sssp_sweeps": bf_it, "sssp_ms_median": round(statistics.median(bf_ms), 3)}
+        row = {"sssp_sweeps": bf_it, "sssp_ms_median": round(statistics.median(bf_ms), 3),
+               "sssp_edges_per_m": round(st["edges_processed"] / max(g.m, 1), 2)}
+        if pr_ms:
+            row.update({"pr_sweeps": pr_it, "pr_ms_median": round(statistics.median(pr_ms), 3)})
+        res[name] = row
+    torch.cuda.synchronize()
     return res
+
+
+VARIANT_ROWS = [("sync", "sync", 0, "refresh"), ("async", "async", 0, "refresh"),
+                ("async_own_l1", "async", 0, "own_l1"), ("sync_frontier", "sync", 0, "frontier"),
+                ("async_frontier", "async", 0, "frontier"), ("async_own_l1_frontier", "async", 0, "own_l1+frontier"),
+                ("delayed32", "delayed", 32, "refresh"), ("delayed256", "delayed", 256, "refresh"),
+                ("delayed4096", "delayed", 4096, "refresh"), ("delayed4096_local", "delayed", 4096, "local")]
+
+
+def run_detail(g, w, srcs, plan, w_d, dag, torch, args):
+    """Per-variant sweeps and times (3 trials) on the benchmark graph (Bellman-Ford with
+    four-byte weights); the paper's variants table."""
+    return _variant_rows(dag, torch, plan, g, int(srcs[0]), w_d, VARIANT_ROWS)
 
 
 def run_config3(dag, torch):
@@ -394,10 +432,7 @@ def run_config3(dag, torch):
     import paper_2110_01409_gb300.inputs as I
 
     out = {}
-    variants = [("sync", "sync", 0, "refresh"), ("async", "async", 0, "refresh"),
-                ("async_own_l1", "async", 0, "own_l1"), ("delayed32", "delayed", 32, "refresh"),
-                ("delayed256", "delayed", 256, "refresh"), ("delayed4096", "delayed", 4096, "refresh"),
-                ("delayed4096_local", "delayed", 4096, "local")]
+    variants = VARIANT_ROWS
     for gname, make in (("banded24", lambda: I.banded(1 << 24, 15, 1024, 1, seed=3)),
                         ("er23", lambda: I.erdos_renyi(1 << 23, 16, seed=3))):
         t0 = time.time()
@@ -408,19 +443,7 @@ def run_config3(dag, torch):
         src = int(I.sources(g, 1, seed=3)[0])
         tab = {"n": g.n, "m": g.m, "graph_gen_s": round(gen_s, 1),
                "locality_P32": round(dag.locality(dag.access_matrix(pl, 32))["diag_share"], 4)}
-        for name, var, dl, rd in variants:
-            pr_ms, pr_it, bf_ms, bf_it = [], [], [], []
-            for _ in range(3):
-                _, st = dag.pagerank(pl, 0.85, 1e-6, var, dl, 1000, reads=rd)
-                assert st["converged"], (gname, name, st)
-                pr_ms.append(st["ms"])
-                pr_it.append(st["iters"])
-                _, st = dag.sssp(pl, src, w8, var, dl, g.n + 1, reads=rd)
-                assert st["converged"], (gname, name, st)
-                bf_ms.append(st["ms"])
-                bf_it.append(st["iters"])
-            tab[name] = {"pr_sweeps": pr_it, "pr_ms_median": round(statistics.median(pr_ms), 3),
-                         "sssp_sweeps": bf_it, "sssp_ms_median": round(statistics.median(bf_ms), 3)}
+        tab.update(_variant_rows(dag, torch, pl, g, src, w8, variants))
         pl.close()
         del w8
         out[gname] = tab
@@ -444,18 +467,7 @@ def run_access(g, plan, dag, torch):
     # global vs local reads (Sec. III-C) where a worker reads mostly its own block
     wb = torch.from_numpy(I.weights_u32(banded, SEED).astype(np.uint8)).cuda()
     src = int(I.sources(banded, 1, seed=SEED)[0])
-    tab = {}
-    for name, var, dl, rd in [("sync", "sync", 0, "refresh"), ("async", "async", 0, "refresh"),
-                              ("async_own_l1", "async", 0, "own_l1"), ("delayed4096", "delayed", 4096, "refresh"),
-                              ("delayed4096_local", "delayed", 4096, "local")]:
-        pr_ms, bf_ms = [], []
-        for _ in range(3):
-            _, st_pr = dag.pagerank(bplan, 0.85, 1e-6, var, dl, 1000, reads=rd)
-            _, st_bf = dag.sssp(bplan, src, wb, var, dl, banded.n + 1, reads=rd)
-            pr_ms.append(st_pr["ms"])
-            bf_ms.append(st_bf["ms"])
-        tab[name] = {"pr_sweeps": st_pr["iters"], "pr_ms_median": round(statistics.median(pr_ms), 3),
-                     "sssp_sweeps": st_bf["iters"], "sssp_ms_median": round(statistics.median(bf_ms), 3)}
+    tab = _variant_rows(dag, torch, bplan, banded, src, wb, VARIANT_ROWS)
     out["banded_variants"] = tab
     bplan.close()
     torch.cuda.synchronize()

@@ -73,7 +73,7 @@ typedef struct {
     int32_t workers;         /* CTAs that held a vertex block (the paper's thread count) */
     int32_t delta;           /* buffer size used (0 for sync/async) */
     int64_t flushes;         /* buffer flushes over the whole solve (delayed only) */
-    int64_t edges_processed; /* m * iters */
+    int64_t edges_processed; /* m * iters; with DAG_SSSP_FRONTIER the edges of the tiles run */
 } dag_stats;
 
 typedef struct dag_plan dag_plan; /* opaque */
@@ -140,6 +140,19 @@ int dag_plan_set_worker_cap(dag_plan* plan, int32_t max_workers);
  * caller (or to a tuner).
  */
 #define DAG_READ_OWN_L1 16
+/*
+ * Frontier Bellman-Ford (dag_sssp / dag_sssp_u8, synchronous or asynchronous
+ * form; the conditionally written updates of Sec. V): a merge-path tile of
+ * in-edges runs in a sweep only when one of its edges' sources got a smaller
+ * distance in the previous sweep (or the tile lies between such an edge and
+ * the end of its target's row); sweep 0 runs every tile. Distances are those
+ * of the plain sweep (the synchronous trajectory is the same, sweep for
+ * sweep); dag_stats.edges_processed counts the edges actually run. The first
+ * solve with a launch shape builds the out-CSR and two int32 maps per edge
+ * (about 8m + 4n bytes, kept in the plan). DAG_ERR_INVALID for PageRank or
+ * the delayed form.
+ */
+#define DAG_SSSP_FRONTIER 32
 
 /*
  * PageRank (Sec. IV-A; stopping rule Sec. IV):
@@ -165,7 +178,8 @@ int dag_pagerank(dag_plan* plan, float d, double tol, dag_variant variant, int32
  * "unconditionally storing updates"); stops after a sweep that lowered no
  * value. d_w: uint32 weight per in-edge (device, [m]); d_dist (device,
  * uint32 [n]) receives the distances, 0xFFFFFFFF for unreachable vertices.
- * flags: DAG_READ_* (delayed form only) | DAG_READ_OWN_L1 (async form only).
+ * flags: DAG_READ_* (delayed form only) | DAG_READ_OWN_L1 (async form only) |
+ * DAG_SSSP_FRONTIER (sync and async forms).
  */
 int dag_sssp(dag_plan* plan, uint32_t src, dag_variant variant, int32_t delta, int32_t max_iters,
              const uint32_t* d_w, uint32_t* d_dist, int32_t flags, dag_stats* h_stats, void* stream);
@@ -298,6 +312,10 @@ int dag_probe_gather(const int32_t* d_idx, int64_t m, const float* d_x, int32_t 
  * counts a block's reads of its own values. 1 <= workers <= 4096.
  */
 int dag_access_matrix(dag_plan* plan, int32_t workers, uint64_t* d_counts, void* stream);
+
+/* Items (rows + in-edges) per merge-path tile of the sweeps, the unit the
+ * frontier runs or skips; fixed when the library is compiled. */
+int32_t dag_tile_items(void);
 
 /* Names an error code. Never NULL. */
 const char* dag_strerror(int code);

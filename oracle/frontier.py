@@ -15,6 +15,10 @@ in-edge u -> v whose source u got a smaller distance in sweep s-1, or lies
 between such an edge's tile and the tile holding v's row end. A processed tile
 relaxes its edges (a row whose start lies in a skipped tile takes only the
 edges of processed tiles); a skipped tile leaves its rows as they are.
+Dense sweeps: when the out-degrees of the rows changed in sweep s-1 sum to
+more than `sparse` per tile, sweep s processes every tile (such changes reach
+nearly every tile anyway, and marking them would cost more than it saves);
+`sparse=None` never takes that shortcut.
 
 For the synchronous sweep this gives exactly the plain trajectory: a row none
 of whose in-neighbours changed cannot change, and edges from unchanged
@@ -51,7 +55,7 @@ def block_tiles(g, start, TILE):
     return edge_tile, end_tile, ntiles
 
 
-def sssp_frontier_sync(g, w, src, start, TILE, max_iters=None):
+def sssp_frontier_sync(g, w, src, start, TILE, max_iters=None, sparse=4.0):
     """Synchronous frontier Bellman-Ford. Returns (dist uint32, sweeps, edges
     processed per sweep, converged). Distances saturate at INF - 1 as in the
     plain oracle; INF marks unreachable vertices."""
@@ -67,16 +71,13 @@ def sssp_frontier_sync(g, w, src, start, TILE, max_iters=None):
     dist[src] = 0
     active = np.ones(T, dtype=bool)
     edges, it, ok = [], 0, False
+    src_of_edge = colidx.astype(np.int64)
     while it < max_iters:
         # relax the edges of processed tiles against the previous iterate
         new = dist.copy()
-        for e in range(m):
-            if not active[edge_tile[e]]:
-                continue
-            u, v = int(colidx[e]), int(row_of_edge[e])
-            if dist[u] == INF:
-                continue
-            new[v] = min(new[v], min(dist[u] + int(w[e]), INF - 1))
+        run = active[edge_tile] & (dist[src_of_edge] != INF)
+        cand = np.minimum(dist[src_of_edge[run]] + w[run], INF - 1)
+        np.minimum.at(new, row_of_edge[run], cand)
         changed = new < dist
         edges.append(int(edges_in_tile[active].sum()))
         it += 1
@@ -84,9 +85,15 @@ def sssp_frontier_sync(g, w, src, start, TILE, max_iters=None):
         if not changed.any():
             ok = True
             break
-        # tiles of the next sweep: from each edge out of a changed source to its row's end
-        active = np.zeros(T, dtype=bool)
-        for e in range(m):
-            if changed[colidx[e]]:
-                active[edge_tile[e]: end_tile[row_of_edge[e]] + 1] = True
+        # tiles of the next sweep: every tile after a dense sweep, otherwise from each edge out
+        # of a changed source to its row's end (a difference array over tile ranges
+        # [edge_tile[e], end_tile[row(e)]])
+        hit = changed[src_of_edge]
+        if sparse is not None and int(hit.sum()) > sparse * T:  # out-degree sum of the changed rows
+            active = np.ones(T, dtype=bool)
+            continue
+        cover = np.zeros(T + 1, dtype=np.int64)
+        np.add.at(cover, edge_tile[hit], 1)
+        np.add.at(cover, end_tile[row_of_edge[hit]] + 1, -1)
+        active = np.cumsum(cover[:T]) > 0
     return dist.astype(np.uint32), it, np.array(edges, dtype=np.int64), ok

@@ -28,6 +28,7 @@ _lock = threading.Lock()
 # (variant, delta[, reads]); reads defaults to "refresh" (see dag.READ_MODES)
 SINGLE_CANDIDATES = [("sync", 0), ("async", 0), ("async", 0, "own_l1"), ("delayed", 32), ("delayed", 256),
                      ("delayed", 4096), ("delayed", 4096, "local")]
+SSSP_EXTRA = [("async", 0, "frontier"), ("async", 0, "own_l1+frontier")]  # Bellman-Ford only
 BATCH_CANDIDATES = [("sync", 0), ("async", 0), ("delayed", 4), ("delayed", 16)]
 WORKER_FRACTIONS = [1.0, 0.5]
 
@@ -99,7 +100,8 @@ def tune(plan: dag.Plan, algo: str, candidates=None, worker_fractions=None, tria
     (Sec. IV-C).
     """
     batched = algo.endswith("batched")
-    cands = [_norm(c) for c in (candidates or (BATCH_CANDIDATES if batched else SINGLE_CANDIDATES))]
+    default = BATCH_CANDIDATES if batched else SINGLE_CANDIDATES + (SSSP_EXTRA if algo == "sssp" else [])
+    cands = [_norm(c) for c in (candidates or default)]
     fracs = worker_fractions or WORKER_FRACTIONS
     B = int(kw["V"].shape[1]) if algo == "ppr_batched" else (int(kw["srcs"].numel()) if algo == "sssp_batched" else 1)
     key = f"{fingerprint(plan)}|{algo}|B{B}"

@@ -54,7 +54,7 @@ struct Timer {
 };
 
 // Reads the device status of a finished solve into h (waits for the stream).
-int finish_solve(dag_plan* plan, int nblocks, int delta, Timer& tm, cudaStream_t s, dag_stats* h)
+int finish_solve(dag_plan* plan, int nblocks, int delta, Timer& tm, cudaStream_t s, dag_stats* h, bool frontier = false)
 {
     SyncBlock sb;
     DAG_CUDA(cudaMemcpyAsync(&sb, plan->sync, sizeof(SyncBlock), cudaMemcpyDeviceToHost, s));
@@ -71,7 +71,7 @@ int finish_solve(dag_plan* plan, int nblocks, int delta, Timer& tm, cudaStream_t
         h->workers = nblocks;
         h->delta = delta;
         h->flushes = sb.flushes;
-        h->edges_processed = (long long)sb.iters * plan->m;
+        h->edges_processed = frontier ? sb.edges : (long long)sb.iters * plan->m;
     }
     if (rc == DAG_ERR_BARRIER_TIMEOUT) set_error(rc, "grid barrier wait ran out of time");
     else if (rc == DAG_ERR_NOT_CONVERGED) set_error(rc, "max_iters reached before the stopping rule");
@@ -134,6 +134,7 @@ extern "C" int dag_pagerank(dag_plan* plan, float d, double tol, dag_variant var
     if (!plan || !d_rank) return set_error(DAG_ERR_INVALID, "null argument");
     if (!(d > 0.0f && d < 1.0f)) return set_error(DAG_ERR_INVALID, "d must lie in (0, 1)");
     if (!(tol > 0.0) || std::isnan(tol)) return set_error(DAG_ERR_INVALID, "tol must be > 0");
+    if (flags & DAG_SSSP_FRONTIER) return set_error(DAG_ERR_INVALID, "the frontier is a Bellman-Ford flag");
     int rc = check_variant(variant, delta, max_iters);
     if (rc) return rc;
     int var = variant;
@@ -196,6 +197,16 @@ int sssp_impl(dag_plan* plan, uint32_t src, int variant, int delta, int max_iter
     p.read_mode = read_mode_of(flags);
     p.local_read = (flags & DAG_READ_LOCAL) ? 1 : 0;
     p.own_l1 = (flags & DAG_READ_OWN_L1) ? 1 : 0;
+    p.frontier = (flags & DAG_SSSP_FRONTIER) ? 1 : 0;
+    if (p.frontier && var == DAG_DELAYED)
+        return set_error(DAG_ERR_INVALID, "the frontier runs the synchronous and asynchronous forms (delta 0)");
+    if (p.frontier) {  // the frontier maps of this launch shape are built (once) outside the timed solve
+        int nb0 = 0, cap0 = 0;
+        Partition* part = nullptr;
+        rc = sweep_shape(plan, w8 ? MODE_BF8 : MODE_BF, var, delta, &nb0, &cap0, &part, s);
+        if (rc == DAG_OK) rc = frontier_maps(plan, part, s);
+        if (rc) return rc;
+    }
     Timer tm;
     tm.start(s, h_stats != nullptr);
     int nb = 0;
@@ -203,10 +214,12 @@ int sssp_impl(dag_plan* plan, uint32_t src, int variant, int delta, int max_iter
     if (rc) return rc;
     tm.stop(s);
     if (!h_stats) return DAG_OK;
-    return finish_solve(plan, nb, var == DAG_DELAYED ? delta : 0, tm, s, h_stats);
+    return finish_solve(plan, nb, var == DAG_DELAYED ? delta : 0, tm, s, h_stats, p.frontier != 0);
 }
 }  // namespace
 }  // namespace dag
+
+extern "C" int32_t dag_tile_items(void) { return TILE; }
 
 extern "C" int dag_sssp(dag_plan* plan, uint32_t src, dag_variant variant, int32_t delta, int32_t max_iters,
                         const uint32_t* d_w, uint32_t* d_dist, int32_t flags, dag_stats* h_stats, void* stream)

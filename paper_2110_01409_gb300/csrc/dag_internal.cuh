@@ -59,7 +59,8 @@ struct __align__(128) SyncBlock {
     double T;                    // teleport total (PageRank)
     double acc_res[3];           // per-sweep residual sums, slot = sweep % 3 (init = slot 2)
     double acc_g[3];             // per-sweep global sums (N for PageRank, sum lambda for the adjoint)
-    double pad1[4];
+    long long edges;             // edges processed (frontier sweeps)
+    double pad1[3];
     alignas(128) double stripe[GSTRIPES * GSTRIDE];  // live global sum (async / delayed)
 };
 
@@ -100,6 +101,14 @@ struct SweepParams {
     int read_mode;          // ReadMode (delayed form)
     int local_read;         // delayed form: read own unflushed rows from the buffer (Sec. III-C)
     int own_l1;             // async form: own block through L1, other blocks through L2
+    // frontier Bellman-Ford: a tile runs in sweep s only when fr_act[tile] == s
+    int frontier;
+    const int* fr_orow;     // out-CSR row pointers [n+1]
+    const int* fr_otile;    // per out-edge: tile of its in-CSR position
+    const int* fr_oend;     // per out-edge: tile that ends its target's row
+    int* fr_act;            // [tiles] sweep stamp of the last mark (zero before the first sweep)
+    int* fr_alist;          // [tiles] the CTAs' active tiles of the current sweep
+    int* fr_chg;            // [n] the CTAs' rows that changed in the current sweep
     // init / output
     const float* init;      // warm start (PR) or nullptr
     void* out;              // float r / lambda, or uint32 dist
@@ -115,6 +124,12 @@ struct Partition {
     int* cta_tile = nullptr;  // device [nblocks+1]
     int* tile_row = nullptr;  // device [tiles+1]
     int* tile_nz = nullptr;   // device [tiles+1]
+    // frontier maps (built on first use)
+    int* fr_otile = nullptr;  // device [m]
+    int* fr_oend = nullptr;   // device [m]
+    int* fr_act = nullptr;    // device [tiles]
+    int* fr_alist = nullptr;  // device [tiles]
+    int* fr_chg = nullptr;    // device [n]
 };
 
 }  // namespace dag
@@ -139,6 +154,7 @@ struct dag_plan {
     void* x1 = nullptr;       // [n]
     dag::SyncBlock* sync = nullptr;
     float* scratch_f = nullptr; // [n] float scratch (adjoint aux)
+    int* fr_orow = nullptr;   // [n+1] out-CSR row pointers (frontier sweeps, built on first use)
     std::map<int, dag::Partition> parts;
     // batched workspace (grown on demand)
     void* bx = nullptr;
@@ -160,6 +176,8 @@ int cuda_check(cudaError_t e, const char* what);
 
 // plan.cu
 int get_partition(dag_plan* plan, int nblocks, Partition** out, cudaStream_t s);
+// The frontier maps of a partition (and the plan's out-CSR row pointers), built once.
+int frontier_maps(dag_plan* plan, Partition* part, cudaStream_t s);
 int max_workers(dag_plan* plan, int mode, int variant, int buf_cap_elems, int* out);
 
 // sweep.cu
@@ -174,7 +192,7 @@ const void* sweep_kernel_ptr(int mode, int variant);
 size_t sweep_ring_bytes(int mode, int variant);
 
 // sweep_tma.cu: the asynchronous form's TMA-staged kernel and its ring size.
-const void* sweep_tma_kernel_ptr(int mode);
+const void* sweep_tma_kernel_ptr(int mode, bool frontier);
 size_t sweep_tma_ring_bytes(int mode);
 // Smallest shared-memory carveout of kernel k that keeps per_sm CTAs of
 // (static_smem + dyn) bytes resident; the rest of the SM's array is L1.

@@ -198,6 +198,61 @@ int launch_transpose(dag_plan* plan, int* out_rowptr, int* out_colidx, int* perm
     return DAG_OK;
 }
 
+// Frontier maps: for every out-edge u -> v (out-CSR order), the tile holding its
+// in-CSR position and the tile holding v's row end. A change of u makes the
+// tiles between the two run again in the next sweep.
+__device__ __forceinline__ int last_le(const int* a, int len, long long x)  // last i < len with a[i] <= x
+{
+    int lo = 0, hi = len - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a[mid] <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void k_frontier_maps(const int* perm, const int* ocol, long long m, const int* tile_nz,
+                                const int* tile_row, int tiles, int* otile, int* oend)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < m; e += (long long)gridDim.x * blockDim.x) {
+        otile[e] = last_le(tile_nz, tiles, perm[e]);
+        oend[e] = last_le(tile_row, tiles, ocol[e]);
+    }
+}
+
+int frontier_maps(dag_plan* plan, Partition* part, cudaStream_t s)
+{
+    if (part->fr_act) return DAG_OK;
+    const int n = plan->n;
+    const long long m = plan->m;
+    int *ocol = nullptr, *perm = nullptr;
+    if (!plan->fr_orow) DAG_CUDA(cudaMalloc(&plan->fr_orow, (size_t)(n + 1) * sizeof(int)));
+    DAG_CUDA(cudaMalloc(&part->fr_otile, (size_t)std::max(m, 1LL) * sizeof(int)));
+    DAG_CUDA(cudaMalloc(&part->fr_oend, (size_t)std::max(m, 1LL) * sizeof(int)));
+    DAG_CUDA(cudaMalloc(&part->fr_alist, (size_t)std::max(part->tiles, 1) * sizeof(int)));
+    DAG_CUDA(cudaMalloc(&part->fr_chg, (size_t)n * sizeof(int)));
+    DAG_CUDA(cudaMalloc(&ocol, (size_t)std::max(m, 1LL) * sizeof(int)));
+    DAG_CUDA(cudaMalloc(&perm, (size_t)std::max(m, 1LL) * sizeof(int)));
+    int rc = launch_transpose(plan, plan->fr_orow, ocol, perm, s);
+    if (rc == DAG_OK && m > 0 && part->tiles > 0) {
+        k_frontier_maps<<<2048, 256, 0, s>>>(perm, ocol, m, part->tile_nz, part->tile_row, part->tiles,
+                                             part->fr_otile, part->fr_oend);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_check(e, "frontier maps");
+    }
+    if (rc == DAG_OK) {
+        const cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = cuda_check(e, "frontier maps");
+    }
+    cudaFree(ocol);
+    cudaFree(perm);
+    if (rc != DAG_OK) return rc;
+    // allocated last: a set fr_act marks the maps complete
+    DAG_CUDA(cudaMalloc(&part->fr_act, (size_t)std::max(part->tiles, 1) * sizeof(int)));
+    return DAG_OK;
+}
+
 // s[u] = sum of w over u's out-edges (one thread per source over the
 // out-CSR, fixed order); val[e] = w[e] / s[colidx[e]].
 __global__ void k_out_sum(const int* orow, const int* perm, const float* w, int n, float* s)
@@ -316,7 +371,13 @@ extern "C" int dag_plan_destroy(dag_plan* p)
         cudaFree(kv.second.cta_tile);
         cudaFree(kv.second.tile_row);
         cudaFree(kv.second.tile_nz);
+        cudaFree(kv.second.fr_otile);
+        cudaFree(kv.second.fr_oend);
+        cudaFree(kv.second.fr_act);
+        cudaFree(kv.second.fr_alist);
+        cudaFree(kv.second.fr_chg);
     }
+    cudaFree(p->fr_orow);
     delete p;
     return DAG_OK;
 }

@@ -127,10 +127,16 @@ __device__ __forceinline__ void stage_gather(Stage<MODE>& st, const uint32_t* xi
     }
 }
 
-template <int MODE, int VAR>
+// FRONTIER (Bellman-Ford, synchronous form): after a sweep whose changed rows
+// feed few tiles (marks <= FR_SPARSE * tiles) only the tiles stamped for the
+// next sweep run (see active_tiles / mark_out_tiles), otherwise all do; the
+// rows a sweep changes are copied into the other array at the start of the
+// next, so both arrays agree on every row a skipped tile leaves alone.
+template <int MODE, int VAR, bool FRONTIER>
 __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams p)
 {
     using O = Op<MODE>;
+    static_assert(!FRONTIER || ((MODE == MODE_BF || MODE == MODE_BF8) && VAR == DAG_SYNC), "frontier: sync BF");
     constexpr bool BF = MODE == MODE_BF || MODE == MODE_BF8;
     constexpr bool SYNC = VAR == DAG_SYNC;
     constexpr bool DELAYED = VAR == DAG_DELAYED;
@@ -203,6 +209,10 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
     const uint64_t pol_vertex = policy_evict_last();
     int buf_first = row_lo, buf_cnt = 0;
     long long flushes = 0;
+    long long edges_done = 0;  // frontier: edges of the tiles this CTA ran (thread 0)
+    long long marks = 0;       // frontier: out-degree sum of this thread's changed rows in the sweep
+    bool dense = true;         // frontier: this sweep runs every tile
+    if (tid == 0) sh.nchg = 0;
     int it = 0;
     bool converged = false;
     double last_res = 0.0;
@@ -221,21 +231,36 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
                                        : (float)((double)p.g_coef * (T - gprev));
         }
 
+        // Tiles of this sweep: all of the CTA's, or (frontier) the stamped ones.
+        int ntl = tile_hi - tile_lo;
+        if constexpr (FRONTIER) {
+            // the rows changed in the previous sweep take their new value in this sweep's output too
+            for (int k = tid; k < sh.nchg; k += NT) {
+                const int v = p.fr_chg[row_lo + k];
+                st_weak_b32(xout + v, ld_weak_b32(xin + v));
+            }
+            __syncthreads();
+            if (tid == 0) sh.nchg = 0;
+            if (!dense) ntl = active_tiles(sh, p.fr_act, it, tile_lo, tile_hi, p.fr_alist);
+        }
+        auto tile_at = [&](int i) { return (FRONTIER && !dense) ? p.fr_alist[tile_lo + i] : tile_lo + i; };
+        int t_prev = -2;  // frontier: the tile run before, for the carry
+
         // Software pipeline: while tile t is walked, tile t+1's edge stream,
         // row ends and old values are in flight (issued after barrier A of t)
         // and its gathers too (issued before barrier C of t).
         Stage<MODE> nx;
-        if (tile_lo < tile_hi) {
-            stage_issue<MODE>(nx, p, xin, tile_lo, tid, weak, pol_edge, pol_vertex);
+        if (ntl > 0) {
+            stage_issue<MODE>(nx, p, xin, tile_at(0), tid, weak, pol_edge, pol_vertex);
             stage_gather<MODE>(nx, xin, tid, weak, pol_vertex, s_buf, 0, 0);
             if constexpr (LIVE_G) {
                 if (warp == 0) nx.gs = ld_relaxed_f64(&sb->stripe[lane * GSTRIDE]);
             }
         }
 
-        for (int t = tile_lo; t <= tile_hi; ++t) {
-            // One pass per tile, plus one extra pass (t == tile_hi) that only completes a pending flush.
-            const bool real = t < tile_hi;
+        for (int i = 0; i <= ntl; ++i) {
+            // One pass per tile, plus one extra pass (i == ntl) that only completes a pending flush.
+            const bool real = i < ntl;
             const int a0 = real ? nx.a0 : 0, b0 = real ? nx.b0 : 0;
             const int NA = real ? nx.NA : 0, NB = real ? nx.NB : 0;
             uint32_t pf_x[RP];
@@ -287,8 +312,14 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
                 }
             }
             if (!real) break;
-            const bool more = t + 1 < tile_hi;
-            if (more) stage_issue<MODE>(nx, p, xin, t + 1, tid, weak, pol_edge, pol_vertex);
+            const bool more = i + 1 < ntl;
+            if constexpr (FRONTIER) {
+                const int t = tile_at(i);
+                if (tid == 0 && t != t_prev + 1) carry = O::identity();  // the row before was not run
+                t_prev = t;
+                if (tid == 0) edges_done += NB;
+            }
+            if (more) stage_issue<MODE>(nx, p, xin, tile_at(i + 1), tid, weak, pol_edge, pol_vertex);
             float gt = gterm;
             if constexpr (LIVE_G) {
                 gt = sh.gt;
@@ -322,6 +353,12 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
                     if constexpr (!BF) dg = ld_stream_f32(p.degf + v);
                 }
                 const uint32_t xnew = row_update<MODE>(p, v, sum, xo_bits, dg, gt, res_part, g_part, dg_part);
+                if constexpr (FRONTIER) {
+                    if (xnew < xo_bits) {  // log the row and count the tile marks it would cause
+                        p.fr_chg[row_lo + atomicAdd(&sh.nchg, 1)] = v;
+                        marks += p.fr_orow[v + 1] - p.fr_orow[v];
+                    }
+                }
                 if constexpr (SYNC) st_weak_b32(xout + v, xnew);
                 else if constexpr (DELAYED) s_buf[v - buf_first] = xnew;
                 else st_relaxed_b32(xout + v, xnew);
@@ -334,7 +371,7 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
             if constexpr (DELAYED) {
                 buf_cnt += NA;
                 // flush at delta, at the block end, or (buffer clamped to what fits) when the next tile might not fit
-                if (buf_cnt >= p.delta || t == tile_hi - 1 || (p.buf_clamped && buf_cnt > p.buf_cap - TILE))
+                if (buf_cnt >= p.delta || i == ntl - 1 || (p.buf_clamped && buf_cnt > p.buf_cap - TILE))
                     flush_pending = true;
             }
         }  // tiles
@@ -344,12 +381,15 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
             buf_cnt = 0;
         }
 
-        // -------- end of sweep: residual, barrier, stopping rule --------
-        double res_d = (double)res_part, g_d = (double)g_part;
+        // -------- end of sweep: residual, barrier, stopping rule (frontier: tile marks) --------
+        double res_d = (double)res_part, g_d = FRONTIER ? (double)marks : (double)g_part;  // marks: exact in FP64
+        marks = 0;
         block_sum2(sh, res_d, g_d);
         if (tid == 0) {
             if (res_d != 0.0) atomicAdd(&sb->acc_res[slot], res_d);
-            if (SYNC && !BF && g_d != 0.0) atomicAdd(&sb->acc_g[slot], g_d);
+            if ((FRONTIER || (SYNC && !BF)) && g_d != 0.0) atomicAdd(&sb->acc_g[slot], g_d);
+            if (FRONTIER && edges_done) atomicAdd((unsigned long long*)&sb->edges, (unsigned long long)edges_done);
+            edges_done = 0;
         }
         if (!grid_barrier(sb, p.nblocks, bar_target, p.timeout_ns)) return;
         if (tid == 0) {
@@ -368,6 +408,14 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
             converged = true;
             ++it;
             break;
+        }
+        if constexpr (FRONTIER) {
+            // sparse next sweep: stamp the tiles the changed rows feed, publish, run only those
+            dense = gprev > FR_SPARSE * (double)p.cta_tile[p.nblocks];
+            if (!dense) {
+                mark_out_tiles(p.fr_chg + row_lo, sh.nchg, p.fr_orow, p.fr_otile, p.fr_oend, p.fr_act, it);
+                if (!grid_barrier(sb, p.nblocks, bar_target, p.timeout_ns)) return;
+            }
         }
     }
 
@@ -396,22 +444,27 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
 
 using KernelFn = void (*)(const SweepParams);
 
-static KernelFn kernel_for(int mode, int variant)
+// The kernel a solve of (mode, variant) runs; frontier: the Bellman-Ford
+// kernels that run only the tiles whose inputs changed (sync and async forms).
+static KernelFn kernel_for(int mode, int variant, bool frontier)
 {
-    if (variant == DAG_ASYNC) return (KernelFn)sweep_tma_kernel_ptr(mode);
+    const bool bf = mode == MODE_BF || mode == MODE_BF8;
+    if (variant == DAG_ASYNC) return (KernelFn)sweep_tma_kernel_ptr(mode, frontier && bf);
+    if (frontier && bf && variant == DAG_SYNC)
+        return mode == MODE_BF ? sweep_kernel<MODE_BF, DAG_SYNC, true> : sweep_kernel<MODE_BF8, DAG_SYNC, true>;
     static const KernelFn table[5][2] = {
-        {sweep_kernel<MODE_PR, DAG_SYNC>, sweep_kernel<MODE_PR, DAG_DELAYED>},
-        {sweep_kernel<MODE_PRW, DAG_SYNC>, sweep_kernel<MODE_PRW, DAG_DELAYED>},
-        {sweep_kernel<MODE_ADJ, DAG_SYNC>, sweep_kernel<MODE_ADJ, DAG_DELAYED>},
-        {sweep_kernel<MODE_BF, DAG_SYNC>, sweep_kernel<MODE_BF, DAG_DELAYED>},
-        {sweep_kernel<MODE_BF8, DAG_SYNC>, sweep_kernel<MODE_BF8, DAG_DELAYED>},
+        {sweep_kernel<MODE_PR, DAG_SYNC, false>, sweep_kernel<MODE_PR, DAG_DELAYED, false>},
+        {sweep_kernel<MODE_PRW, DAG_SYNC, false>, sweep_kernel<MODE_PRW, DAG_DELAYED, false>},
+        {sweep_kernel<MODE_ADJ, DAG_SYNC, false>, sweep_kernel<MODE_ADJ, DAG_DELAYED, false>},
+        {sweep_kernel<MODE_BF, DAG_SYNC, false>, sweep_kernel<MODE_BF, DAG_DELAYED, false>},
+        {sweep_kernel<MODE_BF8, DAG_SYNC, false>, sweep_kernel<MODE_BF8, DAG_DELAYED, false>},
     };
     return table[mode][variant == DAG_DELAYED ? 1 : 0];
 }
 
 // The sweep kernel of (mode, variant), for launches that build their own
 // parameters (the allocation-free entry point).
-const void* sweep_kernel_ptr(int mode, int variant) { return (const void*)kernel_for(mode, variant); }
+const void* sweep_kernel_ptr(int mode, int variant) { return (const void*)kernel_for(mode, variant, false); }
 
 size_t sweep_ring_bytes(int mode, int variant) { return variant == DAG_ASYNC ? sweep_tma_ring_bytes(mode) : 0; }
 
@@ -433,20 +486,30 @@ int set_l1_carveout(const void* k, int device, int threads, size_t static_smem, 
     return DAG_OK;
 }
 
+// CTAs of a (mode, variant) sweep that fit on the GPU at once, with each kernel
+// such a solve may run (plain, and frontier for Bellman-Ford) configured for
+// that residency: dynamic shared memory and L1/shared carveout.
 int max_workers(dag_plan* plan, int mode, int variant, int buf_cap_elems, int* out)
 {
-    KernelFn k = kernel_for(mode, variant);
+    const void* ks[2] = {(const void*)kernel_for(mode, variant, false), (const void*)kernel_for(mode, variant, true)};
+    const int nk = ks[1] != ks[0] ? 2 : 1;
     size_t dyn = sweep_ring_bytes(mode, variant) + ((variant == DAG_DELAYED) ? (size_t)buf_cap_elems * 4 : 0);
     int max_dyn = 0;
     DAG_CUDA(cudaDeviceGetAttribute(&max_dyn, cudaDevAttrMaxSharedMemoryPerBlockOptin, plan->device));
-    cudaFuncAttributes fa;
-    DAG_CUDA(cudaFuncGetAttributes(&fa, (const void*)k));
-    if (dyn + fa.sharedSizeBytes > (size_t)max_dyn)
-        return set_error(DAG_ERR_INVALID, "delta too large: the delay buffer does not fit in shared memory");
-    DAG_CUDA(cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
-    int per_sm = 0;
-    DAG_CUDA(cudaFuncSetAttribute((const void*)k, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-    DAG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k, NT, dyn));
+    cudaFuncAttributes fa{};
+    int per_sm = INT_MAX;
+    for (int i = 0; i < nk; ++i) {
+        cudaFuncAttributes fi;
+        DAG_CUDA(cudaFuncGetAttributes(&fi, ks[i]));
+        if (dyn + fi.sharedSizeBytes > (size_t)max_dyn)
+            return set_error(DAG_ERR_INVALID, "delta too large: the delay buffer does not fit in shared memory");
+        if (i == 0 || fi.sharedSizeBytes > fa.sharedSizeBytes) fa = fi;
+        DAG_CUDA(cudaFuncSetAttribute(ks[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+        DAG_CUDA(cudaFuncSetAttribute(ks[i], cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+        int ps = 0;
+        DAG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, ks[i], NT, dyn));
+        per_sm = std::min(per_sm, ps);
+    }
     if (per_sm < 1) return set_error(DAG_ERR_INVALID, "sweep kernel cannot be resident with this delta");
     if (variant == DAG_ASYNC) {
         // The TMA kernel's streams and coherent gathers bypass L1, but its own-block gathers and
@@ -461,8 +524,10 @@ int max_workers(dag_plan* plan, int mode, int variant, int buf_cap_elems, int* o
         const size_t budget = max_sm > (32 << 10) ? (size_t)max_sm - (32 << 10) : (size_t)max_sm;
         while (per_sm > 1 && (size_t)per_sm * per_cta > budget) --per_sm;
     }
-    const int rc = set_l1_carveout((const void*)k, plan->device, NT, fa.sharedSizeBytes, dyn, per_sm);
-    if (rc) return rc;
+    for (int i = 0; i < nk; ++i) {
+        const int rc = set_l1_carveout(ks[i], plan->device, NT, fa.sharedSizeBytes, dyn, per_sm);
+        if (rc) return rc;
+    }
     *out = per_sm * plan->num_sms;
     return DAG_OK;
 }
@@ -543,13 +608,24 @@ int launch_sweep(dag_plan* plan, int mode, int variant, int delta, SweepParams& 
         p.timeout_ns = plan->skip_timeout_ns;
         plan->skip_barrier_once = 0;
     }
+    if (p.frontier) {
+        const int frc = frontier_maps(plan, part, s);
+        if (frc) return frc;
+        p.fr_orow = plan->fr_orow;
+        p.fr_otile = part->fr_otile;
+        p.fr_oend = part->fr_oend;
+        p.fr_act = part->fr_act;
+        p.fr_alist = part->fr_alist;
+        p.fr_chg = part->fr_chg;
+        DAG_CUDA(cudaMemsetAsync(part->fr_act, 0, (size_t)std::max(part->tiles, 1) * sizeof(int), s));
+    }
     // the asynchronous form's tile copies are TMA bulk copies from 16-byte boundaries of these arrays
     for (const void* a : {(const void*)p.rowptr, (const void*)p.colidx, (const void*)p.w, (const void*)p.w8,
                           (const void*)p.val, (const void*)p.degf, (const void*)p.x0, (const void*)p.x1})
         if (((uintptr_t)a & 15u) != 0)
             return set_error(DAG_ERR_INVALID, "graph, weight and state arrays must be 16-byte aligned");
     DAG_CUDA(cudaMemsetAsync(plan->sync, 0, sizeof(SyncBlock), s));
-    KernelFn k = kernel_for(mode, variant);
+    KernelFn k = kernel_for(mode, variant, p.frontier != 0);
     void* args[] = {(void*)&p};
     size_t dyn = sweep_ring_bytes(mode, variant) + ((variant == DAG_DELAYED) ? (size_t)cap * 4 : 0);
     DAG_CUDA(cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));

@@ -57,6 +57,8 @@ struct SweepShared {
     double red1[NWARP];
     float gt;                            // the tile's global (dangling) term from the live sum
     int abort;                           // a bounded wait of this CTA ran out (TMA kernel)
+    int nchg;                            // frontier: rows of this CTA changed in the sweep
+    int cnt[NWARP];                      // frontier: per-warp counts of the active-tile scan
     double res;                          // broadcast of the sweep residual
     double gprev;                        // broadcast of the previous sweep's global sum
     double T;                            // broadcast of the teleport total / ||c||_1
@@ -175,6 +177,60 @@ __device__ __forceinline__ uint32_t finish_scan(SH& sh, const WalkOut& w)
     if (lane == 0) cin = (warp > 0) ? E_prev : O::identity();
     if (tid > 0 && w.emitted) sh.rowsum[w.i_start] = O::combine(sh.rowsum[w.i_start], cin);
     return __shfl_sync(0xffffffffu, E, NWARP - 1);  // whole warp takes part
+}
+
+// ---------------------------------------------------------------------------
+// Frontier Bellman-Ford (tiles that run only when an input changed). Every
+// sweep counts the tile marks its changed rows would cause (their out-degree
+// sum). When that is at most FR_SPARSE per tile, each CTA stamps s + 1 on the
+// tiles from every out-edge of its changed rows to the tile ending that edge's
+// target row, an extra grid barrier publishes the stamps, and sweep s + 1 runs
+// only the tiles with act[t] == s + 1; otherwise (changes that reach nearly
+// every tile anyway) sweep s + 1 runs every tile and nothing is marked.
+// Sweep 0 runs every tile.
+// ---------------------------------------------------------------------------
+constexpr double FR_SPARSE = 4.0;  // measured: below ~5 marks per tile, tiles start to be skipped
+
+// This CTA's tiles that run in sweep s, in order, into alist[tile_lo ...];
+// returns their count (the same in every thread).
+template <class SH>
+__device__ __forceinline__ int active_tiles(SH& sh, const int* act, int s, int tile_lo, int tile_hi, int* alist)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int total = 0;
+    for (int base = tile_lo; base < tile_hi; base += NT) {
+        const int t = base + tid;
+        const bool on = t < tile_hi && act[t] == s;
+        const unsigned bal = __ballot_sync(0xffffffffu, on);
+        if (lane == 0) sh.cnt[warp] = __popc(bal);
+        __syncthreads();
+        int before = 0, all = 0;
+#pragma unroll
+        for (int k = 0; k < NWARP; ++k) {
+            before += k < warp ? sh.cnt[k] : 0;
+            all += sh.cnt[k];
+        }
+        if (on) alist[tile_lo + total + before + __popc(bal & ((1u << lane) - 1u))] = t;
+        total += all;
+        __syncthreads();  // the list is complete and sh.cnt free again
+    }
+    return total;
+}
+
+// Stamps s + 1 on the tiles that the rows in chg[0 .. nchg) feed: one warp per
+// changed row, its lanes over the row's out-edges.
+__device__ __forceinline__ void mark_out_tiles(const int* chg, int nchg, const int* orow, const int* otile,
+                                               const int* oend, int* act, int s)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = warp; k < nchg; k += NWARP) {
+        const int v = chg[k];
+        const int e1 = orow[v + 1];
+        for (int e = orow[v] + lane; e < e1; e += 32) {
+            const int t1 = oend[e];
+            for (int t = otile[e]; t <= t1; ++t) act[t] = s + 1;
+        }
+    }
 }
 
 // New value of row v from its pull sum and old value (PageRank: x = r/outdeg

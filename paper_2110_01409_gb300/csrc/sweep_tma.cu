@@ -194,11 +194,15 @@ __device__ __forceinline__ uint32_t edge_term(uint32_t xv, const unsigned char* 
     else return __float_as_uint(__uint_as_float(((const uint32_t*)aux)[k]) * __uint_as_float(xv));
 }
 
-template <int MODE>
+// FRONTIER (Bellman-Ford): after a sweep whose changed rows feed few tiles,
+// only the tiles stamped for the next sweep run (see active_tiles /
+// mark_out_tiles), and the ring is filled along that list.
+template <int MODE, bool FRONTIER>
 __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepParams p)
 {
     using R = Ring<MODE>;
     constexpr bool BF = MODE == MODE_BF || MODE == MODE_BF8;
+    static_assert(!FRONTIER || BF, "frontier: Bellman-Ford only");
     constexpr bool LIVE_G = !BF;  // PageRank-type: live global sum
 
     __shared__ SweepShared<false> sh;
@@ -217,6 +221,7 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
         for (int s = 0; s < RING; ++s) mbar_init(&sh.fill_bar[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         sh.abort = 0;
+        sh.nchg = 0;
     }
 
     // ---------------- initial values of the owned rows ----------------
@@ -268,7 +273,10 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
     int it = 0;
     bool converged = false;
     double last_res = 0.0;
-    uint32_t qbase = 0;  // ring fills of earlier sweeps (the fill of tile t is qbase + t - tile_lo)
+    uint32_t qbase = 0;  // ring fills of earlier sweeps (the i-th tile of a sweep is fill qbase + i)
+    long long edges_done = 0;  // frontier: edges of the tiles this CTA ran (thread 0)
+    long long marks = 0;       // frontier: out-degree sum of this thread's changed rows in the sweep
+    bool dense = true;         // frontier: this sweep runs every tile
 
     for (; it < p.max_iters; ++it) {
         const int slot = it % 3;
@@ -276,17 +284,26 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
         float res_part = 0.0f, g_part = 0.0f, dg_part = 0.0f;
         uint32_t carry = Op<MODE>::identity();  // thread 0: partial of the row continuing into the next tile
 
+        // Tiles of this sweep: all of the CTA's, or (frontier) the stamped ones.
+        int ntl = tile_hi - tile_lo;
+        if constexpr (FRONTIER) {
+            __syncthreads();  // the previous sweep's marks are done with sh.nchg
+            if (tid == 0) sh.nchg = 0;
+            if (!dense) ntl = active_tiles(sh, p.fr_act, it, tile_lo, tile_hi, p.fr_alist);
+        }
+        auto tile_at = [&](int i) { return (FRONTIER && !dense) ? p.fr_alist[tile_lo + i] : tile_lo + i; };
+        int t_prev = -2;  // frontier: the tile run before, for the carry
+
         // Pipeline: tile t+2's inputs are being copied and tile t+1's gathers are in
         // flight while tile t is walked, scanned and finished.
         uint32_t term[IPT];  // gathered values of the next tile
         double gs = 0.0;     // warp 0: one stripe of the live global sum for the next tile
         if (tid == 0) {
-            if (tile_lo < tile_hi) issue_fill<MODE>(ring, sh.fill_bar, qbase, p, X, tile_lo, pol_edge, pol_vertex);
-            if (tile_lo + 1 < tile_hi)
-                issue_fill<MODE>(ring, sh.fill_bar, qbase + 1, p, X, tile_lo + 1, pol_edge, pol_vertex);
+            if (ntl > 0) issue_fill<MODE>(ring, sh.fill_bar, qbase, p, X, tile_at(0), pol_edge, pol_vertex);
+            if (ntl > 1) issue_fill<MODE>(ring, sh.fill_bar, qbase + 1, p, X, tile_at(1), pol_edge, pol_vertex);
         }
-        if (tile_lo < tile_hi) {
-            const TileGeo g0 = tile_geo(p, tile_lo);
+        if (ntl > 0) {
+            const TileGeo g0 = tile_geo(p, tile_at(0));
             if (mbar_wait(&sh.fill_bar[qbase % RING], (qbase / RING) & 1u, p.timeout_ns)) {
                 const int* cr = (const int*)(ring + R::OFF_CR) + (qbase % RING) * R::CR_INTS;
                 gather_tile(term, cr + g0.col_off(), g0.NB, X, tid, pol_vertex, own_lo, own_n);
@@ -301,8 +318,9 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
             }
         }
 
-        for (int t = tile_lo; t < tile_hi; ++t) {
-            const uint32_t q = qbase + (uint32_t)(t - tile_lo);
+        for (int i = 0; i < ntl; ++i) {
+            const int t = tile_at(i);
+            const uint32_t q = qbase + (uint32_t)i;
             const TileGeo g = tile_geo(p, t);
             const int a0 = g.a0, b0 = g.b0, NA = g.NA, NB = g.NB;
             const int* rend = (const int*)(ring + R::OFF_CR) + (q % RING) * R::CR_INTS + g.rend_off();
@@ -327,13 +345,18 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
             }
             __syncthreads();  // (A) tile staged; every thread is done with the previous tile
 
-            const bool more = t + 1 < tile_hi;
+            const bool more = i + 1 < ntl;
             const float gt = LIVE_G ? sh.gt : 0.0f;
-            // -------- tile t+2's copies, tile t+1's gathers --------
-            if (tid == 0 && t + 2 < tile_hi)
-                issue_fill<MODE>(ring, sh.fill_bar, q + 2, p, X, t + 2, pol_edge, pol_vertex);
+            if constexpr (FRONTIER) {
+                if (tid == 0 && t != t_prev + 1) carry = Op<MODE>::identity();  // the row before was not run
+                t_prev = t;
+                if (tid == 0) edges_done += NB;
+            }
+            // -------- the copies of the tile after next, the next tile's gathers --------
+            if (tid == 0 && i + 2 < ntl)
+                issue_fill<MODE>(ring, sh.fill_bar, q + 2, p, X, tile_at(i + 2), pol_edge, pol_vertex);
             if (more) {
-                const TileGeo g1 = tile_geo(p, t + 1);
+                const TileGeo g1 = tile_geo(p, tile_at(i + 1));
                 const uint32_t q1 = q + 1;
                 if (mbar_wait(&sh.fill_bar[q1 % RING], (q1 / RING) & 1u, p.timeout_ns)) {
                     const int* cr1 = (const int*)(ring + R::OFF_CR) + (q1 % RING) * R::CR_INTS;
@@ -355,7 +378,7 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
             if (sh.abort) {   // a staging wait ran out (error recorded): drain own copies, leave
                 if (tid == 0) {
                     if (more) (void)mbar_wait(&sh.fill_bar[(q + 1) % RING], ((q + 1) / RING) & 1u, p.timeout_ns);
-                    if (t + 2 < tile_hi)
+                    if (i + 2 < ntl)
                         (void)mbar_wait(&sh.fill_bar[(q + 2) % RING], ((q + 2) / RING) & 1u, p.timeout_ns);
                 }
                 return;  // the other CTAs' barrier waits end on the recorded error
@@ -383,6 +406,12 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
                 }
                 const uint32_t xnew = row_update<MODE>(p, v, sh.rowsum[r], xo_bits, dg, gt, res_part, g_part,
                                                        dg_part);
+                if constexpr (FRONTIER) {
+                    if (xnew < xo_bits) {  // log the row and count the tile marks it would cause
+                        p.fr_chg[row_lo + atomicAdd(&sh.nchg, 1)] = v;
+                        marks += p.fr_orow[v + 1] - p.fr_orow[v];
+                    }
+                }
                 st_relaxed_b32(X + v, xnew);
             }
             if constexpr (LIVE_G) {
@@ -391,15 +420,22 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
                 if (lane == 0 && s != 0.0f) atomicAdd(&sb->stripe[(c % GSTRIPES) * GSTRIDE], (double)s);
             }
         }  // tiles
-        qbase += (uint32_t)(tile_hi - tile_lo);
+        qbase += (uint32_t)ntl;
 
-        // -------- end of sweep: residual, barrier, stopping rule --------
-        double res_d = (double)res_part, g_d = (double)g_part;
+        // -------- end of sweep: residual, barrier, stopping rule (frontier: tile marks) --------
+        double res_d = (double)res_part, g_d = FRONTIER ? (double)marks : (double)g_part;  // marks: exact in FP64
+        marks = 0;
         block_sum2(sh, res_d, g_d);
         if (tid == 0 && res_d != 0.0) atomicAdd(&sb->acc_res[slot], res_d);
+        if (FRONTIER && tid == 0) {
+            if (g_d != 0.0) atomicAdd(&sb->acc_g[slot], g_d);
+            if (edges_done) atomicAdd((unsigned long long*)&sb->edges, (unsigned long long)edges_done);
+            edges_done = 0;
+        }
         if (!grid_barrier(sb, p.nblocks, bar_target, p.timeout_ns)) return;
         if (tid == 0) {
             sh.res = ld_relaxed_f64(&sb->acc_res[slot]);
+            if (FRONTIER) sh.gprev = ld_relaxed_f64(&sb->acc_g[slot]);
             if (c == 0) {
                 const int dead = (it + 2) % 3;  // read by everyone before this barrier
                 sb->acc_res[dead] = 0.0;
@@ -412,6 +448,14 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
             converged = true;
             ++it;
             break;
+        }
+        if constexpr (FRONTIER) {
+            // sparse next sweep: stamp the tiles the changed rows feed, publish, run only those
+            dense = sh.gprev > FR_SPARSE * (double)p.cta_tile[p.nblocks];
+            if (!dense) {
+                mark_out_tiles(p.fr_chg + row_lo, sh.nchg, p.fr_orow, p.fr_otile, p.fr_oend, p.fr_act, it);
+                if (!grid_barrier(sb, p.nblocks, bar_target, p.timeout_ns)) return;
+            }
         }
     }
 
@@ -432,14 +476,14 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
     }
 }
 
-const void* sweep_tma_kernel_ptr(int mode)
+const void* sweep_tma_kernel_ptr(int mode, bool frontier)
 {
     switch (mode) {
-    case MODE_PR: return (const void*)sweep_tma_kernel<MODE_PR>;
-    case MODE_PRW: return (const void*)sweep_tma_kernel<MODE_PRW>;
-    case MODE_ADJ: return (const void*)sweep_tma_kernel<MODE_ADJ>;
-    case MODE_BF: return (const void*)sweep_tma_kernel<MODE_BF>;
-    default: return (const void*)sweep_tma_kernel<MODE_BF8>;
+    case MODE_PR: return (const void*)sweep_tma_kernel<MODE_PR, false>;
+    case MODE_PRW: return (const void*)sweep_tma_kernel<MODE_PRW, false>;
+    case MODE_ADJ: return (const void*)sweep_tma_kernel<MODE_ADJ, false>;
+    case MODE_BF: return frontier ? (const void*)sweep_tma_kernel<MODE_BF, true> : (const void*)sweep_tma_kernel<MODE_BF, false>;
+    default: return frontier ? (const void*)sweep_tma_kernel<MODE_BF8, true> : (const void*)sweep_tma_kernel<MODE_BF8, false>;
     }
 }
 

@@ -23,13 +23,14 @@ VARIANTS = {"sync": SYNC, "async": ASYNC, "delayed": DELAYED}
 WARM_START = 1
 READ_MODES = {"refresh": 0, "coherent": 2, "cached": 4,  # delayed form's reads (DAG_READ_*)
               "local": 8, "local+coherent": 10, "local+cached": 12,
-              "own_l1": 16}  # async form: own block through L1 (DAG_READ_OWN_L1)
+              "own_l1": 16,  # async form: own block through L1 (DAG_READ_OWN_L1)
+              "frontier": 32, "own_l1+frontier": 48}  # Bellman-Ford: run only changed tiles (DAG_SSSP_FRONTIER)
 
 EXPORTS = (
     "dag_plan_create", "dag_plan_destroy", "dag_plan_out_degree", "dag_partition", "dag_workers",
     "dag_pagerank", "dag_sssp", "dag_ppr_batched", "dag_sssp_batched", "dag_transpose",
     "dag_normalize_weights", "dag_pagerank_adjoint", "dag_strerror", "dag_last_error_message",
-    "dag_debug_skip_barrier_once", "dag_debug_stall_staging_once", "dag_pagerank_noalloc", "dag_gather_f32", "dag_plan_set_worker_cap",
+    "dag_debug_skip_barrier_once", "dag_debug_stall_staging_once", "dag_tile_items", "dag_pagerank_noalloc", "dag_gather_f32", "dag_plan_set_worker_cap",
     "dag_sssp_u8", "dag_probe_gather", "dag_access_matrix",
 )
 
@@ -92,6 +93,7 @@ def lib():
             L.dag_last_error_message.restype = ctypes.c_char_p
             L.dag_debug_skip_barrier_once.argtypes = [_vp, _i32]
             L.dag_debug_stall_staging_once.argtypes = [_vp, _i32]
+            L.dag_tile_items.restype = _i32
             L.dag_gather_f32.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp]
             L.dag_plan_set_worker_cap.argtypes = [_vp, _i32]
             L.dag_access_matrix.argtypes = [_vp, _i32, _vp, _vp]
@@ -328,6 +330,11 @@ def access_matrix(plan: Plan, workers: int = 32) -> torch.Tensor:
     out = torch.empty((workers, workers), dtype=torch.int64, device=plan.rowptr.device)
     _raise(lib().dag_access_matrix(plan.h, workers, _ptr(out), _stream()), False)
     return out
+
+
+def tile_items() -> int:
+    """Items (rows + in-edges) per merge-path tile of the sweeps."""
+    return int(lib().dag_tile_items())
 
 
 def locality(counts: torch.Tensor) -> dict:

@@ -32,6 +32,8 @@ def test_hand_worked_path6():
         start = oracle.partition(g, int(P))
         dist, it, ed, ok = frontier.sssp_frontier_sync(g, w, 0, start, int(TILE))
         assert ok and list(dist) == [0, 1, 2, 3, 4, 5]
+        # one change per sweep, out-degree 1: always below the dense threshold
+        assert list(frontier.sssp_frontier_sync(g, w, 0, start, int(TILE), sparse=None)[2]) == list(ed)
         assert it == int(sweeps) and list(ed) == [int(x) for x in edges.split(",")], (P, TILE, list(ed))
 
 
@@ -56,7 +58,7 @@ def test_frontier_matches_plain_sync_and_dijkstra(seed, P, TILE):
     w = I.weights_u32(g, seed)
     src = int(I.sources(g, 1, seed=seed)[0])
     start = oracle.partition(g, P)
-    dist, it, ed, ok = frontier.sssp_frontier_sync(g, w, src, start, TILE)
+    dist, it, ed, ok = frontier.sssp_frontier_sync(g, w, src, start, TILE, sparse=None)
     assert ok and np.array_equal(dist, oracle.dijkstra(g, w, src))
     d_sync, it_sync, upd, ok2 = oracle.sssp(g, w, src, oracle.SYNC)
     assert ok2 and it == it_sync and np.array_equal(dist, d_sync)
@@ -85,3 +87,19 @@ def test_unreachable_and_single_tile():
     assert ok and list(dist) == [0, 3, 7, oracle.INF, oracle.INF] and it == 3
     # one tile: all or nothing; sweep 3 has no tile, since vertex 2 (changed in sweep 2) has no out-edge
     assert list(ed) == [2, 2, 0]
+
+
+def test_dense_sweeps_run_everything_and_never_undercount():
+    # with the dense shortcut a sweep either runs every edge or exactly the marked tiles
+    g = I.rmat(10, 16, seed=6)
+    w = I.weights_u32(g, 6)
+    src = int(I.sources(g, 1, seed=6)[0])
+    start = oracle.partition(g, 4)
+    d_all, it_all, ed_all, _ = frontier.sssp_frontier_sync(g, w, src, start, 128, sparse=None)
+    d_sw, it_sw, ed_sw, ok = frontier.sssp_frontier_sync(g, w, src, start, 128, sparse=4.0)
+    assert ok and np.array_equal(d_sw, d_all) and it_sw == it_all
+    assert np.all((ed_sw == g.m) | (ed_sw == ed_all))
+    assert np.all(ed_sw >= ed_all)
+    # with a threshold of 0 every sweep after the first is dense
+    ed0 = frontier.sssp_frontier_sync(g, w, src, start, 128, sparse=0.0)[2]
+    assert np.all(ed0 == g.m)
