@@ -50,6 +50,21 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def replica_aggregate(ms_local, world, edges_per_rank, device):
+    """Whole-job result of N independent replicas: the slowest rank's time
+    (max over ranks) and every rank's solved edges over it, in GTEPS. With one
+    rank there is nothing to exchange."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        tt = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_local = float(tt.item())
+        dist.barrier()
+    return ms_local, world * edges_per_rank / (ms_local * 1e-3) / 1e9
+
+
 def _dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -218,14 +233,9 @@ def run_gpu(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms_total = t_start.elapsed_time(t_end)
-    if world > 1:
-        tt = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_total = float(tt.item())
-        dist.barrier()
-    ms_step = ms_total / K
     solves = 1 + N_SOURCES
-    value = world * solves * m * K / (ms_total * 1e-3) / 1e9
+    ms_total, value = replica_aggregate(ms_total, world, solves * m * K, dev)
+    ms_step = ms_total / K
 
     # statuses of the timed solves: one more checked step (results must match the warm-up)
     _, st_pr = dag.pagerank(plan, 0.85, 1e-6, "delayed", pr_dl, 1000, out=rank_out, reads=pr_rd)
