@@ -60,7 +60,10 @@ struct __align__(128) SyncBlock {
     double acc_res[3];           // per-sweep residual sums, slot = sweep % 3 (init = slot 2)
     double acc_g[3];             // per-sweep global sums (N for PageRank, sum lambda for the adjoint)
     long long edges;             // edges processed (frontier sweeps)
-    double pad1[3];
+    int fr_cnt[3];               // frontier, shared sweeps: tiles in the sweep's list, slot = sweep % 3
+    int fr_head[3];              //   tiles claimed so far
+    int fr_nchg[3];              //   rows logged as changed
+    int pad2[3];
     alignas(128) double stripe[GSTRIPES * GSTRIDE];  // live global sum (async / delayed)
 };
 
@@ -109,6 +112,8 @@ struct SweepParams {
     int* fr_act;            // [tiles] sweep stamp of the last mark (zero before the first sweep)
     int* fr_alist;          // [tiles] the CTAs' active tiles of the current sweep
     int* fr_chg;            // [n] the CTAs' rows that changed in the current sweep
+    int* fr_glist;          // [tiles] shared sweeps: the tiles any CTA may claim
+    int* fr_gchg;           // [n + tiles] shared sweeps: rows logged as changed (a row may repeat)
     // init / output
     const float* init;      // warm start (PR) or nullptr
     void* out;              // float r / lambda, or uint32 dist
@@ -130,6 +135,8 @@ struct Partition {
     int* fr_act = nullptr;    // device [tiles]
     int* fr_alist = nullptr;  // device [tiles]
     int* fr_chg = nullptr;    // device [n]
+    int* fr_glist = nullptr;  // device [tiles]
+    int* fr_gchg = nullptr;   // device [n + tiles]
 };
 
 }  // namespace dag

@@ -232,6 +232,8 @@ int frontier_maps(dag_plan* plan, Partition* part, cudaStream_t s)
     DAG_CUDA(cudaMalloc(&part->fr_oend, (size_t)std::max(m, 1LL) * sizeof(int)));
     DAG_CUDA(cudaMalloc(&part->fr_alist, (size_t)std::max(part->tiles, 1) * sizeof(int)));
     DAG_CUDA(cudaMalloc(&part->fr_chg, (size_t)n * sizeof(int)));
+    DAG_CUDA(cudaMalloc(&part->fr_glist, (size_t)std::max(part->tiles, 1) * sizeof(int)));
+    DAG_CUDA(cudaMalloc(&part->fr_gchg, ((size_t)n + (size_t)std::max(part->tiles, 1)) * sizeof(int)));
     DAG_CUDA(cudaMalloc(&ocol, (size_t)std::max(m, 1LL) * sizeof(int)));
     DAG_CUDA(cudaMalloc(&perm, (size_t)std::max(m, 1LL) * sizeof(int)));
     int rc = launch_transpose(plan, plan->fr_orow, ocol, perm, s);
@@ -376,6 +378,8 @@ extern "C" int dag_plan_destroy(dag_plan* p)
         cudaFree(kv.second.fr_act);
         cudaFree(kv.second.fr_alist);
         cudaFree(kv.second.fr_chg);
+        cudaFree(kv.second.fr_glist);
+        cudaFree(kv.second.fr_gchg);
     }
     cudaFree(p->fr_orow);
     delete p;

@@ -413,7 +413,8 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
             // sparse next sweep: stamp the tiles the changed rows feed, publish, run only those
             dense = gprev > FR_SPARSE * (double)p.cta_tile[p.nblocks];
             if (!dense) {
-                mark_out_tiles(p.fr_chg + row_lo, sh.nchg, p.fr_orow, p.fr_otile, p.fr_oend, p.fr_act, it);
+                mark_out_tiles(p.fr_chg + row_lo, sh.nchg, p.fr_orow, p.fr_otile, p.fr_oend, p.fr_act, it, warp,
+                               NWARP);
                 if (!grid_barrier(sb, p.nblocks, bar_target, p.timeout_ns)) return;
             }
         }
@@ -617,6 +618,8 @@ int launch_sweep(dag_plan* plan, int mode, int variant, int delta, SweepParams& 
         p.fr_act = part->fr_act;
         p.fr_alist = part->fr_alist;
         p.fr_chg = part->fr_chg;
+        p.fr_glist = part->fr_glist;
+        p.fr_gchg = part->fr_gchg;
         DAG_CUDA(cudaMemsetAsync(part->fr_act, 0, (size_t)std::max(part->tiles, 1) * sizeof(int), s));
     }
     // the asynchronous form's tile copies are TMA bulk copies from 16-byte boundaries of these arrays

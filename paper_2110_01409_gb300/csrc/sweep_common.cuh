@@ -59,6 +59,7 @@ struct SweepShared {
     int abort;                           // a bounded wait of this CTA ran out (TMA kernel)
     int nchg;                            // frontier: rows of this CTA changed in the sweep
     int cnt[NWARP];                      // frontier: per-warp counts of the active-tile scan
+    int tq[RING];                        // TMA kernel: the tile of each ring slot (-1: none)
     double res;                          // broadcast of the sweep residual
     double gprev;                        // broadcast of the previous sweep's global sum
     double T;                            // broadcast of the teleport total / ||c||_1
@@ -218,18 +219,47 @@ __device__ __forceinline__ int active_tiles(SH& sh, const int* act, int s, int t
 }
 
 // Stamps s + 1 on the tiles that the rows in chg[0 .. nchg) feed: one warp per
-// changed row, its lanes over the row's out-edges.
+// changed row (rows first, first + stride, ...), its lanes over the row's
+// out-edges. A CTA's own list: first = warp, stride = NWARP; a list shared by
+// the grid: first = blockIdx * NWARP + warp, stride = gridDim * NWARP.
 __device__ __forceinline__ void mark_out_tiles(const int* chg, int nchg, const int* orow, const int* otile,
-                                               const int* oend, int* act, int s)
+                                               const int* oend, int* act, int s, int first, int stride)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int k = warp; k < nchg; k += NWARP) {
+    const int lane = threadIdx.x & 31;
+    for (int k = first; k < nchg; k += stride) {
         const int v = chg[k];
         const int e1 = orow[v + 1];
         for (int e = orow[v] + lane; e < e1; e += 32) {
             const int t1 = oend[e];
             for (int t = otile[e]; t <= t1; ++t) act[t] = s + 1;
         }
+    }
+}
+
+// Appends this CTA's tiles stamped s to the grid's list glist[0 .. *gcnt)
+// (one atomic per chunk of NT tiles; the order within the list is free).
+template <class SH>
+__device__ __forceinline__ void publish_tiles(SH& sh, const int* act, int s, int tile_lo, int tile_hi, int* glist,
+                                              int* gcnt)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int base = tile_lo; base < tile_hi; base += NT) {
+        const int t = base + tid;
+        const bool on = t < tile_hi && act[t] == s;
+        const unsigned bal = __ballot_sync(0xffffffffu, on);
+        if (lane == 0) sh.cnt[warp] = __popc(bal);
+        __syncthreads();
+        int before = 0, all = 0;
+#pragma unroll
+        for (int k = 0; k < NWARP; ++k) {
+            before += k < warp ? sh.cnt[k] : 0;
+            all += sh.cnt[k];
+        }
+        __syncthreads();  // everyone has read sh.cnt
+        if (tid == 0) sh.cnt[0] = all ? atomicAdd(gcnt, all) : 0;
+        __syncthreads();
+        if (on) glist[sh.cnt[0] + before + __popc(bal & ((1u << lane) - 1u))] = t;
+        __syncthreads();  // sh.cnt free again
     }
 }
 

@@ -284,29 +284,44 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
         float res_part = 0.0f, g_part = 0.0f, dg_part = 0.0f;
         uint32_t carry = Op<MODE>::identity();  // thread 0: partial of the row continuing into the next tile
 
-        // Tiles of this sweep: all of the CTA's, or (frontier) the stamped ones.
-        int ntl = tile_hi - tile_lo;
+        // Tiles of this sweep. Own sweeps: the CTA's own range, in order, with the
+        // carry of a row passed from tile to tile. Shared sweeps (frontier, after a
+        // sweep that changed few rows): the CTAs claim tiles of the sweep's list one
+        // at a time, so a thin frontier is spread over all of them; every row
+        // write is then an atomicMin (a partial row is as valid a relaxation as a
+        // whole one) and own-block L1 reads are off (any CTA may write any row).
+        const bool shared = FRONTIER && !dense;
+        const int own_n_sweep = shared ? 0 : own_n;
+        int next_own = tile_lo;  // own sweeps: the next tile to hand out
+        const int list_cnt = shared ? ld_relaxed_i32(&sb->fr_cnt[slot]) : 0;
         if constexpr (FRONTIER) {
             __syncthreads();  // the previous sweep's marks are done with sh.nchg
             if (tid == 0) sh.nchg = 0;
-            if (!dense) ntl = active_tiles(sh, p.fr_act, it, tile_lo, tile_hi, p.fr_alist);
         }
-        auto tile_at = [&](int i) { return (FRONTIER && !dense) ? p.fr_alist[tile_lo + i] : tile_lo + i; };
-        int t_prev = -2;  // frontier: the tile run before, for the carry
+        // thread 0: the tile of ring position q, or -1 when the sweep has no more
+        auto pick = [&]() -> int {
+            if (!shared) return next_own < tile_hi ? next_own++ : -1;
+            const int k = atomicAdd(&sb->fr_head[slot], 1);
+            return k < list_cnt ? p.fr_glist[k] : -1;
+        };
 
         // Pipeline: tile t+2's inputs are being copied and tile t+1's gathers are in
         // flight while tile t is walked, scanned and finished.
         uint32_t term[IPT];  // gathered values of the next tile
         double gs = 0.0;     // warp 0: one stripe of the live global sum for the next tile
         if (tid == 0) {
-            if (ntl > 0) issue_fill<MODE>(ring, sh.fill_bar, qbase, p, X, tile_at(0), pol_edge, pol_vertex);
-            if (ntl > 1) issue_fill<MODE>(ring, sh.fill_bar, qbase + 1, p, X, tile_at(1), pol_edge, pol_vertex);
+            for (int k = 0; k < 2; ++k) {
+                const int t = pick();
+                sh.tq[(qbase + k) % RING] = t;
+                if (t >= 0) issue_fill<MODE>(ring, sh.fill_bar, qbase + k, p, X, t, pol_edge, pol_vertex);
+            }
         }
-        if (ntl > 0) {
-            const TileGeo g0 = tile_geo(p, tile_at(0));
+        __syncthreads();  // the first two tiles are known
+        if (sh.tq[qbase % RING] >= 0) {
+            const TileGeo g0 = tile_geo(p, sh.tq[qbase % RING]);
             if (mbar_wait(&sh.fill_bar[qbase % RING], (qbase / RING) & 1u, p.timeout_ns)) {
                 const int* cr = (const int*)(ring + R::OFF_CR) + (qbase % RING) * R::CR_INTS;
-                gather_tile(term, cr + g0.col_off(), g0.NB, X, tid, pol_vertex, own_lo, own_n);
+                gather_tile(term, cr + g0.col_off(), g0.NB, X, tid, pol_vertex, own_lo, own_n_sweep);
             } else {
                 sh.abort = 1;
                 atomicCAS(&sb->err, 0, DAG_ERR_BARRIER_TIMEOUT);
@@ -318,9 +333,11 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
             }
         }
 
-        for (int i = 0; i < ntl; ++i) {
-            const int t = tile_at(i);
-            const uint32_t q = qbase + (uint32_t)i;
+        uint32_t ntl = 0;  // tiles run in this sweep (ring positions used)
+        for (;; ++ntl) {
+            const uint32_t q = qbase + ntl;
+            const int t = sh.tq[q % RING];
+            if (t < 0) break;
             const TileGeo g = tile_geo(p, t);
             const int a0 = g.a0, b0 = g.b0, NA = g.NA, NB = g.NB;
             const int* rend = (const int*)(ring + R::OFF_CR) + (q % RING) * R::CR_INTS + g.rend_off();
@@ -345,22 +362,25 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
             }
             __syncthreads();  // (A) tile staged; every thread is done with the previous tile
 
-            const bool more = i + 1 < ntl;
+            const int t1 = sh.tq[(q + 1) % RING];  // the next tile (known since the previous tile)
+            const bool more = t1 >= 0;
             const float gt = LIVE_G ? sh.gt : 0.0f;
             if constexpr (FRONTIER) {
-                if (tid == 0 && t != t_prev + 1) carry = Op<MODE>::identity();  // the row before was not run
-                t_prev = t;
+                if (tid == 0 && shared) carry = Op<MODE>::identity();  // a claimed tile starts afresh
                 if (tid == 0) edges_done += NB;
             }
             // -------- the copies of the tile after next, the next tile's gathers --------
-            if (tid == 0 && i + 2 < ntl)
-                issue_fill<MODE>(ring, sh.fill_bar, q + 2, p, X, tile_at(i + 2), pol_edge, pol_vertex);
+            if (tid == 0) {
+                const int t2 = more ? pick() : -1;
+                sh.tq[(q + 2) % RING] = t2;  // the slot of tile i-1, which nobody reads any more
+                if (t2 >= 0) issue_fill<MODE>(ring, sh.fill_bar, q + 2, p, X, t2, pol_edge, pol_vertex);
+            }
             if (more) {
-                const TileGeo g1 = tile_geo(p, tile_at(i + 1));
+                const TileGeo g1 = tile_geo(p, t1);
                 const uint32_t q1 = q + 1;
                 if (mbar_wait(&sh.fill_bar[q1 % RING], (q1 / RING) & 1u, p.timeout_ns)) {
                     const int* cr1 = (const int*)(ring + R::OFF_CR) + (q1 % RING) * R::CR_INTS;
-                    gather_tile(term, cr1 + g1.col_off(), g1.NB, X, tid, pol_vertex, own_lo, own_n);
+                    gather_tile(term, cr1 + g1.col_off(), g1.NB, X, tid, pol_vertex, own_lo, own_n_sweep);
                 } else {
                     sh.abort = 1;
                     atomicCAS(&sb->err, 0, DAG_ERR_BARRIER_TIMEOUT);
@@ -374,17 +394,31 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
 
             // -------- merge-path walk over this thread's IPT items, block segmented scan --------
             const WalkOut w = walk_tile<MODE, false>(sh, [&](int i) { return rend[i] - b0; }, NA, NB, carry);
-            __syncthreads();  // (B) warp run totals visible
+            __syncthreads();  // (B) warp run totals visible; sh.tq of the tile after next written
             if (sh.abort) {   // a staging wait ran out (error recorded): drain own copies, leave
                 if (tid == 0) {
                     if (more) (void)mbar_wait(&sh.fill_bar[(q + 1) % RING], ((q + 1) / RING) & 1u, p.timeout_ns);
-                    if (i + 2 < ntl)
+                    if (sh.tq[(q + 2) % RING] >= 0)
                         (void)mbar_wait(&sh.fill_bar[(q + 2) % RING], ((q + 2) / RING) & 1u, p.timeout_ns);
                 }
                 return;  // the other CTAs' barrier waits end on the recorded error
             }
             const uint32_t E_last = finish_scan<MODE>(sh, w);
-            if (tid == 0) carry = E_last;  // partial of row NA for the next tile
+            if (tid == 0) {
+                if (!shared) {
+                    carry = E_last;  // partial of row NA for the next tile
+                } else if constexpr (FRONTIER) {
+                    if (E_last != Op<MODE>::identity()) {  // the row continuing into another tile: relax it now
+                        const int v = a0 + NA;
+                        const uint32_t old = atomicMin(X + v, E_last);
+                        if (E_last < old) {
+                            res_part += 1.0f;
+                            p.fr_gchg[atomicAdd(&sb->fr_nchg[slot], 1)] = v;
+                            marks += p.fr_orow[v + 1] - p.fr_orow[v];
+                        }
+                    }
+                }
+            }
             __syncthreads();  // (C) row sums final
 
             // -------- epilogue: new values of the rows this tile completed --------
@@ -395,6 +429,18 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
                 const int r = tid + k * NT;
                 if (r >= NA) break;
                 const int v = a0 + r;
+                if constexpr (FRONTIER) {
+                    if (shared) {
+                        const uint32_t sum = sh.rowsum[r];
+                        const uint32_t prev = atomicMin(X + v, sum);
+                        if (sum < prev) {
+                            res_part += 1.0f;
+                            p.fr_gchg[atomicAdd(&sb->fr_nchg[slot], 1)] = v;
+                            marks += p.fr_orow[v + 1] - p.fr_orow[v];
+                        }
+                        continue;
+                    }
+                }
                 uint32_t xo_bits;
                 float dg = 0.0f;
                 if (k == 0) {  // the first NT rows' inputs came with the tile
@@ -420,7 +466,7 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
                 if (lane == 0 && s != 0.0f) atomicAdd(&sb->stripe[(c % GSTRIPES) * GSTRIDE], (double)s);
             }
         }  // tiles
-        qbase += (uint32_t)ntl;
+        qbase += ntl;
 
         // -------- end of sweep: residual, barrier, stopping rule (frontier: tile marks) --------
         double res_d = (double)res_part, g_d = FRONTIER ? (double)marks : (double)g_part;  // marks: exact in FP64
@@ -435,11 +481,17 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
         if (!grid_barrier(sb, p.nblocks, bar_target, p.timeout_ns)) return;
         if (tid == 0) {
             sh.res = ld_relaxed_f64(&sb->acc_res[slot]);
-            if (FRONTIER) sh.gprev = ld_relaxed_f64(&sb->acc_g[slot]);
+            if (FRONTIER) {
+                sh.gprev = ld_relaxed_f64(&sb->acc_g[slot]);
+                sh.cnt[0] = ld_relaxed_i32(&sb->fr_nchg[slot]);
+            }
             if (c == 0) {
                 const int dead = (it + 2) % 3;  // read by everyone before this barrier
                 sb->acc_res[dead] = 0.0;
                 sb->acc_g[dead] = 0.0;
+                sb->fr_cnt[dead] = 0;
+                sb->fr_head[dead] = 0;
+                sb->fr_nchg[dead] = 0;
             }
         }
         __syncthreads();
@@ -450,10 +502,19 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
             break;
         }
         if constexpr (FRONTIER) {
-            // sparse next sweep: stamp the tiles the changed rows feed, publish, run only those
+            // sparse next sweep: stamp the tiles the changed rows feed, publish them in one list, run that
+            const bool was_shared = shared;
+            const int gchg_cnt = sh.cnt[0];
             dense = sh.gprev > FR_SPARSE * (double)p.cta_tile[p.nblocks];
             if (!dense) {
-                mark_out_tiles(p.fr_chg + row_lo, sh.nchg, p.fr_orow, p.fr_otile, p.fr_oend, p.fr_act, it);
+                if (was_shared)
+                    mark_out_tiles(p.fr_gchg, gchg_cnt, p.fr_orow, p.fr_otile, p.fr_oend, p.fr_act, it,
+                                   c * NWARP + warp, p.nblocks * NWARP);
+                else
+                    mark_out_tiles(p.fr_chg + row_lo, sh.nchg, p.fr_orow, p.fr_otile, p.fr_oend, p.fr_act, it,
+                                   warp, NWARP);
+                if (!grid_barrier(sb, p.nblocks, bar_target, p.timeout_ns)) return;
+                publish_tiles(sh, p.fr_act, it + 1, tile_lo, tile_hi, p.fr_glist, &sb->fr_cnt[(it + 1) % 3]);
                 if (!grid_barrier(sb, p.nblocks, bar_target, p.timeout_ns)) return;
             }
         }
