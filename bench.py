@@ -374,16 +374,29 @@ def run_e2e(args, g, w, srcs, dev, dag, torch, pr_choice, bf_choice):
     d2h = res_pr.numel() * 4 + res_bf.numel() * 4
     K = max(1, min(args.steps, 3))
 
+    side = torch.cuda.Stream()  # copies that overlap the solves: the weights in, the results out
+
     def step():
+        main = torch.cuda.current_stream()
         rp = rp_h.to(dev, non_blocking=True)
         ci = ci_h.to(dev, non_blocking=True)
-        wd = w_h.to(dev, non_blocking=True)
+        with torch.cuda.stream(side):  # the weights arrive while the plan is built and PageRank runs
+            wd = w_h.to(dev, non_blocking=True)
+        w_ready = side.record_event()
+        wd.record_stream(main)
         plan = dag.Plan(rp, ci)
         r, _ = dag.pagerank(plan, 0.85, 1e-6, "delayed", pr_choice[0], 1000, stats=False, reads=pr_choice[1])
-        res_pr.copy_(r, non_blocking=True)
+        side.wait_event(main.record_event())
+        with torch.cuda.stream(side):
+            res_pr.copy_(r, non_blocking=True)
+        r.record_stream(side)
+        main.wait_event(w_ready)
         for j, s in enumerate(srcs):
             d, _ = dag.sssp(plan, int(s), wd, "delayed", bf_choice[0], g.n + 1, stats=False, reads=bf_choice[1])
-            res_bf[j].copy_(d, non_blocking=True)
+            side.wait_event(main.record_event())  # this result goes out while the next source runs
+            with torch.cuda.stream(side):
+                res_bf[j].copy_(d, non_blocking=True)
+            d.record_stream(side)
         torch.cuda.synchronize()
         plan.close()
 

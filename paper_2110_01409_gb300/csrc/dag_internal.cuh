@@ -210,6 +210,7 @@ __global__ void k_check_rowptr(const int* rowptr, int n, long long m, int* bad);
 __global__ void k_out_degree(const int* colidx, long long m, int n, int* outdeg, int* bad);
 __global__ void k_degf(const int* outdeg, float* degf, int n);
 __global__ void k_cta_rows(const int* rowptr, int n, long long total, int P, int* cta_row);
+constexpr int CT_THREADS = 1024;  // threads of k_cta_tiles (one CTA)
 __global__ void k_cta_tiles(const int* rowptr, const int* cta_row, int P, int* cta_tile, int* max_rows);
 __global__ void k_tile_coords(const int* rowptr, int n, long long m, const int* cta_row, const int* cta_tile,
                               int P, int tiles, int* tile_row, int* tile_nz);

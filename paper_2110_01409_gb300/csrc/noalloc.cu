@@ -149,7 +149,7 @@ extern "C" int dag_pagerank_noalloc(const dag_csr* csr, float d, double tol, dag
     for (int iter = 0; iter < 6 && !settled; ++iter) {
         settled = true;
         k_cta_rows<<<(nb + 1 + 255) / 256, 256, 0, s>>>(rowptr, n, (long long)n + m, nb, cta_row);
-        k_cta_tiles<<<1, 1, 0, s>>>(rowptr, cta_row, nb, cta_tile, flags + 2);
+        k_cta_tiles<<<1, CT_THREADS, 0, s>>>(rowptr, cta_row, nb, cta_tile, flags + 2);
         DAG_CUDA(cudaMemcpyAsync(flags + 1, cta_tile + nb, sizeof(int), cudaMemcpyDeviceToDevice, s));
         DAG_CUDA(cudaMemcpyAsync(host_flags, flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
         DAG_CUDA(cudaStreamSynchronize(s));

@@ -1,6 +1,7 @@
 // Plan setup (untimed): CSR checks, out-degrees, the static vertex partition
 // of Sec. III-A per launch shape, the out-edge CSR and weight normalisation.
 #include <cub/device/device_radix_sort.cuh>
+#include <cub/block/block_scan.cuh>
 #include <cub/device/device_scan.cuh>
 
 #include <algorithm>
@@ -22,13 +23,18 @@ __global__ void k_check_rowptr(const int* rowptr, int n, long long m, int* bad)
     if (v < n && rowptr[v + 1] < x) atomicOr(bad, 1);
 }
 
+// Out-degree histogram of the sources. Lanes of a warp holding the same source
+// (hub vertices recur often) add their count with one atomic.
 __global__ void k_out_degree(const int* colidx, long long m, int n, int* outdeg, int* bad)
 {
+    const unsigned lane_lt = (1u << (threadIdx.x & 31)) - 1u;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < m;
          e += (long long)gridDim.x * blockDim.x) {
-        int u = colidx[e];
-        if (u < 0 || u >= n) { atomicOr(bad, 2); continue; }
-        atomicAdd(&outdeg[u], 1);
+        const int u = colidx[e];
+        const bool ok = u >= 0 && u < n;
+        if (!ok) atomicOr(bad, 2);
+        const unsigned peers = __match_any_sync(__activemask(), ok ? u : -1);
+        if (ok && (peers & lane_lt) == 0) atomicAdd(&outdeg[u], __popc(peers));
     }
 }
 
@@ -59,20 +65,36 @@ __global__ void k_cta_rows(const int* rowptr, int n, long long total, int P, int
     cta_row[p] = lo;
 }
 
-// Tile counts and their exclusive prefix, one thread (P is at most a few thousand).
-__global__ void k_cta_tiles(const int* rowptr, const int* cta_row, int P, int* cta_tile, int* max_rows)
+// Tile counts of the P blocks and their exclusive prefix (cta_tile[0..P]), and
+// the largest block's row count; one CTA of CT_THREADS threads, chunk by chunk.
+__global__ void __launch_bounds__(CT_THREADS) k_cta_tiles(const int* rowptr, const int* cta_row, int P,
+                                                          int* cta_tile, int* max_rows)
 {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    int acc = 0, mr = 0;
-    for (int p = 0; p < P; ++p) {
-        cta_tile[p] = acc;
-        int r0 = cta_row[p], r1 = cta_row[p + 1];
-        long long items = (long long)(r1 - r0) + (rowptr[r1] - rowptr[r0]);
-        acc += (int)((items + TILE - 1) / TILE);
-        mr = max(mr, r1 - r0);
+    using Scan = cub::BlockScan<int, CT_THREADS>;
+    __shared__ typename Scan::TempStorage tmp;
+    __shared__ int carry, mr;
+    if (threadIdx.x == 0) { carry = 0; mr = 0; }
+    for (int base = 0; base < P; base += CT_THREADS) {
+        const int p = base + threadIdx.x;
+        int cnt = 0;
+        if (p < P) {
+            const int r0 = cta_row[p], r1 = cta_row[p + 1];
+            const long long items = (long long)(r1 - r0) + (rowptr[r1] - rowptr[r0]);
+            cnt = (int)((items + TILE - 1) / TILE);
+            atomicMax(&mr, r1 - r0);
+        }
+        __syncthreads();  // carry of the previous chunk is final; tmp is free
+        int excl = 0, chunk = 0;
+        Scan(tmp).ExclusiveSum(cnt, excl, chunk);
+        if (p < P) cta_tile[p] = carry + excl;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += chunk;
     }
-    cta_tile[P] = acc;
-    *max_rows = mr;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        cta_tile[P] = carry;
+        *max_rows = mr;
+    }
 }
 
 __global__ void k_tile_coords(const int* rowptr, int n, long long m, const int* cta_row, const int* cta_tile,
@@ -112,7 +134,7 @@ int get_partition(dag_plan* plan, int P, Partition** out, cudaStream_t s)
     DAG_CUDA(cudaMalloc(&mr_dev, sizeof(int)));
     long long total = (long long)plan->n + plan->m;
     k_cta_rows<<<(P + 1 + 255) / 256, 256, 0, s>>>(plan->rowptr, plan->n, total, P, part.cta_row);
-    k_cta_tiles<<<1, 1, 0, s>>>(plan->rowptr, part.cta_row, P, part.cta_tile, mr_dev);
+    k_cta_tiles<<<1, CT_THREADS, 0, s>>>(plan->rowptr, part.cta_row, P, part.cta_tile, mr_dev);
     int tiles = 0;
     DAG_CUDA(cudaMemcpyAsync(&tiles, part.cta_tile + P, sizeof(int), cudaMemcpyDeviceToHost, s));
     DAG_CUDA(cudaMemcpyAsync(&part.max_rows, mr_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
