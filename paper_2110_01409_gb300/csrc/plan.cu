@@ -155,11 +155,28 @@ int get_partition(dag_plan* plan, int P, Partition** out, cudaStream_t s)
 // Out-edge CSR: a stable radix sort of the in-edges by source keeps, within
 // each source, the in-CSR order, i.e. ascending targets.
 // ---------------------------------------------------------------------------
+// dst[e] = the row of in-edge e. One warp per 32 rows, all lanes on each row's
+// edges in turn, so a hub row (tens of thousands of edges) is not one thread's.
 __global__ void k_edge_dst(const int* rowptr, int n, int* dst)
 {
-    int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= n) return;
-    for (int e = rowptr[v]; e < rowptr[v + 1]; ++e) dst[e] = v;
+    const int lane = threadIdx.x & 31;
+    const long long v0 = ((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5) * 32;
+    if (v0 >= n) return;
+    const int v1 = (int)min(v0 + 32, (long long)n);
+    for (int v = (int)v0; v < v1; ++v) {
+        const int e1 = rowptr[v + 1];
+        for (int e = rowptr[v] + lane; e < e1; e += 32) dst[e] = v;
+    }
+}
+
+// a[x] = t for x in [lo[t], lo[t+1]), t < count: one warp per segment.
+__global__ void k_fill_segments(const int* lo, int count, int* a)
+{
+    const int lane = threadIdx.x & 31;
+    const long long t = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    if (t >= count) return;
+    const int x1 = lo[t + 1];
+    for (int x = lo[t] + lane; x < x1; x += 32) a[x] = (int)t;
 }
 __global__ void k_iota(int* a, long long m)
 {
@@ -223,23 +240,15 @@ int launch_transpose(dag_plan* plan, int* out_rowptr, int* out_colidx, int* perm
 // Frontier maps: for every out-edge u -> v (out-CSR order), the tile holding its
 // in-CSR position and the tile holding v's row end. A change of u makes the
 // tiles between the two run again in the next sweep.
-__device__ __forceinline__ int last_le(const int* a, int len, long long x)  // last i < len with a[i] <= x
-{
-    int lo = 0, hi = len - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (a[mid] <= x) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
 
-__global__ void k_frontier_maps(const int* perm, const int* ocol, long long m, const int* tile_nz,
-                                const int* tile_row, int tiles, int* otile, int* oend)
+// otile[e] = etile[perm[e]], oend[e] = rtile[ocol[e]]: the tiles of every
+// out-edge's in-CSR position and of its target's row end.
+__global__ void k_frontier_maps(const int* perm, const int* ocol, long long m, const int* etile, const int* rtile,
+                                int* otile, int* oend)
 {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < m; e += (long long)gridDim.x * blockDim.x) {
-        otile[e] = last_le(tile_nz, tiles, perm[e]);
-        oend[e] = last_le(tile_row, tiles, ocol[e]);
+        otile[e] = etile[perm[e]];
+        oend[e] = rtile[ocol[e]];
     }
 }
 
@@ -260,10 +269,27 @@ int frontier_maps(dag_plan* plan, Partition* part, cudaStream_t s)
     DAG_CUDA(cudaMalloc(&perm, (size_t)std::max(m, 1LL) * sizeof(int)));
     int rc = launch_transpose(plan, plan->fr_orow, ocol, perm, s);
     if (rc == DAG_OK && m > 0 && part->tiles > 0) {
-        k_frontier_maps<<<2048, 256, 0, s>>>(perm, ocol, m, part->tile_nz, part->tile_row, part->tiles,
-                                             part->fr_otile, part->fr_oend);
-        const cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) rc = cuda_check(e, "frontier maps");
+        // the tile of every in-edge and of every row end (tiles cover both in order), then per out-edge
+        int *etile = nullptr, *rtile = nullptr;
+        if (cudaMalloc(&etile, (size_t)m * sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&rtile, (size_t)n * sizeof(int)) != cudaSuccess) {
+            cudaFree(etile);
+            cudaGetLastError();
+            rc = set_error(DAG_ERR_NOMEM, "frontier maps");
+        } else {
+            const int blocks = (int)(((long long)part->tiles * 32 + 255) / 256);
+            k_fill_segments<<<blocks, 256, 0, s>>>(part->tile_nz, part->tiles, etile);
+            k_fill_segments<<<blocks, 256, 0, s>>>(part->tile_row, part->tiles, rtile);
+            k_frontier_maps<<<2048, 256, 0, s>>>(perm, ocol, m, etile, rtile, part->fr_otile, part->fr_oend);
+            const cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) rc = cuda_check(e, "frontier maps");
+            if (rc == DAG_OK) {
+                const cudaError_t e2 = cudaStreamSynchronize(s);
+                if (e2 != cudaSuccess) rc = cuda_check(e2, "frontier maps");
+            }
+            cudaFree(etile);
+            cudaFree(rtile);
+        }
     }
     if (rc == DAG_OK) {
         const cudaError_t e = cudaStreamSynchronize(s);
