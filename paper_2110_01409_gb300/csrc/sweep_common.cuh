@@ -60,6 +60,7 @@ struct SweepShared {
     int nchg;                            // frontier: rows of this CTA changed in the sweep
     int cnt[NWARP];                      // frontier: per-warp counts of the active-tile scan
     int tq[RING];                        // TMA kernel: the tile of each ring slot (-1: none)
+    float dgw[NWARP];                    // TMA kernel: the warps' shares of a tile's change of N
     double res;                          // broadcast of the sweep residual
     double gprev;                        // broadcast of the previous sweep's global sum
     double T;                            // broadcast of the teleport total / ||c||_1

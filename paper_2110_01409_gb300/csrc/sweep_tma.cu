@@ -131,6 +131,23 @@ __device__ __forceinline__ void tma_load(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
+// Lane 0 of warp 1 adds the warps' shares of the last tile's change of the
+// live sum N to this CTA's stripe (one FP64 atomic per tile instead of one per
+// warp: the stripe lines are read by every CTA each tile) and clears them.
+template <class SH>
+__device__ __forceinline__ void flush_dg(SH& sh, SyncBlock* sb, int c)
+{
+    if (threadIdx.x == 32) {
+        float tot = 0.0f;
+#pragma unroll
+        for (int k = 0; k < NWARP; ++k) {
+            tot += sh.dgw[k];
+            sh.dgw[k] = 0.0f;
+        }
+        if (tot != 0.0f) atomicAdd(&sb->stripe[(c % GSTRIPES) * GSTRIDE], (double)tot);
+    }
+}
+
 // Thread 0: starts the copies of tile t into the ring slot of fill q.
 template <int MODE>
 __device__ __forceinline__ void issue_fill(unsigned char* ring, unsigned long long* bars, uint32_t q,
@@ -222,6 +239,7 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         sh.abort = 0;
         sh.nchg = 0;
+        for (int k = 0; k < NWARP; ++k) sh.dgw[k] = 0.0f;
     }
 
     // ---------------- initial values of the owned rows ----------------
@@ -361,6 +379,7 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
                 }
             }
             __syncthreads();  // (A) tile staged; every thread is done with the previous tile
+            if constexpr (LIVE_G) flush_dg(sh, sb, c);  // the previous tile's change of N, one atomic per CTA
 
             const int t1 = sh.tq[(q + 1) % RING];  // the next tile (known since the previous tile)
             const bool more = t1 >= 0;
@@ -460,13 +479,17 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
                 }
                 st_relaxed_b32(X + v, xnew);
             }
-            if constexpr (LIVE_G) {
+            if constexpr (LIVE_G) {  // this tile's change of N: one share per warp, added after barrier (A)
                 const float s = warp_sum(dg_part);
                 dg_part = 0.0f;
-                if (lane == 0 && s != 0.0f) atomicAdd(&sb->stripe[(c % GSTRIPES) * GSTRIDE], (double)s);
+                if (lane == 0) sh.dgw[warp] = s;
             }
         }  // tiles
         qbase += ntl;
+        if constexpr (LIVE_G) {
+            __syncthreads();  // the last tile's shares
+            flush_dg(sh, sb, c);
+        }
 
         // -------- end of sweep: residual, barrier, stopping rule (frontier: tile marks) --------
         double res_d = (double)res_part, g_d = FRONTIER ? (double)marks : (double)g_part;  // marks: exact in FP64
