@@ -36,7 +36,7 @@ constexpr int TILE = NT * IPT;    // items per tile
 constexpr int NWARP = NT / 32;
 constexpr int RING = 3;           // tile staging slots of the sweep kernel (tiles t, t+1, t+2)
 constexpr int GSTRIPES = 32;      // stripes of the live dangling/global-sum accumulator
-constexpr int GSTRIDE = 16;       // doubles between stripes: one 128-byte L2 line each, since
+constexpr int GSTRIDE = 16;       // 8-byte words between stripes: one 128-byte L2 line each, since
                                   // atomics to stripes sharing a line serialise on it
 
 enum Mode { MODE_PR = 0, MODE_PRW = 1, MODE_ADJ = 2, MODE_BF = 3, MODE_BF8 = 4 };  // BF8: uint8 weights
@@ -64,7 +64,7 @@ struct __align__(128) SyncBlock {
     int fr_head[3];              //   tiles claimed so far
     int fr_nchg[3];              //   rows logged as changed
     int pad2[3];
-    alignas(128) double stripe[GSTRIPES * GSTRIDE];  // live global sum (async / delayed)
+    alignas(128) long long stripe[GSTRIPES * GSTRIDE];  // live global sum, fixed point (async / delayed)
 };
 
 // Parameters of one sweep launch.
@@ -328,6 +328,12 @@ __device__ __forceinline__ double ld_relaxed_f64(const double* p)
 {
     double v;
     asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ long long ld_relaxed_i64(const long long* p)
+{
+    long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 __device__ __forceinline__ int ld_relaxed_i32(const int* p)

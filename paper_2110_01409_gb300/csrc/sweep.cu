@@ -58,7 +58,7 @@ struct Stage {
     int rend[IPT];       // tile-relative row ends
     uint32_t pfx[RP];    // old values of the first RP * NT rows
     float pfd[RP];       // their out-degrees
-    double gs;           // one stripe of the live global sum (warp 0)
+    long long gs;        // one stripe of the live global sum (warp 0)
 };
 
 // Issues the coalesced loads of tile t (everything except the gathers).
@@ -182,7 +182,6 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
             if (tid == 0) {
                 atomicAdd(&sb->acc_g[2], gpart);
                 atomicAdd(&sb->T, tpart);
-                if (LIVE_G) atomicAdd(&sb->stripe[(c % GSTRIPES) * GSTRIDE], gpart);
             }
         }
     }
@@ -200,6 +199,8 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
         T = (MODE == MODE_ADJ || p.base) ? sh.T : 1.0;
     }
     double gprev = BF ? 0.0 : sh.gprev;
+    LiveSum L{};
+    if constexpr (LIVE_G) L = live_sum_setup<MODE>(p, T, gprev);
     const double tol = (MODE == MODE_ADJ) ? p.tol * T : p.tol;
 
     // sync reads the previous iterate with ordinary loads; async reads the live
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
             stage_issue<MODE>(nx, p, xin, tile_at(0), tid, weak, pol_edge, pol_vertex);
             stage_gather<MODE>(nx, xin, tid, weak, pol_vertex, s_buf, 0, 0);
             if constexpr (LIVE_G) {
-                if (warp == 0) nx.gs = ld_relaxed_f64(&sb->stripe[lane * GSTRIDE]);
+                if (warp == 0) nx.gs = ld_relaxed_i64(&sb->stripe[lane * GSTRIDE]);
             }
         }
 
@@ -276,12 +277,9 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
 #pragma unroll
                 for (int k = 0; k < RP; ++k) { pf_x[k] = nx.pfx[k]; pf_d[k] = nx.pfd[k]; }
                 if constexpr (LIVE_G) {
-                    if (warp == 0) {
-                        // the tile's global term, formed once (FP64 is scarce on this part)
-                        const double G = warp_sum(nx.gs);
-                        if (lane == 0)
-                            sh.gt = (MODE == MODE_ADJ) ? (float)((double)p.g_coef * G)
-                                                       : (float)((double)p.g_coef * (T - G));
+                    if (warp == 0) {  // the tile's global term, formed once
+                        const long long G = warp_sum(nx.gs);
+                        if (lane == 0) sh.gt = live_term<MODE>(L, G);
                     }
                 }
             }
@@ -298,7 +296,7 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
                         __syncwarp();
                         if (lane == 0 && s != 0.0f) {
                             __threadfence();  // this warp's flushed values before its share of N
-                            atomicAdd(&sb->stripe[(c % GSTRIPES) * GSTRIDE], (double)s);
+                            live_add(sb, c % GSTRIPES, s, L.S);
                         }
                     }
                     if (tid == 0) {
@@ -323,7 +321,7 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
             float gt = gterm;
             if constexpr (LIVE_G) {
                 gt = sh.gt;
-                if (warp == 0 && more) nx.gs = ld_relaxed_f64(&sb->stripe[lane * GSTRIDE]);
+                if (warp == 0 && more) nx.gs = ld_relaxed_i64(&sb->stripe[lane * GSTRIDE]);
             }
 
             // -------- merge-path walk over this thread's IPT items, block segmented scan --------
@@ -362,11 +360,6 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
                 if constexpr (SYNC) st_weak_b32(xout + v, xnew);
                 else if constexpr (DELAYED) s_buf[v - buf_first] = xnew;
                 else st_relaxed_b32(xout + v, xnew);
-            }
-            if constexpr (VAR == DAG_ASYNC && !BF) {
-                const float s = warp_sum(dg_part);
-                dg_part = 0.0f;
-                if (lane == 0 && s != 0.0f) atomicAdd(&sb->stripe[(c % GSTRIPES) * GSTRIDE], (double)s);
             }
             if constexpr (DELAYED) {
                 buf_cnt += NA;

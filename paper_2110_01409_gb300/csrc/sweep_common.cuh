@@ -264,6 +264,71 @@ __device__ __forceinline__ void publish_tiles(SH& sh, const int* act, int s, int
     }
 }
 
+// ---------------------------------------------------------------------------
+// Live global sum N of the asynchronous and delayed sweeps (PageRank: the mass
+// on rows with out-edges, so that T - N is the dangling mass every row
+// receives, Sec. IV-A; adjoint: the sum of lambda), read by every tile. It is
+// kept in 64-bit fixed point with unit 2^-S: the stripes hold its change since
+// the start of the solve, added with integer atomics, and a reader sums them
+// with integer shuffles. No tile does FP64 arithmetic then (FP64 issues at a
+// small fraction of the FP32 rate on this part), and the sum does not depend
+// on the order in which the adds land. S is chosen once per solve so that the
+// bound 4 T / (1 - d) on |N| stays below 2^62 units.
+// ---------------------------------------------------------------------------
+struct LiveSum {
+    int S;           // the unit is 2^-S
+    long long base;  // PageRank: T - N(0); adjoint: N(0); in units
+    float scale;     // g_coef * 2^-S
+};
+
+// T: the teleport total (adjoint: ||c||_1); N0: N at the start of the solve.
+template <int MODE>
+__device__ __forceinline__ LiveSum live_sum_setup(const SweepParams& p, double T, double N0)
+{
+    LiveSum L;
+    int ex;
+    (void)frexp(4.0 * fmax(T, 1e-30) / fmax(1.0 - (double)p.d, 1e-3), &ex);  // the bound is below 2^ex
+    L.S = min(90, 62 - ex);
+    const double unit = ldexp(1.0, L.S);
+    L.base = __double2ll_rn(((MODE == MODE_ADJ) ? N0 : T - N0) * unit);
+    L.scale = (float)((double)p.g_coef / unit);
+    return L;
+}
+
+// f in units of 2^-S, rounded to nearest (ties away from zero), by integer
+// operations on its bits: |f| = m * 2^(e - 150) for the 24-bit significand m.
+// Subnormals (below any unit used here) give 0.
+__device__ __forceinline__ long long live_units(float f, int S)
+{
+    const uint32_t b = __float_as_uint(f);
+    const int e = (int)((b >> 23) & 0xffu);
+    if (e == 0) return 0;
+    const long long m = (long long)((b & 0x7fffffu) | 0x800000u);
+    const int sh = e - 150 + S;
+    long long r;
+    if (sh >= 0) r = sh < 39 ? m << sh : (1LL << 62);  // past the bound: saturate
+    else r = sh >= -24 ? ((m >> (-sh - 1)) + 1) >> 1 : 0;
+    return (b >> 31) ? -r : r;
+}
+
+// Adds f (a change of N) to stripe k.
+__device__ __forceinline__ void live_add(SyncBlock* sb, int k, float f, int S)
+{
+    const long long u = live_units(f, S);
+    if (u != 0) atomicAdd((unsigned long long*)&sb->stripe[k * GSTRIDE], (unsigned long long)u);
+}
+
+// The global term of a tile from the stripe sum G (the change of N): PageRank
+// g_coef (T - N), adjoint g_coef N. The 64-bit value is converted as
+// hi * 2^32 + lo (two exact-or-rounded 32-bit conversions, one rounded sum).
+template <int MODE>
+__device__ __forceinline__ float live_term(const LiveSum& L, long long G)
+{
+    const long long v = (MODE == MODE_ADJ) ? L.base + G : L.base - G;
+    const float f = (float)(int)(v >> 32) * 4294967296.0f + (float)(uint32_t)v;
+    return L.scale * f;
+}
+
 // New value of row v from its pull sum and old value (PageRank: x = r/outdeg
 // with dg = outdeg; adjoint: lambda; Bellman-Ford: dist), with the residual
 // and global-sum contributions.

@@ -132,10 +132,10 @@ __device__ __forceinline__ void tma_load(void* dst, const void* src, uint32_t by
 }
 
 // Lane 0 of warp 1 adds the warps' shares of the last tile's change of the
-// live sum N to this CTA's stripe (one FP64 atomic per tile instead of one per
+// live sum N to this CTA's stripe (one atomic per tile instead of one per
 // warp: the stripe lines are read by every CTA each tile) and clears them.
 template <class SH>
-__device__ __forceinline__ void flush_dg(SH& sh, SyncBlock* sb, int c)
+__device__ __forceinline__ void flush_dg(SH& sh, SyncBlock* sb, int c, int S)
 {
     if (threadIdx.x == 32) {
         float tot = 0.0f;
@@ -144,7 +144,7 @@ __device__ __forceinline__ void flush_dg(SH& sh, SyncBlock* sb, int c)
             tot += sh.dgw[k];
             sh.dgw[k] = 0.0f;
         }
-        if (tot != 0.0f) atomicAdd(&sb->stripe[(c % GSTRIPES) * GSTRIDE], (double)tot);
+        live_add(sb, c % GSTRIPES, tot, S);
     }
 }
 
@@ -269,7 +269,6 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
             if (tid == 0) {
                 atomicAdd(&sb->acc_g[2], gpart);
                 atomicAdd(&sb->T, tpart);
-                atomicAdd(&sb->stripe[(c % GSTRIPES) * GSTRIDE], gpart);
             }
         }
     }
@@ -283,6 +282,8 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
     }
     __syncthreads();
     if constexpr (!BF) T = (MODE == MODE_ADJ || p.base) ? sh.T : 1.0;  // a uniform teleport sums to 1 exactly
+    LiveSum L{};
+    if constexpr (LIVE_G) L = live_sum_setup<MODE>(p, T, sh.gprev);
     const double tol = (MODE == MODE_ADJ) ? p.tol * T : p.tol;
 
     const int own_lo = row_lo, own_n = p.own_l1 ? row_hi - row_lo : 0;
@@ -326,7 +327,7 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
         // Pipeline: tile t+2's inputs are being copied and tile t+1's gathers are in
         // flight while tile t is walked, scanned and finished.
         uint32_t term[IPT];  // gathered values of the next tile
-        double gs = 0.0;     // warp 0: one stripe of the live global sum for the next tile
+        long long gs = 0;    // warp 0: one stripe of the live global sum for the next tile
         if (tid == 0) {
             for (int k = 0; k < 2; ++k) {
                 const int t = pick();
@@ -347,7 +348,7 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
                 for (int k = 0; k < IPT; ++k) term[k] = 0u;
             }
             if constexpr (LIVE_G) {
-                if (warp == 0) gs = ld_relaxed_f64(&sb->stripe[lane * GSTRIDE]);
+                if (warp == 0) gs = ld_relaxed_i64(&sb->stripe[lane * GSTRIDE]);
             }
         }
 
@@ -369,17 +370,14 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
                     if (jj < NB) sh.val[jj] = edge_term<MODE>(term[k], aux, ao + jj);
                 }
                 if constexpr (LIVE_G) {
-                    if (warp == 0) {
-                        // the tile's global term, formed once (FP64 is scarce on this part)
-                        const double G = warp_sum(gs);
-                        if (lane == 0)
-                            sh.gt = (MODE == MODE_ADJ) ? (float)((double)p.g_coef * G)
-                                                       : (float)((double)p.g_coef * (T - G));
+                    if (warp == 0) {  // the tile's global term, formed once
+                        const long long G = warp_sum(gs);
+                        if (lane == 0) sh.gt = live_term<MODE>(L, G);
                     }
                 }
             }
             __syncthreads();  // (A) tile staged; every thread is done with the previous tile
-            if constexpr (LIVE_G) flush_dg(sh, sb, c);  // the previous tile's change of N, one atomic per CTA
+            if constexpr (LIVE_G) flush_dg(sh, sb, c, L.S);  // the previous tile's change of N, one atomic per CTA
 
             const int t1 = sh.tq[(q + 1) % RING];  // the next tile (known since the previous tile)
             const bool more = t1 >= 0;
@@ -407,7 +405,7 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
                     for (int k = 0; k < IPT; ++k) term[k] = 0u;
                 }
                 if constexpr (LIVE_G) {
-                    if (warp == 0) gs = ld_relaxed_f64(&sb->stripe[lane * GSTRIDE]);
+                    if (warp == 0) gs = ld_relaxed_i64(&sb->stripe[lane * GSTRIDE]);
                 }
             }
 
@@ -488,7 +486,7 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
         qbase += ntl;
         if constexpr (LIVE_G) {
             __syncthreads();  // the last tile's shares
-            flush_dg(sh, sb, c);
+            flush_dg(sh, sb, c, L.S);
         }
 
         // -------- end of sweep: residual, barrier, stopping rule (frontier: tile marks) --------
