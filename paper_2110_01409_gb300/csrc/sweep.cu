@@ -351,12 +351,8 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
                     if constexpr (!BF) dg = ld_stream_f32(p.degf + v);
                 }
                 const uint32_t xnew = row_update<MODE>(p, v, sum, xo_bits, dg, gt, res_part, g_part, dg_part);
-                if constexpr (FRONTIER) {
-                    if (xnew < xo_bits) {  // log the row and count the tile marks it would cause
-                        p.fr_chg[row_lo + atomicAdd(&sh.nchg, 1)] = v;
-                        marks += p.fr_orow[v + 1] - p.fr_orow[v];
-                    }
-                }
+                if constexpr (FRONTIER)  // the row goes on the CTA's list; its marks are counted at the sweep's end
+                    log_changed(p.fr_chg + row_lo, &sh.nchg, xnew < xo_bits, v, epilogue_lanes(NA, k));
                 if constexpr (SYNC) st_weak_b32(xout + v, xnew);
                 else if constexpr (DELAYED) s_buf[v - buf_first] = xnew;
                 else st_relaxed_b32(xout + v, xnew);
@@ -375,6 +371,10 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
         }
 
         // -------- end of sweep: residual, barrier, stopping rule (frontier: tile marks) --------
+        if constexpr (FRONTIER) {
+            __syncthreads();  // the CTA's list of changed rows is complete
+            marks += changed_marks(p.fr_chg + row_lo, sh.nchg, p.fr_orow);
+        }
         double res_d = (double)res_part, g_d = FRONTIER ? (double)marks : (double)g_part;  // marks: exact in FP64
         marks = 0;
         block_sum2(sh, res_d, g_d);

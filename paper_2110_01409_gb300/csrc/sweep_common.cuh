@@ -237,6 +237,42 @@ __device__ __forceinline__ void mark_out_tiles(const int* chg, int nchg, const i
     }
 }
 
+// The lanes of this warp whose epilogue row tid + k * NT is below NA (a
+// prefix of the warp; the caller's lane is one of them).
+__device__ __forceinline__ unsigned epilogue_lanes(int NA, int k)
+{
+    const int rem = NA - ((int)threadIdx.x & ~31) - k * NT;
+    return rem >= 32 ? 0xffffffffu : (1u << rem) - 1u;
+}
+
+// Appends row v to the CTA's list of changed rows when `changed` (one shared
+// atomic per warp; the order within the list is free). Every lane of `lanes`
+// calls it.
+__device__ __forceinline__ void log_changed(int* list, int* cnt, bool changed, int v, unsigned lanes)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned bal = __ballot_sync(lanes, changed);
+    if (bal == 0u) return;
+    const int leader = __ffs(bal) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(cnt, __popc(bal));
+    base = __shfl_sync(lanes, base, leader);
+    if (changed) list[base + __popc(bal & ((1u << lane) - 1u))] = v;
+}
+
+// This thread's share of the out-degree sum of the rows in list[0 .. cnt)
+// (the tile marks they would cause), read once at the end of a sweep so that
+// the loads are all in flight together instead of in each tile's epilogue.
+__device__ __forceinline__ int changed_marks(const int* list, int cnt, const int* orow)
+{
+    int s = 0;
+    for (int k = threadIdx.x; k < cnt; k += NT) {
+        const int v = list[k];
+        s += orow[v + 1] - orow[v];
+    }
+    return s;
+}
+
 // Appends this CTA's tiles stamped s to the grid's list glist[0 .. *gcnt)
 // (one atomic per chunk of NT tiles; the order within the list is free).
 template <class SH>

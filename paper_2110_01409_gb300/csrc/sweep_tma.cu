@@ -293,8 +293,8 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
     bool converged = false;
     double last_res = 0.0;
     uint32_t qbase = 0;  // ring fills of earlier sweeps (the i-th tile of a sweep is fill qbase + i)
-    long long edges_done = 0;  // frontier: edges of the tiles this CTA ran (thread 0)
-    long long marks = 0;       // frontier: out-degree sum of this thread's changed rows in the sweep
+    int edges_done = 0;        // frontier: edges of the tiles this CTA claimed in a shared sweep (thread 0)
+    int marks = 0;             // frontier: out-degree sum of this thread's changed rows in the sweep (<= m)
     bool dense = true;         // frontier: this sweep runs every tile
 
     for (; it < p.max_iters; ++it) {
@@ -383,8 +383,10 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
             const bool more = t1 >= 0;
             const float gt = LIVE_G ? sh.gt : 0.0f;
             if constexpr (FRONTIER) {
-                if (tid == 0 && shared) carry = Op<MODE>::identity();  // a claimed tile starts afresh
-                if (tid == 0) edges_done += NB;
+                if (tid == 0 && shared) {
+                    carry = Op<MODE>::identity();  // a claimed tile starts afresh
+                    edges_done += NB;
+                }
             }
             // -------- the copies of the tile after next, the next tile's gathers --------
             if (tid == 0) {
@@ -469,12 +471,8 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
                 }
                 const uint32_t xnew = row_update<MODE>(p, v, sh.rowsum[r], xo_bits, dg, gt, res_part, g_part,
                                                        dg_part);
-                if constexpr (FRONTIER) {
-                    if (xnew < xo_bits) {  // log the row and count the tile marks it would cause
-                        p.fr_chg[row_lo + atomicAdd(&sh.nchg, 1)] = v;
-                        marks += p.fr_orow[v + 1] - p.fr_orow[v];
-                    }
-                }
+                if constexpr (FRONTIER)  // the row goes on the CTA's list; its marks are counted at the sweep's end
+                    log_changed(p.fr_chg + row_lo, &sh.nchg, xnew < xo_bits, v, epilogue_lanes(NA, k));
                 st_relaxed_b32(X + v, xnew);
             }
             if constexpr (LIVE_G) {  // this tile's change of N: one share per warp, added after barrier (A)
@@ -490,13 +488,21 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
         }
 
         // -------- end of sweep: residual, barrier, stopping rule (frontier: tile marks) --------
+        if constexpr (FRONTIER) {
+            if (!shared) {  // an own sweep's changed rows are on the CTA's list (a shared sweep counted them)
+                __syncthreads();
+                marks += changed_marks(p.fr_chg + row_lo, sh.nchg, p.fr_orow);
+            }
+        }
         double res_d = (double)res_part, g_d = FRONTIER ? (double)marks : (double)g_part;  // marks: exact in FP64
         marks = 0;
         block_sum2(sh, res_d, g_d);
         if (tid == 0 && res_d != 0.0) atomicAdd(&sb->acc_res[slot], res_d);
         if (FRONTIER && tid == 0) {
             if (g_d != 0.0) atomicAdd(&sb->acc_g[slot], g_d);
-            if (edges_done) atomicAdd((unsigned long long*)&sb->edges, (unsigned long long)edges_done);
+            // edges of the tiles run: an own sweep runs all of the CTA's tiles
+            const int e = shared ? edges_done : p.tile_nz[tile_hi] - p.tile_nz[tile_lo];
+            if (e) atomicAdd((unsigned long long*)&sb->edges, (unsigned long long)e);
             edges_done = 0;
         }
         if (!grid_barrier(sb, p.nblocks, bar_target, p.timeout_ns)) return;
