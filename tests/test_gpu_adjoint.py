@@ -88,6 +88,34 @@ def test_adjoint_larger_graph_vs_jacobi_oracle(dag):
     assert _rel(gt.cpu().numpy(), gt_ref) <= 1e-4
 
 
+@pytest.fixture(scope="module")
+def scaled_case(dag):
+    g = I.rmat(14, 16, seed=12)
+    w, t, c = _problem(g, 6, 512)
+    val64, s64 = oracle.normalize(g, w.astype(np.float64))
+    rr = oracle.pagerank_fixed_point(g, 0.85, t, val64)
+    lam, _ = oracle.pagerank_adjoint(g, val64, c, 0.85, tol=1e-14)
+    gw_ref, gt_ref = oracle.pagerank_grads(g, val64, s64, 0.85, rr, lam)
+    return g, w, t, c, gw_ref, gt_ref
+
+
+@pytest.mark.parametrize("alpha", [1e-6, 1e6])
+@pytest.mark.parametrize("variant,delta", [("async", 0), ("delayed", 64)])
+def test_adjoint_gradients_scale_with_c(dag, scaled_case, variant, delta, alpha):
+    # The adjoint is linear in c and stops relative to ||c||_1, so c -> alpha c scales both
+    # gradients by alpha. The asynchronous and delayed sweeps keep the live sum of lambda in
+    # fixed point with a unit set from ||c||_1; this checks that unit far from ||c||_1 ~ 1.
+    g, w, t, c, gw_ref, gt_ref = scaled_case
+    plan = dag.Plan.from_graph(g, "cuda")
+    model = dag.WeightedPageRank(plan, tol=1e-7, variant=variant, delta=delta)
+    r, val, s, st = model.forward(torch.from_numpy(w).cuda(), torch.from_numpy(t.astype(np.float32)).cuda())
+    assert st["converged"]
+    gw, gt, _, st2 = model.backward(val, s, r, torch.from_numpy((c * alpha).astype(np.float32)).cuda())
+    assert st2["converged"]
+    assert _rel(gw.double().cpu().numpy() / alpha, gw_ref) <= 1e-4
+    assert _rel(gt.double().cpu().numpy() / alpha, gt_ref) <= 1e-4
+
+
 def test_transpose_and_normalize_match_definitions(dag):
     g = I.rmat(12, 16, seed=14)
     plan = dag.Plan.from_graph(g, "cuda")
