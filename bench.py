@@ -1,7 +1,7 @@
 """Benchmark: delayed-asynchronous PageRank + Bellman-Ford on RMAT scale 22.
 
 One step = one PageRank solve (d = 0.85, tol 1e-6) plus eight Bellman-Ford
-solves (fixed sources, uint32 weights in [1, 255]) on the RMAT scale-22 graph
+solves (fixed sources, one-byte weights in [1, 255]) on the RMAT scale-22 graph
 (a=.57 b=.19 c=.19, edge factor 16, seed 2), all in the persistent CUDA
 kernels behind the C ABI, each with the delayed method's buffer size delta
 picked by the autotuner among {0, 32, 256, 4096} (delta = 0 is the

@@ -1,0 +1,60 @@
+"""Host-side arithmetic of the benchmark's roofline figures (no GPU): the
+algorithmic bytes per sweep and per frontier launch, and the recorded-traffic
+lookup (scaling by sweeps or by edges run, null once the kernel sources no
+longer match the recorded hash)."""
+import os
+
+import pytest
+
+import bench
+
+
+def test_algorithmic_bytes_by_hand():
+    n, m = 10, 100
+    # rowptr 4(n+1) + own old + new value 8n (+ out-degree 4n for PageRank), colidx 4m + weights
+    assert bench.algorithmic_bytes(n, m, "pr") == 44 + 80 + 40 + 4 * 100
+    assert bench.algorithmic_bytes(n, m, "bf") == 44 + 80 + 8 * 100
+    assert bench.algorithmic_bytes(n, m, "bf8") == 44 + 80 + 5 * 100
+    # frontier launch: per-edge part over the edges run, per-vertex part left to the caller
+    assert bench.algorithmic_bytes(n, m, "bf8", edges=37) == (5 * 37, 44 + 80)
+
+
+def _record(tmp_path, digest):
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "sweep_traffic.txt").write_text(
+        "# comment: ignored\n"
+        f"sweep_source_sha256: {digest}\n"
+        f"sweep_tma_kernel<BF8> rmat{bench.SCALE} dram_bytes_per_sweep: 1000\n"
+        f"sweep_tma_kernel<BF8,frontier> rmat{bench.SCALE} dram_bytes_per_edge_run: 2.5\n")
+
+
+def test_recorded_traffic_scales_by_sweeps_and_edges(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "sweep_source_hash", lambda: "abc")
+    _record(tmp_path, "abc")
+    assert bench._recorded_traffic("sweep_tma_kernel<BF8>", 7) == 7000
+    assert bench._recorded_traffic("sweep_tma_kernel<BF8,frontier>", 11, edges=400) == 1000
+    assert bench._recorded_traffic("sweep_tma_kernel<PR>", 3) is None  # not recorded
+
+
+def test_recorded_traffic_is_null_after_a_source_change(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "sweep_source_hash", lambda: "new")
+    _record(tmp_path, "old")
+    assert bench._recorded_traffic("sweep_tma_kernel<BF8>", 7) is None
+
+
+def test_committed_record_parses():
+    path = os.path.join(bench.ROOT, "profiles", "sweep_traffic.txt")
+    keys = {}
+    with open(path) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#") and ":" in line:
+                k, v = line.split(":", 1)
+                keys[k.strip()] = v.strip()
+    assert len(keys["sweep_source_sha256"]) == 64
+    for kernel in ("sweep_tma_kernel<BF8>", "sweep_tma_kernel<PR>"):
+        assert float(keys[f"{kernel} rmat{bench.SCALE} dram_bytes_per_sweep"]) > 0
+    assert float(keys[f"sweep_tma_kernel<BF8,frontier> rmat{bench.SCALE} dram_bytes_per_edge_run"]) > 0
+    if keys["sweep_source_sha256"] != bench.sweep_source_hash():
+        pytest.skip("kernel sources changed since the capture: the bench reports traffic as null")
