@@ -174,9 +174,8 @@ int dag_pagerank(dag_plan* plan, float d, double tol, dag_variant variant, int32
 
 /*
  * Bellman-Ford SSSP (Sec. IV): dist'_v = min(dist_v, min over in-edges with
- * dist_u finite of dist_u + w_uv), every value stored every sweep (Sec. IV,
- * "unconditionally storing updates"); stops after a sweep that lowered no
- * value. d_w: uint32 weight per in-edge (device, [m]); d_dist (device,
+ * dist_u finite of dist_u + w_uv), every value stored every sweep, changed
+ * or not (Sec. IV); stops after a sweep that lowered no value. d_w: uint32 weight per in-edge (device, [m]); d_dist (device,
  * uint32 [n]) receives the distances, 0xFFFFFFFF for unreachable vertices.
  * flags: DAG_READ_* (delayed form only) | DAG_READ_OWN_L1 (async form only) |
  * DAG_SSSP_FRONTIER (sync and async forms).

@@ -38,8 +38,8 @@
  *    change sum_v |r'_v - r_v| is <= tol; "iters" counts the sweeps run,
  *    that last one included.
  *  - Bellman-Ford (Sec. IV): d'_v = min(d_v, min_{u in in(v), d_u < INF} d_u + w_uv),
- *    stop after a sweep that changed nothing. Every sweep stores every value
- *    ("unconditionally storing updates", Sec. IV).
+ *    stop after a sweep that changed nothing. Every sweep stores every value,
+ *    changed or not (Sec. IV).
  *  - Dijkstra's algorithm (binary heap) gives the exact distances.
  *  - The PageRank adjoint (no counterpart in the paper; the plain definition of
  *    the gradient of a linear fixed point) and its edge/teleport gradients.
