@@ -79,10 +79,17 @@ class Clocks:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, path: str | None = None):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # the samples go to --clocks-csv (rank-suffixed) when given, else to a temporary file
+        if path:
+            root, ext = os.path.splitext(path)
+            self.path = f"{root}_rank{index}{ext or '.csv'}"
+        else:
+            import tempfile
+
+            self.path = os.path.join(tempfile.gettempdir(), f"dag_bench_clocks_{os.getpid()}_rank{index}.csv")
 
     def start(self):
         try:
@@ -215,7 +222,7 @@ def run_gpu(args):
     pr_ev = [(ev(), ev()) for _ in range(K)]
     bf_ev = [[(ev(), ev()) for _ in range(N_SOURCES)] for _ in range(K)]
     t_start, t_end = ev(), ev()
-    clocks = Clocks(local)
+    clocks = Clocks(local, args.clocks_csv)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -647,6 +654,8 @@ def main():
     ap.add_argument("--impl", default="dag", choices=["dag", "reference"])
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--clocks-csv", default=None,
+                    help="keep the nvidia-smi clock samples of the timed region in this file (rank-suffixed)")
     ap.add_argument("--quick", dest="extras", action="store_false",
                     help="skip the variant table, the adjoint and the batched measurements")
     args = ap.parse_args()
