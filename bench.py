@@ -314,7 +314,7 @@ def run_gpu(args):
                                    "sssp": {_cand(c): round(c["ms"], 3) for c in tune_bf["candidates"]
                                             if "ms" in c}},
                    "n": n, "m": m, "sources": [int(s) for s in srcs], "workers": st_pr["workers"],
-                   "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (CSR+weights ~0.55 GB)",
+                   "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (CSR + one-byte weights 0.34 GB)",
                    "graph_gen_s": round(gen_s, 2)},
         "per_solve": {"pagerank_ms": round(pr_ms, 3), "pagerank_sweeps": pr_sweeps,
                       "sssp_ms": round(bf_ms, 3), "sssp_sweeps": bf_sweeps,
