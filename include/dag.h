@@ -226,6 +226,19 @@ int dag_sssp_batched(dag_plan* plan, dag_variant variant, int32_t delta, int32_t
                      dag_batch_stats* h_stats, void* stream);
 
 /*
+ * Batched launches through CUDA graphs (on != 0; off when a plan is created).
+ * dag_ppr_batched and dag_sssp_batched then capture each launch shape (kernel,
+ * grid, block, shared memory, control block) once into a graph owned by the
+ * plan: the reset of the per-column control block and the one cooperative
+ * kernel launch. Later calls of that shape replay it with their own arguments.
+ * When capture or instantiation fails, that shape falls back to the direct
+ * launch for the plan's lifetime. Results do not depend on the setting.
+ * dag_plan_destroy releases the graphs. Returns DAG_OK, or DAG_ERR_INVALID
+ * for a null plan.
+ */
+int dag_plan_set_batched_graph(dag_plan* plan, int32_t on);
+
+/*
  * Out-edge CSR of the plan's graph (for the adjoint pull). d_out_rowptr
  * (device int32 [n+1]), d_out_colidx (device int32 [m]: targets v of u's
  * out-edges, ascending), d_perm (device int32 [m]): in-edge index of each

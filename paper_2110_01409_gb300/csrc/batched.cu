@@ -12,6 +12,10 @@
 // chunk) pair: each warp buffers delta rows of its 32 columns in shared
 // memory and copies them out when the buffer is full or its block is done.
 #include <climits>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
 
 #include "dag_internal.cuh"
 
@@ -304,6 +308,124 @@ static BKernel bkernel_for(int is_bf, int variant)
     return table[is_bf][variant];
 }
 
+// ---------------------------------------------------------------------------
+// CUDA graphs of batched launches (dag_plan_set_batched_graph). A launch shape
+// (kernel, grid, block, shared memory, control block) is captured once into a
+// graph of two nodes: the reset of the control block and the cooperative
+// kernel. Every call replays it with its own kernel arguments. Capture runs on
+// a private stream (the caller's may be the legacy default stream, which
+// cannot be captured); when capture or instantiation fails, the shape is
+// marked and its calls launch directly. The cache sits here, keyed by plan,
+// and is released by dag_plan_destroy.
+// ---------------------------------------------------------------------------
+struct BatchGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t knode = nullptr;  // the kernel node, whose arguments each call sets
+    bool failed = false;              // capture or instantiation failed: launch directly
+};
+using ShapeKey = std::tuple<const void*, int, int, size_t, size_t, const void*>;
+struct PlanGraphs {
+    bool on = false;
+    std::map<ShapeKey, BatchGraph> shapes;
+};
+static std::mutex g_graph_mu;
+static std::map<const dag_plan*, PlanGraphs> g_graphs;
+
+static bool batched_graph_on(const dag_plan* plan)
+{
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    auto it = g_graphs.find(plan);
+    return it != g_graphs.end() && it->second.on;
+}
+
+// Records the reset and the kernel launch into bg (nothing runs); on any
+// failure bg.failed is set and the error state cleared.
+static void capture_shape(BatchGraph& bg, const void* k, int nb, int threads, size_t dyn, void* bsync,
+                          size_t cbytes, void** args)
+{
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        bg.failed = true;
+        return;
+    }
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    cudaGraphNode_t kn = nullptr;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        const cudaError_t e1 = cudaMemsetAsync(bsync, 0, cbytes, cs);
+        const cudaError_t e2 = cudaLaunchCooperativeKernel(k, dim3(nb), dim3(threads), args, dyn, cs);
+        const cudaError_t e3 = cudaStreamEndCapture(cs, &g);  // ends capture mode whatever happened
+        if (e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess && g &&
+            cudaGraphInstantiate(&ex, g, 0) == cudaSuccess) {
+            size_t cnt = 0;
+            if (cudaGraphGetNodes(g, nullptr, &cnt) == cudaSuccess && cnt > 0) {
+                std::vector<cudaGraphNode_t> nodes(cnt);
+                if (cudaGraphGetNodes(g, nodes.data(), &cnt) == cudaSuccess) {
+                    for (size_t i = 0; i < cnt; ++i) {
+                        cudaGraphNodeType t;
+                        if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
+                            kn = nodes[i];
+                    }
+                }
+            }
+        }
+    }
+    cudaStreamDestroy(cs);
+    if (!kn) {
+        if (ex) cudaGraphExecDestroy(ex);
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        bg.failed = true;
+        return;
+    }
+    bg.graph = g;
+    bg.exec = ex;
+    bg.knode = kn;
+}
+
+// One batched launch on stream s through the plan's graph of this shape
+// (captured on first use), or directly when the shape cannot be captured.
+static cudaError_t graph_launch(dag_plan* plan, const void* k, int nb, int threads, size_t dyn, size_t cbytes,
+                                void** args, cudaStream_t s)
+{
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    BatchGraph& bg = g_graphs[plan].shapes[ShapeKey(k, nb, threads, dyn, cbytes, plan->bsync)];
+    if (!bg.exec && !bg.failed) capture_shape(bg, k, nb, threads, dyn, plan->bsync, cbytes, args);
+    if (!bg.failed) {
+        cudaKernelNodeParams kp{};
+        kp.func = const_cast<void*>(k);
+        kp.gridDim = dim3(nb);
+        kp.blockDim = dim3(threads);
+        kp.sharedMemBytes = (unsigned)dyn;
+        kp.kernelParams = args;
+        kp.extra = nullptr;
+        // the replay must run with this call's arguments: if they cannot be set, or the graph
+        // cannot be launched, nothing was enqueued, and the shape launches directly from now on
+        if (cudaGraphExecKernelNodeSetParams(bg.exec, bg.knode, &kp) == cudaSuccess &&
+            cudaGraphLaunch(bg.exec, s) == cudaSuccess)
+            return cudaSuccess;
+        cudaGetLastError();
+        bg.failed = true;
+    }
+    const cudaError_t e = cudaMemsetAsync(plan->bsync, 0, cbytes, s);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchCooperativeKernel(k, dim3(nb), dim3(threads), args, dyn, s);
+}
+
+void release_batched_graphs(const dag_plan* plan)
+{
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    auto it = g_graphs.find(plan);
+    if (it == g_graphs.end()) return;
+    for (auto& kv : it->second.shapes) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+    }
+    g_graphs.erase(it);
+}
+
 int launch_batched(dag_plan* plan, int is_bf, int variant, int delta, int max_iters, int B, float d, double tol,
                    const void* V_or_src, const uint32_t* w, void* out, int* iters, dag_batch_stats* st,
                    cudaStream_t s)
@@ -365,7 +487,8 @@ int launch_batched(dag_plan* plan, int is_bf, int variant, int delta, int max_it
         }
         plan->bsync_bytes = cbytes;
     }
-    DAG_CUDA(cudaMemsetAsync(plan->bsync, 0, cbytes, s));
+    const bool use_graph = batched_graph_on(plan);
+    if (!use_graph) DAG_CUDA(cudaMemsetAsync(plan->bsync, 0, cbytes, s));  // the graph holds its own reset
     BatchParams p{};
     p.n = n;
     p.B = B;
@@ -402,7 +525,8 @@ int launch_batched(dag_plan* plan, int is_bf, int variant, int delta, int max_it
         cudaEventRecord(e0, s);
     }
     void* args[] = {(void*)&p};
-    cudaError_t le = cudaLaunchCooperativeKernel((const void*)k, dim3(nb), dim3(threads), args, dyn, s);
+    cudaError_t le = use_graph ? graph_launch(plan, (const void*)k, nb, threads, dyn, cbytes, args, s)
+                               : cudaLaunchCooperativeKernel((const void*)k, dim3(nb), dim3(threads), args, dyn, s);
     if (le != cudaSuccess) {
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
@@ -435,3 +559,11 @@ int launch_batched(dag_plan* plan, int is_bf, int variant, int delta, int max_it
 }
 
 }  // namespace dag
+
+extern "C" int dag_plan_set_batched_graph(dag_plan* plan, int32_t on)
+{
+    if (!plan) return dag::set_error(DAG_ERR_INVALID, "null plan");
+    std::lock_guard<std::mutex> lk(dag::g_graph_mu);
+    dag::g_graphs[plan].on = on != 0;
+    return DAG_OK;
+}

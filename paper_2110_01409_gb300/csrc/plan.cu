@@ -405,9 +405,14 @@ extern "C" int dag_plan_create(const dag_csr* csr, int32_t barrier_timeout_ms, d
     return DAG_OK;
 }
 
+namespace dag {
+void release_batched_graphs(const dag_plan* plan);  // batched.cu: the plan's CUDA graphs
+}
+
 extern "C" int dag_plan_destroy(dag_plan* p)
 {
     if (!p) return DAG_OK;
+    dag::release_batched_graphs(p);
     cudaFree(p->outdeg);
     cudaFree(p->degf);
     cudaFree(p->x0);

@@ -31,7 +31,7 @@ EXPORTS = (
     "dag_pagerank", "dag_sssp", "dag_ppr_batched", "dag_sssp_batched", "dag_transpose",
     "dag_normalize_weights", "dag_pagerank_adjoint", "dag_strerror", "dag_last_error_message",
     "dag_debug_skip_barrier_once", "dag_debug_stall_staging_once", "dag_tile_items", "dag_pagerank_noalloc", "dag_gather_f32", "dag_plan_set_worker_cap",
-    "dag_sssp_u8", "dag_probe_gather", "dag_access_matrix",
+    "dag_sssp_u8", "dag_probe_gather", "dag_access_matrix", "dag_plan_set_batched_graph",
 )
 
 
@@ -96,6 +96,7 @@ def lib():
             L.dag_tile_items.restype = _i32
             L.dag_gather_f32.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp]
             L.dag_plan_set_worker_cap.argtypes = [_vp, _i32]
+            L.dag_plan_set_batched_graph.argtypes = [_vp, _i32]
             L.dag_access_matrix.argtypes = [_vp, _i32, _vp, _vp]
             L.dag_probe_gather.argtypes = [_vp, ctypes.c_int64, _vp, _i32, _i32, _i32, ctypes.POINTER(_f32), _vp]
             L.dag_sssp_u8.argtypes = [_vp, ctypes.c_uint32, _i32, _i32, _i32, _vp, _vp, _i32,
@@ -189,6 +190,11 @@ class Plan:
         w = _i32(0)
         _raise(lib().dag_workers(self.h, _variant(variant), delta, ctypes.byref(w)), False)
         return w.value
+
+    def set_batched_graph(self, on: bool):
+        """Batched solves on this plan through CUDA graphs captured once per launch shape (on), or
+        launched directly (off, the default)."""
+        _raise(lib().dag_plan_set_batched_graph(self.h, 1 if on else 0), False)
 
     def set_worker_cap(self, max_workers: int):
         """At most max_workers CTAs per solve (0: as many as fit)."""
