@@ -41,6 +41,9 @@ WORKLOAD = (f"rmat{SCALE}: pagerank d=0.85 tol=1e-6 + sssp x{N_SOURCES} sources,
             f"(delta 0 also with own-block L1 reads, and for sssp the tile frontier)")
 
 
+HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e, nominal (the roofline's frac uses the measured copy peak)
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -321,6 +324,7 @@ def run_gpu(args):
                       "gteps_work_rate": round(((pr_sweeps + N_SOURCES * bf_sweeps) * m) / (ms_step * 1e-3) / 1e9, 3)},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "frac_of_nominal": round(achieved / HBM_NOMINAL_GBS, 4),
                      "bytes_per_launch": int(dom_bytes), "traffic": traffic},
         "gather_floor": gather_floor,
         "clocks": clk,
