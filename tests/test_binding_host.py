@@ -1,0 +1,45 @@
+"""The Python binding fails loudly instead of falling back to the CPU: host
+tensors and wrong shapes are refused before any library call, and a missing
+libdag.so is an ImportError (no GPU needed)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2110_01409_gb300 import dag
+import paper_2110_01409_gb300.inputs as I
+
+
+def test_plan_refuses_host_tensors():
+    g = I.rmat(6, 4, seed=1)
+    with pytest.raises(ValueError, match="CUDA"):
+        dag.Plan(torch.from_numpy(g.rowptr), torch.from_numpy(g.colidx))
+
+
+@pytest.mark.parametrize("bad", ["host", "dtype", "size", "strided"])
+def test_device_argument_checks(bad):
+    t = torch.zeros(8, dtype=torch.int32)
+    if bad == "dtype":
+        t = t.float()
+    elif bad == "size":
+        t = t[:7]
+    elif bad == "strided":
+        t = torch.zeros(16, dtype=torch.int32)[::2]
+    with pytest.raises(ValueError):
+        dag._dev(t, torch.int32, 8, "x")
+
+
+def test_missing_library_is_an_import_error(monkeypatch, tmp_path):
+    monkeypatch.setattr(dag, "LIB_PATH", str(tmp_path / "libdag.so"))
+    monkeypatch.setattr(dag, "_lib", None)
+    with pytest.raises(ImportError, match="libdag.so not found"):
+        dag.lib()
+
+
+def test_variant_and_read_mode_names():
+    assert dag._variant("sync") == 0 and dag._variant("async") == 1 and dag._variant("delayed") == 2
+    # read paths are disjoint bit flags of the ABI, combinations included
+    for name, flags in dag.READ_MODES.items():
+        parts = name.split("+")
+        if len(parts) > 1:
+            assert flags == sum(dag.READ_MODES[p] for p in parts), name
+    assert dag.READ_MODES["refresh"] == 0
