@@ -54,3 +54,36 @@ def test_null_arguments_rejected_on_host(lib):
     assert lib.dag_plan_create(None, 0, None) == -1
     assert lib.dag_pagerank(None, ctypes.c_float(0.85), ctypes.c_double(1e-6), 0, 0, 10, None, None, None, 0,
                             None, None) == -1
+
+
+def test_null_arguments_are_refused_without_a_gpu(lib):
+    # every entry point that takes a plan or a CSR refuses a null one with DAG_ERR_INVALID and a
+    # message, before touching the device; destroying a null plan is a no-op
+    f, d = ctypes.c_float, ctypes.c_double
+    N = None
+    lib.dag_last_error_message.restype = ctypes.c_char_p
+    calls = {
+        "dag_plan_create": lambda: lib.dag_plan_create(N, 0, ctypes.byref(ctypes.c_void_p())),
+        "dag_plan_out_degree": lambda: lib.dag_plan_out_degree(N, N, N),
+        "dag_partition": lambda: lib.dag_partition(N, 4, N),
+        "dag_workers": lambda: lib.dag_workers(N, 1, 0, ctypes.byref(ctypes.c_int32())),
+        "dag_plan_set_worker_cap": lambda: lib.dag_plan_set_worker_cap(N, 0),
+        "dag_plan_set_batched_graph": lambda: lib.dag_plan_set_batched_graph(N, 1),
+        "dag_pagerank": lambda: lib.dag_pagerank(N, f(0.85), d(1e-6), 1, 0, 10, N, N, N, 0, N, N),
+        "dag_sssp": lambda: lib.dag_sssp(N, 0, 1, 0, 10, N, N, 0, N, N),
+        "dag_sssp_u8": lambda: lib.dag_sssp_u8(N, 0, 1, 0, 10, N, N, 0, N, N),
+        "dag_ppr_batched": lambda: lib.dag_ppr_batched(N, f(0.85), d(1e-6), 1, 0, 10, 4, N, N, N, N, N),
+        "dag_sssp_batched": lambda: lib.dag_sssp_batched(N, 1, 0, 10, 4, N, N, N, N, N, N),
+        "dag_transpose": lambda: lib.dag_transpose(N, N, N, N, N),
+        "dag_normalize_weights": lambda: lib.dag_normalize_weights(N, N, N, N, N),
+        "dag_pagerank_adjoint": lambda: lib.dag_pagerank_adjoint(N, N, f(0.85), d(1e-6), 1, 0, 10, N, N, N, N, N,
+                                                                 N, N, N, N, N),
+        "dag_pagerank_noalloc": lambda: lib.dag_pagerank_noalloc(N, f(0.85), d(1e-6), 1, 0, 10, N, N, N, N),
+        "dag_access_matrix": lambda: lib.dag_access_matrix(N, 4, N, N),
+        "dag_debug_skip_barrier_once": lambda: lib.dag_debug_skip_barrier_once(N, 100),
+        "dag_debug_stall_staging_once": lambda: lib.dag_debug_stall_staging_once(N, 100),
+    }
+    for name, call in calls.items():
+        assert call() == -1, name
+        assert lib.dag_last_error_message(), name
+    assert lib.dag_plan_destroy(N) == 0
