@@ -167,6 +167,9 @@ int dag_plan_set_worker_cap(dag_plan* plan, int32_t max_workers);
  * (device, float [n]) receives r; with DAG_PR_WARM_START it also gives r^0.
  * Without it r^0 = t. FP32 values, FP64 residual and dangling sums.
  * flags: DAG_PR_WARM_START | one DAG_READ_* (delayed form only) | DAG_READ_OWN_L1 (async form only).
+ * A delayed sweep with 0 < delta < dag_tile_items() cuts its tiles so that
+ * none completes more than delta rows, so the buffer is flushed after about
+ * every delta rows (a tile's rows are computed together and flushed at its end).
  */
 int dag_pagerank(dag_plan* plan, float d, double tol, dag_variant variant, int32_t delta,
                  int32_t max_iters, const float* d_teleport, const float* d_val, float* d_rank,
@@ -291,8 +294,12 @@ int dag_pagerank_adjoint(dag_plan* in_plan, dag_plan* out_plan, float d, double 
  *  - Limits: n <= DAG_NOALLOC_MAX_N and m <= DAG_NOALLOC_MAX_M; a larger
  *    graph returns DAG_ERR_INVALID and changes nothing.
  *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current. Make that first call
- *    before any stream capture.
+ *    (cudaGetSymbolAddress) with that device current and keeps it for the
+ *    process. Make that first call before any stream capture. A device reset
+ *    (cudaDeviceReset) invalidates the kept address: after one, this entry
+ *    point must not be called again in the same process.
+ *  - The call checks the CSR on the device (rowptr order, colidx range) and
+ *    returns DAG_ERR_INVALID for a bad one.
  *  - All calls share the array, and it keeps the previous call's contents
  *    (each call clears what it needs zeroed). Calls whose GPU work overlaps,
  *    for instance on two streams, race on it: serialise them.

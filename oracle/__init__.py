@@ -57,7 +57,8 @@ def _load():
             _lib = ctypes.CDLL(_SO)
             for f in ("orc_pagerank_sync", "orc_pagerank_delayed", "orc_pagerank_delayed_view", "orc_sssp_sync",
                       "orc_sssp_delayed", "orc_sssp_delayed_view",
-                      "orc_dijkstra", "orc_pagerank_adjoint", "orc_pagerank_threads", "orc_sssp_threads"):
+                      "orc_dijkstra", "orc_pagerank_adjoint", "orc_pagerank_threads", "orc_sssp_threads",
+                      "orc_pagerank_sync_par"):
                 getattr(_lib, f).restype = ctypes.c_int
     return _lib
 
@@ -120,9 +121,22 @@ def pagerank(g, variant=SYNC, d=0.85, tol=1e-6, max_iters=10000, P=1, delta=0, t
     return r, int(iters.value), hist[: iters.value], rc == 0
 
 
-def pagerank_fixed_point(g, d=0.85, tele=None, val=None, tol=1e-13, max_iters=100000):
-    """The fixed point r* by fp64 Jacobi to an L1 change <= tol (error <= tol*d/(1-d))."""
-    r, it, _, ok = pagerank(g, SYNC, d=d, tol=tol, max_iters=max_iters, tele=tele, val=val)
+def pagerank_fixed_point(g, d=0.85, tele=None, val=None, tol=1e-13, max_iters=100000, threads=1):
+    """The fixed point r* by fp64 Jacobi to an L1 change <= tol (error <= tol*d/(1-d)).
+    threads > 1 computes each sweep's rows on that many OpenMP threads (same iterates)."""
+    if threads <= 1:
+        r, it, _, ok = pagerank(g, SYNC, d=d, tol=tol, max_iters=max_iters, tele=tele, val=val)
+    else:
+        tele, val = _f64(tele), _f64(val)
+        r = tele.copy() if tele is not None else np.full(g.n, 1.0 / g.n)
+        iters = ctypes.c_int32(0)
+        rc = _load().orc_pagerank_sync_par(ctypes.c_int32(g.n), _p(_i32(g.rowptr)), _p(_i32(g.colidx)), _p(val),
+                                           ctypes.c_double(d), _p(tele), ctypes.c_double(tol),
+                                           ctypes.c_int32(max_iters), ctypes.c_int32(threads), _p(r),
+                                           ctypes.byref(iters))
+        if rc < 0:
+            raise RuntimeError("oracle fixed point failed")
+        ok = rc == 0
     if not ok:
         raise RuntimeError("fixed point did not converge")
     return r

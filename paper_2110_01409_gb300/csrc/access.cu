@@ -50,7 +50,7 @@ extern "C" int dag_access_matrix(dag_plan* plan, int32_t workers, uint64_t* d_co
     if (!plan || !d_counts || workers < 1 || workers > 4096) return set_error(DAG_ERR_INVALID, "bad argument");
     cudaStream_t s = (cudaStream_t)stream;
     Partition* part = nullptr;
-    int rc = get_partition(plan, workers, &part, s);
+    int rc = get_partition(plan, workers, &part, s, 0);
     if (rc) return rc;
     DAG_CUDA(cudaMemsetAsync(d_counts, 0, (size_t)workers * workers * sizeof(unsigned long long), s));
     if (part->tiles == 0) return DAG_OK;

@@ -53,7 +53,7 @@ int launch_edge_grad(dag_plan* plan, float d, const float* val, const float* s_n
     (void)val;
     const int P = plan->num_sms * 4;
     Partition* part = nullptr;
-    int rc = get_partition(plan, P, &part, st);
+    int rc = get_partition(plan, P, &part, st, 0);
     if (rc) return rc;
     if (grad_w && plan->m > 0)
         k_edge_grad<<<P, NT, 0, st>>>(plan->rowptr, plan->colidx, part->cta_tile, part->tile_row, part->tile_nz, d,

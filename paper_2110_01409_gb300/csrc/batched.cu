@@ -462,7 +462,7 @@ int launch_batched(dag_plan* plan, int is_bf, int variant, int delta, int max_it
     int nb = per_sm * plan->num_sms;
     if (plan->worker_cap > 0 && nb > plan->worker_cap) nb = plan->worker_cap;
     Partition* part = nullptr;
-    int rc = get_partition(plan, nb, &part, s);
+    int rc = get_partition(plan, nb, &part, s, 0);
     if (rc) return rc;
     // workspace: X1 (sync) and the per-column control block
     size_t xbytes = (variant == DAG_SYNC) ? (size_t)n * B * 4 : 0;

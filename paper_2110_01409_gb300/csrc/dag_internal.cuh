@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <map>
 #include <string>
 #include <vector>
@@ -45,6 +46,9 @@ enum Mode { MODE_PR = 0, MODE_PRW = 1, MODE_ADJ = 2, MODE_BF = 3, MODE_BF8 = 4 }
 enum ReadMode { READ_CACHED_REFRESH = 0, READ_COHERENT = 1, READ_CACHED = 2 };
 
 constexpr uint32_t INF = 0xFFFFFFFFu;
+
+// Default time limit of every device-side wait (grid barrier, staging ring).
+constexpr long long DEFAULT_TIMEOUT_NS = 2000000000LL;
 
 // Device-side control block of one solve (lives in the plan's workspace,
 // zeroed before each launch).
@@ -123,6 +127,7 @@ struct SweepParams {
 // Partition of one launch shape, cached per plan.
 struct Partition {
     int nblocks = 0;
+    int row_cap = 0;          // > 0: a tile completes at most this many rows (delayed sweeps, small delta)
     int tiles = 0;
     int max_rows = 0;
     int* cta_row = nullptr;   // device [nblocks+1]
@@ -148,7 +153,7 @@ struct dag_plan {
     const int* colidx = nullptr;
     int device = 0;
     int num_sms = 0;
-    long long timeout_ns = 2000000000LL;
+    long long timeout_ns = dag::DEFAULT_TIMEOUT_NS;
     int skip_barrier_once = 0;
     int stall_staging_once = 0;
     long long skip_timeout_ns = 0;
@@ -162,7 +167,7 @@ struct dag_plan {
     dag::SyncBlock* sync = nullptr;
     float* scratch_f = nullptr; // [n] float scratch (adjoint aux)
     int* fr_orow = nullptr;   // [n+1] out-CSR row pointers (frontier sweeps, built on first use)
-    std::map<int, dag::Partition> parts;
+    std::map<long long, dag::Partition> parts;  // key: nblocks | row_cap << 32
     // batched workspace (grown on demand)
     void* bx = nullptr;
     size_t bx_bytes = 0;
@@ -182,7 +187,8 @@ int cuda_check(cudaError_t e, const char* what);
     } while (0)
 
 // plan.cu
-int get_partition(dag_plan* plan, int nblocks, Partition** out, cudaStream_t s);
+int get_partition(dag_plan* plan, int nblocks, Partition** out, cudaStream_t s, int row_cap);
+
 // The frontier maps of a partition (and the plan's out-CSR row pointers), built once.
 int frontier_maps(dag_plan* plan, Partition* part, cudaStream_t s);
 int max_workers(dag_plan* plan, int mode, int variant, int buf_cap_elems, int* out);
@@ -191,7 +197,15 @@ int max_workers(dag_plan* plan, int mode, int variant, int buf_cap_elems, int* o
 int launch_sweep(dag_plan* plan, int mode, int variant, int delta, SweepParams& p, cudaStream_t s,
                  int* out_nblocks);
 int sweep_shape(dag_plan* plan, int mode, int variant, int delta, int* nb_out, int* cap_out, Partition** part_out,
-                cudaStream_t s);
+                cudaStream_t s, int* clamped_out = nullptr);
+// The launch-shape rule of sweep_shape with the partition built by the caller
+// (`partition(nblocks, &max_rows)`), for launches without a plan's workspace.
+int settle_shape(dag_plan* plan, int mode, int variant, int delta,
+                 const std::function<int(int nblocks, int* max_rows)>& partition, int* nb_out, int* cap_out,
+                 int* clamped_out);
+// Rows a tile of a delayed sweep may complete (0: no cap): a buffer of delta
+// rows can only be flushed at a tile end.
+inline int delayed_row_cap(int variant, int delta) { return (variant == DAG_DELAYED && delta > 0 && delta < TILE) ? delta : 0; }
 
 const void* sweep_kernel_ptr(int mode, int variant);
 // Dynamic shared memory of a sweep launch in front of the delay buffer: the
@@ -209,7 +223,7 @@ int set_l1_carveout(const void* k, int device, int threads, size_t static_smem, 
 __global__ void k_check_rowptr(const int* rowptr, int n, long long m, int* bad);
 __global__ void k_out_degree(const int* colidx, long long m, int n, int* outdeg, int* bad);
 __global__ void k_degf(const int* outdeg, float* degf, int n);
-__global__ void k_cta_rows(const int* rowptr, int n, long long total, int P, int* cta_row);
+__global__ void k_cta_rows(const int* rowptr, int n, long long total, int P, int* cta_row, int row_w);
 constexpr int CT_THREADS = 1024;  // threads of k_cta_tiles (one CTA)
 __global__ void k_cta_tiles(const int* rowptr, const int* cta_row, int P, int* cta_tile, int* max_rows);
 __global__ void k_tile_coords(const int* rowptr, int n, long long m, const int* cta_row, const int* cta_tile,

@@ -124,51 +124,28 @@ extern "C" int dag_pagerank_noalloc(const dag_csr* csr, float d, double tol, dag
     k_degf<<<(n + 255) / 256, 256, 0, s>>>(outdeg, degf, n);
     DAG_CUDA(cudaGetLastError());
 
-    // launch shape: same rule as dag_pagerank's, with the partition built in the scratch array
+    // launch shape: dag_pagerank's rule (settle_shape), with the partition built in the scratch array
     dag_plan shape;  // host-side description only (device and SM count)
     shape.device = device;
     shape.n = n;
     shape.m = m;
     DAG_CUDA(cudaDeviceGetAttribute(&shape.num_sms, cudaDevAttrMultiProcessorCount, device));
-    int nb = 0;
-    rc = max_workers(&shape, MODE_PR, var, 0, &nb);
-    if (rc) return rc;
-    if (nb > NA_MAX_CTAS) nb = NA_MAX_CTAS;
     int host_flags[4] = {0, 0, 0, 0};
-    int cap = 0;
-    bool clamped = false;
-    long long max_cap = 0;
-    {
-        int max_dyn = 0;
-        cudaFuncAttributes fa;
-        DAG_CUDA(cudaDeviceGetAttribute(&max_dyn, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
-        DAG_CUDA(cudaFuncGetAttributes(&fa, sweep_kernel_ptr(MODE_PR, var)));
-        max_cap = ((long long)max_dyn - (long long)fa.sharedSizeBytes - (long long)sweep_ring_bytes(MODE_PR, var)) / 4;
-    }
-    bool settled = false;  // CTAs per SM only fall (4, 3, 2, 1), so a few passes settle the shape
-    for (int iter = 0; iter < 6 && !settled; ++iter) {
-        settled = true;
-        k_cta_rows<<<(nb + 1 + 255) / 256, 256, 0, s>>>(rowptr, n, (long long)n + m, nb, cta_row);
+    auto build = [&](int nb, int* max_rows) -> int {
+        if (nb > NA_MAX_CTAS) return set_error(DAG_ERR_INVALID, "more CTAs than the no-alloc scratch holds");
+        k_cta_rows<<<(nb + 1 + 255) / 256, 256, 0, s>>>(rowptr, n, (long long)n + m, nb, cta_row, 1);
         k_cta_tiles<<<1, CT_THREADS, 0, s>>>(rowptr, cta_row, nb, cta_tile, flags + 2);
         DAG_CUDA(cudaMemcpyAsync(flags + 1, cta_tile + nb, sizeof(int), cudaMemcpyDeviceToDevice, s));
         DAG_CUDA(cudaMemcpyAsync(host_flags, flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
         DAG_CUDA(cudaStreamSynchronize(s));
         if (host_flags[0]) return set_error(DAG_ERR_INVALID, "invalid CSR (rowptr order or colidx range)");
-        if (var != DAG_DELAYED) break;
-        long long need = (long long)delta - 1 + TILE;
-        if (need > host_flags[2]) need = host_flags[2];
-        if (need > max_cap) need = max_cap;
-        clamped = need < std::min((long long)delta - 1 + TILE, (long long)host_flags[2]);
-        cap = (int)(need < 1 ? 1 : need);
-        int nb2 = 0;
-        rc = max_workers(&shape, MODE_PR, var, cap, &nb2);
-        if (rc) return rc;
-        if (nb2 < nb) {
-            nb = nb2;
-            settled = false;
-        }
-    }
-    if (!settled) return set_error(DAG_ERR_INVALID, "launch shape did not settle");
+        *max_rows = host_flags[2];
+        return DAG_OK;
+    };
+    shape.worker_cap = NA_MAX_CTAS;
+    int nb = 0, cap = 0, clamped = 0;
+    rc = settle_shape(&shape, MODE_PR, var, delta, build, &nb, &cap, &clamped);
+    if (rc) return rc;
     const int tiles = host_flags[1];
     if (tiles > NA_MAX_TILES) return set_error(DAG_ERR_INVALID, "partition exceeds the no-alloc scratch");
     k_tile_coords<<<(tiles + 1 + 255) / 256, 256, 0, s>>>(rowptr, n, m, cta_row, cta_tile, nb, tiles, tile_row,
@@ -190,7 +167,7 @@ extern "C" int dag_pagerank_noalloc(const dag_csr* csr, float d, double tol, dag
     p.max_iters = max_iters;
     p.delta = (var == DAG_DELAYED) ? delta : 0;
     p.buf_cap = cap;
-    p.buf_clamped = clamped ? 1 : 0;
+    p.buf_clamped = clamped;
     p.x0 = base + OFF_X0;
     p.x1 = base + OFF_X1;
     p.cta_row = cta_row;
@@ -198,7 +175,7 @@ extern "C" int dag_pagerank_noalloc(const dag_csr* csr, float d, double tol, dag
     p.tile_row = tile_row;
     p.tile_nz = tile_nz;
     p.sync = sync;
-    p.timeout_ns = 2000000000LL;
+    p.timeout_ns = DEFAULT_TIMEOUT_NS;
     p.out = d_rank;
     DAG_CUDA(cudaMemsetAsync(sync, 0, sizeof(SyncBlock), s));
     const void* k = sweep_kernel_ptr(MODE_PR, var);

@@ -44,12 +44,27 @@ __global__ void k_degf(const int* outdeg, float* degf, int n)
     if (v < n) degf[v] = (float)outdeg[v];
 }
 
+__global__ void k_iota(int* a, long long m)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < m; e += (long long)gridDim.x * blockDim.x)
+        a[e] = (int)e;
+}
+
+static int bits_for(int n)
+{
+    int b = 1;
+    while (b < 31 && (1LL << b) < n) ++b;
+    return b;
+}
+
 // ---------------------------------------------------------------------------
 // Partition: block p starts at min { v : v + rowptr[v] >= ceil(p (n+m) / P) }
 // (every vertex weighs in-degree + 1), then each block is cut into merge-path
 // tiles of TILE items; a tile's start is (rows ended before it, edges before it).
 // ---------------------------------------------------------------------------
-__global__ void k_cta_rows(const int* rowptr, int n, long long total, int P, int* cta_row)
+// row_w: weight of a row beside its in-edges (1: Sec. III-A's in-degree + 1;
+// row-capped tiles weigh rows more, see get_partition); total = row_w n + m.
+__global__ void k_cta_rows(const int* rowptr, int n, long long total, int P, int* cta_row, int row_w)
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p > P) return;
@@ -59,7 +74,7 @@ __global__ void k_cta_rows(const int* rowptr, int n, long long total, int P, int
     int lo = 0, hi = n;
     while (lo < hi) {
         int mid = (lo + hi) >> 1;
-        if ((long long)mid + rowptr[mid] >= target) hi = mid;
+        if ((long long)row_w * mid + rowptr[mid] >= target) hi = mid;
         else lo = mid + 1;
     }
     cta_row[p] = lo;
@@ -122,19 +137,117 @@ __global__ void k_tile_coords(const int* rowptr, int n, long long m, const int* 
     tile_nz[k] = (int)(diag - a);
 }
 
-int get_partition(dag_plan* plan, int P, Partition** out, cudaStream_t s)
+// Tiles capped at R completed rows (delayed sweeps whose delta is below a
+// tile's rows: a tile's rows are computed together, so a buffer of delta rows
+// can only be flushed at a tile end, and capping the rows per tile lets it
+// flush after about every delta rows). A tile of block p ends at the first of:
+// TILE items, the item that ends its R-th row, the block end. One thread per
+// block walks its tiles; `count` mode writes the tile count of the block,
+// else the merge-path coordinates from tile_row/tile_nz[cta_tile[p]] on.
+__device__ __forceinline__ int rows_ended_before(const int* rowptr, int a, int r1, long long diag)
 {
-    auto it = plan->parts.find(P);
+    // first v in [a, r1] with v + rowptr[v+1] >= diag (v = r1: all of the block's rows ended)
+    int lo = a, hi = r1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((long long)mid + rowptr[mid + 1] >= diag) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
+
+__global__ void k_capped_tiles(const int* rowptr, const int* cta_row, int P, int R, int* cnt, const int* cta_tile,
+                               int* tile_row, int* tile_nz)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const int r0 = cta_row[p], r1 = cta_row[p + 1];
+    const long long d_end = (long long)r1 + rowptr[r1];
+    int a = r0;
+    long long d = (long long)r0 + rowptr[r0];
+    int k = 0;
+    while (d < d_end) {
+        if (tile_row) {
+            tile_row[cta_tile[p] + k] = a;
+            tile_nz[cta_tile[p] + k] = (int)(d - a);
+        }
+        long long dn = d + TILE;
+        if (a + R - 1 < r1) {  // the item that ends row a + R - 1, the R-th row from a
+            const long long dc = (long long)(a + R - 1) + rowptr[a + R] + 1;
+            if (dc < dn) dn = dc;
+        }
+        if (dn > d_end) dn = d_end;
+        a = rows_ended_before(rowptr, a, r1, dn);
+        d = dn;
+        ++k;
+    }
+    if (cnt) cnt[p] = k;
+}
+
+// Exclusive prefix of per-block tile counts into cta_tile[0..P] and the
+// largest block's row count (one CTA of CT_THREADS threads).
+__global__ void __launch_bounds__(CT_THREADS) k_prefix_tiles(const int* cnt, const int* cta_row, int P,
+                                                             int* cta_tile, int* max_rows)
+{
+    using Scan = cub::BlockScan<int, CT_THREADS>;
+    __shared__ typename Scan::TempStorage tmp;
+    __shared__ int carry, mr;
+    if (threadIdx.x == 0) { carry = 0; mr = 0; }
+    for (int base = 0; base < P; base += CT_THREADS) {
+        const int p = base + threadIdx.x;
+        int c = 0;
+        if (p < P) {
+            c = cnt[p];
+            atomicMax(&mr, cta_row[p + 1] - cta_row[p]);
+        }
+        __syncthreads();
+        int excl = 0, chunk = 0;
+        Scan(tmp).ExclusiveSum(c, excl, chunk);
+        if (p < P) cta_tile[p] = carry + excl;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += chunk;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        cta_tile[P] = carry;
+        *max_rows = mr;
+    }
+}
+
+__global__ void k_tile_end(int tiles, int n, long long m, int* tile_row, int* tile_nz)
+{
+    tile_row[tiles] = n;
+    tile_nz[tiles] = (int)m;
+}
+
+int get_partition(dag_plan* plan, int P, Partition** out, cudaStream_t s, int row_cap)
+{
+    if (row_cap >= TILE) row_cap = 0;  // a tile never holds more than TILE rows
+    const long long key = (long long)P | ((long long)row_cap << 32);
+    auto it = plan->parts.find(key);
     if (it != plan->parts.end()) { *out = &it->second; return DAG_OK; }
     Partition part;
     part.nblocks = P;
+    part.row_cap = row_cap;
     int* mr_dev = nullptr;
+    int* cnt = nullptr;
     DAG_CUDA(cudaMalloc(&part.cta_row, (P + 1) * sizeof(int)));
     DAG_CUDA(cudaMalloc(&part.cta_tile, (P + 1) * sizeof(int)));
     DAG_CUDA(cudaMalloc(&mr_dev, sizeof(int)));
-    long long total = (long long)plan->n + plan->m;
-    k_cta_rows<<<(P + 1 + 255) / 256, 256, 0, s>>>(plan->rowptr, plan->n, total, P, part.cta_row);
-    k_cta_tiles<<<1, CT_THREADS, 0, s>>>(plan->rowptr, part.cta_row, P, part.cta_tile, mr_dev);
+    // Row-capped tiles cost a tile per row_cap rows even where rows have no
+    // edges, so their blocks weigh each row ceil(TILE / row_cap) instead of 1:
+    // a block's tile count then follows its weight, as it does uncapped.
+    const int row_w = row_cap > 0 ? (TILE + row_cap - 1) / row_cap : 1;
+    long long total = (long long)row_w * plan->n + plan->m;
+    k_cta_rows<<<(P + 1 + 255) / 256, 256, 0, s>>>(plan->rowptr, plan->n, total, P, part.cta_row, row_w);
+    if (row_cap > 0) {
+        DAG_CUDA(cudaMalloc(&cnt, P * sizeof(int)));
+        k_capped_tiles<<<(P + 127) / 128, 128, 0, s>>>(plan->rowptr, part.cta_row, P, row_cap, cnt, nullptr,
+                                                      nullptr, nullptr);
+        k_prefix_tiles<<<1, CT_THREADS, 0, s>>>(cnt, part.cta_row, P, part.cta_tile, mr_dev);
+    } else {
+        k_cta_tiles<<<1, CT_THREADS, 0, s>>>(plan->rowptr, part.cta_row, P, part.cta_tile, mr_dev);
+    }
     int tiles = 0;
     DAG_CUDA(cudaMemcpyAsync(&tiles, part.cta_tile + P, sizeof(int), cudaMemcpyDeviceToHost, s));
     DAG_CUDA(cudaMemcpyAsync(&part.max_rows, mr_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -143,10 +256,19 @@ int get_partition(dag_plan* plan, int P, Partition** out, cudaStream_t s)
     part.tiles = tiles;
     DAG_CUDA(cudaMalloc(&part.tile_row, (tiles + 1) * sizeof(int)));
     DAG_CUDA(cudaMalloc(&part.tile_nz, (tiles + 1) * sizeof(int)));
-    k_tile_coords<<<(tiles + 1 + 255) / 256, 256, 0, s>>>(plan->rowptr, plan->n, plan->m, part.cta_row,
-                                                           part.cta_tile, P, tiles, part.tile_row, part.tile_nz);
+    if (row_cap > 0) {
+        k_capped_tiles<<<(P + 127) / 128, 128, 0, s>>>(plan->rowptr, part.cta_row, P, row_cap, nullptr,
+                                                      part.cta_tile, part.tile_row, part.tile_nz);
+        k_tile_end<<<1, 1, 0, s>>>(tiles, plan->n, plan->m, part.tile_row, part.tile_nz);
+        DAG_CUDA(cudaStreamSynchronize(s));
+        cudaFree(cnt);
+    } else {
+        k_tile_coords<<<(tiles + 1 + 255) / 256, 256, 0, s>>>(plan->rowptr, plan->n, plan->m, part.cta_row,
+                                                               part.cta_tile, P, tiles, part.tile_row,
+                                                               part.tile_nz);
+    }
     DAG_CUDA(cudaGetLastError());
-    auto ins = plan->parts.emplace(P, part);
+    auto ins = plan->parts.emplace(key, part);
     *out = &ins.first->second;
     return DAG_OK;
 }
@@ -178,23 +300,12 @@ __global__ void k_fill_segments(const int* lo, int count, int* a)
     const int x1 = lo[t + 1];
     for (int x = lo[t] + lane; x < x1; x += 32) a[x] = (int)t;
 }
-__global__ void k_iota(int* a, long long m)
-{
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < m; e += (long long)gridDim.x * blockDim.x)
-        a[e] = (int)e;
-}
 __global__ void k_gather_i32(const int* src, const int* idx, int* out, long long m)
 {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < m; e += (long long)gridDim.x * blockDim.x)
         out[e] = src[idx[e]];
 }
 
-static int bits_for(int n)
-{
-    int b = 1;
-    while (b < 31 && (1LL << b) < n) ++b;
-    return b;
-}
 
 int launch_transpose(dag_plan* plan, int* out_rowptr, int* out_colidx, int* perm, cudaStream_t s)
 {
@@ -451,7 +562,7 @@ extern "C" int dag_partition(dag_plan* p, int32_t workers, int32_t* h_start)
 {
     if (!p || !h_start || workers < 1) return set_error(DAG_ERR_INVALID, "bad argument");
     Partition* part = nullptr;
-    int rc = get_partition(p, workers, &part, 0);
+    int rc = get_partition(p, workers, &part, 0, 0);
     if (rc) return rc;
     DAG_CUDA(cudaMemcpy(h_start, part->cta_row, (size_t)(workers + 1) * sizeof(int), cudaMemcpyDeviceToHost));
     return DAG_OK;

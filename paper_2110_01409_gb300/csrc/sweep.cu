@@ -38,8 +38,9 @@
 // plus the delay buffer) because its gathers of the previous iterate or of the
 // SM's view of the live array are ordinary loads that live off L1 hits.
 #include <algorithm>
-#include <cstdint>
 #include <climits>
+#include <cstdint>
+#include <functional>
 #include <type_traits>
 
 #include "sweep_common.cuh"
@@ -526,19 +527,23 @@ int max_workers(dag_plan* plan, int mode, int variant, int buf_cap_elems, int* o
     return DAG_OK;
 }
 
-// Launch shape of a sweep: CTA count, delay-buffer capacity and partition.
-// A delayed sweep's buffer holds at most min(delta - 1 + TILE, rows of the
-// CTA) values (a flush empties it once it reaches delta after a tile). Fewer
-// CTAs mean longer blocks, so the shape is settled by a short fixed-point loop.
-int sweep_shape(dag_plan* plan, int mode, int variant, int delta, int* nb_out, int* cap_out, Partition** part_out,
-                cudaStream_t s)
+// Launch shape of a sweep: CTA count and delay-buffer capacity. A delayed
+// sweep's buffer holds at most min(delta - 1 + TILE, rows of the largest block)
+// values (a flush empties it once it reaches delta after a tile), and at most
+// what fits in shared memory beside the kernel's static share (then it is
+// clamped: flushed when the next tile might not fit). Fewer CTAs mean longer
+// blocks, so the shape is settled by a short fixed-point loop; `partition`
+// builds the static partition of Sec. III-A for a CTA count and returns its
+// largest block's row count.
+int settle_shape(dag_plan* plan, int mode, int variant, int delta,
+                 const std::function<int(int nblocks, int* max_rows)>& partition, int* nb_out, int* cap_out,
+                 int* clamped_out)
 {
     int nb = 0;
     int rc = max_workers(plan, mode, variant, 0, &nb);
     if (rc) return rc;
     if (plan->worker_cap > 0 && nb > plan->worker_cap) nb = plan->worker_cap;
-    int cap = 0;
-    Partition* part = nullptr;
+    int cap = 0, clamped = 0;
     long long max_cap = 0;  // largest buffer (values) one CTA can hold beside its static shared memory
     {
         int max_dyn = 0;
@@ -549,13 +554,14 @@ int sweep_shape(dag_plan* plan, int mode, int variant, int delta, int* nb_out, i
     }
     bool settled = false;  // CTAs per SM only fall (4, 3, 2, 1), so a few passes settle the shape
     for (int iter = 0; iter < 6 && !settled; ++iter) {
-        rc = get_partition(plan, nb, &part, s);
+        int max_rows = 0;
+        rc = partition(nb, &max_rows);
         if (rc) return rc;
         settled = true;
         if (variant != DAG_DELAYED) break;
-        long long need = (long long)delta - 1 + TILE;
-        if (need > part->max_rows) need = part->max_rows;
-        if (need > max_cap) need = max_cap;  // a larger buffer does not fit: it flushes when full
+        const long long want = std::min((long long)delta - 1 + TILE, (long long)max_rows);
+        const long long need = std::min(want, max_cap);  // a larger buffer does not fit: it flushes when full
+        clamped = need < want ? 1 : 0;
         cap = (int)(need < 1 ? 1 : need);
         int nb2 = 0;
         rc = max_workers(plan, mode, variant, cap, &nb2);
@@ -568,22 +574,40 @@ int sweep_shape(dag_plan* plan, int mode, int variant, int delta, int* nb_out, i
     if (!settled) return set_error(DAG_ERR_INVALID, "sweep launch shape did not settle");
     *nb_out = nb;
     *cap_out = cap;
+    *clamped_out = clamped;
+    return DAG_OK;
+}
+
+// Launch shape and the plan's cached partition for it (a delayed sweep with
+// delta below a tile's items gets tiles of at most delta rows).
+int sweep_shape(dag_plan* plan, int mode, int variant, int delta, int* nb_out, int* cap_out, Partition** part_out,
+                cudaStream_t s, int* clamped_out)
+{
+    Partition* part = nullptr;
+    int clamped = 0;
+    auto build = [&](int nb, int* max_rows) {
+        const int rc = get_partition(plan, nb, &part, s, delayed_row_cap(variant, delta));
+        if (rc == DAG_OK) *max_rows = part->max_rows;
+        return rc;
+    };
+    const int rc = settle_shape(plan, mode, variant, delta, build, nb_out, cap_out, &clamped);
+    if (rc) return rc;
     *part_out = part;
+    if (clamped_out) *clamped_out = clamped;
     return DAG_OK;
 }
 
 int launch_sweep(dag_plan* plan, int mode, int variant, int delta, SweepParams& p, cudaStream_t s,
                  int* out_nblocks)
 {
-    int nb = 0, cap = 0;
+    int nb = 0, cap = 0, clamped = 0;
     Partition* part = nullptr;
-    int rc = sweep_shape(plan, mode, variant, delta, &nb, &cap, &part, s);
+    int rc = sweep_shape(plan, mode, variant, delta, &nb, &cap, &part, s, &clamped);
     if (rc) return rc;
     p.nblocks = nb;
     p.delta = (variant == DAG_DELAYED) ? delta : 0;
     p.buf_cap = cap;
-    p.buf_clamped = (variant == DAG_DELAYED && (long long)cap < std::min((long long)delta - 1 + TILE,
-                                                                          (long long)part->max_rows)) ? 1 : 0;
+    p.buf_clamped = clamped;
     p.cta_row = part->cta_row;
     p.cta_tile = part->cta_tile;
     p.tile_row = part->tile_row;

@@ -320,6 +320,8 @@ def pagerank_noalloc(rowptr: torch.Tensor, colidx: torch.Tensor, d=0.85, tol=1e-
     inside the library (n <= 2^20, m <= 2^24). Returns (rank, stats)."""
     n, m = rowptr.numel() - 1, colidx.numel()
     _dev(rowptr, torch.int32, n + 1, "rowptr")
+    if m:
+        _dev(colidx, torch.int32, m, "colidx")
     out = out if out is not None else torch.empty(n, dtype=torch.float32, device=rowptr.device)
     _dev(out, torch.float32, n, "out")
     _dev(teleport, torch.float32, n, "teleport")

@@ -43,3 +43,30 @@ def test_variant_and_read_mode_names():
         if len(parts) > 1:
             assert flags == sum(dag.READ_MODES[p] for p in parts), name
     assert dag.READ_MODES["refresh"] == 0
+
+
+@pytest.mark.parametrize("bad", ["host", "int64"])
+def test_noalloc_refuses_bad_colidx_before_any_library_call(bad, monkeypatch):
+    # rowptr and out would pass; a host or int64 colidx must be refused in Python,
+    # before its address could reach the kernels
+    calls = []
+    monkeypatch.setattr(dag, "lib", lambda: calls.append(1))
+    rowptr = torch.zeros(9, dtype=torch.int32)
+    colidx = torch.zeros(4, dtype=torch.int64 if bad == "int64" else torch.int32)
+    monkeypatch.setattr(dag, "_dev", _dev_accepting(rowptr))
+    with pytest.raises(ValueError, match="colidx"):
+        dag.pagerank_noalloc(rowptr, colidx, out=torch.zeros(8))
+    assert not calls
+
+
+def _dev_accepting(rowptr):
+    """_dev that lets the (host) rowptr and output through, so that the colidx
+    check is the one that fails."""
+    real = dag._dev
+
+    def check(t, dtype, n, name):
+        if name in ("rowptr", "out", "teleport"):
+            return t
+        return real(t, dtype, n, name)
+
+    return check

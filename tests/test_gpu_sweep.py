@@ -232,9 +232,14 @@ def test_flush_counts_follow_delta(dag):
     start = plan.partition(P)
     nonempty = int(np.sum(np.diff(start) > 0))
     assert st["flushes"] == nonempty * st["iters"]
-    # small delta: a flush after every tile that completes >= delta rows, so more per sweep
-    _, st16 = dag.pagerank(plan, 0.85, 1e-6, "delayed", 16)
-    assert st16["flushes"] / st16["iters"] > 1.5 * nonempty
+    # delta below a tile's rows: tiles complete at most delta rows and a flush follows as soon as the
+    # buffer holds >= delta, so each flush carries delta .. 2 delta - 1 rows (fewer only at a block end):
+    # n / (2 delta - 1) <= flushes per sweep <= n / delta + blocks
+    for delta in (16, 64):
+        _, st_d = dag.pagerank(plan, 0.85, 1e-6, "delayed", delta)
+        assert st_d["converged"]
+        per_sweep = st_d["flushes"] / st_d["iters"]
+        assert g.n / (2 * delta - 1) <= per_sweep <= g.n / delta + st_d["workers"], (delta, per_sweep)
 
 
 @pytest.mark.parametrize("variant,delta", [("sync", 0), ("async", 0), ("delayed", 16), ("delayed", 5000)])

@@ -231,3 +231,32 @@ def test_partition_balances_in_degree():
     ideal = (g.n + g.m) / P
     maxrow = np.max(np.diff(g.rowptr)) + 1
     assert np.all(wsum <= ideal + maxrow + 1)
+
+
+@pytest.mark.parametrize("threads", [2, 4])
+def test_threaded_fixed_point_equals_serial_jacobi(threads):
+    # the threaded form runs the same synchronous sweeps; only the order of two sums differs
+    g = I.rmat(11, 16, seed=9)
+    serial = oracle.pagerank_fixed_point(g, 0.85, tol=1e-12)
+    par = oracle.pagerank_fixed_point(g, 0.85, tol=1e-12, threads=threads)
+    assert np.abs(serial - par).sum() <= 1e-13
+    # and it is the dense solve's fixed point
+    assert np.abs(par - oracle.dense_pagerank(g, 0.85)).sum() <= 1e-10
+
+
+def test_threaded_fixed_point_closed_forms():
+    # in-star: k leaves -> centre (dangling); r_leaf = 1/(n + d k), r_centre = (1 + d k)/(n + d k)
+    k, d = 5, 0.85
+    n = k + 1
+    g = I.from_edges(n, np.arange(1, n), np.zeros(k, dtype=np.int64))
+    r = oracle.pagerank_fixed_point(g, d, tol=1e-15, threads=3)
+    assert abs(r[0] - (1 + d * k) / (n + d * k)) <= 1e-13
+    assert np.all(np.abs(r[1:] - 1 / (n + d * k)) <= 1e-13)
+    # personalized teleport on a directed cycle: r_{s+j} = (1-d) d^j / (1 - d^n)
+    n, s = 16, 3
+    g = I.from_edges(n, np.arange(n), (np.arange(n) + 1) % n)
+    t = np.zeros(n)
+    t[s] = 1.0
+    r = oracle.pagerank_fixed_point(g, d, tele=t, tol=1e-15, threads=2)
+    j = (np.arange(n) - s) % n
+    assert np.abs(r - (1 - d) * d ** j / (1 - d ** n)).max() <= 1e-13
