@@ -38,7 +38,8 @@ PR_DELTA, SSSP_DELTA = 32, 32  # fixed-delta runs of the variant table and the C
 DELTAS = (0, 32, 256, 4096)
 WORKLOAD = (f"rmat{SCALE}: pagerank d=0.85 tol=1e-6 + sssp x{N_SOURCES} sources, "
             f"delayed method, delta picked per algorithm over {list(DELTAS)} "
-            f"(delta 0 also with own-block L1 reads, and for sssp the tile frontier)")
+            f"(delta 0 also with own-block L1 reads, and for sssp the tile frontier) "
+            f"and over warp-worker sweeps (sync, delta 16 / 256, async with three warp tile shapes)")
 
 
 HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e, nominal (the roofline's frac uses the measured copy peak)
@@ -146,7 +147,9 @@ def build_inputs():
 
 
 def _cand(c):
-    return str(c["delta"]) + ("" if c["reads"] == "refresh" else "+" + c["reads"])
+    v = "sync" if c["variant"] == "sync" else str(c["delta"])
+    tile = f"x{c['warp_tile']}" if c["reads"].startswith("warp") else ""
+    return v + ("" if c["reads"] == "refresh" else "+" + c["reads"]) + tile
 
 
 def algorithmic_bytes(n, m, kind, edges=None):
@@ -195,7 +198,10 @@ def run_gpu(args):
     # ---- delta per algorithm: the autotuner over the delayed method's delta (0 = async end) ----
     from paper_2110_01409_gb300 import autotune
 
-    cands = [("delayed", dl) for dl in DELTAS] + [("delayed", 0, "own_l1")]
+    # CTA-tile sweeps over delta, plus warp-worker sweeps (three warp tile shapes for the async end)
+    warp_cands = [("sync", 0, "warp"), ("delayed", 16, "warp"), ("delayed", 256, "warp+cached")] + \
+        [("delayed", 0, "warp+cached", ipt) for ipt in (5, 7, 11)]
+    cands = [("delayed", dl) for dl in DELTAS] + [("delayed", 0, "own_l1")] + warp_cands
     cands_bf = cands + [("delayed", 0, "frontier"), ("delayed", 0, "own_l1+frontier")]
     tune_pr = autotune.tune(plan, "pagerank", candidates=cands, worker_fractions=[1.0], trials=2, cache=None)
     tune_bf = autotune.tune(plan, "sssp", candidates=cands_bf, worker_fractions=[1.0], trials=2, cache=None,
@@ -203,16 +209,26 @@ def run_gpu(args):
     plan.set_worker_cap(0)
     pr_dl, bf_dl = tune_pr["delta"], tune_bf["delta"]
     pr_rd, bf_rd = tune_pr["reads"], tune_bf["reads"]
+    pr_var, bf_var = tune_pr["variant"], tune_bf["variant"]
+    pr_tile, bf_tile = tune_pr["warp_tile"], tune_bf["warp_tile"]
+
+    def pagerank_solve(**kw):  # the tuned choice (its warp tile is a host-side plan setting)
+        plan.set_warp_tile(pr_tile)
+        return dag.pagerank(plan, 0.85, 1e-6, pr_var, pr_dl, 1000, out=rank_out, reads=pr_rd, **kw)
+
+    def sssp_solve(s, k, **kw):
+        plan.set_warp_tile(bf_tile)
+        return dag.sssp(plan, int(s), w8_d, bf_var, bf_dl, n + 1, out=dist_out[k], reads=bf_rd, **kw)
 
     # ---- warm-up with statuses (also records per-solve sweeps) ----
     pr_iters, bf_iters, bf_edges = [], [], []
     for _ in range(args.warmup):
-        _, st = dag.pagerank(plan, 0.85, 1e-6, "delayed", pr_dl, 1000, out=rank_out, reads=pr_rd)
+        _, st = pagerank_solve()
         assert st["converged"], st
         pr_iters.append(st["iters"])
         its = []
         for k, s in enumerate(srcs):
-            _, st = dag.sssp(plan, int(s), w8_d, "delayed", bf_dl, n + 1, out=dist_out[k], reads=bf_rd)
+            _, st = sssp_solve(s, k)
             assert st["converged"], st
             its.append(st["iters"])
             bf_edges.append(st["edges_processed"])
@@ -225,6 +241,7 @@ def run_gpu(args):
     pr_ev = [(ev(), ev()) for _ in range(K)]
     bf_ev = [[(ev(), ev()) for _ in range(N_SOURCES)] for _ in range(K)]
     t_start, t_end = ev(), ev()
+    status = torch.zeros((K, 1 + N_SOURCES, 3), dtype=torch.int32, device=dev)  # each timed solve's status
     clocks = Clocks(local, args.clocks_csv)
     if world > 1:
         dist.barrier()
@@ -233,12 +250,14 @@ def run_gpu(args):
     t_start.record(stream)
     for k in range(K):
         pr_ev[k][0].record(stream)
-        dag.pagerank(plan, 0.85, 1e-6, "delayed", pr_dl, 1000, out=rank_out, stats=False, reads=pr_rd)
+        pagerank_solve(stats=False)
         pr_ev[k][1].record(stream)
+        plan.last_status_to(status[k, 0])
         for j, s in enumerate(srcs):
             bf_ev[k][j][0].record(stream)
-            dag.sssp(plan, int(s), w8_d, "delayed", bf_dl, n + 1, out=dist_out[j], stats=False, reads=bf_rd)
+            sssp_solve(s, j, stats=False)
             bf_ev[k][j][1].record(stream)
+            plan.last_status_to(status[k, 1 + j])
     t_end.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -247,8 +266,10 @@ def run_gpu(args):
     ms_total, value = replica_aggregate(ms_total, world, solves * m * K, dev)
     ms_step = ms_total / K
 
-    # statuses of the timed solves: one more checked step (results must match the warm-up)
-    _, st_pr = dag.pagerank(plan, 0.85, 1e-6, "delayed", pr_dl, 1000, out=rank_out, reads=pr_rd)
+    # every timed solve converged without error (read on the device, checked after the region)
+    st_all = status.cpu()
+    assert bool((st_all[..., 0] == 0).all()) and bool((st_all[..., 1] == 1).all()), st_all
+    _, st_pr = pagerank_solve()
     assert st_pr["converged"]
     pr_ms = statistics.mean(a.elapsed_time(b) for a, b in pr_ev)
     bf_ms = statistics.mean(a.elapsed_time(b) for row in bf_ev for a, b in row)
@@ -260,31 +281,31 @@ def run_gpu(args):
     bf_bytes = e_bytes + v_bytes * bf_sweeps
     peak, peak_kind = _peaks()
     # dominant kernel by total time in the step
-    # delta 0 runs the asynchronous form's TMA-staged kernel, delta > 0 the register-staged one
-    kname = lambda mode, dl, rd="": (f"sweep_kernel<{mode},DELAYED>" if dl > 0 else  # noqa: E731
-                                     f"sweep_tma_kernel<{mode}{',frontier' if 'frontier' in rd else ''}>")
     if bf_ms * N_SOURCES >= pr_ms:
-        dom, dom_bytes, dom_ms, dom_sweeps = kname("BF8", bf_dl, bf_rd), bf_bytes, bf_ms, bf_sweeps
+        dom, dom_bytes, dom_ms, dom_sweeps = kernel_name("BF8", bf_var, bf_dl, bf_rd, bf_tile), bf_bytes, bf_ms, \
+            bf_sweeps
     else:
-        dom, dom_bytes, dom_ms, dom_sweeps = kname("PR", pr_dl), pr_bytes, pr_ms, pr_sweeps
+        dom, dom_bytes, dom_ms, dom_sweeps = kernel_name("PR", pr_var, pr_dl, pr_rd, pr_tile), pr_bytes, pr_ms, \
+            pr_sweeps
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
-    traffic = _recorded_traffic(dom, dom_sweeps, bf_edges_mean if dom.startswith("sweep_tma_kernel<BF8") else None)
+    traffic = _recorded_traffic(dom, dom_sweeps, bf_edges_mean if "frontier" in dom else None)
 
     # ---- the sweep's real ceiling: one streamed gather pass over the same colidx (dag_probe_gather) ----
-    coherent = bf_dl == 0  # the async sweep gathers with relaxed gpu-scope loads
+    coherent = gathers_coherent(bf_var, bf_dl, bf_rd)
     probe_ms = dag.probe_gather(plan, rank_out, coherent=coherent, repeats=5)
     # the launch against the probe's time for the edges it ran (sweeps * m, or the frontier's count)
     bf_sweep_ms = bf_ms / bf_sweeps
     gather_floor = {"probe_ms_per_pass": round(probe_ms, 4), "loads": "relaxed (L2)" if coherent else "ordinary",
                     "sweep_ms": round(bf_sweep_ms, 4), "edges_per_launch_over_m": round(bf_edges_mean / m, 3),
                     "frac": round(probe_ms * (bf_edges_mean / m) / bf_ms, 3),
-                    "kernel": kname("BF8", bf_dl, bf_rd)}
+                    "kernel": kernel_name("BF8", bf_var, bf_dl, bf_rd, bf_tile)}
 
     # ---- e2e through the public API from pinned host buffers ----
     # e2e builds a plan per step: the frontier's maps (one out-CSR sort per plan, ~9 ms at this size)
     # cost more than they save over one step's 8 solves, so e2e runs the same read path without them
     bf_rd_e2e = bf_rd.replace("+frontier", "").replace("frontier", "refresh")
-    e2e = run_e2e(args, g, w, srcs, dev, dag, torch, (pr_dl, pr_rd), (bf_dl, bf_rd_e2e)) if args.e2e else None
+    e2e = run_e2e(args, g, w, srcs, dev, dag, torch, (pr_var, pr_dl, pr_rd, pr_tile),
+                  (bf_var, bf_dl, bf_rd_e2e, bf_tile)) if args.e2e else None
     if e2e is not None:
         e2e["sssp_reads"] = bf_rd_e2e
 
@@ -310,8 +331,11 @@ def run_gpu(args):
         "dtype": "f32/u32",
         "data": "synthetic (seeded RMAT stand-in for the GAP Kron graph)",
         "config": {"workload": WORKLOAD, "weights": "uint8 per edge (values in [1, 255])",
+                   "variant": {"pagerank": pr_var, "sssp": bf_var},
                    "delta": {"pagerank": pr_dl, "sssp": bf_dl},
                    "reads": {"pagerank": pr_rd, "sssp": bf_rd},
+                   "warp_tile_items": {"pagerank": 32 * pr_tile if pr_rd.startswith("warp") else None,
+                                       "sssp": 32 * bf_tile if bf_rd.startswith("warp") else None},
                    "autotune_ms": {"pagerank": {_cand(c): round(c["ms"], 3) for c in tune_pr["candidates"]
                                                 if "ms" in c},
                                    "sssp": {_cand(c): round(c["ms"], 3) for c in tune_bf["candidates"]
@@ -328,7 +352,7 @@ def run_gpu(args):
                      "bytes_per_launch": int(dom_bytes), "traffic": traffic},
         "gather_floor": gather_floor,
         "clocks": clk,
-        "gpu_launches": K * solves,
+        "gpu_launches": 2 * K * solves,  # each solve's sweep kernel and its status copy
         "e2e": e2e,
     }
     if rank == 0 and args.cpu_baseline:
@@ -341,11 +365,27 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def kernel_name(mode, variant, delta, reads, warp_tile=7):
+    """The sweep kernel a solve runs (for the roofline's kernel and the ncu launch list)."""
+    var = "ASYNC" if variant == "async" or (variant == "delayed" and delta == 0) else variant.upper()
+    if reads.startswith("warp"):
+        return f"sweep_warp_kernel<{mode},{var},{warp_tile}>"
+    if var == "ASYNC":
+        return f"sweep_tma_kernel<{mode}{',frontier' if 'frontier' in reads else ''}>"
+    return f"sweep_kernel<{mode},{var}{',frontier' if 'frontier' in reads else ''}>"
+
+
+def gathers_coherent(variant, delta, reads):
+    """True when the solve gathers with gpu-scope loads served by L2 (the async form's default)."""
+    asynch = variant == "async" or (variant == "delayed" and delta == 0)
+    return ("coherent" in reads) or (asynch and "cached" not in reads and not reads.startswith("own_l1"))
+
+
 def sweep_source_hash():
     """sha256 of the sweep kernel's sources: a recorded ncu traffic figure is
     used only while it still describes the kernel that runs."""
     h = hashlib.sha256()
-    for f in ("sweep.cu", "sweep_tma.cu", "sweep_common.cuh", "dag_internal.cuh"):
+    for f in ("sweep.cu", "sweep_tma.cu", "sweep_warp.cu", "sweep_common.cuh", "dag_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2110_01409_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -396,14 +436,16 @@ def run_e2e(args, g, w, srcs, dev, dag, torch, pr_choice, bf_choice):
         w_ready = side.record_event()
         wd.record_stream(main)
         plan = dag.Plan(rp, ci)
-        r, _ = dag.pagerank(plan, 0.85, 1e-6, "delayed", pr_choice[0], 1000, stats=False, reads=pr_choice[1])
+        plan.set_warp_tile(pr_choice[3])
+        r, _ = dag.pagerank(plan, 0.85, 1e-6, pr_choice[0], pr_choice[1], 1000, stats=False, reads=pr_choice[2])
         side.wait_event(main.record_event())
         with torch.cuda.stream(side):
             res_pr.copy_(r, non_blocking=True)
         r.record_stream(side)
         main.wait_event(w_ready)
+        plan.set_warp_tile(bf_choice[3])
         for j, s in enumerate(srcs):
-            d, _ = dag.sssp(plan, int(s), wd, "delayed", bf_choice[0], g.n + 1, stats=False, reads=bf_choice[1])
+            d, _ = dag.sssp(plan, int(s), wd, bf_choice[0], bf_choice[1], g.n + 1, stats=False, reads=bf_choice[2])
             side.wait_event(main.record_event())  # this result goes out while the next source runs
             with torch.cuda.stream(side):
                 res_bf[j].copy_(d, non_blocking=True)

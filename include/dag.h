@@ -109,6 +109,7 @@ int dag_workers(dag_plan* plan, dag_variant variant, int32_t delta, int32_t* out
  * blocks, i.e. more rows per CTA; the autotuner varies it.
  */
 int dag_plan_set_worker_cap(dag_plan* plan, int32_t max_workers);
+/* (With DAG_WARP_WORKERS the cap counts CTAs too: eight warp workers each.) */
 
 /* Flags of dag_pagerank / dag_sssp. */
 #define DAG_PR_WARM_START 1 /* start from d_rank instead of the teleport vector (PageRank) */
@@ -153,6 +154,29 @@ int dag_plan_set_worker_cap(dag_plan* plan, int32_t max_workers);
  * the delayed form.
  */
 #define DAG_SSSP_FRONTIER 32
+/*
+ * Warp workers (dag_pagerank, dag_sssp, dag_sssp_u8; every variant): the
+ * worker of Sec. III-A is one warp instead of one CTA. The merge path of the
+ * whole graph (rows and in-edges in vertex order) is cut into tiles of
+ * dag_warp_tile_items(plan) items and each warp takes an equal run of them, so
+ * workers are balanced by in-degree + 1 as Sec. III-A asks; a warp owns the
+ * rows that end in its run, and a row whose in-edges span several runs gets
+ * the earlier runs' partial sums at the end of the sweep. delta counts rows
+ * per warp (each warp has its own buffer). No CTA-wide barrier inside a sweep.
+ * The asynchronous form reads through L2 (DAG_READ_CACHED: ordinary loads,
+ * refreshed by the barrier between sweeps). DAG_ERR_INVALID with
+ * DAG_SSSP_FRONTIER, DAG_READ_LOCAL or DAG_READ_OWN_L1.
+ */
+#define DAG_WARP_WORKERS 64
+/*
+ * Warp tile shape of the plan's warp-worker sweeps: 32 lanes x items_per_lane
+ * items (5, 7 or 11; 7 when a plan is created), a tuning choice. Shorter tiles
+ * mean more tiles in flight per warp's run; longer ones, fewer merge-path
+ * searches per item. DAG_ERR_INVALID for another value or a null plan.
+ */
+int dag_plan_set_warp_tile(dag_plan* plan, int32_t items_per_lane);
+/* Items (rows + in-edges) per warp tile of the plan's warp-worker sweeps (the default shape's for NULL). */
+int32_t dag_warp_tile_items(const dag_plan* plan);
 
 /*
  * PageRank (Sec. IV-A; stopping rule Sec. IV):
@@ -331,6 +355,15 @@ int dag_probe_gather(const int32_t* d_idx, int64_t m, const float* d_x, int32_t 
  * counts a block's reads of its own values. 1 <= workers <= 4096.
  */
 int dag_access_matrix(dag_plan* plan, int32_t workers, uint64_t* d_counts, void* stream);
+
+/*
+ * Status of the plan's last single-vector solve (dag_pagerank, dag_sssp,
+ * dag_sssp_u8, the adjoint's out_plan) without waiting for it: enqueues on
+ * `stream` a copy of {err (DAG_OK or DAG_ERR_BARRIER_TIMEOUT), converged
+ * (0/1), sweeps run} into d_status (device int32 [3]). For callers that launch
+ * solves back to back with h_stats = NULL and check them afterwards.
+ */
+int dag_plan_last_status(const dag_plan* plan, int32_t* d_status, void* stream);
 
 /* Items (rows + in-edges) per merge-path tile of the sweeps, the unit the
  * frontier runs or skips; fixed when the library is compiled. */

@@ -6,9 +6,11 @@ platform, the input and the algorithm (Sec. IV, V). This tuner picks it
 empirically: it runs complete solves for a small grid of candidates on the
 caller's graph and problem and keeps the fastest, measured with the library's
 own CUDA-event timing. Results are cached in a JSON file keyed by a graph
-fingerprint, so a graph is tuned once per machine. The tile shape (items per
-merge-path tile) is fixed when the library is compiled (256 threads x 7
-items, chosen by sweeping launch shapes on the benchmark graph).
+fingerprint, so a graph is tuned once per machine. Two tile shapes are in
+play: the CTA tiles of the default sweeps (256 threads x 7 items, fixed when
+the library is compiled) and the warp tiles of warp-worker sweeps
+(reads "warp...", DAG_WARP_WORKERS), 32 lanes x 5, 7 or 11 items, which a
+candidate's fourth field selects.
 """
 from __future__ import annotations
 
@@ -25,9 +27,13 @@ from . import dag
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "dag_autotune.json")
 _lock = threading.Lock()
 
-# (variant, delta[, reads]); reads defaults to "refresh" (see dag.READ_MODES)
+# (variant, delta[, reads[, warp tile items per lane]]); reads defaults to "refresh" (see
+# dag.READ_MODES), the warp tile to 7 items per lane (used by the "warp..." read paths only)
 SINGLE_CANDIDATES = [("sync", 0), ("async", 0), ("async", 0, "own_l1"), ("delayed", 32), ("delayed", 256),
-                     ("delayed", 4096), ("delayed", 4096, "local")]
+                     ("delayed", 4096), ("delayed", 4096, "local"),
+                     ("sync", 0, "warp"), ("async", 0, "warp+cached"), ("async", 0, "warp+cached", 5),
+                     ("async", 0, "warp+cached", 11), ("delayed", 16, "warp"), ("delayed", 256, "warp+cached")]
+WARP_TILES = (5, 7, 11)
 SSSP_EXTRA = [("async", 0, "frontier"), ("async", 0, "own_l1+frontier")]  # Bellman-Ford only
 BATCH_CANDIDATES = [("sync", 0), ("async", 0), ("delayed", 4), ("delayed", 16)]
 WORKER_FRACTIONS = [1.0, 0.5]
@@ -62,8 +68,12 @@ def _store(path, key, value):
 
 
 def _norm(c):
-    """(variant, delta, reads) from a 2- or 3-tuple candidate."""
-    return (c[0], int(c[1]), c[2] if len(c) > 2 else "refresh")
+    """(variant, delta, reads, warp tile) from a 2-, 3- or 4-tuple candidate."""
+    reads = c[2] if len(c) > 2 else "refresh"
+    ipt = int(c[3]) if len(c) > 3 else 7
+    if ipt not in WARP_TILES:
+        raise ValueError(f"warp tile of {ipt} items per lane is not built")
+    return (c[0], int(c[1]), reads, ipt)
 
 
 def _run(plan, algo, variant, delta, reads, kw):
@@ -109,6 +119,8 @@ def tune(plan: dag.Plan, algo: str, candidates=None, worker_fractions=None, tria
         hit = _load(cache).get(key)
         if hit:
             plan.set_worker_cap(hit["workers"])
+            if str(hit.get("reads", "")).startswith("warp"):
+                plan.set_warp_tile(hit.get("warp_tile", 7))
             return hit
     plan.set_worker_cap(0)
     full = plan.workers("async", 0)
@@ -121,26 +133,30 @@ def tune(plan: dag.Plan, algo: str, candidates=None, worker_fractions=None, tria
     for frac in fracs:
         cap = max(1, int(full * frac))
         plan.set_worker_cap(0 if frac >= 1.0 else cap)
-        for variant, delta, reads in cands:
+        for variant, delta, reads, ipt in cands:
             times, sweeps = [], []
             try:
+                if reads.startswith("warp"):
+                    plan.set_warp_tile(ipt)
                 for _ in range(trials):
                     ms, st = _run(plan, algo, variant, delta, reads, kw)
                     times.append(ms)
                     sweeps.append(st.get("iters", st.get("sweeps")))
             except dag.DagError as e:  # e.g. a delta whose buffer cannot be resident
-                results.append(dict(variant=variant, delta=delta, reads=reads, workers=0 if frac >= 1.0 else cap,
-                                    error=str(e)))
+                results.append(dict(variant=variant, delta=delta, reads=reads, warp_tile=ipt,
+                                    workers=0 if frac >= 1.0 else cap, error=str(e)))
                 continue
-            results.append(dict(variant=variant, delta=delta, reads=reads, workers=0 if frac >= 1.0 else cap,
-                                ms=float(np.median(times)), sweeps=sweeps))
+            results.append(dict(variant=variant, delta=delta, reads=reads, warp_tile=ipt,
+                                workers=0 if frac >= 1.0 else cap, ms=float(np.median(times)), sweeps=sweeps))
     ok = [r for r in results if "ms" in r]
     best = min(ok, key=lambda r: r["ms"])
-    choice = dict(variant=best["variant"], delta=best["delta"], reads=best["reads"], workers=best["workers"],
-                  ms=best["ms"], candidates=results)
+    choice = dict(variant=best["variant"], delta=best["delta"], reads=best["reads"], warp_tile=best["warp_tile"],
+                  workers=best["workers"], ms=best["ms"], candidates=results)
     if signal is not None:
         choice["locality"] = signal
     plan.set_worker_cap(best["workers"])
+    if best["reads"].startswith("warp"):
+        plan.set_warp_tile(best["warp_tile"])
     if cache:
         _store(cache, key, choice)
     torch.cuda.synchronize()

@@ -160,6 +160,7 @@ extern "C" int dag_pagerank(dag_plan* plan, float d, double tol, dag_variant var
     p.read_mode = read_mode_of(flags);
     p.local_read = (flags & DAG_READ_LOCAL) ? 1 : 0;
     p.own_l1 = (flags & DAG_READ_OWN_L1) ? 1 : 0;
+    p.warp = (flags & DAG_WARP_WORKERS) ? 1 : 0;
     Timer tm;
     tm.start(s, h_stats != nullptr);
     int nb = 0;
@@ -198,6 +199,8 @@ int sssp_impl(dag_plan* plan, uint32_t src, int variant, int delta, int max_iter
     p.local_read = (flags & DAG_READ_LOCAL) ? 1 : 0;
     p.own_l1 = (flags & DAG_READ_OWN_L1) ? 1 : 0;
     p.frontier = (flags & DAG_SSSP_FRONTIER) ? 1 : 0;
+    p.warp = (flags & DAG_WARP_WORKERS) ? 1 : 0;
+    if (p.warp && p.frontier) return set_error(DAG_ERR_INVALID, "the frontier runs the CTA-tile sweeps");
     if (p.frontier && var == DAG_DELAYED)
         return set_error(DAG_ERR_INVALID, "the frontier runs the synchronous and asynchronous forms (delta 0)");
     if (p.frontier) {  // the frontier maps of this launch shape are built (once) outside the timed solve
@@ -220,6 +223,23 @@ int sssp_impl(dag_plan* plan, uint32_t src, int variant, int delta, int max_iter
 }  // namespace dag
 
 extern "C" int32_t dag_tile_items(void) { return TILE; }
+
+namespace dag {
+__global__ void k_copy_status(const SyncBlock* sb, int32_t* out)
+{
+    out[0] = sb->err;
+    out[1] = sb->converged;
+    out[2] = sb->iters;
+}
+}  // namespace dag
+
+extern "C" int dag_plan_last_status(const dag_plan* plan, int32_t* d_status, void* stream)
+{
+    if (!plan || !d_status) return set_error(DAG_ERR_INVALID, "null argument");
+    k_copy_status<<<1, 1, 0, (cudaStream_t)stream>>>(plan->sync, d_status);
+    DAG_CUDA(cudaGetLastError());
+    return DAG_OK;
+}
 
 extern "C" int dag_sssp(dag_plan* plan, uint32_t src, dag_variant variant, int32_t delta, int32_t max_iters,
                         const uint32_t* d_w, uint32_t* d_dist, int32_t flags, dag_stats* h_stats, void* stream)

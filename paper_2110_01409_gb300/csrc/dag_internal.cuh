@@ -118,6 +118,9 @@ struct SweepParams {
     int* fr_chg;            // [n] the CTAs' rows that changed in the current sweep
     int* fr_glist;          // [tiles] shared sweeps: the tiles any CTA may claim
     int* fr_gchg;           // [n + tiles] shared sweeps: rows logged as changed (a row may repeat)
+    // warp workers (sweep_warp.cu): cta_row / cta_tile hold each warp's first row / tile
+    int warp;                     // 1: one worker per warp
+    unsigned long long* wpub;     // [warps] partial of the row each run leaves unfinished, with its sweep stamp
     // init / output
     const float* init;      // warm start (PR) or nullptr
     void* out;              // float r / lambda, or uint32 dist
@@ -142,6 +145,7 @@ struct Partition {
     int* fr_chg = nullptr;    // device [n]
     int* fr_glist = nullptr;  // device [tiles]
     int* fr_gchg = nullptr;   // device [n + tiles]
+    unsigned long long* wpub = nullptr;  // warp workers: [nblocks] published partials
 };
 
 }  // namespace dag
@@ -158,6 +162,7 @@ struct dag_plan {
     int stall_staging_once = 0;
     long long skip_timeout_ns = 0;
     int worker_cap = 0;       // > 0: at most this many CTAs per solve (more rows per CTA)
+    int warp_ipt = 7;         // items per lane of the warp-worker tiles (5, 7 or 11)
     // per-vertex data
     int* outdeg = nullptr;    // [n]
     float* degf = nullptr;    // [n]
@@ -218,6 +223,15 @@ size_t sweep_tma_ring_bytes(int mode);
 // Smallest shared-memory carveout of kernel k that keeps per_sm CTAs of
 // (static_smem + dyn) bytes resident; the rest of the SM's array is L1.
 int set_l1_carveout(const void* k, int device, int threads, size_t static_smem, size_t dyn, int per_sm);
+
+// Warp workers: the whole merge path cut into tiles of `tile` items, warp w
+// of W taking tiles [floor(w T / W), floor((w+1) T / W)); cta_tile / cta_row
+// hold each warp's first tile / first owned row (the partition's nblocks is W).
+int get_warp_partition(dag_plan* plan, int W, int tile, Partition** out, cudaStream_t s);
+// sweep_warp.cu
+const void* sweep_warp_kernel_ptr(int mode, int variant, int ipt);
+int launch_warp_sweep(dag_plan* plan, int mode, int variant, int delta, SweepParams& p, cudaStream_t s,
+                      int* out_nblocks);
 
 // plan.cu kernels reused by the allocation-free entry point (noalloc.cu)
 __global__ void k_check_rowptr(const int* rowptr, int n, long long m, int* bad);

@@ -273,6 +273,62 @@ int get_partition(dag_plan* plan, int P, Partition** out, cudaStream_t s, int ro
     return DAG_OK;
 }
 
+// Warp-worker partition: tile k starts at diagonal k * tile of the whole merge
+// path; its coordinates are (rows ended before it, edges before it).
+__global__ void k_warp_tile_coords(const int* rowptr, int n, long long m, int tile, int tiles, int* tile_row,
+                                   int* tile_nz)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > tiles) return;
+    if (k == tiles) { tile_row[k] = n; tile_nz[k] = (int)m; return; }
+    const long long diag = (long long)k * tile;
+    int lo = 0, hi = n;  // first v with v + rowptr[v+1] >= diag
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((long long)mid + rowptr[mid + 1] >= diag) hi = mid;
+        else lo = mid + 1;
+    }
+    tile_row[k] = lo;
+    tile_nz[k] = (int)(diag - lo);
+}
+__global__ void k_warp_runs(const int* tile_row, int tiles, int W, int* wtile, int* wrow)
+{
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w > W) return;
+    const int t = (int)((long long)w * tiles / W);
+    wtile[w] = t;
+    wrow[w] = tile_row[t];
+}
+
+int get_warp_partition(dag_plan* plan, int W, int tile, Partition** out, cudaStream_t s)
+{
+    const long long key = (1LL << 62) | ((long long)tile << 32) | (long long)W;
+    auto it = plan->parts.find(key);
+    if (it != plan->parts.end()) { *out = &it->second; return DAG_OK; }
+    Partition part;
+    part.nblocks = W;
+    const long long total = (long long)plan->n + plan->m;
+    const long long T = (total + tile - 1) / tile;
+    if (T >= (1LL << 31)) return set_error(DAG_ERR_INVALID, "graph too large for warp tiles");
+    part.tiles = (int)T;
+    DAG_CUDA(cudaMalloc(&part.cta_row, (W + 1) * sizeof(int)));
+    DAG_CUDA(cudaMalloc(&part.cta_tile, (W + 1) * sizeof(int)));
+    DAG_CUDA(cudaMalloc(&part.tile_row, (T + 1) * sizeof(int)));
+    DAG_CUDA(cudaMalloc(&part.tile_nz, (T + 1) * sizeof(int)));
+    DAG_CUDA(cudaMalloc(&part.wpub, W * sizeof(unsigned long long)));
+    k_warp_tile_coords<<<(unsigned)((T + 1 + 255) / 256), 256, 0, s>>>(plan->rowptr, plan->n, plan->m, tile, (int)T,
+                                                                       part.tile_row, part.tile_nz);
+    k_warp_runs<<<(W + 1 + 255) / 256, 256, 0, s>>>(part.tile_row, (int)T, W, part.cta_tile, part.cta_row);
+    DAG_CUDA(cudaGetLastError());
+    std::vector<int> wrow(W + 1);
+    DAG_CUDA(cudaMemcpyAsync(wrow.data(), part.cta_row, (W + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+    DAG_CUDA(cudaStreamSynchronize(s));
+    for (int w = 0; w < W; ++w) part.max_rows = std::max(part.max_rows, wrow[w + 1] - wrow[w]);
+    auto ins = plan->parts.emplace(key, part);
+    *out = &ins.first->second;
+    return DAG_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Out-edge CSR: a stable radix sort of the in-edges by source keeps, within
 // each source, the in-CSR order, i.e. ascending targets.
@@ -544,6 +600,7 @@ extern "C" int dag_plan_destroy(dag_plan* p)
         cudaFree(kv.second.fr_chg);
         cudaFree(kv.second.fr_glist);
         cudaFree(kv.second.fr_gchg);
+        cudaFree(kv.second.wpub);
     }
     cudaFree(p->fr_orow);
     delete p;

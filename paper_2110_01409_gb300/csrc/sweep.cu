@@ -600,6 +600,7 @@ int sweep_shape(dag_plan* plan, int mode, int variant, int delta, int* nb_out, i
 int launch_sweep(dag_plan* plan, int mode, int variant, int delta, SweepParams& p, cudaStream_t s,
                  int* out_nblocks)
 {
+    if (p.warp) return launch_warp_sweep(plan, mode, variant, delta, p, s, out_nblocks);
     int nb = 0, cap = 0, clamped = 0;
     Partition* part = nullptr;
     int rc = sweep_shape(plan, mode, variant, delta, &nb, &cap, &part, s, &clamped);

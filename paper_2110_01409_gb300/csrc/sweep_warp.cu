@@ -1,0 +1,603 @@
+// Warp-worker pull sweep: PageRank (plain and weighted), its adjoint and
+// Bellman-Ford in the synchronous, asynchronous and delayed-asynchronous
+// forms, with one warp per worker and no CTA-wide barrier inside a sweep.
+//
+// Paper mapping (Blanco, McMillan, Low, HPEC 2021):
+//  * worker = one warp. The merge path of the whole graph (rows and in-edges
+//    in vertex order, Merrill & Garland) is cut into warp tiles of WTILE items
+//    and every worker takes an equal run of consecutive tiles, so each carries
+//    the same in-degree + 1 weight (Sec. III-A's balance) and owns the rows
+//    whose end item lies in its run (contiguous in vertex order). A row whose
+//    in-edges span two runs (a hub, or a cut inside a row) is owned by the run
+//    that ends it; the earlier runs' partial sums reach it at the end of the
+//    sweep through a bounded look-back (below);
+//  * pull update of each owned vertex from its in-neighbours (Sec. III-A);
+//  * sync: values go to the second array (Sec. I); async: values are written
+//    in place as soon as a warp tile completes them (Sec. I); delayed: values
+//    go to the warp's buffer in shared memory and reach the global array when
+//    it holds >= delta values or the run is done (Sec. III, III-B); reads come
+//    from the global array (the "global read" form, Sec. III-C);
+//  * one grid barrier per iteration (Sec. I) and the stopping rules of Sec. IV.
+//
+// Why warps: the CTA-tile kernels (sweep.cu, sweep_tma.cu) stop all eight
+// warps at three barriers per 1,792-item tile, so each tile waits for its
+// slowest gather; here each warp walks its own 224-item tiles with a
+// shuffle-only segmented scan and issues the next tile's edge stream and
+// gathers before walking the current one, so the SM's 32 warps keep their
+// gathers in flight independently.
+//
+// Row straddling two runs. At the end of its run a warp publishes the partial
+// of the row it leaves unfinished (one 64-bit word: sweep stamp and value).
+// A warp whose run starts inside a row holds back that row's value and, after
+// its own run, adds the partials published by the preceding warps back to the
+// one where the row starts (several when a hub spans whole runs); each wait is
+// bounded by the launch's timeout. The row then gets its new value like any
+// other, so every row is computed once per sweep; only its write comes at the
+// end of the sweep.
+#include <algorithm>
+#include <climits>
+#include <cstdint>
+
+#include "sweep_common.cuh"
+
+namespace dag {
+
+// Warp tile shapes: items per lane (odd: fewer bank conflicts in the walk);
+// the plan picks one (dag_plan_set_warp_tile), WIPT_DEFAULT unless told.
+constexpr int WIPT_DEFAULT = 7;
+constexpr int WWARPS = NWARP;        // warps per CTA (block reductions and the grid barrier are per CTA)
+constexpr int WMINBLOCKS = 4;        // CTAs per SM the register budget is sized for
+constexpr int LIVE_EVERY = 8;        // async / delayed PageRank: a warp reads and adds to the live sum every 8
+                                     // tiles (1,792 items, the CTA-tile kernels' tile), not every tile
+
+template <int WTILE>
+struct WarpShared {
+    int end[WWARPS][WTILE + 1];      // tile-relative row ends (+ sentinel)
+    uint32_t val[WWARPS][WTILE];     // edge terms of the tile
+    uint32_t sum[WWARPS][WTILE];     // per-row reduction of the tile
+    double red0[NWARP];
+    double red1[NWARP];
+    double res, gprev, T;
+};
+
+// Inputs of the next warp tile, loaded while the current one is walked.
+template <int WIPT>
+struct WStage {
+    int a0, b0, NA, NB;
+    uint32_t term[WIPT];  // edge terms: gathered value, combined with the edge's weight / value
+    uint32_t xo;          // old value of row a0 + lane
+    float dg;             // its out-degree (PageRank)
+    long long gs;         // one stripe of the live global sum (async / delayed PageRank)
+};
+
+template <int MODE, int WIPT>
+__device__ __forceinline__ void wfetch(WStage<WIPT>& st, const SweepParams& p, const uint32_t* xin, int t, int lane, int rmode,
+                                       bool live, uint64_t pol_edge, uint64_t pol_vertex)
+{
+    constexpr bool BF = MODE == MODE_BF || MODE == MODE_BF8;
+    st.a0 = p.tile_row[t];
+    st.b0 = p.tile_nz[t];
+    st.NA = p.tile_row[t + 1] - st.a0;
+    st.NB = p.tile_nz[t + 1] - st.b0;
+    int col[WIPT];
+    uint32_t aux[WIPT];
+#pragma unroll
+    for (int q = 0; q < WIPT; ++q) {
+        const int j = lane + 32 * q;
+        col[q] = -1;
+        aux[q] = 0u;
+        if (j < st.NB) {
+            col[q] = (int)ld_edge_b32(p.colidx + st.b0 + j, pol_edge);
+            if constexpr (MODE == MODE_BF) aux[q] = ld_edge_b32(p.w + st.b0 + j, pol_edge);
+            if constexpr (MODE == MODE_BF8) aux[q] = ld_edge_u8(p.w8 + st.b0 + j, pol_edge);
+            if constexpr (MODE == MODE_PRW || MODE == MODE_ADJ) aux[q] = ld_edge_b32(p.val + st.b0 + j, pol_edge);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < WIPT; ++q) {
+        uint32_t term = Op<MODE>::identity();
+        if (col[q] >= 0) {
+            const uint32_t xv = rmode == READ_COHERENT ? ld_relaxed_keep_b32(xin + col[q], pol_vertex)
+                                                       : ld_weak_keep_b32(xin + col[q], pol_vertex);
+            if constexpr (BF) term = relax(xv, aux[q]);
+            else if constexpr (MODE == MODE_PR) term = xv;
+            else term = __float_as_uint(__uint_as_float(aux[q]) * __uint_as_float(xv));
+        }
+        st.term[q] = term;
+    }
+    st.xo = 0u;
+    st.dg = 0.0f;
+    if (lane < st.NA) {  // only this warp writes its rows, so a value loaded ahead is still the current one
+        st.xo = ld_weak_keep_b32(xin + st.a0 + lane, pol_vertex);
+        if constexpr (!BF) st.dg = __uint_as_float(ld_vertex_b32(p.degf + st.a0 + lane, pol_vertex));
+    }
+    if (live) st.gs = ld_relaxed_i64(&p.sync->stripe[lane * GSTRIDE]);
+}
+
+// One warp tile's merge path, warp segmented scan and per-row sums into
+// sum[0 .. NA). carry: the partial of the row continuing from the previous
+// tile; returns the partial of row NA (continuing into the next tile).
+template <int MODE, int WIPT>
+__device__ __forceinline__ uint32_t wwalk(const int* end, const uint32_t* val, uint32_t* sum, int NA, int NB,
+                                          uint32_t carry, int lane)
+{
+    using O = Op<MODE>;
+    const int L = NA + NB;
+    const int k0 = min(lane * WIPT, L);
+    int lo = max(0, k0 - NB), hi = min(k0, NA);
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (end[mid] <= k0 - 1 - mid) lo = mid + 1;
+        else hi = mid;
+    }
+    int i = lo, j = k0 - lo;
+    const int i_start = i;
+    bool emitted = false;
+    uint32_t acc = lane == 0 ? carry : O::identity();
+    int re = end[i];
+#pragma unroll
+    for (int q = 0; q < WIPT; ++q) {
+        if (k0 + q < L) {
+            if (re <= j) {
+                sum[i] = acc;
+                emitted = true;
+                acc = O::identity();
+                ++i;
+                re = end[i];
+            } else {
+                acc = O::combine(acc, val[j]);
+                ++j;
+            }
+        }
+    }
+    // inclusive segmented scan of (row in progress, partial) over the lanes
+    const int key = i;
+    uint32_t sv = acc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t ov = __shfl_up_sync(0xffffffffu, sv, o);
+        const int ok = __shfl_up_sync(0xffffffffu, key, o);
+        if (lane >= o && ok == key) sv = O::combine(sv, ov);
+    }
+    const uint32_t cin = __shfl_up_sync(0xffffffffu, sv, 1);
+    const int kprev = __shfl_up_sync(0xffffffffu, key, 1);
+    if (lane > 0 && emitted && kprev == i_start) sum[i_start] = O::combine(sum[i_start], cin);
+    return __shfl_sync(0xffffffffu, sv, 31);
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// The partial that warp k published for sweep `stamp` (waits, bounded); false
+// when the wait ran out or another CTA recorded an error.
+__device__ __forceinline__ bool wait_published(const unsigned long long* pub, int k, unsigned stamp, SyncBlock* sb,
+                                               long long timeout_ns, uint32_t* out)
+{
+    const unsigned long long t0 = globaltimer_ns();
+    unsigned spins = 0;
+    for (;;) {
+        const unsigned long long v = ld_relaxed_u64(pub + k);
+        if ((unsigned)(v >> 32) == stamp) {
+            *out = (uint32_t)v;
+            return true;
+        }
+        if (ld_relaxed_i32(&sb->err) != 0) return false;
+        if ((++spins & 15u) == 0 && (long long)(globaltimer_ns() - t0) > timeout_ns) {
+            atomicCAS(&sb->err, 0, DAG_ERR_BARRIER_TIMEOUT);
+            return false;
+        }
+        __nanosleep(64);
+    }
+}
+
+template <int MODE, int VAR, int WIPT>
+__global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_warp_kernel(const SweepParams p)
+{
+    constexpr int WTILE = 32 * WIPT;
+    using O = Op<MODE>;
+    constexpr bool BF = MODE == MODE_BF || MODE == MODE_BF8;
+    constexpr bool SYNC = VAR == DAG_SYNC;
+    constexpr bool ASYNC = VAR == DAG_ASYNC;
+    constexpr bool DELAYED = VAR == DAG_DELAYED;
+    constexpr bool LIVE_G = !SYNC && !BF;  // async/delayed PageRank-type: live global sum
+    constexpr unsigned FULL = 0xffffffffu;
+
+    __shared__ WarpShared<WTILE> sh;
+    extern __shared__ __align__(16) uint32_t w_buf[];  // delayed: p.buf_cap values per warp
+
+    const int c = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wl = tid >> 5;
+    const int w = c * WWARPS + wl;  // this worker
+    SyncBlock* sb = p.sync;
+    unsigned long long bar_target = 0;
+    uint32_t* X0 = (uint32_t*)p.x0;
+    uint32_t* X1 = (uint32_t*)p.x1;
+    const int row_lo = p.cta_row[w], row_hi = p.cta_row[w + 1];  // rows whose end item lies in the run
+    const int t_lo = p.cta_tile[w], t_hi = p.cta_tile[w + 1];
+    const float inv_n = 1.0f / (float)p.n;
+    int* end = sh.end[wl];
+    uint32_t* val = sh.val[wl];
+    uint32_t* sum = sh.sum[wl];
+    uint32_t* buf = w_buf + (size_t)wl * (DELAYED ? p.buf_cap : 0);
+    // the run starts inside a row: its first row waits for the earlier runs' partials
+    const bool mid0 = t_lo < t_hi && p.tile_nz[t_lo] > p.rowptr[p.tile_row[t_lo]];
+    const bool head = mid0 && row_hi > row_lo;
+
+    // ---------------- initial values of the owned rows ----------------
+    {
+        double gpart = 0.0, tpart = 0.0;
+        for (int v = row_lo + lane; v < row_hi; v += 32) {
+            if constexpr (BF) {
+                X0[v] = (v == (int)p.src) ? 0u : INF;
+            } else if constexpr (MODE == MODE_ADJ) {
+                const float cv = p.base[v];
+                const float l0 = p.init ? p.init[v] : cv;
+                X0[v] = __float_as_uint(l0);
+                gpart += (double)l0;
+                tpart += fabs((double)cv);
+            } else {
+                const float t = p.base ? p.base[v] : inv_n;
+                const float r0 = p.init ? p.init[v] : t;
+                const float dg = p.degf[v];
+                X0[v] = __float_as_uint((MODE == MODE_PR && dg > 0.0f) ? r0 / dg : r0);
+                if (dg > 0.0f) gpart += (double)r0;
+                tpart += (double)t;
+            }
+        }
+        if constexpr (!BF) {
+            block_sum2(sh, gpart, tpart);
+            if (tid == 0) {
+                atomicAdd(&sb->acc_g[2], gpart);
+                atomicAdd(&sb->T, tpart);
+            }
+        }
+    }
+    if (p.skip_barrier_cta0 && c == 0) return;  // test hook: the others' waits must run out
+    if (!grid_barrier(sb, p.nblocks, bar_target, p.timeout_ns)) return;
+
+    double T = 1.0;
+    if (tid == 0 && !BF) {
+        sh.T = ld_relaxed_f64(&sb->T);
+        sh.gprev = ld_relaxed_f64(&sb->acc_g[2]);
+    }
+    __syncthreads();
+    if constexpr (!BF) T = (MODE == MODE_ADJ || p.base) ? sh.T : 1.0;  // a uniform teleport sums to 1 exactly
+    double gprev = BF ? 0.0 : sh.gprev;
+    LiveSum L{};
+    if constexpr (LIVE_G) L = live_sum_setup<MODE>(p, T, gprev);
+    const double tol = (MODE == MODE_ADJ) ? p.tol * T : p.tol;
+    // gathers: sync reads the previous iterate with ordinary loads; async reads the live array
+    // in L2 (DAG_READ_CACHED: ordinary loads, refreshed by the grid barrier); delayed per p.read_mode
+    const int rmode = SYNC ? READ_CACHED : ASYNC ? (p.read_mode == READ_CACHED ? READ_CACHED : READ_COHERENT)
+                                                  : p.read_mode;
+    const uint64_t pol_edge = policy_evict_first();
+    const uint64_t pol_vertex = policy_evict_last();
+    long long flushes = 0;
+    int it = 0;
+    bool converged = false;
+    double last_res = 0.0;
+
+    for (; it < p.max_iters; ++it) {
+        const int slot = it % 3;
+        const unsigned stamp = (unsigned)it + 1u;
+        const uint32_t* xin = SYNC ? ((it & 1) ? X1 : X0) : X0;
+        uint32_t* xout = SYNC ? ((it & 1) ? X0 : X1) : X0;
+        // per-lane partial sums in FP32 (few rows each); FP64 from the block reduction on
+        float res_part = 0.0f, g_part = 0.0f, dg_part = 0.0f;
+        uint32_t carry = O::identity();
+        bool head_pending = head;
+        uint32_t head_part = O::identity();
+        int buf_first = row_lo + (head ? 1 : 0), buf_cnt = 0;
+        float gt = 0.0f;
+        if constexpr (SYNC && !BF)
+            gt = (MODE == MODE_ADJ) ? (float)((double)p.g_coef * gprev) : (float)((double)p.g_coef * (T - gprev));
+
+        WStage<WIPT> nx;
+        if (t_lo < t_hi) wfetch<MODE, WIPT>(nx, p, xin, t_lo, lane, rmode, LIVE_G, pol_edge, pol_vertex);
+        for (int t = t_lo; t < t_hi; ++t) {
+            const int a0 = nx.a0, b0 = nx.b0, NA = nx.NA, NB = nx.NB;
+            const uint32_t pf_xo = nx.xo;
+            const float pf_dg = nx.dg;
+            if constexpr (LIVE_G) {  // the global term, from the live sum read with every LIVE_EVERY-th tile
+                if (((t - t_lo) & (LIVE_EVERY - 1)) == 0) gt = live_term<MODE>(L, warp_sum(nx.gs));
+            }
+            __syncwarp();  // the previous tile's epilogue is done with end / val / sum
+#pragma unroll
+            for (int q = 0; q < WIPT; ++q) {
+                const int j = lane + 32 * q;
+                if (j < NB) val[j] = nx.term[q];
+            }
+            for (int i = lane; i < NA; i += 32) end[i] = (int)ld_vertex_b32(p.rowptr + a0 + i + 1, pol_vertex) - b0;
+            if (lane == 0) end[NA] = INT_MAX;
+            if (t + 1 < t_hi)
+                wfetch<MODE, WIPT>(nx, p, xin, t + 1, lane, rmode, LIVE_G && ((t + 1 - t_lo) & (LIVE_EVERY - 1)) == 0,
+                             pol_edge, pol_vertex);
+            __syncwarp();
+            carry = wwalk<MODE, WIPT>(end, val, sum, NA, NB, carry, lane);
+            __syncwarp();
+
+            // -------- new values of the rows this tile completed --------
+            const int skip = (head_pending && NA > 0) ? 1 : 0;  // the run's first row waits for the look-back
+            if (skip && lane == 0) head_part = sum[0];
+            head_pending = head_pending && NA == 0;
+            // rows lane + 32 k: the first came with the tile, the others' inputs are loaded together
+            uint32_t xo_k[WIPT];
+            float dg_k[WIPT];
+            xo_k[0] = pf_xo;
+            dg_k[0] = pf_dg;
+#pragma unroll
+            for (int k = 1; k < WIPT; ++k) {
+                const int r = lane + 32 * k;
+                xo_k[k] = 0u;
+                dg_k[k] = 0.0f;
+                if (r < NA) {
+                    xo_k[k] = ld_weak_b32(xin + a0 + r);
+                    if constexpr (!BF) dg_k[k] = ld_stream_f32(p.degf + a0 + r);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < WIPT; ++k) {
+                const int r = lane + 32 * k;
+                if (r >= NA || (k == 0 && lane == 0 && skip)) continue;
+                const int v = a0 + r;
+                const uint32_t xnew = row_update<MODE>(p, v, sum[r], xo_k[k], dg_k[k], gt, res_part, g_part, dg_part);
+                if constexpr (SYNC) st_weak_b32(xout + v, xnew);
+                else if constexpr (ASYNC) st_relaxed_b32(X0 + v, xnew);
+                else buf[v - buf_first] = xnew;
+            }
+            if constexpr (ASYNC && LIVE_G) {
+                if (((t - t_lo) & (LIVE_EVERY - 1)) == LIVE_EVERY - 1) {  // this warp's change of N
+                    const float s = warp_sum(dg_part);
+                    dg_part = 0.0f;
+                    if (lane == 0 && s != 0.0f) live_add(sb, w % GSTRIPES, s, L.S);
+                }
+            }
+            if constexpr (DELAYED) {
+                buf_cnt += NA - skip;
+                if (buf_cnt >= p.delta || t == t_hi - 1 || (p.buf_clamped && buf_cnt > p.buf_cap - WTILE)) {
+                    __syncwarp();  // the buffer's values are written
+                    for (int k = lane; k < buf_cnt; k += 32) st_relaxed_b32(X0 + buf_first + k, buf[k]);
+                    if constexpr (LIVE_G) {
+                        const float s = warp_sum(dg_part);
+                        dg_part = 0.0f;
+                        __syncwarp();
+                        if (lane == 0 && s != 0.0f) {
+                            __threadfence();  // this warp's flushed values before its share of N
+                            live_add(sb, w % GSTRIPES, s, L.S);
+                        }
+                    }
+                    if (lane == 0) {
+                        // refresh this SM's view: later ordinary loads see what other workers published
+                        if (rmode == READ_CACHED_REFRESH) asm volatile("fence.acq_rel.gpu;" ::: "memory");
+                        ++flushes;
+                    }
+                    buf_first += buf_cnt;
+                    buf_cnt = 0;
+                    __syncwarp();  // the buffer is free again
+                }
+            }
+        }  // tiles
+
+        // -------- the row this run leaves unfinished, and the one it started inside --------
+        if (lane == 0) st_relaxed_u64(p.wpub + w, ((unsigned long long)stamp << 32) | carry);
+        if (head) {
+            uint32_t s = __shfl_sync(FULL, head_part, 0);
+            bool ok = true;
+            for (int k = w - 1; k >= 0; --k) {
+                uint32_t pk = 0u;
+                if (lane == 0) ok = wait_published(p.wpub, k, stamp, sb, p.timeout_ns, &pk);
+                ok = __shfl_sync(FULL, ok, 0);
+                pk = __shfl_sync(FULL, pk, 0);
+                if (!ok) break;
+                s = O::combine(s, pk);
+                // the row starts in run k unless run k ends no row and itself starts inside the row
+                const int tk0 = p.cta_tile[k], tk1 = p.cta_tile[k + 1];
+                const bool k_emits = p.cta_row[k + 1] > p.cta_row[k];
+                const bool k_mid = tk0 >= tk1 || p.tile_nz[tk0] > p.rowptr[p.tile_row[tk0]];
+                if (k_emits || !k_mid) break;
+            }
+            if (ok && lane == 0) {
+                const int v = row_lo;
+                const uint32_t xo = ld_weak_b32(xin + v);
+                const float dg = BF ? 0.0f : p.degf[v];
+                if constexpr (LIVE_G) {  // the live global term as the row is computed
+                    long long G = 0;
+                    for (int k = 0; k < GSTRIPES; ++k) G += ld_relaxed_i64(&sb->stripe[k * GSTRIDE]);
+                    gt = live_term<MODE>(L, G);
+                }
+                const uint32_t xnew = row_update<MODE>(p, v, s, xo, dg, gt, res_part, g_part, dg_part);
+                if constexpr (SYNC) st_weak_b32(xout + v, xnew);
+                else st_relaxed_b32(X0 + v, xnew);
+            }
+        }
+        if constexpr (LIVE_G) {  // the rest of this warp's change of N
+            const float s = warp_sum(dg_part);
+            dg_part = 0.0f;
+            if (lane == 0 && s != 0.0f) live_add(sb, w % GSTRIPES, s, L.S);
+        }
+
+        // -------- end of sweep: residual, barrier, stopping rule --------
+        double res_d = (double)res_part, g_d = (double)g_part;
+        block_sum2(sh, res_d, g_d);
+        if (tid == 0) {
+            if (res_d != 0.0) atomicAdd(&sb->acc_res[slot], res_d);
+            if (SYNC && !BF && g_d != 0.0) atomicAdd(&sb->acc_g[slot], g_d);
+        }
+        if (!grid_barrier(sb, p.nblocks, bar_target, p.timeout_ns)) return;
+        if (tid == 0) {
+            sh.res = ld_relaxed_f64(&sb->acc_res[slot]);
+            sh.gprev = ld_relaxed_f64(&sb->acc_g[slot]);
+            if (c == 0) {
+                const int dead = (it + 2) % 3;  // read by everyone before this barrier
+                sb->acc_res[dead] = 0.0;
+                sb->acc_g[dead] = 0.0;
+            }
+        }
+        __syncthreads();
+        last_res = sh.res;
+        gprev = sh.gprev;
+        if (last_res <= tol) {
+            converged = true;
+            ++it;
+            break;
+        }
+    }
+
+    // ---------------- output of the owned rows ----------------
+    {
+        const uint32_t* xf = SYNC ? ((it & 1) ? X1 : X0) : X0;
+        for (int v = row_lo + lane; v < row_hi; v += 32) {
+            const uint32_t x = ld_relaxed_b32(xf + v);
+            if constexpr (BF || MODE == MODE_ADJ || MODE == MODE_PRW) {
+                ((uint32_t*)p.out)[v] = x;
+            } else {
+                const float dg = p.degf[v];
+                ((float*)p.out)[v] = dg > 0.0f ? __uint_as_float(x) * dg : __uint_as_float(x);
+            }
+        }
+    }
+    if (lane == 0 && flushes) atomicAdd((unsigned long long*)&sb->flushes, (unsigned long long)flushes);
+    if (tid == 0 && c == 0) {
+        sb->iters = it;
+        sb->residual = last_res;
+        sb->converged = converged ? 1 : 0;
+    }
+}
+
+// Kernel of (mode, variant, items per lane); nullptr for a shape not built.
+const void* sweep_warp_kernel_ptr(int mode, int variant, int ipt)
+{
+#define DAG_WARP_ROW(M, I)                                                                                    \
+    {(const void*)sweep_warp_kernel<M, DAG_SYNC, I>, (const void*)sweep_warp_kernel<M, DAG_ASYNC, I>,       \
+     (const void*)sweep_warp_kernel<M, DAG_DELAYED, I>}
+#define DAG_WARP_SHAPE(I) \
+    {DAG_WARP_ROW(MODE_PR, I), DAG_WARP_ROW(MODE_PRW, I), DAG_WARP_ROW(MODE_ADJ, I), DAG_WARP_ROW(MODE_BF, I), \
+     DAG_WARP_ROW(MODE_BF8, I)}
+    static const void* const table[3][5][3] = {DAG_WARP_SHAPE(5), DAG_WARP_SHAPE(7), DAG_WARP_SHAPE(11)};
+#undef DAG_WARP_SHAPE
+#undef DAG_WARP_ROW
+    const int k = ipt == 5 ? 0 : ipt == 7 ? 1 : ipt == 11 ? 2 : -1;
+    return k < 0 ? nullptr : table[k][mode][variant];
+}
+
+// Launch shape of a warp-worker sweep: CTAs resident at once (cooperative
+// launch), warps = CTAs * WWARPS workers, and the delayed form's buffer of
+// min(delta - 1 + WTILE, rows of the longest run) values per warp, clamped to
+// what fits in shared memory (flushed when the next tile might not fit).
+static int warp_shape(dag_plan* plan, int mode, int variant, int delta, int* nb_out, int* cap_out, int* clamped_out,
+                      Partition** part_out, cudaStream_t s)
+{
+    const int WTILE = 32 * plan->warp_ipt;
+    const void* k = sweep_warp_kernel_ptr(mode, variant, plan->warp_ipt);
+    if (!k) return set_error(DAG_ERR_INVALID, "no warp tile of that shape");
+    cudaFuncAttributes fa{};
+    DAG_CUDA(cudaFuncGetAttributes(&fa, k));
+    int max_dyn = 0;
+    DAG_CUDA(cudaDeviceGetAttribute(&max_dyn, cudaDevAttrMaxSharedMemoryPerBlockOptin, plan->device));
+    const long long max_cap = ((long long)max_dyn - (long long)fa.sharedSizeBytes) / (4LL * WWARPS);
+    int cap = 0, clamped = 0, nb = 0;
+    Partition* part = nullptr;
+    auto resident = [&](int cap_elems, int* out) -> int {
+        const size_t dyn = (size_t)WWARPS * (size_t)cap_elems * 4;
+        DAG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+        DAG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+        int per_sm = 0;
+        DAG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, dyn));
+        if (per_sm < 1) return set_error(DAG_ERR_INVALID, "warp sweep cannot be resident with this delta");
+        const int rc = set_l1_carveout(k, plan->device, NT, fa.sharedSizeBytes, dyn, per_sm);
+        if (rc) return rc;
+        int n_cta = per_sm * plan->num_sms;
+        if (plan->worker_cap > 0) n_cta = std::min(n_cta, plan->worker_cap);  // the cap counts CTAs
+        *out = n_cta;
+        return DAG_OK;
+    };
+    int rc = resident(0, &nb);
+    if (rc) return rc;
+    bool settled = false;  // CTAs per SM only fall, so a few passes settle the shape
+    for (int iter = 0; iter < 6 && !settled; ++iter) {
+        rc = get_warp_partition(plan, nb * WWARPS, WTILE, &part, s);
+        if (rc) return rc;
+        settled = true;
+        if (variant != DAG_DELAYED) break;
+        const long long want = std::min((long long)delta - 1 + WTILE, (long long)std::max(part->max_rows, 1));
+        const long long need = std::min(want, max_cap);
+        clamped = need < want ? 1 : 0;
+        if (clamped && need < WTILE + 1) return set_error(DAG_ERR_INVALID, "delay buffer does not fit in shared memory");
+        cap = (int)std::max(need, 1LL);
+        int nb2 = 0;
+        rc = resident(cap, &nb2);
+        if (rc) return rc;
+        if (nb2 < nb) {
+            nb = nb2;
+            settled = false;
+        }
+    }
+    if (!settled) return set_error(DAG_ERR_INVALID, "warp sweep launch shape did not settle");
+    *nb_out = nb;
+    *cap_out = cap;
+    *clamped_out = clamped;
+    *part_out = part;
+    return DAG_OK;
+}
+
+int launch_warp_sweep(dag_plan* plan, int mode, int variant, int delta, SweepParams& p, cudaStream_t s,
+                      int* out_nblocks)
+{
+    if (p.frontier) return set_error(DAG_ERR_INVALID, "the frontier runs the CTA-tile sweeps");
+    if (p.local_read || p.own_l1) return set_error(DAG_ERR_INVALID, "local and own-block reads run the CTA-tile sweeps");
+    int nb = 0, cap = 0, clamped = 0;
+    Partition* part = nullptr;
+    int rc = warp_shape(plan, mode, variant, delta, &nb, &cap, &clamped, &part, s);
+    if (rc) return rc;
+    p.nblocks = nb;
+    p.delta = (variant == DAG_DELAYED) ? delta : 0;
+    p.buf_cap = cap;
+    p.buf_clamped = clamped;
+    p.cta_row = part->cta_row;
+    p.cta_tile = part->cta_tile;
+    p.tile_row = part->tile_row;
+    p.tile_nz = part->tile_nz;
+    p.wpub = part->wpub;
+    p.sync = plan->sync;
+    p.timeout_ns = plan->timeout_ns;
+    p.skip_barrier_cta0 = 0;
+    p.stall_fill = 0;
+    if (plan->skip_barrier_once) {
+        p.skip_barrier_cta0 = 1;
+        p.timeout_ns = plan->skip_timeout_ns;
+        plan->skip_barrier_once = 0;
+    }
+    DAG_CUDA(cudaMemsetAsync(plan->sync, 0, sizeof(SyncBlock), s));
+    // stamps of an earlier solve must not pass for this one's
+    DAG_CUDA(cudaMemsetAsync(part->wpub, 0, (size_t)part->nblocks * sizeof(unsigned long long), s));
+    const void* k = sweep_warp_kernel_ptr(mode, variant, plan->warp_ipt);
+    const size_t dyn = (size_t)WWARPS * (size_t)cap * 4;
+    DAG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    void* args[] = {(void*)&p};
+    DAG_CUDA(cudaLaunchCooperativeKernel(k, dim3(nb), dim3(NT), args, dyn, s));
+    *out_nblocks = nb * WWARPS;
+    return DAG_OK;
+}
+
+}  // namespace dag
+
+extern "C" int dag_plan_set_warp_tile(dag_plan* plan, int32_t items_per_lane)
+{
+    if (!plan) return dag::set_error(DAG_ERR_INVALID, "null plan");
+    if (!dag::sweep_warp_kernel_ptr(dag::MODE_PR, DAG_SYNC, items_per_lane))
+        return dag::set_error(DAG_ERR_INVALID, "items per lane must be 5, 7 or 11");
+    plan->warp_ipt = items_per_lane;
+    return DAG_OK;
+}
+
+extern "C" int32_t dag_warp_tile_items(const dag_plan* plan)
+{
+    return 32 * (plan ? plan->warp_ipt : dag::WIPT_DEFAULT);
+}

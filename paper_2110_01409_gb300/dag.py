@@ -24,14 +24,16 @@ WARM_START = 1
 READ_MODES = {"refresh": 0, "coherent": 2, "cached": 4,  # delayed form's reads (DAG_READ_*)
               "local": 8, "local+coherent": 10, "local+cached": 12,
               "own_l1": 16,  # async form: own block through L1 (DAG_READ_OWN_L1)
-              "frontier": 32, "own_l1+frontier": 48}  # Bellman-Ford: run only changed tiles (DAG_SSSP_FRONTIER)
+              "frontier": 32, "own_l1+frontier": 48,  # Bellman-Ford: run only changed tiles (DAG_SSSP_FRONTIER)
+              "warp": 64, "warp+coherent": 66, "warp+cached": 68}  # one worker per warp (DAG_WARP_WORKERS)
 
 EXPORTS = (
     "dag_plan_create", "dag_plan_destroy", "dag_plan_out_degree", "dag_partition", "dag_workers",
     "dag_pagerank", "dag_sssp", "dag_ppr_batched", "dag_sssp_batched", "dag_transpose",
     "dag_normalize_weights", "dag_pagerank_adjoint", "dag_strerror", "dag_last_error_message",
     "dag_debug_skip_barrier_once", "dag_debug_stall_staging_once", "dag_tile_items", "dag_pagerank_noalloc", "dag_gather_f32", "dag_plan_set_worker_cap",
-    "dag_sssp_u8", "dag_probe_gather", "dag_access_matrix", "dag_plan_set_batched_graph",
+    "dag_sssp_u8", "dag_probe_gather", "dag_access_matrix", "dag_plan_set_batched_graph", "dag_warp_tile_items",
+    "dag_plan_set_warp_tile", "dag_plan_last_status",
 )
 
 
@@ -94,6 +96,10 @@ def lib():
             L.dag_debug_skip_barrier_once.argtypes = [_vp, _i32]
             L.dag_debug_stall_staging_once.argtypes = [_vp, _i32]
             L.dag_tile_items.restype = _i32
+            L.dag_warp_tile_items.restype = _i32
+            L.dag_warp_tile_items.argtypes = [_vp]
+            L.dag_plan_set_warp_tile.argtypes = [_vp, _i32]
+            L.dag_plan_last_status.argtypes = [_vp, _vp, _vp]
             L.dag_gather_f32.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp]
             L.dag_plan_set_worker_cap.argtypes = [_vp, _i32]
             L.dag_plan_set_batched_graph.argtypes = [_vp, _i32]
@@ -104,7 +110,7 @@ def lib():
             L.dag_pagerank_noalloc.argtypes = [ctypes.POINTER(_Csr), _f32, _f64, _i32, _i32, _i32, _vp, _vp,
                                                ctypes.POINTER(_Stats), _vp]
             for f in EXPORTS:
-                if f not in ("dag_strerror", "dag_last_error_message"):
+                if f not in ("dag_strerror", "dag_last_error_message", "dag_tile_items", "dag_warp_tile_items"):
                     getattr(L, f).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -195,6 +201,18 @@ class Plan:
         """Batched solves on this plan through CUDA graphs captured once per launch shape (on), or
         launched directly (off, the default)."""
         _raise(lib().dag_plan_set_batched_graph(self.h, 1 if on else 0), False)
+
+    def set_warp_tile(self, items_per_lane: int):
+        """Warp tile shape (32 x items_per_lane items, 5, 7 or 11) of warp-worker solves."""
+        _raise(lib().dag_plan_set_warp_tile(self.h, items_per_lane), False)
+
+    def warp_tile_items(self) -> int:
+        return int(lib().dag_warp_tile_items(self.h))
+
+    def last_status_to(self, out: torch.Tensor, stream=None):
+        """Enqueues a copy of the last solve's (err, converged, sweeps) into out (CUDA int32 [3]); no wait."""
+        _dev(out, torch.int32, 3, "out")
+        _raise(lib().dag_plan_last_status(self.h, _ptr(out), _stream(stream)), False)
 
     def set_worker_cap(self, max_workers: int):
         """At most max_workers CTAs per solve (0: as many as fit)."""

@@ -69,6 +69,8 @@ def test_null_arguments_are_refused_without_a_gpu(lib):
         "dag_workers": lambda: lib.dag_workers(N, 1, 0, ctypes.byref(ctypes.c_int32())),
         "dag_plan_set_worker_cap": lambda: lib.dag_plan_set_worker_cap(N, 0),
         "dag_plan_set_batched_graph": lambda: lib.dag_plan_set_batched_graph(N, 1),
+        "dag_plan_set_warp_tile": lambda: lib.dag_plan_set_warp_tile(N, 7),
+        "dag_plan_last_status": lambda: lib.dag_plan_last_status(N, N, N),
         "dag_pagerank": lambda: lib.dag_pagerank(N, f(0.85), d(1e-6), 1, 0, 10, N, N, N, 0, N, N),
         "dag_sssp": lambda: lib.dag_sssp(N, 0, 1, 0, 10, N, N, 0, N, N),
         "dag_sssp_u8": lambda: lib.dag_sssp_u8(N, 0, 1, 0, 10, N, N, 0, N, N),

@@ -16,12 +16,16 @@ class FakePlan:
         self.rowptr = torch.from_numpy(np.sort(rng.integers(0, m, n + 1)).astype(np.int32))
         self.colidx = torch.from_numpy(rng.integers(0, n, m).astype(np.int32))
         self.caps = []
+        self.tiles = []
 
     def workers(self, variant="async", delta=0):
         return 608
 
     def set_worker_cap(self, cap):
         self.caps.append(cap)
+
+    def set_warp_tile(self, ipt):
+        self.tiles.append(ipt)
 
 
 def _fake_run(times, calls, fail=()):
@@ -39,9 +43,12 @@ def _no_device(monkeypatch):
     monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
 
 
-def test_norm_fills_the_read_path():
-    assert A._norm(("async", 0)) == ("async", 0, "refresh")
-    assert A._norm(("async", "0", "own_l1")) == ("async", 0, "own_l1")
+def test_norm_fills_the_read_path_and_warp_tile():
+    assert A._norm(("async", 0)) == ("async", 0, "refresh", 7)
+    assert A._norm(("async", "0", "own_l1")) == ("async", 0, "own_l1", 7)
+    assert A._norm(("async", 0, "warp+cached", 11)) == ("async", 0, "warp+cached", 11)
+    with pytest.raises(ValueError):
+        A._norm(("async", 0, "warp", 9))  # no such warp tile is built
 
 
 def test_fingerprint_depends_on_the_graph():
@@ -55,7 +62,7 @@ def test_tune_picks_the_fastest_over_candidates_and_worker_fractions(monkeypatch
     plan = FakePlan()
     cands = [("async", 0), ("delayed", 32), ("async", 0, "own_l1")]
     times = {}
-    for i, (v, d, r) in enumerate(A._norm(c) for c in cands):
+    for i, (v, d, r, _) in enumerate(A._norm(c) for c in cands):
         times[(v, d, r, 0)] = 5.0 + i
         times[(v, d, r, 304)] = 3.5 if (v, d) == ("delayed", 32) else 9.0
     calls = []
@@ -107,3 +114,20 @@ def test_locality_cutoff_drops_the_buffered_candidates(monkeypatch):
     ch = A.tune(plan, "pagerank", candidates=[("async", 0), ("delayed", 32)], worker_fractions=[1.0],
                 cache=None, locality_cutoff=0.9)
     assert ch["variant"] == "delayed"  # below the cutoff every candidate is timed
+
+
+def test_warp_candidates_set_their_tile_and_the_choice_keeps_it(monkeypatch):
+    plan = FakePlan()
+    cands = [("async", 0, "warp+cached", 5), ("async", 0, "warp+cached", 11), ("sync", 0)]
+    times = {("async", 0, "warp+cached", 0): 2.0, ("sync", 0, "refresh", 0): 4.0}
+    seen = []
+
+    def run(plan_, algo, variant, delta, reads, kw):
+        seen.append((reads, plan_.tiles[-1] if reads.startswith("warp") else None))
+        ms = 1.0 if (reads, plan_.tiles[-1]) == ("warp+cached", 11) else times[(variant, delta, reads, 0)]
+        return ms, {"iters": 3}
+
+    monkeypatch.setattr(A, "_run", run)
+    ch = A.tune(plan, "pagerank", candidates=cands, worker_fractions=[1.0], trials=1, cache=None)
+    assert ("warp+cached", 5) in seen and ("warp+cached", 11) in seen
+    assert (ch["reads"], ch["warp_tile"]) == ("warp+cached", 11) and plan.tiles[-1] == 11

@@ -328,11 +328,26 @@ def test_autotune_cache_and_locality_cutoff(dag, tmp_path):
     plan = _plan(dag, I.banded(1 << 16, 15, 16, 1, seed=6))  # band 16: local even at thousands of blocks
     c1 = autotune.tune(plan, "pagerank", worker_fractions=[1.0], trials=1, cache=cache, tol=1e-6)
     want = {autotune._norm(c) for c in autotune.SINGLE_CANDIDATES}
-    assert {(r["variant"], r["delta"], r["reads"]) for r in c1["candidates"]} == want
-    assert (c1["variant"], c1["delta"], c1["reads"]) in want
+    assert {(r["variant"], r["delta"], r["reads"], r["warp_tile"]) for r in c1["candidates"]} == want
+    assert (c1["variant"], c1["delta"], c1["reads"], c1["warp_tile"]) in want
     c2 = autotune.tune(plan, "pagerank", worker_fractions=[1.0], trials=1, cache=cache, tol=1e-6)
     assert c2 == c1  # served from the cache
     c3 = autotune.tune(plan, "pagerank", worker_fractions=[1.0], trials=1, cache=None, tol=1e-6,
                        locality_cutoff=0.5)
     assert c3["locality"]["diag_share"] > 0.5
     assert all(r["variant"] != "delayed" for r in c3["candidates"])
+
+
+def test_last_status_copied_on_the_device(dag):
+    # dag_plan_last_status: the last solve's (err, converged, sweeps) into a device array, no host wait
+    g = I.rmat(12, 16, seed=4)
+    plan = _plan(dag, g)
+    st_dev = torch.full((2, 3), -7, dtype=torch.int32, device="cuda")
+    _, st = dag.pagerank(plan, 0.85, 1e-6, "async", 0)
+    dag.pagerank(plan, 0.85, 1e-6, "async", 0, stats=False)
+    plan.last_status_to(st_dev[0])
+    dag.pagerank(plan, 0.85, 1e-6, "sync", 0, max_iters=2, stats=False)  # stops before the rule is met
+    plan.last_status_to(st_dev[1])
+    got = st_dev.cpu().numpy()
+    assert got[0, 0] == 0 and got[0, 1] == 1 and got[0, 2] > 2
+    assert got[1, 0] == 0 and got[1, 1] == 0 and got[1, 2] == 2
