@@ -492,7 +492,9 @@ VARIANT_ROWS = [("sync", "sync", 0, "refresh"), ("async", "async", 0, "refresh")
                 ("async_own_l1", "async", 0, "own_l1"), ("sync_frontier", "sync", 0, "frontier"),
                 ("async_frontier", "async", 0, "frontier"), ("async_own_l1_frontier", "async", 0, "own_l1+frontier"),
                 ("delayed32", "delayed", 32, "refresh"), ("delayed256", "delayed", 256, "refresh"),
-                ("delayed4096", "delayed", 4096, "refresh"), ("delayed4096_local", "delayed", 4096, "local")]
+                ("delayed4096", "delayed", 4096, "refresh"), ("delayed4096_local", "delayed", 4096, "local"),
+                ("warp_sync", "sync", 0, "warp"), ("warp_async_cached", "async", 0, "warp+cached"),
+                ("warp_delayed16", "delayed", 16, "warp"), ("warp_delayed256_cached", "delayed", 256, "warp+cached")]
 
 
 def run_detail(g, w, srcs, plan, w_d, dag, torch, args):
