@@ -636,7 +636,7 @@ def run_batched(dag, torch):
     plan = dag.Plan.from_graph(g, "cuda")
     sets = I.ppr_seed_sets(g.n, 256, seed=4)
     V = torch.from_numpy(I.teleport_matrix(g.n, sets)).cuda()
-    w = torch.from_numpy(I.weights_u32(g, 4).view(np.int32)).cuda()
+    w = torch.from_numpy(I.weights_u32(g, 4).astype(np.uint8)).cuda()  # one-byte weights (values in [1, 255])
     srcs = torch.from_numpy(I.sources(g, 64, seed=4).view(np.int32)).cuda()
     tuned_ppr = autotune.tune(plan, "ppr_batched", cache=None, trials=1, V=V)
     R, it, st = dag.ppr_batched(plan, V, 0.85, 1e-6, tuned_ppr["variant"], tuned_ppr["delta"])
@@ -649,10 +649,23 @@ def run_batched(dag, torch):
     for c in range(8):
         _, s1 = dag.pagerank(plan, 0.85, 1e-6, "async", 0, teleport=Vc[c].contiguous())
         one_ppr.append(s1["ms"])
-        _, s2 = dag.sssp(plan, int(srcs[c]), w, "async", 0)
+        _, s2 = dag.sssp(plan, int(srcs[c]), w, "async", 0, reads="own_l1+frontier")
         one_bf.append(s2["ms"])
-    m = g.m
+    m, n = g.m, g.n
+    peak, peak_kind = _peaks()
+
+    def roof(nbytes, ms):
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        return {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                "frac": round(gbs / peak, 4), "bytes_per_launch": int(nbytes)}
+
+    # algorithmic bytes: the CSR once per sweep, per active column its own rows (12n PPR: teleport, old,
+    # new; 8n SSSP: old, new) and its gathers (4m: X[n][B] is far larger than L2); weights once per sweep
+    ppr_bytes = st["sweeps"] * (4 * (n + 1) + 4 * m) + st["column_sweeps"] * (12 * n + 4 * m)
+    bf_bytes = st2["sweeps"] * (4 * (n + 1) + 5 * m) + st2["column_sweeps"] * (8 * n + 4 * m)
     return {"graph": {"n": g.n, "m": m, "seed": 4},
+            "roofline": {"ppr": roof(ppr_bytes, st["ms"]), "sssp": roof(bf_bytes, st2["ms"])},
+            "cuda_graph": {"ppr": st["graph"], "sssp": st2["graph"]},
             "ppr": {"B": 256, "choice": {k: tuned_ppr[k] for k in ("variant", "delta", "workers")},
                     "ms": round(st["ms"], 3), "sweeps": st["sweeps"], "column_sweeps": st["column_sweeps"],
                     "gteps_solve_rate": round(256 * m / (st["ms"] * 1e-3) / 1e9, 2),

@@ -227,6 +227,7 @@ typedef struct {
     int32_t workers;
     int32_t delta;
     int64_t column_sweeps;   /* sum over columns of the sweeps each ran */
+    int32_t graph;           /* 1: the launch was a replay of the plan's CUDA graph of its shape, 0: direct */
 } dag_batch_stats;
 
 /*
@@ -252,8 +253,15 @@ int dag_sssp_batched(dag_plan* plan, dag_variant variant, int32_t delta, int32_t
                      const uint32_t* d_src, const uint32_t* d_w, uint32_t* d_D, int32_t* d_iters,
                      dag_batch_stats* h_stats, void* stream);
 
+/* dag_sssp_batched with one-byte weights (d_w8: uint8 per in-edge, device, [m]); same results as
+ * dag_sssp_batched with the same weights, a quarter of the weight stream per sweep. */
+int dag_sssp_batched_u8(dag_plan* plan, dag_variant variant, int32_t delta, int32_t max_iters, int32_t B,
+                        const uint32_t* d_src, const uint8_t* d_w8, uint32_t* d_D, int32_t* d_iters,
+                        dag_batch_stats* h_stats, void* stream);
+
 /*
- * Batched launches through CUDA graphs (on != 0; off when a plan is created).
+ * Batched launches through CUDA graphs (on != 0, the default for a new plan;
+ * 0 launches directly).
  * dag_ppr_batched and dag_sssp_batched then capture each launch shape (kernel,
  * grid, block, shared memory, control block) once into a graph owned by the
  * plan: the reset of the per-column control block and the one cooperative

@@ -327,9 +327,11 @@ extern "C" int dag_ppr_batched(dag_plan* plan, float d, double tol, dag_variant 
                           (cudaStream_t)stream);
 }
 
-extern "C" int dag_sssp_batched(dag_plan* plan, dag_variant variant, int32_t delta, int32_t max_iters, int32_t B,
-                                const uint32_t* d_src, const uint32_t* d_w, uint32_t* d_D, int32_t* d_iters,
-                                dag_batch_stats* h_stats, void* stream)
+namespace dag {
+namespace {
+int sssp_batched_impl(dag_plan* plan, int variant, int delta, int max_iters, int B, const uint32_t* d_src,
+                      const void* d_w, int wbytes, uint32_t* d_D, int32_t* d_iters, dag_batch_stats* h_stats,
+                      cudaStream_t s)
 {
     if (!plan || !d_src || !d_D || !d_iters || (plan->m > 0 && !d_w))
         return set_error(DAG_ERR_INVALID, "null argument");
@@ -338,6 +340,24 @@ extern "C" int dag_sssp_batched(dag_plan* plan, dag_variant variant, int32_t del
     if (rc) return rc;
     int var = variant;
     if (var == DAG_DELAYED && delta == 0) var = DAG_ASYNC;
-    return launch_batched(plan, 1, var, delta, max_iters, B, 0.0f, 0.0, d_src, d_w, d_D, d_iters, h_stats,
-                          (cudaStream_t)stream);
+    return launch_batched(plan, wbytes == 1 ? 2 : 1, var, delta, max_iters, B, 0.0f, 0.0, d_src,
+                          (const uint32_t*)d_w, d_D, d_iters, h_stats, s);
+}
+}  // namespace
+}  // namespace dag
+
+extern "C" int dag_sssp_batched(dag_plan* plan, dag_variant variant, int32_t delta, int32_t max_iters, int32_t B,
+                                const uint32_t* d_src, const uint32_t* d_w, uint32_t* d_D, int32_t* d_iters,
+                                dag_batch_stats* h_stats, void* stream)
+{
+    return sssp_batched_impl(plan, variant, delta, max_iters, B, d_src, d_w, 4, d_D, d_iters, h_stats,
+                             (cudaStream_t)stream);
+}
+
+extern "C" int dag_sssp_batched_u8(dag_plan* plan, dag_variant variant, int32_t delta, int32_t max_iters, int32_t B,
+                                   const uint32_t* d_src, const uint8_t* d_w8, uint32_t* d_D, int32_t* d_iters,
+                                   dag_batch_stats* h_stats, void* stream)
+{
+    return sssp_batched_impl(plan, variant, delta, max_iters, B, d_src, d_w8, 1, d_D, d_iters, h_stats,
+                             (cudaStream_t)stream);
 }

@@ -14,6 +14,7 @@
 #include <climits>
 #include <map>
 #include <mutex>
+#include <string>
 #include <tuple>
 #include <vector>
 
@@ -28,6 +29,7 @@ struct BatchParams {
     const int* rowptr;
     const int* colidx;
     const uint32_t* w;
+    const uint8_t* w8;     // one-byte weights (BF8), else nullptr
     const float* degf;
     const float* V;        // PPR teleports [n][B]
     const uint32_t* src;   // BF sources [B]
@@ -73,7 +75,7 @@ __device__ __forceinline__ uint32_t b_relax(uint32_t du, uint32_t w)
     return (s < du || s == INF) ? INF - 1u : s;
 }
 
-template <bool BF, int VAR>
+template <bool BF, int VAR, bool W8 = false>
 __global__ void batched_kernel(const BatchParams p)
 {
     constexpr bool SYNC = VAR == DAG_SYNC;
@@ -148,7 +150,8 @@ __global__ void batched_kernel(const BatchParams p)
             if (threadIdx.x == 0) s_end[NA] = INT_MAX;
             for (int j = threadIdx.x; j < NB; j += blockDim.x) {
                 s_col[j] = ld_stream_i32(p.colidx + b0 + j);
-                if constexpr (BF) s_w[j] = ld_stream_u32(p.w + b0 + j);
+                if constexpr (BF && W8) s_w[j] = (uint32_t)p.w8[b0 + j];
+                else if constexpr (BF) s_w[j] = ld_stream_u32(p.w + b0 + j);
             }
             __syncthreads();
             if (!warp_active) continue;
@@ -299,11 +302,14 @@ __global__ void batched_kernel(const BatchParams p)
 
 using BKernel = void (*)(const BatchParams);
 
+// is_bf: 0 PPR, 1 Bellman-Ford with four-byte weights, 2 with one-byte weights
 static BKernel bkernel_for(int is_bf, int variant)
 {
-    static const BKernel table[2][3] = {
+    static const BKernel table[3][3] = {
         {batched_kernel<false, DAG_SYNC>, batched_kernel<false, DAG_ASYNC>, batched_kernel<false, DAG_DELAYED>},
         {batched_kernel<true, DAG_SYNC>, batched_kernel<true, DAG_ASYNC>, batched_kernel<true, DAG_DELAYED>},
+        {batched_kernel<true, DAG_SYNC, true>, batched_kernel<true, DAG_ASYNC, true>,
+         batched_kernel<true, DAG_DELAYED, true>},
     };
     return table[is_bf][variant];
 }
@@ -326,7 +332,7 @@ struct BatchGraph {
 };
 using ShapeKey = std::tuple<const void*, int, int, size_t, size_t, const void*>;
 struct PlanGraphs {
-    bool on = false;
+    bool on = true;  // graphs are the default for every plan
     std::map<ShapeKey, BatchGraph> shapes;
 };
 static std::mutex g_graph_mu;
@@ -336,7 +342,7 @@ static bool batched_graph_on(const dag_plan* plan)
 {
     std::lock_guard<std::mutex> lk(g_graph_mu);
     auto it = g_graphs.find(plan);
-    return it != g_graphs.end() && it->second.on;
+    return it == g_graphs.end() || it->second.on;  // on unless the plan turned it off
 }
 
 // Records the reset and the kernel launch into bg (nothing runs); on any
@@ -353,12 +359,21 @@ static void capture_shape(BatchGraph& bg, const void* k, int nb, int threads, si
     cudaGraph_t g = nullptr;
     cudaGraphExec_t ex = nullptr;
     cudaGraphNode_t kn = nullptr;
-    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    const cudaError_t e0 = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e0 != cudaSuccess) set_error(DAG_OK, std::string("batched graph: begin capture: ") + cudaGetErrorString(e0));
+    if (e0 == cudaSuccess) {
         const cudaError_t e1 = cudaMemsetAsync(bsync, 0, cbytes, cs);
         const cudaError_t e2 = cudaLaunchCooperativeKernel(k, dim3(nb), dim3(threads), args, dyn, cs);
         const cudaError_t e3 = cudaStreamEndCapture(cs, &g);  // ends capture mode whatever happened
-        if (e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess && g &&
-            cudaGraphInstantiate(&ex, g, 0) == cudaSuccess) {
+        cudaError_t e4 = cudaErrorUnknown;
+        if (e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess && g) e4 = cudaGraphInstantiate(&ex, g, 0);
+        const cudaError_t bad = e1 != cudaSuccess ? e1 : e2 != cudaSuccess ? e2 : e3 != cudaSuccess ? e3 : e4;
+        if (bad != cudaSuccess)  // recorded for dag_last_error_message; the call itself launches directly
+            set_error(DAG_OK, std::string("batched graph: capture (memset, launch, end, instantiate ") +
+                                  std::to_string((int)e1) + " " + std::to_string((int)e2) + " " +
+                                  std::to_string((int)e3) + " " + std::to_string((int)e4) + "): " +
+                                  cudaGetErrorString(bad));
+        if (e4 == cudaSuccess) {
             size_t cnt = 0;
             if (cudaGraphGetNodes(g, nullptr, &cnt) == cudaSuccess && cnt > 0) {
                 std::vector<cudaGraphNode_t> nodes(cnt);
@@ -373,6 +388,19 @@ static void capture_shape(BatchGraph& bg, const void* k, int nb, int threads, si
         }
     }
     cudaStreamDestroy(cs);
+    if (!kn && ex) {
+        size_t cnt = 0;
+        cudaGraphGetNodes(g, nullptr, &cnt);
+        std::string types;
+        std::vector<cudaGraphNode_t> nodes(cnt);
+        if (cnt) cudaGraphGetNodes(g, nodes.data(), &cnt);
+        for (size_t i = 0; i < cnt; ++i) {
+            cudaGraphNodeType t;
+            cudaGraphNodeGetType(nodes[i], &t);
+            types += " " + std::to_string((int)t);
+        }
+        set_error(DAG_OK, "batched graph: no kernel node among " + std::to_string(cnt) + " nodes:" + types);
+    }
     if (!kn) {
         if (ex) cudaGraphExecDestroy(ex);
         if (g) cudaGraphDestroy(g);
@@ -388,8 +416,9 @@ static void capture_shape(BatchGraph& bg, const void* k, int nb, int threads, si
 // One batched launch on stream s through the plan's graph of this shape
 // (captured on first use), or directly when the shape cannot be captured.
 static cudaError_t graph_launch(dag_plan* plan, const void* k, int nb, int threads, size_t dyn, size_t cbytes,
-                                void** args, cudaStream_t s)
+                                void** args, cudaStream_t s, bool* replayed)
 {
+    *replayed = false;
     std::lock_guard<std::mutex> lk(g_graph_mu);
     BatchGraph& bg = g_graphs[plan].shapes[ShapeKey(k, nb, threads, dyn, cbytes, plan->bsync)];
     if (!bg.exec && !bg.failed) capture_shape(bg, k, nb, threads, dyn, plan->bsync, cbytes, args);
@@ -403,9 +432,13 @@ static cudaError_t graph_launch(dag_plan* plan, const void* k, int nb, int threa
         kp.extra = nullptr;
         // the replay must run with this call's arguments: if they cannot be set, or the graph
         // cannot be launched, nothing was enqueued, and the shape launches directly from now on
-        if (cudaGraphExecKernelNodeSetParams(bg.exec, bg.knode, &kp) == cudaSuccess &&
-            cudaGraphLaunch(bg.exec, s) == cudaSuccess)
+        const cudaError_t ep = cudaGraphExecKernelNodeSetParams(bg.exec, bg.knode, &kp);
+        const cudaError_t el = ep == cudaSuccess ? cudaGraphLaunch(bg.exec, s) : ep;
+        if (el == cudaSuccess) {
+            *replayed = true;
             return cudaSuccess;
+        }
+        set_error(DAG_OK, std::string("batched graph: replay: ") + cudaGetErrorString(el));
         cudaGetLastError();
         bg.failed = true;
     }
@@ -495,7 +528,8 @@ int launch_batched(dag_plan* plan, int is_bf, int variant, int delta, int max_it
     p.nblocks = nb;
     p.rowptr = plan->rowptr;
     p.colidx = plan->colidx;
-    p.w = w;
+    p.w = is_bf == 1 ? w : nullptr;
+    p.w8 = is_bf == 2 ? (const uint8_t*)w : nullptr;
     p.degf = plan->degf;
     p.V = is_bf ? nullptr : (const float*)V_or_src;
     p.src = is_bf ? (const uint32_t*)V_or_src : nullptr;
@@ -525,7 +559,8 @@ int launch_batched(dag_plan* plan, int is_bf, int variant, int delta, int max_it
         cudaEventRecord(e0, s);
     }
     void* args[] = {(void*)&p};
-    cudaError_t le = use_graph ? graph_launch(plan, (const void*)k, nb, threads, dyn, cbytes, args, s)
+    bool replayed = false;
+    cudaError_t le = use_graph ? graph_launch(plan, (const void*)k, nb, threads, dyn, cbytes, args, s, &replayed)
                                : cudaLaunchCooperativeKernel((const void*)k, dim3(nb), dim3(threads), args, dyn, s);
     if (le != cudaSuccess) {
         if (e0) cudaEventDestroy(e0);
@@ -554,6 +589,7 @@ int launch_batched(dag_plan* plan, int is_bf, int variant, int delta, int max_it
     st->workers = nb;
     st->delta = dl;
     st->column_sweeps = colsw;
+    st->graph = replayed ? 1 : 0;
     if (rc2 == DAG_ERR_BARRIER_TIMEOUT) set_error(rc2, "grid barrier wait ran out of time");
     return rc2;
 }

@@ -33,7 +33,7 @@ EXPORTS = (
     "dag_normalize_weights", "dag_pagerank_adjoint", "dag_strerror", "dag_last_error_message",
     "dag_debug_skip_barrier_once", "dag_debug_stall_staging_once", "dag_tile_items", "dag_pagerank_noalloc", "dag_gather_f32", "dag_plan_set_worker_cap",
     "dag_sssp_u8", "dag_probe_gather", "dag_access_matrix", "dag_plan_set_batched_graph", "dag_warp_tile_items",
-    "dag_plan_set_warp_tile", "dag_plan_last_status",
+    "dag_plan_set_warp_tile", "dag_plan_last_status", "dag_sssp_batched_u8",
 )
 
 
@@ -56,7 +56,8 @@ class _Stats(ctypes.Structure):
 
 class _BStats(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_int32), ("err", ctypes.c_int32), ("ms", ctypes.c_float),
-                ("workers", ctypes.c_int32), ("delta", ctypes.c_int32), ("column_sweeps", ctypes.c_int64)]
+                ("workers", ctypes.c_int32), ("delta", ctypes.c_int32), ("column_sweeps", ctypes.c_int64),
+                ("graph", ctypes.c_int32)]
 
 
 _lib = None
@@ -85,6 +86,8 @@ def lib():
                                           ctypes.POINTER(_BStats), _vp]
             L.dag_sssp_batched.argtypes = [_vp, _i32, _i32, _i32, _i32, _vp, _vp, _vp, _vp,
                                            ctypes.POINTER(_BStats), _vp]
+            L.dag_sssp_batched_u8.argtypes = [_vp, _i32, _i32, _i32, _i32, _vp, _vp, _vp, _vp,
+                                              ctypes.POINTER(_BStats), _vp]
             L.dag_transpose.argtypes = [_vp, _vp, _vp, _vp, _vp]
             L.dag_normalize_weights.argtypes = [_vp, _vp, _vp, _vp, _vp]
             L.dag_pagerank_adjoint.argtypes = [_vp, _vp, _f32, _f64, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp,
@@ -263,7 +266,7 @@ def sssp(plan: Plan, src: int, w, variant="delayed", delta=32, max_iters=None, o
 
 def _bstats(st: _BStats) -> dict:
     return dict(sweeps=st.sweeps, err=st.err, converged=st.err == OK, ms=st.ms, workers=st.workers,
-                delta=st.delta, column_sweeps=st.column_sweeps)
+                delta=st.delta, column_sweeps=st.column_sweeps, graph=bool(st.graph))
 
 
 def ppr_batched(plan: Plan, V: torch.Tensor, d=0.85, tol=1e-6, variant="async", delta=0, max_iters=1000,
@@ -282,16 +285,19 @@ def ppr_batched(plan: Plan, V: torch.Tensor, d=0.85, tol=1e-6, variant="async", 
 
 def sssp_batched(plan: Plan, srcs: torch.Tensor, w, variant="async", delta=0, max_iters=None, out=None,
                  stream=None, stats=True):
-    """B Bellman-Ford solves; srcs int32 [B]. Returns (D int32 [n, B] holding uint32 bits, iters, stats)."""
+    """B Bellman-Ford solves; srcs int32 [B]; w: int32 view of uint32 weights (dag_sssp_batched) or uint8
+    weights (dag_sssp_batched_u8). Returns (D int32 [n, B] holding uint32 bits, iters, stats)."""
     B = srcs.numel()
     _dev(srcs, torch.int32, B, "srcs")
+    u8 = w is not None and w.dtype == torch.uint8
     if plan.m:
-        _dev(w, torch.int32, plan.m, "w")
+        _dev(w, torch.uint8 if u8 else torch.int32, plan.m, "w")
     out = out if out is not None else torch.empty((plan.n, B), dtype=torch.int32, device=srcs.device)
     iters = torch.empty(B, dtype=torch.int32, device=srcs.device)
     max_iters = plan.n + 1 if max_iters is None else max_iters
     st = _BStats()
-    rc = lib().dag_sssp_batched(plan.h, _variant(variant), delta, max_iters, B, _ptr(srcs),
+    fn = lib().dag_sssp_batched_u8 if u8 else lib().dag_sssp_batched
+    rc = fn(plan.h, _variant(variant), delta, max_iters, B, _ptr(srcs),
                                 _ptr(w) if plan.m else None, _ptr(out), _ptr(iters),
                                 ctypes.byref(st) if stats else None, _stream(stream))
     _raise(rc)

@@ -76,6 +76,7 @@ def test_null_arguments_are_refused_without_a_gpu(lib):
         "dag_sssp_u8": lambda: lib.dag_sssp_u8(N, 0, 1, 0, 10, N, N, 0, N, N),
         "dag_ppr_batched": lambda: lib.dag_ppr_batched(N, f(0.85), d(1e-6), 1, 0, 10, 4, N, N, N, N, N),
         "dag_sssp_batched": lambda: lib.dag_sssp_batched(N, 1, 0, 10, 4, N, N, N, N, N, N),
+        "dag_sssp_batched_u8": lambda: lib.dag_sssp_batched_u8(N, 1, 0, 10, 4, N, N, N, N, N, N),
         "dag_transpose": lambda: lib.dag_transpose(N, N, N, N, N),
         "dag_normalize_weights": lambda: lib.dag_normalize_weights(N, N, N, N, N),
         "dag_pagerank_adjoint": lambda: lib.dag_pagerank_adjoint(N, N, f(0.85), d(1e-6), 1, 0, 10, N, N, N, N, N,

@@ -94,3 +94,59 @@ def test_batched_single_column_and_bad_source(dag, graph):
     w = torch.from_numpy(I.weights_u32(g, 1).view(np.int32)).cuda()
     with pytest.raises(dag.DagError):
         dag.sssp_batched(plan, torch.tensor([0, g.n + 5], dtype=torch.int32, device="cuda"), w)
+
+
+def test_batched_graph_replays_equal_direct_launches_and_the_oracle(dag, graph):
+    # the batched launch is replayed from the plan's CUDA graph of its shape (the default); calls with new
+    # buffers, new teleport matrices and a new B replay with their own arguments. In the synchronous form
+    # every column's arithmetic is fixed, so replays and direct launches agree bit for bit.
+    g = graph
+    plan_g = dag.Plan.from_graph(g, "cuda")  # graphs on
+    plan_d = dag.Plan.from_graph(g, "cuda")
+    plan_d.set_batched_graph(False)
+    for B, seed in [(40, 11), (40, 12), (33, 13), (64, 14), (40, 15)]:
+        sets = I.ppr_seed_sets(g.n, B, seed=seed)
+        V = torch.from_numpy(I.teleport_matrix(g.n, sets)).cuda()
+        out = torch.full_like(V, -1.0)  # a fresh output buffer each call
+        Rg, itg, stg = dag.ppr_batched(plan_g, V, 0.85, 1e-6, "sync", 0, out=out)
+        Rd, itd, std = dag.ppr_batched(plan_d, V.clone(), 0.85, 1e-6, "sync", 0)
+        assert stg["graph"] and not std["graph"], (B, stg, std, dag.lib().dag_last_error_message().decode())
+        assert stg["converged"] and std["converged"]
+        assert torch.equal(Rg, Rd) and torch.equal(itg, itd)
+        Vh = V.cpu().numpy().astype(np.float64)
+        for c in (0, B - 1):
+            rstar = oracle.pagerank_fixed_point(g, 0.85, tele=Vh[:, c])
+            assert np.abs(Rg[:, c].cpu().numpy().astype(np.float64) - rstar).sum() <= 1e-5, (B, c)
+    # the asynchronous form too (results agree within the parity bound, not bit for bit)
+    sets = I.ppr_seed_sets(g.n, 40, seed=16)
+    V = torch.from_numpy(I.teleport_matrix(g.n, sets)).cuda()
+    Rg, _, stg = dag.ppr_batched(plan_g, V, 0.85, 1e-6, "async", 0)
+    assert stg["graph"] and stg["converged"]
+    rstar = oracle.pagerank_fixed_point(g, 0.85, tele=V[:, 7].cpu().numpy().astype(np.float64))
+    assert np.abs(Rg[:, 7].cpu().numpy().astype(np.float64) - rstar).sum() <= 1e-5
+    # Bellman-Ford replays: new sources, new B, both weight widths
+    w = I.weights_u32(g, 9)
+    for B, seed in [(33, 5), (20, 6)]:
+        srcs = torch.from_numpy(I.sources(g, B, seed=seed).view(np.int32)).cuda()
+        for wd in (torch.from_numpy(w.view(np.int32)).cuda(), torch.from_numpy(w.astype(np.uint8)).cuda()):
+            D, _, st = dag.sssp_batched(plan_g, srcs, wd, "async", 0)
+            assert st["graph"] and st["converged"]
+            D = D.cpu().numpy().view(np.uint32)
+            for c in (0, B - 1):
+                assert np.array_equal(D[:, c], oracle.dijkstra(g, w, int(srcs[c])))
+
+
+@pytest.mark.parametrize("variant,delta", [("sync", 0), ("async", 0), ("delayed", 8)])
+def test_sssp_batched_one_byte_weights(dag, graph, variant, delta):
+    g = graph
+    w = I.weights_u32(g, 9)
+    srcs = torch.from_numpy(I.sources(g, 40, seed=8).view(np.int32)).cuda()
+    plan = dag.Plan.from_graph(g, "cuda")
+    D8, it8, st8 = dag.sssp_batched(plan, srcs, torch.from_numpy(w.astype(np.uint8)).cuda(), variant, delta)
+    D4, it4, st4 = dag.sssp_batched(plan, srcs, torch.from_numpy(w.view(np.int32)).cuda(), variant, delta)
+    assert st8["converged"] and torch.equal(D8, D4)
+    if variant == "sync":
+        assert torch.equal(it8, it4)
+    D8 = D8.cpu().numpy().view(np.uint32)
+    for c in (0, 17, 39):
+        assert np.array_equal(D8[:, c], oracle.dijkstra(g, w, int(srcs[c])))
