@@ -202,6 +202,7 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
     double gprev = BF ? 0.0 : sh.gprev;
     LiveSum L{};
     if constexpr (LIVE_G) L = live_sum_setup<MODE>(p, T, gprev);
+    double adj_sum = gprev;  // adjoint: sum lambda as the sweep starts
     const double tol = (MODE == MODE_ADJ) ? p.tol * T : p.tol;
 
     // sync reads the previous iterate with ordinary loads; async reads the live
@@ -402,6 +403,23 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
             converged = true;
             ++it;
             break;
+        }
+        if constexpr (MODE == MODE_ADJ) {  // deflation of the slow mode along 1 (adjoint_shift)
+            if constexpr (LIVE_G) {
+                if (tid == 0) sh.gprev = live_value(sb, L);
+                __syncthreads();
+            }
+            const double sum_new = sh.gprev;
+            const float shift = adjoint_shift(p, sum_new, adj_sum);
+            uint32_t* xs = SYNC ? xout : X0;  // the next sweep's input
+            for (int v = row_lo + tid; v < row_hi; v += NT)
+                st_relaxed_b32(xs + v, __float_as_uint(__uint_as_float(ld_relaxed_b32(xs + v)) + shift));
+            adj_sum = sum_new + (double)p.n * shift;
+            if constexpr (SYNC) gprev = adj_sum;
+            if constexpr (LIVE_G) {
+                if (c == 0 && tid == 0) live_add(sb, 0, (float)((double)p.n * shift), L.S);
+            }
+            if (!grid_barrier(sb, p.nblocks, bar_target, p.timeout_ns)) return;  // every value shifted
         }
         if constexpr (FRONTIER) {
             // sparse next sweep: stamp the tiles the changed rows feed, publish, run only those

@@ -365,6 +365,29 @@ __device__ __forceinline__ float live_term(const LiveSum& L, long long G)
     return L.scale * f;
 }
 
+// Adjoint deflation. The adjoint's iteration operator B = d M^T + d g 1^T / n
+// has B 1 = d 1 (every column of M sums to 1 over a vertex's out-edges, and a
+// dangling vertex gets d (sum lambda)/n), so the error's component along 1
+// decays only at rate d per sweep. After each sweep that did not meet the
+// stopping rule every value is shifted by d / (1 - d) times the sweep's mean
+// change: for the synchronous sweep this replaces B by B + 1 w^T with
+// w^T 1 = -d, which keeps B's other eigenvalues, sends the one of 1 to 0 and
+// leaves the fixed point where it was (a Wielandt deflation of the known
+// eigenpair (d, 1)); the in-place forms use the same shift.
+__device__ __forceinline__ float adjoint_shift(const SweepParams& p, double sum_new, double sum_old)
+{
+    return (float)((double)p.d / (1.0 - (double)p.d) * (sum_new - sum_old) / (double)p.n);
+}
+
+// The live sum's value (sum lambda for the adjoint) from its stripes, read
+// by one thread once every CTA has reached a grid barrier.
+__device__ __forceinline__ double live_value(const SyncBlock* sb, const LiveSum& L)
+{
+    long long G = 0;
+    for (int k = 0; k < GSTRIPES; ++k) G += ld_relaxed_i64(&sb->stripe[k * GSTRIDE]);
+    return ldexp((double)(L.base + G), -L.S);
+}
+
 // New value of row v from its pull sum and old value (PageRank: x = r/outdeg
 // with dg = outdeg; adjoint: lambda; Bellman-Ford: dist), with the residual
 // and global-sum contributions.

@@ -284,6 +284,7 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
     if constexpr (!BF) T = (MODE == MODE_ADJ || p.base) ? sh.T : 1.0;  // a uniform teleport sums to 1 exactly
     LiveSum L{};
     if constexpr (LIVE_G) L = live_sum_setup<MODE>(p, T, sh.gprev);
+    double adj_sum = sh.gprev;  // adjoint: sum lambda as the sweep starts
     const double tol = (MODE == MODE_ADJ) ? p.tol * T : p.tol;
 
     const int own_lo = row_lo, own_n = p.own_l1 ? row_hi - row_lo : 0;
@@ -527,6 +528,17 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
             converged = true;
             ++it;
             break;
+        }
+        if constexpr (MODE == MODE_ADJ) {  // deflation of the slow mode along 1 (adjoint_shift)
+            if (tid == 0) sh.gprev = live_value(sb, L);
+            __syncthreads();
+            const double sum_new = sh.gprev;
+            const float shift = adjoint_shift(p, sum_new, adj_sum);
+            for (int v = row_lo + tid; v < row_hi; v += NT)
+                st_relaxed_b32(X + v, __float_as_uint(__uint_as_float(ld_relaxed_b32(X + v)) + shift));
+            adj_sum = sum_new + (double)p.n * shift;
+            if (c == 0 && tid == 0) live_add(sb, 0, (float)((double)p.n * shift), L.S);
+            if (!grid_barrier(sb, p.nblocks, bar_target, p.timeout_ns)) return;  // every value shifted
         }
         if constexpr (FRONTIER) {
             // sparse next sweep: stamp the tiles the changed rows feed, publish them in one list, run that

@@ -131,3 +131,22 @@ def test_transpose_and_normalize_match_definitions(dag):
     assert np.max(np.abs(val.cpu().numpy() - v64)) <= 1e-6
     has = s64 > 0
     assert np.max(np.abs(s.cpu().numpy()[has] - s64[has]) / s64[has]) <= 1e-5
+
+
+@pytest.mark.parametrize("variant,delta", [("sync", 0), ("async", 0), ("delayed", 64)])
+def test_adjoint_deflation_cuts_the_slow_mode(dag, scaled_case, variant, delta):
+    # The adjoint's slow error mode along 1 (B 1 = d 1) is deflated after every sweep, so the
+    # adjoint solve needs far fewer sweeps than the plain Jacobi adjoint at the same tolerance
+    # (the oracle, which does not deflate), and its gradients stay within the dense bound.
+    g, w, t, c, gw_ref, gt_ref = scaled_case
+    plan = dag.Plan.from_graph(g, "cuda")
+    model = dag.WeightedPageRank(plan, tol=1e-6, variant=variant, delta=delta)
+    r, val, s, st = model.forward(torch.from_numpy(w).cuda(), torch.from_numpy(t.astype(np.float32)).cuda())
+    gw, gt, _, st2 = model.backward(val, s, r, torch.from_numpy(c.astype(np.float32)).cuda())
+    assert st2["converged"]
+    val64, _ = oracle.normalize(g, w.astype(np.float64))
+    _, jacobi_sweeps = oracle.pagerank_adjoint(g, val64, c, 0.85, tol=1e-6)
+    assert st2["iters"] <= jacobi_sweeps // 2, (st2["iters"], jacobi_sweeps)
+    assert st2["iters"] <= 2 * st["iters"]
+    assert _rel(gw.cpu().numpy(), gw_ref) <= 1e-4
+    assert _rel(gt.cpu().numpy(), gt_ref) <= 1e-4
