@@ -707,6 +707,95 @@ def run_adjoint(g, plan, dag, torch):
     return out
 
 
+def run_gpu_rowshard(args):
+    """--shard rows: the same step (1 PageRank + 8 Bellman-Ford, synchronous) with the rows of one
+    graph split over the ranks (rowshard.py): every sweep each rank computes its Sec. III-A row
+    range on its GPU, then an all-gather of the ranges and an all-reduce of the FP64 sums. Total
+    work is fixed as ranks are added ("scaling": "strong")."""
+    import torch
+
+    from paper_2110_01409_gb300 import build as B
+    from paper_2110_01409_gb300 import dag
+    from paper_2110_01409_gb300 import rowshard as RS
+
+    rank, world, local = _dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    g, w, srcs, gen_s = build_inputs()
+    n, m = g.n, g.m
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    plan = dag.Plan(torch.from_numpy(g.rowptr).to(dev), torch.from_numpy(g.colidx).to(dev))
+    w8 = torch.from_numpy(w.astype(np.uint8)).to(dev)
+
+    def step():
+        r, it_pr, ok = RS.pagerank_row_sharded(dag, plan, rank, world)
+        its = [it_pr]
+        for s in srcs:
+            _, it, ok2 = RS.sssp_row_sharded(dag, plan, int(s), w8, rank, world)
+            ok = ok and ok2
+            its.append(it)
+        return its, ok
+
+    for _ in range(args.warmup):
+        its, ok = step()
+        assert ok, its
+    K = args.steps
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(local, args.clocks_csv)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0.record(stream)
+    sweeps = []
+    for _ in range(K):
+        its, ok = step()
+        assert ok, its
+        sweeps.append(its)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms_local = t0.elapsed_time(t1)
+    solves = 1 + N_SOURCES
+    ms_total, value = replica_aggregate(ms_local, 1, solves * m * K, dev)
+    if world > 1:  # the whole job's time is the slowest rank's; every rank solved the same problems together
+        tt = torch.tensor([ms_local], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_total = float(tt.item())
+        value = solves * m * K / (ms_total * 1e-3) / 1e9
+    pr_sweeps = statistics.mean(s[0] for s in sweeps)
+    bf_sweeps = statistics.mean(x for s in sweeps for x in s[1:])
+    step_bytes = algorithmic_bytes(n, m, "pr") * pr_sweeps + algorithmic_bytes(n, m, "bf8") * bf_sweeps * N_SOURCES
+    per_gpu = step_bytes * K / (ms_total * 1e-3) / 1e9 / world
+    peak, peak_kind = _peaks()
+    out = {"metric": METRIC, "value": round(value, 3), "unit": "GTEPS", "n_gpus": world, "steps": K,
+           "warmup": args.warmup, "ms_per_step": round(ms_total / K, 3), "higher_is_better": True,
+           "scaling": "strong", "vs_baseline": None, "dtype": "f32/u32",
+           "data": "synthetic (seeded RMAT stand-in for the GAP Kron graph)",
+           "config": {"workload": f"rmat{SCALE}: pagerank + sssp x{N_SOURCES}, synchronous, rows split over "
+                                  f"{world} GPU(s) (Sec. III-A blocks at GPU granularity)",
+                      "n": n, "m": m, "parallelism": f"rows x{world}", "sweeps": {"pagerank": pr_sweeps,
+                                                                                  "sssp": bf_sweeps},
+                      "l2": "inputs larger than L2 (CSR + one-byte weights 0.34 GB)", "graph_gen_s": round(gen_s, 2)},
+           "roofline": {"bound": "hbm", "kernel": "sweep_warp_kernel<*,SYNC> (row range)", "achieved": round(per_gpu, 1),
+                        "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(per_gpu / peak, 4),
+                        "per": "GPU", "traffic": None},
+           # per step: PageRank's state conversions, each sweep's row-range kernel and its sums copy
+           "clocks": clk, "gpu_launches": int(K * (2 + 2 * pr_sweeps + 2 * bf_sweeps * N_SOURCES)), "e2e": None}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -719,11 +808,16 @@ def main():
                     help="keep the nvidia-smi clock samples of the timed region in this file (rank-suffixed)")
     ap.add_argument("--quick", dest="extras", action="store_false",
                     help="skip the variant table, the adjoint and the batched measurements")
+    ap.add_argument("--shard", default="replicas", choices=["replicas", "rows"],
+                    help="with several GPUs: independent replicas of the step (default) or one step with the rows "
+                         "of the graph split over the GPUs")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.shard == "rows":
+        run_gpu_rowshard(args)
     else:
         run_gpu(args)
 

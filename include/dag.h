@@ -373,6 +373,44 @@ int dag_access_matrix(dag_plan* plan, int32_t workers, uint64_t* d_counts, void*
  */
 int dag_plan_last_status(const dag_plan* plan, int32_t* d_status, void* stream);
 
+/*
+ * Row sharding across GPUs (one process per GPU, every GPU holding the whole
+ * graph in its own plan): the static partition of Sec. III-A at GPU
+ * granularity (dag_partition with one block per GPU) gives each GPU a row
+ * range; a synchronous sweep (Sec. I) is one dag_*_sweep_rows call per GPU
+ * on the whole previous iterate, followed by an exchange of the new row
+ * ranges (an all-gather) and of the two FP64 sums (an all-reduce) between
+ * the GPUs. No counterpart in the paper beyond its synchronous sweep.
+ *
+ * PageRank keeps the state x of the sweeps: x_v = r_v / outdeg(v) for a
+ * vertex with out-edges, r_v for one without. dag_rank_to_state converts r
+ * into x (d_r, d_x device float [n]) and, when d_linked_mass (device double)
+ * is given, writes the mass on vertices with out-edges N = sum r_v there;
+ * dag_state_to_rank converts back. Both enqueue on `stream`, no wait.
+ */
+int dag_rank_to_state(const dag_plan* plan, const float* d_r, float* d_x, double* d_linked_mass, void* stream);
+int dag_state_to_rank(const dag_plan* plan, const float* d_x, float* d_r, void* stream);
+/*
+ * One synchronous PageRank sweep (the row update of dag_pagerank) of rows
+ * [row_lo, row_hi) from the whole previous iterate d_x_in (state form, device
+ * float [n]): d_x_out[row_lo .. row_hi) receive the new states (the rest of
+ * d_x_out is not touched). teleport_total = sum of d_teleport (1 when NULL,
+ * uniform); linked_mass = N of d_x_in's iterate (the dangling mass is
+ * teleport_total - linked_mass). d_sums (device double [2]) receives the
+ * range's sum |r' - r| and its N of the new iterate. No wait; the sweep's
+ * grid barrier is bounded as in every solve.
+ */
+int dag_pagerank_sweep_rows(dag_plan* plan, float d, int32_t row_lo, int32_t row_hi, const float* d_teleport,
+                            double teleport_total, double linked_mass, const float* d_x_in, float* d_x_out,
+                            double* d_sums, void* stream);
+/*
+ * One synchronous Bellman-Ford sweep of rows [row_lo, row_hi) with one-byte
+ * weights: d_dist_out[v] = min(d_dist_in[v], min over in-edges of
+ * d_dist_in[u] + w) for v in the range; d_sums[0] = rows lowered (FP64).
+ */
+int dag_sssp_sweep_rows(dag_plan* plan, int32_t row_lo, int32_t row_hi, const uint8_t* d_w8,
+                        const uint32_t* d_dist_in, uint32_t* d_dist_out, double* d_sums, void* stream);
+
 /* Items (rows + in-edges) per merge-path tile of the sweeps, the unit the
  * frontier runs or skips; fixed when the library is compiled. */
 int32_t dag_tile_items(void);

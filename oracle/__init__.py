@@ -58,7 +58,7 @@ def _load():
             for f in ("orc_pagerank_sync", "orc_pagerank_delayed", "orc_pagerank_delayed_view", "orc_sssp_sync",
                       "orc_sssp_delayed", "orc_sssp_delayed_view",
                       "orc_dijkstra", "orc_pagerank_adjoint", "orc_pagerank_threads", "orc_sssp_threads",
-                      "orc_pagerank_sync_par"):
+                      "orc_pagerank_sync_par", "orc_pagerank_sweep_rows"):
                 getattr(_lib, f).restype = ctypes.c_int
     return _lib
 
@@ -140,6 +140,31 @@ def pagerank_fixed_point(g, d=0.85, tele=None, val=None, tol=1e-13, max_iters=10
     if not ok:
         raise RuntimeError("fixed point did not converge")
     return r
+
+
+def pagerank_sweep_rows(g, lo, hi, r_in, r_out, d=0.85, tele=None, N=None):
+    """One synchronous sweep of rows [lo, hi) into r_out (fp64); N: mass on vertices with out-edges
+    of r_in (computed here when not given). Returns (residual over the range, N over the range)."""
+    tele = _f64(tele)
+    T = 1.0 if tele is None else float(tele.sum())
+    if N is None:
+        N = float(r_in[out_degree(g) > 0].sum())
+    sums = np.zeros(2)
+    rc = _load().orc_pagerank_sweep_rows(ctypes.c_int32(g.n), _p(_i32(g.rowptr)), _p(_i32(g.colidx)), _p(None),
+                                         ctypes.c_double(d), _p(tele), ctypes.c_double(T), ctypes.c_double(N),
+                                         ctypes.c_int32(lo), ctypes.c_int32(hi), _p(r_in), _p(r_out), _p(sums))
+    if rc != 0:
+        raise RuntimeError("oracle row sweep failed")
+    return float(sums[0]), float(sums[1])
+
+
+def sssp_sweep_rows(g, w, lo, hi, d_in, d_out) -> int:
+    """One synchronous Bellman-Ford sweep of rows [lo, hi) into d_out (uint32); returns rows lowered."""
+    lib = _load()
+    lib.orc_sssp_sweep_rows.restype = ctypes.c_int64
+    return int(lib.orc_sssp_sweep_rows(ctypes.c_int32(g.n), _p(_i32(g.rowptr)), _p(_i32(g.colidx)),
+                                       _p(np.ascontiguousarray(w, dtype=np.uint32)), ctypes.c_int32(lo),
+                                       ctypes.c_int32(hi), _p(d_in), _p(d_out)))
 
 
 def sssp(g, w, src, variant=SYNC, P=1, delta=0, max_iters=None, local_read=False):

@@ -217,6 +217,34 @@ int orc_pagerank_sync_par(int32_t n, const int32_t* rowptr, const int32_t* colid
     return rc;
 }
 
+/*
+ * One synchronous PageRank sweep of rows [lo, hi) only (the rows one GPU owns
+ * when the rows are split across GPUs): r_out[v] = pr_row(r_in) for v in the
+ * range, with the dangling mass T - N taken from the caller (N: sum of r_in
+ * over vertices with out-edges, summed over every range by the caller).
+ * sums[0] = sum |r_out - r_in| and sums[1] = sum of r_out over the range's
+ * vertices with out-edges. Returns -1 on allocation failure.
+ */
+int orc_pagerank_sweep_rows(int32_t n, const int32_t* rowptr, const int32_t* colidx, const double* val, double d,
+                            const double* tele, double T, double N, int32_t lo, int32_t hi, const double* r_in,
+                            double* r_out, double* sums)
+{
+    int32_t* outdeg = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+    if (!outdeg) return -1;
+    orc_out_degree(n, rowptr, colidx, outdeg);
+    pr_problem q = {n, rowptr, colidx, val, outdeg, d, tele, T};
+    double res = 0.0, linked = 0.0;
+    for (int32_t v = lo; v < hi; ++v) {
+        r_out[v] = pr_row(&q, r_in, T - N, v);
+        res += fabs(r_out[v] - r_in[v]);
+        if (outdeg[v] != 0) linked += r_out[v];
+    }
+    sums[0] = res;
+    sums[1] = linked;
+    free(outdeg);
+    return 0;
+}
+
 int orc_pagerank_delayed_view(int32_t n, const int32_t* rowptr, const int32_t* colidx, const double* val,
                               double d, const double* tele, double tol, int32_t max_iters,
                               int32_t P, int32_t delta, int32_t local_read, double* r, int32_t* iters,
@@ -381,6 +409,28 @@ int orc_sssp_sync(int32_t n, const int32_t* rowptr, const int32_t* colidx, const
 }
 
 /* Delayed-asynchronous Bellman-Ford (delta = 0: asynchronous), P round-robin workers. */
+/*
+ * One synchronous Bellman-Ford sweep of rows [lo, hi) only:
+ * d_out[v] = min(d_in[v], min over in-edges with d_in[u] finite of d_in[u] + w)
+ * for v in the range. Returns the number of rows lowered.
+ */
+int64_t orc_sssp_sweep_rows(int32_t n, const int32_t* rowptr, const int32_t* colidx, const uint32_t* w, int32_t lo,
+                            int32_t hi, const uint32_t* d_in, uint32_t* d_out)
+{
+    (void)n;
+    int64_t changed = 0;
+    for (int32_t v = lo; v < hi; ++v) {
+        uint32_t best = d_in[v];
+        for (int32_t e = rowptr[v]; e < rowptr[v + 1]; ++e) {
+            const uint32_t du = d_in[colidx[e]];
+            if (du != ORC_INF && du + w[e] < best) best = du + w[e];
+        }
+        d_out[v] = best;
+        if (best < d_in[v]) ++changed;
+    }
+    return changed;
+}
+
 int orc_sssp_delayed_view(int32_t n, const int32_t* rowptr, const int32_t* colidx, const uint32_t* w,
                           uint32_t src, int32_t max_iters, int32_t P, int32_t delta, int32_t local_read,
                           uint32_t* dist, int32_t* iters, int64_t* updates);

@@ -361,3 +361,89 @@ extern "C" int dag_sssp_batched_u8(dag_plan* plan, dag_variant variant, int32_t 
     return sssp_batched_impl(plan, variant, delta, max_iters, B, d_src, d_w8, 1, d_D, d_iters, h_stats,
                              (cudaStream_t)stream);
 }
+
+// ---------------------------------------------------------------------------
+// Row-range sweeps (row sharding across GPUs) and the state conversions
+// ---------------------------------------------------------------------------
+namespace dag {
+__global__ void k_rank_to_state(const float* r, const float* degf, int n, float* x, double* linked)
+{
+    double part = 0.0;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const float dg = degf[v];
+        x[v] = dg > 0.0f ? r[v] / dg : r[v];
+        if (dg > 0.0f) part += (double)r[v];
+    }
+    if (linked) {
+        part = warp_sum(part);
+        if ((threadIdx.x & 31) == 0 && part != 0.0) atomicAdd(linked, part);
+    }
+}
+__global__ void k_state_to_rank(const float* x, const float* degf, int n, float* r)
+{
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const float dg = degf[v];
+        r[v] = dg > 0.0f ? x[v] * dg : x[v];
+    }
+}
+}  // namespace dag
+
+extern "C" int dag_rank_to_state(const dag_plan* plan, const float* d_r, float* d_x, double* d_linked_mass,
+                                 void* stream)
+{
+    if (!plan || !d_r || !d_x) return set_error(DAG_ERR_INVALID, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (d_linked_mass) DAG_CUDA(cudaMemsetAsync(d_linked_mass, 0, sizeof(double), s));
+    k_rank_to_state<<<1024, 256, 0, s>>>(d_r, plan->degf, plan->n, d_x, d_linked_mass);
+    DAG_CUDA(cudaGetLastError());
+    return DAG_OK;
+}
+
+extern "C" int dag_state_to_rank(const dag_plan* plan, const float* d_x, float* d_r, void* stream)
+{
+    if (!plan || !d_r || !d_x) return set_error(DAG_ERR_INVALID, "null argument");
+    k_state_to_rank<<<1024, 256, 0, (cudaStream_t)stream>>>(d_x, plan->degf, plan->n, d_r);
+    DAG_CUDA(cudaGetLastError());
+    return DAG_OK;
+}
+
+extern "C" int dag_pagerank_sweep_rows(dag_plan* plan, float d, int32_t row_lo, int32_t row_hi,
+                                       const float* d_teleport, double teleport_total, double linked_mass,
+                                       const float* d_x_in, float* d_x_out, double* d_sums, void* stream)
+{
+    if (!plan || !d_x_in || !d_x_out || !d_sums) return set_error(DAG_ERR_INVALID, "null argument");
+    if (row_lo < 0 || row_lo > row_hi || row_hi > plan->n) return set_error(DAG_ERR_INVALID, "bad row range");
+    if (!(d > 0.0f && d < 1.0f)) return set_error(DAG_ERR_INVALID, "d must lie in (0, 1)");
+    SweepParams p{};
+    p.n = plan->n;
+    p.rowptr = plan->rowptr;
+    p.colidx = plan->colidx;
+    p.degf = plan->degf;
+    p.base = d_teleport;
+    p.base_scale = 1.0f - d;
+    p.uniform_base = (1.0f - d) / (float)plan->n;
+    p.d = d;
+    p.g_coef = d / (float)plan->n;
+    p.x0 = (void*)d_x_in;
+    p.x1 = d_x_out;
+    p.shard_T = teleport_total;
+    p.shard_N = linked_mass;
+    return sweep_rows(plan, MODE_PR, row_lo, row_hi, p, d_sums, (cudaStream_t)stream);
+}
+
+extern "C" int dag_sssp_sweep_rows(dag_plan* plan, int32_t row_lo, int32_t row_hi, const uint8_t* d_w8,
+                                   const uint32_t* d_dist_in, uint32_t* d_dist_out, double* d_sums, void* stream)
+{
+    if (!plan || !d_dist_in || !d_dist_out || !d_sums || (plan->m > 0 && !d_w8))
+        return set_error(DAG_ERR_INVALID, "null argument");
+    if (row_lo < 0 || row_lo > row_hi || row_hi > plan->n) return set_error(DAG_ERR_INVALID, "bad row range");
+    SweepParams p{};
+    p.n = plan->n;
+    p.rowptr = plan->rowptr;
+    p.colidx = plan->colidx;
+    p.w8 = d_w8;
+    p.degf = plan->degf;
+    p.x0 = (void*)d_dist_in;
+    p.x1 = d_dist_out;
+    return sweep_rows(plan, MODE_BF8, row_lo, row_hi, p, d_sums, (cudaStream_t)stream);
+}

@@ -7,6 +7,7 @@
 #include <functional>
 #include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/dag.h"
@@ -120,6 +121,8 @@ struct SweepParams {
     int* fr_gchg;           // [n + tiles] shared sweeps: rows logged as changed (a row may repeat)
     // warp workers (sweep_warp.cu): cta_row / cta_tile hold each warp's first row / tile
     int warp;                     // 1: one worker per warp
+    int shard;                    // 1: one synchronous sweep of a row range, x0 / x1 given (sweep_rows)
+    double shard_T, shard_N;      //    teleport total and mass on vertices with out-edges of x0's iterate
     unsigned long long* wpub;     // [warps] partial of the row each run leaves unfinished, with its sweep stamp
     // init / output
     const float* init;      // warm start (PR) or nullptr
@@ -173,6 +176,7 @@ struct dag_plan {
     float* scratch_f = nullptr; // [n] float scratch (adjoint aux)
     int* fr_orow = nullptr;   // [n+1] out-CSR row pointers (frontier sweeps, built on first use)
     std::map<long long, dag::Partition> parts;  // key: nblocks | row_cap << 32
+    std::map<std::tuple<int, int, int, int>, dag::Partition> range_parts;  // (warps, tile, lo, hi)
     // batched workspace (grown on demand)
     void* bx = nullptr;
     size_t bx_bytes = 0;
@@ -228,6 +232,9 @@ int set_l1_carveout(const void* k, int device, int threads, size_t static_smem, 
 // of W taking tiles [floor(w T / W), floor((w+1) T / W)); cta_tile / cta_row
 // hold each warp's first tile / first owned row (the partition's nblocks is W).
 int get_warp_partition(dag_plan* plan, int W, int tile, Partition** out, cudaStream_t s);
+// The same over the merge path of rows [lo, hi) only (row-range sweeps).
+int get_warp_partition_range(dag_plan* plan, int W, int tile, int lo, int hi, Partition** out, cudaStream_t s);
+int sweep_rows(dag_plan* plan, int mode, int lo, int hi, SweepParams& p, double* d_sums, cudaStream_t s);
 // sweep_warp.cu
 const void* sweep_warp_kernel_ptr(int mode, int variant, int ipt);
 int launch_warp_sweep(dag_plan* plan, int mode, int variant, int delta, SweepParams& p, cudaStream_t s,

@@ -291,6 +291,24 @@ __global__ void k_warp_tile_coords(const int* rowptr, int n, long long m, int ti
     tile_row[k] = lo;
     tile_nz[k] = (int)(diag - lo);
 }
+// Tile k of the merge path of rows [lo, hi): diagonal min(d_lo + k tile, d_hi).
+__global__ void k_range_tile_coords(const int* rowptr, int lo, int hi, int tile, int tiles, int* tile_row,
+                                    int* tile_nz)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > tiles) return;
+    const long long d_lo = (long long)lo + rowptr[lo], d_hi = (long long)hi + rowptr[hi];
+    const long long diag = k == tiles ? d_hi : d_lo + (long long)k * tile;
+    int a = lo, b = hi;  // first v in [lo, hi] with v + rowptr[v+1] >= diag
+    while (a < b) {
+        const int mid = (a + b) >> 1;
+        if ((long long)mid + rowptr[mid + 1] >= diag) b = mid;
+        else a = mid + 1;
+    }
+    tile_row[k] = a;
+    tile_nz[k] = (int)(diag - a);
+}
+
 __global__ void k_warp_runs(const int* tile_row, int tiles, int W, int* wtile, int* wrow)
 {
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
@@ -325,6 +343,34 @@ int get_warp_partition(dag_plan* plan, int W, int tile, Partition** out, cudaStr
     DAG_CUDA(cudaStreamSynchronize(s));
     for (int w = 0; w < W; ++w) part.max_rows = std::max(part.max_rows, wrow[w + 1] - wrow[w]);
     auto ins = plan->parts.emplace(key, part);
+    *out = &ins.first->second;
+    return DAG_OK;
+}
+
+int get_warp_partition_range(dag_plan* plan, int W, int tile, int lo, int hi, Partition** out, cudaStream_t s)
+{
+    const auto key = std::make_tuple(W, tile, lo, hi);
+    auto it = plan->range_parts.find(key);
+    if (it != plan->range_parts.end()) { *out = &it->second; return DAG_OK; }
+    std::vector<int> rp(2);
+    DAG_CUDA(cudaMemcpy(&rp[0], plan->rowptr + lo, sizeof(int), cudaMemcpyDeviceToHost));
+    DAG_CUDA(cudaMemcpy(&rp[1], plan->rowptr + hi, sizeof(int), cudaMemcpyDeviceToHost));
+    const long long items = (long long)(hi - lo) + (rp[1] - rp[0]);
+    const long long T = std::max(1LL, (items + tile - 1) / tile);
+    Partition part;
+    part.nblocks = W;
+    part.tiles = (int)T;
+    DAG_CUDA(cudaMalloc(&part.cta_row, (W + 1) * sizeof(int)));
+    DAG_CUDA(cudaMalloc(&part.cta_tile, (W + 1) * sizeof(int)));
+    DAG_CUDA(cudaMalloc(&part.tile_row, (T + 1) * sizeof(int)));
+    DAG_CUDA(cudaMalloc(&part.tile_nz, (T + 1) * sizeof(int)));
+    DAG_CUDA(cudaMalloc(&part.wpub, W * sizeof(unsigned long long)));
+    k_range_tile_coords<<<(unsigned)((T + 1 + 255) / 256), 256, 0, s>>>(plan->rowptr, lo, hi, tile, (int)T,
+                                                                        part.tile_row, part.tile_nz);
+    k_warp_runs<<<(W + 1 + 255) / 256, 256, 0, s>>>(part.tile_row, (int)T, W, part.cta_tile, part.cta_row);
+    DAG_CUDA(cudaGetLastError());
+    DAG_CUDA(cudaStreamSynchronize(s));
+    auto ins = plan->range_parts.emplace(key, part);
     *out = &ins.first->second;
     return DAG_OK;
 }
@@ -600,6 +646,13 @@ extern "C" int dag_plan_destroy(dag_plan* p)
         cudaFree(kv.second.fr_chg);
         cudaFree(kv.second.fr_glist);
         cudaFree(kv.second.fr_gchg);
+        cudaFree(kv.second.wpub);
+    }
+    for (auto& kv : p->range_parts) {
+        cudaFree(kv.second.cta_row);
+        cudaFree(kv.second.cta_tile);
+        cudaFree(kv.second.tile_row);
+        cudaFree(kv.second.tile_nz);
         cudaFree(kv.second.wpub);
     }
     cudaFree(p->fr_orow);

@@ -230,8 +230,8 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_warp_kernel(const SweepP
     const bool mid0 = t_lo < t_hi && p.tile_nz[t_lo] > p.rowptr[p.tile_row[t_lo]];
     const bool head = mid0 && row_hi > row_lo;
 
-    // ---------------- initial values of the owned rows ----------------
-    {
+    // ---------------- initial values of the owned rows (a row-range sweep is given them) ----------------
+    if (!p.shard) {
         double gpart = 0.0, tpart = 0.0;
         for (int v = row_lo + lane; v < row_hi; v += 32) {
             if constexpr (BF) {
@@ -260,15 +260,15 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_warp_kernel(const SweepP
         }
     }
     if (p.skip_barrier_cta0 && c == 0) return;  // test hook: the others' waits must run out
-    if (!grid_barrier(sb, p.nblocks, bar_target, p.timeout_ns)) return;
+    if (!p.shard && !grid_barrier(sb, p.nblocks, bar_target, p.timeout_ns)) return;
 
     double T = 1.0;
     if (tid == 0 && !BF) {
-        sh.T = ld_relaxed_f64(&sb->T);
-        sh.gprev = ld_relaxed_f64(&sb->acc_g[2]);
+        sh.T = p.shard ? p.shard_T : ld_relaxed_f64(&sb->T);
+        sh.gprev = p.shard ? p.shard_N : ld_relaxed_f64(&sb->acc_g[2]);
     }
     __syncthreads();
-    if constexpr (!BF) T = (MODE == MODE_ADJ || p.base) ? sh.T : 1.0;  // a uniform teleport sums to 1 exactly
+    if constexpr (!BF) T = (MODE == MODE_ADJ || p.base || p.shard) ? sh.T : 1.0;  // a uniform teleport sums to 1
     double gprev = BF ? 0.0 : sh.gprev;
     LiveSum L{};
     if constexpr (LIVE_G) L = live_sum_setup<MODE>(p, T, gprev);
@@ -450,8 +450,8 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_warp_kernel(const SweepP
         }
     }
 
-    // ---------------- output of the owned rows ----------------
-    {
+    // ---------------- output of the owned rows (a row-range sweep leaves them in x1) ----------------
+    if (!p.shard) {
         const uint32_t* xf = SYNC ? ((it & 1) ? X1 : X0) : X0;
         for (int v = row_lo + lane; v < row_hi; v += 32) {
             const uint32_t x = ld_relaxed_b32(xf + v);
@@ -583,6 +583,56 @@ int launch_warp_sweep(dag_plan* plan, int mode, int variant, int delta, SweepPar
     void* args[] = {(void*)&p};
     DAG_CUDA(cudaLaunchCooperativeKernel(k, dim3(nb), dim3(NT), args, dyn, s));
     *out_nblocks = nb * WWARPS;
+    return DAG_OK;
+}
+
+// One synchronous sweep over rows [lo, hi) of the plan's graph (row sharding
+// across GPUs, rowshard.py): x_in is the whole previous iterate, the new
+// values of the range go to x_out[lo, hi), and d_sums receives {sum |r' - r|
+// over the range (PageRank; Bellman-Ford: rows lowered), sum of r' over the
+// range's vertices with out-edges (PageRank)} in FP64. The range's merge path
+// is cut into warp tiles and warp runs as in a whole sweep.
+__global__ void k_copy_sums(const SyncBlock* sb, double* out)
+{
+    out[0] = sb->acc_res[0];
+    out[1] = sb->acc_g[0];
+}
+
+int sweep_rows(dag_plan* plan, int mode, int lo, int hi, SweepParams& p, double* d_sums, cudaStream_t s)
+{
+    const int WTILE = 32 * plan->warp_ipt;
+    const void* k = sweep_warp_kernel_ptr(mode, DAG_SYNC, plan->warp_ipt);
+    cudaFuncAttributes fa{};
+    DAG_CUDA(cudaFuncGetAttributes(&fa, k));
+    DAG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 0));
+    int per_sm = 0;
+    DAG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, 0));
+    if (per_sm < 1) return set_error(DAG_ERR_INVALID, "row sweep cannot be resident");
+    int nb = per_sm * plan->num_sms;
+    if (plan->worker_cap > 0) nb = std::min(nb, plan->worker_cap);
+    Partition* part = nullptr;
+    int rc = get_warp_partition_range(plan, nb * WWARPS, WTILE, lo, hi, &part, s);
+    if (rc) return rc;
+    p.nblocks = nb;
+    p.max_iters = 1;
+    p.tol = 0.0;
+    p.delta = 0;
+    p.buf_cap = 0;
+    p.buf_clamped = 0;
+    p.shard = 1;
+    p.cta_row = part->cta_row;
+    p.cta_tile = part->cta_tile;
+    p.tile_row = part->tile_row;
+    p.tile_nz = part->tile_nz;
+    p.wpub = part->wpub;
+    p.sync = plan->sync;
+    p.timeout_ns = plan->timeout_ns;
+    DAG_CUDA(cudaMemsetAsync(plan->sync, 0, sizeof(SyncBlock), s));
+    DAG_CUDA(cudaMemsetAsync(part->wpub, 0, (size_t)part->nblocks * sizeof(unsigned long long), s));
+    void* args[] = {(void*)&p};
+    DAG_CUDA(cudaLaunchCooperativeKernel(k, dim3(nb), dim3(NT), args, 0, s));
+    k_copy_sums<<<1, 1, 0, s>>>(plan->sync, d_sums);
+    DAG_CUDA(cudaGetLastError());
     return DAG_OK;
 }
 

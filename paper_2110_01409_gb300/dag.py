@@ -33,7 +33,8 @@ EXPORTS = (
     "dag_normalize_weights", "dag_pagerank_adjoint", "dag_strerror", "dag_last_error_message",
     "dag_debug_skip_barrier_once", "dag_debug_stall_staging_once", "dag_tile_items", "dag_pagerank_noalloc", "dag_gather_f32", "dag_plan_set_worker_cap",
     "dag_sssp_u8", "dag_probe_gather", "dag_access_matrix", "dag_plan_set_batched_graph", "dag_warp_tile_items",
-    "dag_plan_set_warp_tile", "dag_plan_last_status", "dag_sssp_batched_u8",
+    "dag_plan_set_warp_tile", "dag_plan_last_status", "dag_sssp_batched_u8", "dag_rank_to_state",
+    "dag_state_to_rank", "dag_pagerank_sweep_rows", "dag_sssp_sweep_rows",
 )
 
 
@@ -103,6 +104,10 @@ def lib():
             L.dag_warp_tile_items.argtypes = [_vp]
             L.dag_plan_set_warp_tile.argtypes = [_vp, _i32]
             L.dag_plan_last_status.argtypes = [_vp, _vp, _vp]
+            L.dag_rank_to_state.argtypes = [_vp, _vp, _vp, _vp, _vp]
+            L.dag_state_to_rank.argtypes = [_vp, _vp, _vp, _vp]
+            L.dag_pagerank_sweep_rows.argtypes = [_vp, _f32, _i32, _i32, _vp, _f64, _f64, _vp, _vp, _vp, _vp]
+            L.dag_sssp_sweep_rows.argtypes = [_vp, _i32, _i32, _vp, _vp, _vp, _vp, _vp]
             L.dag_gather_f32.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp]
             L.dag_plan_set_worker_cap.argtypes = [_vp, _i32]
             L.dag_plan_set_batched_graph.argtypes = [_vp, _i32]
@@ -434,3 +439,40 @@ class PageRankFn(torch.autograd.Function):
         gw, gt, _, st = ctx.model.backward(val, s, r, grad_r.contiguous().float())
         ctx.backward_stats = st
         return gw, (gt if ctx.has_t else None), None
+
+
+def rank_to_state(plan: Plan, r: torch.Tensor, x: torch.Tensor, linked: torch.Tensor | None = None):
+    """x = r / outdeg (r on vertices without out-edges); linked (CUDA float64 [1]) gets sum r over
+    vertices with out-edges."""
+    _dev(r, torch.float32, plan.n, "r")
+    _dev(x, torch.float32, plan.n, "x")
+    _dev(linked, torch.float64, 1, "linked")
+    _raise(lib().dag_rank_to_state(plan.h, _ptr(r), _ptr(x), _ptr(linked), _stream()), False)
+
+
+def state_to_rank(plan: Plan, x: torch.Tensor, r: torch.Tensor):
+    _dev(x, torch.float32, plan.n, "x")
+    _dev(r, torch.float32, plan.n, "r")
+    _raise(lib().dag_state_to_rank(plan.h, _ptr(x), _ptr(r), _stream()), False)
+
+
+def pagerank_sweep_rows(plan: Plan, lo: int, hi: int, x_in, x_out, sums, d=0.85, teleport=None,
+                        teleport_total=1.0, linked_mass=0.0):
+    """One synchronous PageRank sweep of rows [lo, hi) (dag_pagerank_sweep_rows); sums: CUDA float64 [2]."""
+    for t, nm in ((x_in, "x_in"), (x_out, "x_out")):
+        _dev(t, torch.float32, plan.n, nm)
+    _dev(sums, torch.float64, 2, "sums")
+    _dev(teleport, torch.float32, plan.n, "teleport")
+    _raise(lib().dag_pagerank_sweep_rows(plan.h, d, lo, hi, _ptr(teleport), teleport_total, linked_mass,
+                                         _ptr(x_in), _ptr(x_out), _ptr(sums), _stream()), False)
+
+
+def sssp_sweep_rows(plan: Plan, lo: int, hi: int, w8, dist_in, dist_out, sums):
+    """One synchronous Bellman-Ford sweep of rows [lo, hi) (dag_sssp_sweep_rows); sums: CUDA float64 [2]."""
+    for t, nm in ((dist_in, "dist_in"), (dist_out, "dist_out")):
+        _dev(t, torch.int32, plan.n, nm)
+    if plan.m:
+        _dev(w8, torch.uint8, plan.m, "w8")
+    _dev(sums, torch.float64, 2, "sums")
+    _raise(lib().dag_sssp_sweep_rows(plan.h, lo, hi, _ptr(w8), _ptr(dist_in), _ptr(dist_out), _ptr(sums),
+                                     _stream()), False)

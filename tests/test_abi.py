@@ -71,6 +71,11 @@ def test_null_arguments_are_refused_without_a_gpu(lib):
         "dag_plan_set_batched_graph": lambda: lib.dag_plan_set_batched_graph(N, 1),
         "dag_plan_set_warp_tile": lambda: lib.dag_plan_set_warp_tile(N, 7),
         "dag_plan_last_status": lambda: lib.dag_plan_last_status(N, N, N),
+        "dag_rank_to_state": lambda: lib.dag_rank_to_state(N, N, N, N, N),
+        "dag_state_to_rank": lambda: lib.dag_state_to_rank(N, N, N, N),
+        "dag_pagerank_sweep_rows": lambda: lib.dag_pagerank_sweep_rows(N, f(0.85), 0, 1, N, d(1.0), d(0.0), N, N,
+                                                                       N, N),
+        "dag_sssp_sweep_rows": lambda: lib.dag_sssp_sweep_rows(N, 0, 1, N, N, N, N, N),
         "dag_pagerank": lambda: lib.dag_pagerank(N, f(0.85), d(1e-6), 1, 0, 10, N, N, N, 0, N, N),
         "dag_sssp": lambda: lib.dag_sssp(N, 0, 1, 0, 10, N, N, 0, N, N),
         "dag_sssp_u8": lambda: lib.dag_sssp_u8(N, 0, 1, 0, 10, N, N, 0, N, N),

@@ -260,3 +260,20 @@ def test_threaded_fixed_point_closed_forms():
     r = oracle.pagerank_fixed_point(g, d, tele=t, tol=1e-15, threads=2)
     j = (np.arange(n) - s) % n
     assert np.abs(r - (1 - d) * d ** j / (1 - d ** n)).max() <= 1e-13
+
+
+def test_row_sweeps_cover_one_sync_sweep():
+    # sweeping [0, n) in two row ranges with the whole previous iterate is one synchronous sweep
+    g = I.rmat(10, 16, seed=1)
+    r0 = np.full(g.n, 1.0 / g.n)
+    want, it, hist, _ = oracle.pagerank(g, oracle.SYNC, tol=0.0, max_iters=1, r0=r0)
+    out = np.zeros(g.n)
+    cut = 400
+    a = oracle.pagerank_sweep_rows(g, 0, cut, r0, out)
+    b = oracle.pagerank_sweep_rows(g, cut, g.n, r0, out)
+    assert np.array_equal(out, want)
+    assert a[0] + b[0] == pytest.approx(hist[0], rel=1e-13)
+    od = np.bincount(g.colidx, minlength=g.n)
+    assert a[1] + b[1] == pytest.approx(want[od > 0].sum(), rel=1e-13)
+    # an empty range changes nothing
+    assert oracle.pagerank_sweep_rows(g, 5, 5, r0, out) == (0.0, 0.0)

@@ -142,3 +142,14 @@ def test_threaded_form_matches_dijkstra():
     for variant, delta in [(0, 0), (1, 0), (2, 32)]:
         dist, it, sec, ok = oracle.sssp_threads(g, w, 0, variant, threads=4, delta=delta)
         assert ok and np.array_equal(dist, ref)
+
+
+def test_row_sweeps_cover_one_sync_sweep_sssp():
+    g = I.rmat(10, 16, seed=1)
+    w = I.weights_u32(g, 1)
+    d0 = np.full(g.n, oracle.INF, dtype=np.uint32)
+    d0[0] = 0
+    want, _, upd, _ = oracle.sssp(g, w, 0, oracle.SYNC, max_iters=1)
+    out = np.zeros(g.n, dtype=np.uint32)
+    c = oracle.sssp_sweep_rows(g, w, 0, 300, d0, out) + oracle.sssp_sweep_rows(g, w, 300, g.n, d0, out)
+    assert np.array_equal(out, want) and c == upd[0]
