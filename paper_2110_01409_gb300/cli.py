@@ -40,10 +40,12 @@ def main():
     ap.add_argument("--reads", default="refresh", choices=list(dag.READ_MODES))
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--warp-tile", type=int, default=7, help="items per lane of warp tiles (reads warp...)")
     args = ap.parse_args()
     B.build()
     g = make_graph(args.graph, args.scale, args.seed)
     plan = dag.Plan.from_graph(g, "cuda")
+    plan.set_warp_tile(args.warp_tile)
     out = []
     for _ in range(args.repeat):
         if args.algo == "pagerank":
