@@ -290,6 +290,20 @@ def run_gpu(args):
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
     traffic = _recorded_traffic(dom, dom_sweeps, bf_edges_mean if "frontier" in dom else None)
 
+    # ---- the delayed variant's own fraction: the fastest delta > 0 candidate of each algorithm ----
+    def delayed_roof(tuned, kind, mode):
+        best = min((c for c in tuned["candidates"] if "ms" in c and c["variant"] == "delayed" and c["delta"] > 0),
+                   key=lambda c: c["ms"], default=None)
+        if best is None:
+            return None
+        sweeps = statistics.mean(best["sweeps"])
+        gbs = algorithmic_bytes(n, m, kind) * sweeps / (best["ms"] * 1e-3) / 1e9
+        return {"kernel": kernel_name(mode, "delayed", best["delta"], best["reads"], best["warp_tile"]),
+                "delta": best["delta"], "reads": best["reads"], "ms": round(best["ms"], 3), "sweeps": sweeps,
+                "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4)}
+
+    delayed_roofline = {"pagerank": delayed_roof(tune_pr, "pr", "PR"), "sssp": delayed_roof(tune_bf, "bf8", "BF8")}
+
     # ---- the sweep's real ceiling: one streamed gather pass over the same colidx (dag_probe_gather) ----
     coherent = gathers_coherent(bf_var, bf_dl, bf_rd)
     probe_ms = dag.probe_gather(plan, rank_out, coherent=coherent, repeats=5)
@@ -351,6 +365,7 @@ def run_gpu(args):
                      "frac_of_nominal": round(achieved / HBM_NOMINAL_GBS, 4),
                      "bytes_per_launch": int(dom_bytes), "traffic": traffic},
         "gather_floor": gather_floor,
+        "delayed_roofline": delayed_roofline,
         "clocks": clk,
         "gpu_launches": 2 * K * solves,  # each solve's sweep kernel and its status copy
         "e2e": e2e,
