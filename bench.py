@@ -200,7 +200,8 @@ def run_gpu(args):
 
     # CTA-tile sweeps over delta, plus warp-worker sweeps (three warp tile shapes for the async end)
     warp_cands = [("sync", 0, "warp"), ("delayed", 16, "warp"), ("delayed", 256, "warp+cached")] + \
-        [("delayed", 0, "warp+cached", ipt) for ipt in (5, 7, 11)]
+        [("delayed", 0, "warp+cached", ipt) for ipt in (5, 7, 11)] + \
+        [("delayed", 0, "ordered+cached", ipt) for ipt in (7, 11)]
     cands = [("delayed", dl) for dl in DELTAS] + [("delayed", 0, "own_l1")] + warp_cands
     cands_bf = cands + [("delayed", 0, "frontier"), ("delayed", 0, "own_l1+frontier")]
     tune_pr = autotune.tune(plan, "pagerank", candidates=cands, worker_fractions=[1.0], trials=2, cache=None)
@@ -385,6 +386,8 @@ def kernel_name(mode, variant, delta, reads, warp_tile=7):
     var = "ASYNC" if variant == "async" or (variant == "delayed" and delta == 0) else variant.upper()
     if reads.startswith("warp"):
         return f"sweep_warp_kernel<{mode},{var},{warp_tile}>"
+    if reads.startswith("ordered"):
+        return f"sweep_ordered_kernel<{mode},{warp_tile}>"
     if var == "ASYNC":
         return f"sweep_tma_kernel<{mode}{',frontier' if 'frontier' in reads else ''}>"
     return f"sweep_kernel<{mode},{var}{',frontier' if 'frontier' in reads else ''}>"
@@ -509,7 +512,8 @@ VARIANT_ROWS = [("sync", "sync", 0, "refresh"), ("async", "async", 0, "refresh")
                 ("delayed32", "delayed", 32, "refresh"), ("delayed256", "delayed", 256, "refresh"),
                 ("delayed4096", "delayed", 4096, "refresh"), ("delayed4096_local", "delayed", 4096, "local"),
                 ("warp_sync", "sync", 0, "warp"), ("warp_async_cached", "async", 0, "warp+cached"),
-                ("warp_delayed16", "delayed", 16, "warp"), ("warp_delayed256_cached", "delayed", 256, "warp+cached")]
+                ("warp_delayed16", "delayed", 16, "warp"), ("warp_delayed256_cached", "delayed", 256, "warp+cached"),
+                ("ordered_cached", "async", 0, "ordered+cached")]
 
 
 def run_detail(g, w, srcs, plan, w_d, dag, torch, args):

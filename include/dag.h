@@ -169,6 +169,17 @@ int dag_plan_set_worker_cap(dag_plan* plan, int32_t max_workers);
  */
 #define DAG_WARP_WORKERS 64
 /*
+ * Ordered warp sweeps (asynchronous form of dag_pagerank, dag_sssp,
+ * dag_sssp_u8; implies warp workers): the warps take the tiles of the whole
+ * merge path in turn, tile t to warp t mod W, so a sweep visits the vertices
+ * in vertex order across the GPU, one in-order stream as a single worker's
+ * asynchronous sweep (Sec. I) with every warp on it, instead of one stream per
+ * worker; rows spanning tiles are finished by a bounded look-back over per-tile
+ * published partials. DAG_READ_CACHED selects ordinary (L1) gathers, else L2.
+ * DAG_ERR_INVALID with the synchronous or delayed form.
+ */
+#define DAG_WARP_ORDERED 128
+/*
  * Warp tile shape of the plan's warp-worker sweeps: 32 lanes x items_per_lane
  * items (5, 7 or 11; 7 when a plan is created), a tuning choice. Shorter tiles
  * mean more tiles in flight per warp's run; longer ones, fewer merge-path

@@ -9,7 +9,8 @@ own CUDA-event timing. Results are cached in a JSON file keyed by a graph
 fingerprint, so a graph is tuned once per machine. Two tile shapes are in
 play: the CTA tiles of the default sweeps (256 threads x 7 items, fixed when
 the library is compiled) and the warp tiles of warp-worker sweeps
-(reads "warp...", DAG_WARP_WORKERS), 32 lanes x 5, 7 or 11 items, which a
+(reads "warp...", DAG_WARP_WORKERS) and of ordered warp sweeps (reads
+"ordered...", DAG_WARP_ORDERED), 32 lanes x 5, 7 or 11 items, which a
 candidate's fourth field selects.
 """
 from __future__ import annotations
@@ -28,11 +29,12 @@ DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "dag_autotune.js
 _lock = threading.Lock()
 
 # (variant, delta[, reads[, warp tile items per lane]]); reads defaults to "refresh" (see
-# dag.READ_MODES), the warp tile to 7 items per lane (used by the "warp..." read paths only)
+# dag.READ_MODES), the warp tile to 7 items per lane (used by the "warp..." and "ordered..." read paths only)
 SINGLE_CANDIDATES = [("sync", 0), ("async", 0), ("async", 0, "own_l1"), ("delayed", 32), ("delayed", 256),
                      ("delayed", 4096), ("delayed", 4096, "local"),
                      ("sync", 0, "warp"), ("async", 0, "warp+cached"), ("async", 0, "warp+cached", 5),
-                     ("async", 0, "warp+cached", 11), ("delayed", 16, "warp"), ("delayed", 256, "warp+cached")]
+                     ("async", 0, "warp+cached", 11), ("delayed", 16, "warp"), ("delayed", 256, "warp+cached"),
+                     ("async", 0, "ordered+cached", 7), ("async", 0, "ordered+cached", 11)]
 WARP_TILES = (5, 7, 11)
 SSSP_EXTRA = [("async", 0, "frontier"), ("async", 0, "own_l1+frontier")]  # Bellman-Ford only
 BATCH_CANDIDATES = [("sync", 0), ("async", 0), ("delayed", 4), ("delayed", 16)]

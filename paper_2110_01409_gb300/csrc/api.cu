@@ -160,7 +160,8 @@ extern "C" int dag_pagerank(dag_plan* plan, float d, double tol, dag_variant var
     p.read_mode = read_mode_of(flags);
     p.local_read = (flags & DAG_READ_LOCAL) ? 1 : 0;
     p.own_l1 = (flags & DAG_READ_OWN_L1) ? 1 : 0;
-    p.warp = (flags & DAG_WARP_WORKERS) ? 1 : 0;
+    p.warp = (flags & (DAG_WARP_WORKERS | DAG_WARP_ORDERED)) ? 1 : 0;
+    p.ordered = (flags & DAG_WARP_ORDERED) ? 1 : 0;
     Timer tm;
     tm.start(s, h_stats != nullptr);
     int nb = 0;
@@ -199,7 +200,8 @@ int sssp_impl(dag_plan* plan, uint32_t src, int variant, int delta, int max_iter
     p.local_read = (flags & DAG_READ_LOCAL) ? 1 : 0;
     p.own_l1 = (flags & DAG_READ_OWN_L1) ? 1 : 0;
     p.frontier = (flags & DAG_SSSP_FRONTIER) ? 1 : 0;
-    p.warp = (flags & DAG_WARP_WORKERS) ? 1 : 0;
+    p.warp = (flags & (DAG_WARP_WORKERS | DAG_WARP_ORDERED)) ? 1 : 0;
+    p.ordered = (flags & DAG_WARP_ORDERED) ? 1 : 0;
     if (p.warp && p.frontier) return set_error(DAG_ERR_INVALID, "the frontier runs the CTA-tile sweeps");
     if (p.frontier && var == DAG_DELAYED)
         return set_error(DAG_ERR_INVALID, "the frontier runs the synchronous and asynchronous forms (delta 0)");

@@ -121,6 +121,8 @@ struct SweepParams {
     int* fr_gchg;           // [n + tiles] shared sweeps: rows logged as changed (a row may repeat)
     // warp workers (sweep_warp.cu): cta_row / cta_tile hold each warp's first row / tile
     int warp;                     // 1: one worker per warp
+    int ordered;                  // 1: warps take the tiles of the whole merge path in turn (async form)
+    int ntiles;                   //    tiles of that merge path; wpub then holds one word per tile
     int shard;                    // 1: one synchronous sweep of a row range, x0 / x1 given (sweep_rows)
     double shard_T, shard_N;      //    teleport total and mass on vertices with out-edges of x0's iterate
     unsigned long long* wpub;     // [warps] partial of the row each run leaves unfinished, with its sweep stamp
@@ -149,6 +151,7 @@ struct Partition {
     int* fr_glist = nullptr;  // device [tiles]
     int* fr_gchg = nullptr;   // device [n + tiles]
     unsigned long long* wpub = nullptr;  // warp workers: [nblocks] published partials
+    unsigned long long* tpub = nullptr;  // ordered warp sweeps: [tiles] published partials (built on first use)
 };
 
 }  // namespace dag
@@ -237,6 +240,7 @@ int get_warp_partition_range(dag_plan* plan, int W, int tile, int lo, int hi, Pa
 int sweep_rows(dag_plan* plan, int mode, int lo, int hi, SweepParams& p, double* d_sums, cudaStream_t s);
 // sweep_warp.cu
 const void* sweep_warp_kernel_ptr(int mode, int variant, int ipt);
+const void* sweep_ordered_kernel_ptr(int mode, int ipt);
 int launch_warp_sweep(dag_plan* plan, int mode, int variant, int delta, SweepParams& p, cudaStream_t s,
                       int* out_nblocks);
 

@@ -647,6 +647,7 @@ extern "C" int dag_plan_destroy(dag_plan* p)
         cudaFree(kv.second.fr_glist);
         cudaFree(kv.second.fr_gchg);
         cudaFree(kv.second.wpub);
+        cudaFree(kv.second.tpub);
     }
     for (auto& kv : p->range_parts) {
         cudaFree(kv.second.cta_row);

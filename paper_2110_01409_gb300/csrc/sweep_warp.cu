@@ -64,6 +64,7 @@ struct WarpShared {
 template <int WIPT>
 struct WStage {
     int a0, b0, NA, NB;
+    int rp0;              // rowptr[a0]: the tile starts inside row a0 when b0 > rp0
     uint32_t term[WIPT];  // edge terms: gathered value, combined with the edge's weight / value
     uint32_t xo;          // old value of row a0 + lane
     float dg;             // its out-degree (PageRank)
@@ -79,6 +80,7 @@ __device__ __forceinline__ void wfetch(WStage<WIPT>& st, const SweepParams& p, c
     st.b0 = p.tile_nz[t];
     st.NA = p.tile_row[t + 1] - st.a0;
     st.NB = p.tile_nz[t + 1] - st.b0;
+    st.rp0 = (int)ld_vertex_b32(p.rowptr + st.a0, pol_vertex);
     int col[WIPT];
     uint32_t aux[WIPT];
 #pragma unroll
@@ -471,6 +473,302 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_warp_kernel(const SweepP
     }
 }
 
+// ---------------------------------------------------------------------------
+// Ordered warp sweep (asynchronous form, DAG_WARP_ORDERED): the warps take the
+// tiles of the whole merge path in turn instead of each walking a run of its
+// own, tile t to warp t mod W, so at any moment the GPU works on one window of
+// W consecutive tiles and a sweep visits the vertices in order across the GPU:
+// one in-order stream, as a single thread's asynchronous sweep (Sec. I) with
+// every warp on it. A row whose in-edges
+// span tiles is finished with a decoupled look-back over per-tile published
+// partials (Merrill & Garland's single-pass scan): every tile publishes the
+// partial of the row it leaves unfinished at once (inclusive when that row
+// starts inside the tile, else an aggregate, upgraded to inclusive later), and
+// the tile that ends a row begun earlier adds the published partials back to
+// the first inclusive one, 32 tiles per step (one per lane). A warp resolves
+// its tile's look-back after walking its next tile, by when the tiles before
+// it have published (a tile publishes before its warp resolves anything
+// older, so the lowest pending tile can always finish); each wait is bounded
+// by the launch's timeout.
+// ---------------------------------------------------------------------------
+constexpr unsigned TPUB_INCL = 0x80000000u;  // the published value is the row's partial from its start
+
+// The word tile j published in sweep `stamp` (waits, bounded); false when the wait ran out or another CTA
+// recorded an error.
+__device__ __forceinline__ bool wait_tile(const unsigned long long* pub, int j, unsigned stamp, SyncBlock* sb,
+                                          long long timeout_ns, unsigned long long* out)
+{
+    const unsigned long long t0 = globaltimer_ns();
+    unsigned spins = 0;
+    for (;;) {
+        const unsigned long long v = ld_relaxed_u64(pub + j);
+        if (((unsigned)(v >> 32) & ~TPUB_INCL) == stamp) {
+            *out = v;
+            return true;
+        }
+        if (ld_relaxed_i32(&sb->err) != 0) return false;
+        if ((++spins & 15u) == 0 && (long long)(globaltimer_ns() - t0) > timeout_ns) {
+            atomicCAS(&sb->err, 0, DAG_ERR_BARRIER_TIMEOUT);
+            return false;
+        }
+        __nanosleep(32);
+    }
+}
+
+template <int MODE, int WIPT>
+__global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_ordered_kernel(const SweepParams p)
+{
+    using O = Op<MODE>;
+    constexpr int WTILE = 32 * WIPT;
+    constexpr bool BF = MODE == MODE_BF || MODE == MODE_BF8;
+    constexpr bool LIVE_G = !BF;
+    constexpr unsigned FULL = 0xffffffffu;
+    (void)WTILE;
+
+    __shared__ WarpShared<32 * WIPT> sh;
+    const int c = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wl = tid >> 5;
+    const int w = c * WWARPS + wl;
+    const int W = p.nblocks * WWARPS, T = p.ntiles;  // warp w takes tiles w, w + W, w + 2W, ...
+    SyncBlock* sb = p.sync;
+    unsigned long long bar_target = 0;
+    uint32_t* X = (uint32_t*)p.x0;
+    unsigned long long* pub = p.wpub;  // [T]
+    const float inv_n = 1.0f / (float)p.n;
+    int* end = sh.end[wl];
+    uint32_t* val = sh.val[wl];
+    uint32_t* sum = sh.sum[wl];
+    const long long gthreads = (long long)p.nblocks * NT, gtid = (long long)c * NT + tid;
+
+    // ---------------- initial values (any thread any row: nothing reads them before the barrier) ----------------
+    {
+        double gpart = 0.0, tpart = 0.0;
+        for (long long vv = gtid; vv < p.n; vv += gthreads) {
+            const int v = (int)vv;
+            if constexpr (BF) {
+                X[v] = (v == (int)p.src) ? 0u : INF;
+            } else if constexpr (MODE == MODE_ADJ) {
+                const float cv = p.base[v];
+                const float l0 = p.init ? p.init[v] : cv;
+                X[v] = __float_as_uint(l0);
+                gpart += (double)l0;
+                tpart += fabs((double)cv);
+            } else {
+                const float t = p.base ? p.base[v] : inv_n;
+                const float r0 = p.init ? p.init[v] : t;
+                const float dg = p.degf[v];
+                X[v] = __float_as_uint((MODE == MODE_PR && dg > 0.0f) ? r0 / dg : r0);
+                if (dg > 0.0f) gpart += (double)r0;
+                tpart += (double)t;
+            }
+        }
+        if constexpr (!BF) {
+            block_sum2(sh, gpart, tpart);
+            if (tid == 0) {
+                atomicAdd(&sb->acc_g[2], gpart);
+                atomicAdd(&sb->T, tpart);
+            }
+        }
+    }
+    if (p.skip_barrier_cta0 && c == 0) return;  // test hook: the others' waits must run out
+    if (!grid_barrier(sb, p.nblocks, bar_target, p.timeout_ns)) return;
+
+    double T_tot = 1.0;
+    if (tid == 0 && !BF) {
+        sh.T = ld_relaxed_f64(&sb->T);
+        sh.gprev = ld_relaxed_f64(&sb->acc_g[2]);
+    }
+    __syncthreads();
+    if constexpr (!BF) T_tot = (MODE == MODE_ADJ || p.base) ? sh.T : 1.0;
+    LiveSum L{};
+    if constexpr (LIVE_G) L = live_sum_setup<MODE>(p, T_tot, sh.gprev);
+    const double tol = (MODE == MODE_ADJ) ? p.tol * T_tot : p.tol;
+    const int rmode = p.read_mode == READ_CACHED ? READ_CACHED : READ_COHERENT;
+    const uint64_t pol_edge = policy_evict_first();
+    const uint64_t pol_vertex = policy_evict_last();
+    int it = 0;
+    bool converged = false;
+    double last_res = 0.0;
+
+    for (; it < p.max_iters; ++it) {
+        const int slot = it % 3;
+        const unsigned stamp = (unsigned)it + 1u;
+        float res_part = 0.0f, g_part = 0.0f, dg_part = 0.0f;
+        float gt = 0.0f;
+        // the look-back this warp still owes (warp-uniform): tile, its first row, the tile's partial of it,
+        // whether the row ends in the tile (else the tile's published aggregate is upgraded), its inputs
+        int pend_t = -1, pend_row = 0, pend_fin = 0;
+        uint32_t pend_val = 0u, pend_xo = 0u;
+        float pend_dg = 0.0f;
+        bool ok = true;
+
+        // Adds the partials published by the tiles before pend_t back to the first inclusive one, then
+        // finishes the pending row or publishes the tile's inclusive partial. The warp looks back 32
+        // tiles at a time, one per lane (lane i reads tile hi - i), as in a single-pass scan's look-back:
+        // the nearest inclusive entry ends the walk, the partials after it are reduced over the lanes.
+        auto resolve = [&]() {
+            if (pend_t < 0) return;
+            uint32_t C = O::identity();
+            for (int hi = pend_t - 1; ok;) {
+                const int j = hi - lane;
+                unsigned long long v = 0ull;
+                bool got = true;
+                if (j >= 0) got = wait_tile(pub, j, stamp, sb, p.timeout_ns, &v);
+                ok = __all_sync(FULL, got) != 0;
+                if (!ok) break;
+                const unsigned incl = __ballot_sync(FULL, j >= 0 && (((unsigned)(v >> 32)) & TPUB_INCL) != 0);
+                const int stop = incl ? __ffs(incl) - 1 : 31;  // the nearest inclusive entry, else the whole window
+                uint32_t mine = (j >= 0 && lane <= stop) ? (uint32_t)v : O::identity();
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) mine = O::combine(mine, __shfl_xor_sync(FULL, mine, o));
+                C = O::combine(C, mine);
+                if (incl || hi < 32) break;  // tile 0 is always inclusive, so the walk ends by then
+                hi -= 32;
+            }
+            if (ok && lane == 0) {
+                const uint32_t total = O::combine(C, pend_val);
+                if (pend_fin) {
+                    const uint32_t xnew =
+                        row_update<MODE>(p, pend_row, total, pend_xo, pend_dg, gt, res_part, g_part, dg_part);
+                    st_relaxed_b32(X + pend_row, xnew);
+                } else {
+                    st_relaxed_u64(pub + pend_t, ((unsigned long long)(stamp | TPUB_INCL) << 32) | total);
+                }
+            }
+            pend_t = -1;
+        };
+
+        WStage<WIPT> nx;
+        int k = 0;  // this warp's tiles so far in the sweep
+        if (w < T) wfetch<MODE, WIPT>(nx, p, X, w, lane, rmode, LIVE_G, pol_edge, pol_vertex);
+        for (int t = w; t < T && ok; t += W, ++k) {
+            const int a0 = nx.a0, b0 = nx.b0, NA = nx.NA, NB = nx.NB;
+            const bool cont = b0 > nx.rp0;  // the tile starts inside row a0
+            const uint32_t pf_xo = nx.xo;
+            const float pf_dg = nx.dg;
+            if constexpr (LIVE_G) {
+                if ((k & (LIVE_EVERY - 1)) == 0) gt = live_term<MODE>(L, warp_sum(nx.gs));
+            }
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < WIPT; ++q) {
+                const int j = lane + 32 * q;
+                if (j < NB) val[j] = nx.term[q];
+            }
+            for (int i = lane; i < NA; i += 32) end[i] = (int)ld_vertex_b32(p.rowptr + a0 + i + 1, pol_vertex) - b0;
+            if (lane == 0) end[NA] = INT_MAX;
+            if (t + W < T)
+                wfetch<MODE, WIPT>(nx, p, X, t + W, lane, rmode, LIVE_G && ((k + 1) & (LIVE_EVERY - 1)) == 0,
+                                   pol_edge, pol_vertex);
+            __syncwarp();
+            const uint32_t trail = wwalk<MODE, WIPT>(end, val, sum, NA, NB, O::identity(), lane);
+            __syncwarp();
+            // the partial of the row left unfinished: inclusive unless the tile lies inside a row begun before
+            const bool incl = NA > 0 || !cont;
+            if (lane == 0)
+                st_relaxed_u64(pub + t, ((unsigned long long)(stamp | (incl ? TPUB_INCL : 0u)) << 32) | trail);
+
+            // -------- rows this tile completed (its first one, begun before, waits for the look-back) --------
+            const int skip = (cont && NA > 0) ? 1 : 0;
+            const uint32_t first_sum = __shfl_sync(FULL, NA > 0 ? sum[0] : 0u, 0);
+            uint32_t xo_k[WIPT];
+            float dg_k[WIPT];
+            xo_k[0] = pf_xo;
+            dg_k[0] = pf_dg;
+#pragma unroll
+            for (int q = 1; q < WIPT; ++q) {
+                const int r = lane + 32 * q;
+                xo_k[q] = 0u;
+                dg_k[q] = 0.0f;
+                if (r < NA) {
+                    xo_k[q] = ld_weak_b32(X + a0 + r);
+                    if constexpr (!BF) dg_k[q] = ld_stream_f32(p.degf + a0 + r);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < WIPT; ++q) {
+                const int r = lane + 32 * q;
+                if (r >= NA || (q == 0 && lane == 0 && skip)) continue;
+                const int v = a0 + r;
+                const uint32_t xnew = row_update<MODE>(p, v, sum[r], xo_k[q], dg_k[q], gt, res_part, g_part, dg_part);
+                st_relaxed_b32(X + v, xnew);
+            }
+            // -------- the previous tile's look-back, then this tile's becomes pending --------
+            resolve();
+            if (cont) {
+                pend_t = t;
+                pend_row = a0;
+                pend_fin = NA > 0 ? 1 : 0;
+                pend_val = NA > 0 ? first_sum : trail;
+                pend_xo = __shfl_sync(FULL, pf_xo, 0);
+                pend_dg = __shfl_sync(FULL, pf_dg, 0);
+            }
+            if constexpr (LIVE_G) {
+                if ((k & (LIVE_EVERY - 1)) == LIVE_EVERY - 1) {  // this warp's change of N
+                    const float s = warp_sum(dg_part);
+                    dg_part = 0.0f;
+                    if (lane == 0 && s != 0.0f) live_add(sb, w % GSTRIPES, s, L.S);
+                }
+            }
+        }  // tiles
+        resolve();
+        if constexpr (LIVE_G) {
+            const float s = warp_sum(dg_part);
+            dg_part = 0.0f;
+            if (lane == 0 && s != 0.0f) live_add(sb, w % GSTRIPES, s, L.S);
+        }
+
+        // -------- end of sweep: residual, barrier, stopping rule --------
+        double res_d = (double)res_part, g_d = (double)g_part;
+        block_sum2(sh, res_d, g_d);
+        if (tid == 0 && res_d != 0.0) atomicAdd(&sb->acc_res[slot], res_d);
+        if (!grid_barrier(sb, p.nblocks, bar_target, p.timeout_ns)) return;
+        if (tid == 0) {
+            sh.res = ld_relaxed_f64(&sb->acc_res[slot]);
+            if (c == 0) {
+                const int dead = (it + 2) % 3;  // read by everyone before this barrier
+                sb->acc_res[dead] = 0.0;
+                sb->acc_g[dead] = 0.0;
+            }
+        }
+        __syncthreads();
+        last_res = sh.res;
+        if (last_res <= tol) {
+            converged = true;
+            ++it;
+            break;
+        }
+    }
+
+    // ---------------- output ----------------
+    for (long long vv = gtid; vv < p.n; vv += gthreads) {
+        const int v = (int)vv;
+        const uint32_t x = ld_relaxed_b32(X + v);
+        if constexpr (BF || MODE == MODE_ADJ || MODE == MODE_PRW) {
+            ((uint32_t*)p.out)[v] = x;
+        } else {
+            const float dg = p.degf[v];
+            ((float*)p.out)[v] = dg > 0.0f ? __uint_as_float(x) * dg : __uint_as_float(x);
+        }
+    }
+    if (tid == 0 && c == 0) {
+        sb->iters = it;
+        sb->residual = last_res;
+        sb->converged = converged ? 1 : 0;
+    }
+}
+
+const void* sweep_ordered_kernel_ptr(int mode, int ipt)
+{
+#define DAG_ORD_ROW(I)                                                                                        \
+    {(const void*)sweep_ordered_kernel<MODE_PR, I>, (const void*)sweep_ordered_kernel<MODE_PRW, I>,         \
+     (const void*)sweep_ordered_kernel<MODE_ADJ, I>, (const void*)sweep_ordered_kernel<MODE_BF, I>,         \
+     (const void*)sweep_ordered_kernel<MODE_BF8, I>}
+    static const void* const table[3][5] = {DAG_ORD_ROW(5), DAG_ORD_ROW(7), DAG_ORD_ROW(11)};
+#undef DAG_ORD_ROW
+    const int k = ipt == 5 ? 0 : ipt == 7 ? 1 : ipt == 11 ? 2 : -1;
+    return k < 0 ? nullptr : table[k][mode];
+}
+
 // Kernel of (mode, variant, items per lane); nullptr for a shape not built.
 const void* sweep_warp_kernel_ptr(int mode, int variant, int ipt)
 {
@@ -492,10 +790,11 @@ const void* sweep_warp_kernel_ptr(int mode, int variant, int ipt)
 // min(delta - 1 + WTILE, rows of the longest run) values per warp, clamped to
 // what fits in shared memory (flushed when the next tile might not fit).
 static int warp_shape(dag_plan* plan, int mode, int variant, int delta, int* nb_out, int* cap_out, int* clamped_out,
-                      Partition** part_out, cudaStream_t s)
+                      Partition** part_out, cudaStream_t s, bool ordered)
 {
     const int WTILE = 32 * plan->warp_ipt;
-    const void* k = sweep_warp_kernel_ptr(mode, variant, plan->warp_ipt);
+    const void* k = ordered ? sweep_ordered_kernel_ptr(mode, plan->warp_ipt)
+                            : sweep_warp_kernel_ptr(mode, variant, plan->warp_ipt);
     if (!k) return set_error(DAG_ERR_INVALID, "no warp tile of that shape");
     cudaFuncAttributes fa{};
     DAG_CUDA(cudaFuncGetAttributes(&fa, k));
@@ -552,10 +851,14 @@ int launch_warp_sweep(dag_plan* plan, int mode, int variant, int delta, SweepPar
 {
     if (p.frontier) return set_error(DAG_ERR_INVALID, "the frontier runs the CTA-tile sweeps");
     if (p.local_read || p.own_l1) return set_error(DAG_ERR_INVALID, "local and own-block reads run the CTA-tile sweeps");
+    const bool ordered = p.ordered != 0;
+    if (ordered && variant != DAG_ASYNC)
+        return set_error(DAG_ERR_INVALID, "ordered warp sweeps run the asynchronous form (delta 0)");
     int nb = 0, cap = 0, clamped = 0;
     Partition* part = nullptr;
-    int rc = warp_shape(plan, mode, variant, delta, &nb, &cap, &clamped, &part, s);
+    int rc = warp_shape(plan, mode, variant, delta, &nb, &cap, &clamped, &part, s, ordered);
     if (rc) return rc;
+    if (ordered && !part->tpub) DAG_CUDA(cudaMalloc(&part->tpub, (size_t)part->tiles * sizeof(unsigned long long)));
     p.nblocks = nb;
     p.delta = (variant == DAG_DELAYED) ? delta : 0;
     p.buf_cap = cap;
@@ -564,7 +867,8 @@ int launch_warp_sweep(dag_plan* plan, int mode, int variant, int delta, SweepPar
     p.cta_tile = part->cta_tile;
     p.tile_row = part->tile_row;
     p.tile_nz = part->tile_nz;
-    p.wpub = part->wpub;
+    p.wpub = ordered ? part->tpub : part->wpub;
+    p.ntiles = part->tiles;
     p.sync = plan->sync;
     p.timeout_ns = plan->timeout_ns;
     p.skip_barrier_cta0 = 0;
@@ -576,8 +880,10 @@ int launch_warp_sweep(dag_plan* plan, int mode, int variant, int delta, SweepPar
     }
     DAG_CUDA(cudaMemsetAsync(plan->sync, 0, sizeof(SyncBlock), s));
     // stamps of an earlier solve must not pass for this one's
-    DAG_CUDA(cudaMemsetAsync(part->wpub, 0, (size_t)part->nblocks * sizeof(unsigned long long), s));
-    const void* k = sweep_warp_kernel_ptr(mode, variant, plan->warp_ipt);
+    DAG_CUDA(cudaMemsetAsync(p.wpub, 0, (size_t)(ordered ? part->tiles : part->nblocks) * sizeof(unsigned long long),
+                             s));
+    const void* k = ordered ? sweep_ordered_kernel_ptr(mode, plan->warp_ipt)
+                            : sweep_warp_kernel_ptr(mode, variant, plan->warp_ipt);
     const size_t dyn = (size_t)WWARPS * (size_t)cap * 4;
     DAG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     void* args[] = {(void*)&p};

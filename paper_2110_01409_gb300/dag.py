@@ -25,7 +25,8 @@ READ_MODES = {"refresh": 0, "coherent": 2, "cached": 4,  # delayed form's reads 
               "local": 8, "local+coherent": 10, "local+cached": 12,
               "own_l1": 16,  # async form: own block through L1 (DAG_READ_OWN_L1)
               "frontier": 32, "own_l1+frontier": 48,  # Bellman-Ford: run only changed tiles (DAG_SSSP_FRONTIER)
-              "warp": 64, "warp+coherent": 66, "warp+cached": 68}  # one worker per warp (DAG_WARP_WORKERS)
+              "warp": 64, "warp+coherent": 66, "warp+cached": 68,  # one worker per warp (DAG_WARP_WORKERS)
+              "ordered": 128, "ordered+cached": 132}  # async: warps take the path's tiles in turn (DAG_WARP_ORDERED)
 
 EXPORTS = (
     "dag_plan_create", "dag_plan_destroy", "dag_plan_out_degree", "dag_partition", "dag_workers",

@@ -53,8 +53,10 @@ def test_committed_record_parses():
                 k, v = line.split(":", 1)
                 keys[k.strip()] = v.strip()
     assert len(keys["sweep_source_sha256"]) == 64
-    for kernel in ("sweep_tma_kernel<BF8>", "sweep_tma_kernel<PR>"):
-        assert float(keys[f"{kernel} rmat{bench.SCALE} dram_bytes_per_sweep"]) > 0
+    figures = {k: float(v) for k, v in keys.items() if k != "sweep_source_sha256"}
+    assert figures and all(v > 0 for v in figures.values())
+    assert all(k.endswith((f"rmat{bench.SCALE} dram_bytes_per_sweep", f"rmat{bench.SCALE} dram_bytes_per_edge_run"))
+               for k in figures)
     assert float(keys[f"sweep_tma_kernel<BF8,frontier> rmat{bench.SCALE} dram_bytes_per_edge_run"]) > 0
     if keys["sweep_source_sha256"] != bench.sweep_source_hash():
         pytest.skip("kernel sources changed since the capture: the bench reports traffic as null")

@@ -76,25 +76,30 @@ def _l1(r, ref):
     return float(np.abs(r.double().cpu().numpy() - ref).sum())
 
 
-# every (variant, delta, reads) the benchmark's tuner or variant table runs on the scale-22 graph
-PR_FULL = [("sync", 0, "refresh"), ("async", 0, "refresh"), ("async", 0, "own_l1"), ("delayed", 32, "refresh"),
-           ("delayed", 256, "refresh"), ("delayed", 4096, "refresh"), ("delayed", 4096, "local"),
-           ("sync", 0, "warp"), ("async", 0, "warp+cached"), ("delayed", 16, "warp"), ("delayed", 256, "warp+cached")]
-SSSP_FULL = PR_FULL + [("sync", 0, "frontier"), ("async", 0, "frontier"), ("async", 0, "own_l1+frontier")]
+# every (variant, delta, reads, warp tile items per lane) the benchmark's tuner or variant table runs on the
+# scale-22 graph
+PR_FULL = [("sync", 0, "refresh", 7), ("async", 0, "refresh", 7), ("async", 0, "own_l1", 7),
+           ("delayed", 32, "refresh", 7), ("delayed", 256, "refresh", 7), ("delayed", 4096, "refresh", 7),
+           ("delayed", 4096, "local", 7), ("sync", 0, "warp", 7), ("async", 0, "warp+cached", 5),
+           ("async", 0, "warp+cached", 7), ("async", 0, "warp+cached", 11), ("delayed", 16, "warp", 7),
+           ("delayed", 256, "warp+cached", 7), ("async", 0, "ordered+cached", 7), ("async", 0, "ordered+cached", 11)]
+SSSP_FULL = PR_FULL + [("sync", 0, "frontier", 7), ("async", 0, "frontier", 7), ("async", 0, "own_l1+frontier", 7)]
 
 
-@pytest.mark.parametrize("variant,delta,reads", PR_FULL)
-def test_pagerank_full_size_against_fixed_point(big, big_rstar, variant, delta, reads):
+@pytest.mark.parametrize("variant,delta,reads,ipt", PR_FULL)
+def test_pagerank_full_size_against_fixed_point(big, big_rstar, variant, delta, reads, ipt):
     dag, g, w, srcs, plan, w8, src_e, dst_e = big
+    plan.set_warp_tile(ipt)
     r, st = dag.pagerank(plan, 0.85, 1e-6, variant, delta, 1000, reads=reads)
     assert st["converged"], st
     assert _l1(r, big_rstar) <= 1e-5
     assert abs(float(r.double().sum()) - 1.0) <= 1e-5
 
 
-@pytest.mark.parametrize("variant,delta,reads", SSSP_FULL)
-def test_sssp_full_size_optimal(big, variant, delta, reads):
+@pytest.mark.parametrize("variant,delta,reads,ipt", SSSP_FULL)
+def test_sssp_full_size_optimal(big, variant, delta, reads, ipt):
     dag, g, w, srcs, plan, w8, src_e, dst_e = big
+    plan.set_warp_tile(ipt)
     sources = srcs if reads == "own_l1+frontier" else srcs[:2]
     for k, s in enumerate(sources):
         d, st = dag.sssp(plan, int(s), w8, variant, delta, g.n + 1, reads=reads)
@@ -121,7 +126,7 @@ BENCH_ROWS = [("sync", 0, "refresh"), ("async", 0, "refresh"), ("async", 0, "own
               ("async", 0, "frontier"), ("async", 0, "own_l1+frontier"), ("delayed", 32, "refresh"),
               ("delayed", 256, "refresh"), ("delayed", 4096, "refresh"), ("delayed", 4096, "local"),
               ("sync", 0, "warp"), ("async", 0, "warp+cached"), ("delayed", 16, "warp"),
-              ("delayed", 256, "warp+cached")]
+              ("delayed", 256, "warp+cached"), ("async", 0, "ordered+cached")]
 
 
 @pytest.fixture(scope="module", params=[c[0] for c in CONFIG3])
@@ -145,7 +150,7 @@ def test_config3_full_size(config3):
         assert st["converged"], (variant, delta, reads, st)
         _check_optimal(d.cpu().numpy().view(np.uint32), src, w, src_e, dst_e, g.n)
     for variant, delta, reads in (("async", 0, "refresh"), ("delayed", 256, "refresh"), ("async", 0, "warp+cached"),
-                                  ("async", 0, "own_l1")):
+                                  ("async", 0, "own_l1"), ("async", 0, "ordered+cached")):
         r, st = dag.pagerank(plan, 0.85, 1e-6, variant, delta, 1000, reads=reads)
         assert st["converged"], (variant, delta, reads, st)
         assert _l1(r, rstar) <= 1e-5, (variant, delta, reads)

@@ -18,7 +18,8 @@ pytestmark = pytest.mark.gpu
 
 VARIANTS = [("sync", 0, "warp"), ("async", 0, "warp"), ("async", 0, "warp+cached"), ("delayed", 1, "warp"),
             ("delayed", 16, "warp"), ("delayed", 256, "warp"), ("delayed", 4096, "warp"),
-            ("delayed", 256, "warp+coherent"), ("delayed", 256, "warp+cached")]
+            ("delayed", 256, "warp+coherent"), ("delayed", 256, "warp+cached"),
+            ("async", 0, "ordered"), ("async", 0, "ordered+cached")]
 
 
 @pytest.fixture(scope="module")
@@ -98,9 +99,10 @@ def test_warp_weighted_pagerank_and_teleport(dag):
     t = np.zeros(g.n)
     t[[5, 99, 4000]] = 1.0 / 3.0
     rstar = oracle.pagerank_fixed_point(g, 0.85, tele=t, val=vref)
-    for variant, delta in (("sync", 0), ("async", 0), ("delayed", 64)):
+    for variant, delta, reads in (("sync", 0, "warp"), ("async", 0, "warp"), ("delayed", 64, "warp"),
+                                  ("async", 0, "ordered")):
         r, st = dag.pagerank(plan, 0.85, 1e-6, variant, delta, teleport=torch.from_numpy(t.astype(np.float32)).cuda(),
-                             val=val, reads="warp")
+                             val=val, reads=reads)
         assert st["converged"] and _l1(r, rstar) <= 1e-5
 
 
@@ -145,10 +147,31 @@ def test_warp_tile_shapes(dag, ipt):
             rstar = oracle.pagerank_fixed_point(g, 0.85, tol=1e-11, threads=4)
         w = I.weights_u32(g, 7)
         ref = oracle.dijkstra(g, w, 1)
-        for variant, delta, reads in (("async", 0, "warp+cached"), ("delayed", 64, "warp"), ("sync", 0, "warp")):
+        for variant, delta, reads in (("async", 0, "warp+cached"), ("delayed", 64, "warp"), ("sync", 0, "warp"),
+                                      ("async", 0, "ordered+cached")):
             r, st = dag.pagerank(plan, 0.85, 1e-6, variant, delta, reads=reads)
             assert st["converged"] and _l1(r, rstar) <= 1e-5
             dd, st2 = dag.sssp(plan, 1, torch.from_numpy(w.astype(np.uint8)).cuda(), variant, delta, reads=reads)
             assert st2["converged"] and np.array_equal(dd.cpu().numpy().view(np.uint32), ref)
     with pytest.raises(dag.DagError):
         dag.Plan.from_graph(GRAPHS[0], "cuda").set_warp_tile(6)
+
+
+def test_ordered_refuses_sync_and_delayed(dag):
+    g = I.rmat(10, 16, seed=1)
+    plan = dag.Plan.from_graph(g, "cuda")
+    for variant, delta in (("sync", 0), ("delayed", 16)):
+        with pytest.raises(dag.DagError) as ei:
+            dag.pagerank(plan, 0.85, 1e-6, variant, delta, reads="ordered")
+        assert ei.value.code == dag.ERR_INVALID
+
+
+def test_ordered_barrier_timeout_leaves_context_usable(dag):
+    g = I.rmat(12, 16, seed=2)
+    plan = dag.Plan.from_graph(g, "cuda")
+    plan.debug_skip_barrier_once(100)
+    with pytest.raises(dag.DagError) as ei:
+        dag.pagerank(plan, 0.85, 1e-6, "async", 0, reads="ordered")
+    assert ei.value.code == dag.ERR_BARRIER_TIMEOUT
+    r, st = dag.pagerank(plan, 0.85, 1e-6, "async", 0, reads="ordered")
+    assert st["converged"] and _l1(r, oracle.pagerank_fixed_point(g, 0.85)) <= 1e-5
