@@ -38,8 +38,9 @@ PR_DELTA, SSSP_DELTA = 32, 32  # fixed-delta runs of the variant table and the C
 DELTAS = (0, 32, 256, 4096)
 WORKLOAD = (f"rmat{SCALE}: pagerank d=0.85 tol=1e-6 + sssp x{N_SOURCES} sources, "
             f"delayed method, delta picked per algorithm over {list(DELTAS)} "
-            f"(delta 0 also with own-block L1 reads, and for sssp the tile frontier) "
-            f"and over warp-worker sweeps (sync, delta 16 / 256, async with three warp tile shapes)")
+            f"(delta 0 also with own-block or all L1 reads, and for sssp the tile frontier on CTA or warp tiles) "
+            f"and over warp-worker sweeps (sync, delta 16 / 256, async with three warp tile shapes) "
+            f"and ordered warp sweeps (async, two warp tile shapes)")
 
 
 HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e, nominal (the roofline's frac uses the measured copy peak)
@@ -148,7 +149,7 @@ def build_inputs():
 
 def _cand(c):
     v = "sync" if c["variant"] == "sync" else str(c["delta"])
-    tile = f"x{c['warp_tile']}" if c["reads"].startswith("warp") else ""
+    tile = f"x{c['warp_tile']}" if c["reads"].startswith(("warp", "ordered")) else ""
     return v + ("" if c["reads"] == "refresh" else "+" + c["reads"]) + tile
 
 
@@ -202,8 +203,9 @@ def run_gpu(args):
     warp_cands = [("sync", 0, "warp"), ("delayed", 16, "warp"), ("delayed", 256, "warp+cached")] + \
         [("delayed", 0, "warp+cached", ipt) for ipt in (5, 7, 11)] + \
         [("delayed", 0, "ordered+cached", ipt) for ipt in (7, 11)]
-    cands = [("delayed", dl) for dl in DELTAS] + [("delayed", 0, "own_l1")] + warp_cands
-    cands_bf = cands + [("delayed", 0, "frontier"), ("delayed", 0, "own_l1+frontier")]
+    cands = [("delayed", dl) for dl in DELTAS] + [("delayed", 0, "own_l1"), ("delayed", 0, "cached")] + warp_cands
+    cands_bf = cands + [("delayed", 0, "frontier"), ("delayed", 0, "own_l1+frontier"), ("delayed", 0, "cached+frontier"),
+                        ("delayed", 0, "warp+frontier"), ("delayed", 0, "warp+cached+frontier")]
     tune_pr = autotune.tune(plan, "pagerank", candidates=cands, worker_fractions=[1.0], trials=2, cache=None)
     tune_bf = autotune.tune(plan, "sssp", candidates=cands_bf, worker_fractions=[1.0], trials=2, cache=None,
                             src=int(srcs[0]), w=w8_d)
@@ -349,8 +351,8 @@ def run_gpu(args):
                    "variant": {"pagerank": pr_var, "sssp": bf_var},
                    "delta": {"pagerank": pr_dl, "sssp": bf_dl},
                    "reads": {"pagerank": pr_rd, "sssp": bf_rd},
-                   "warp_tile_items": {"pagerank": 32 * pr_tile if pr_rd.startswith("warp") else None,
-                                       "sssp": 32 * bf_tile if bf_rd.startswith("warp") else None},
+                   "warp_tile_items": {"pagerank": 32 * pr_tile if pr_rd.startswith(("warp", "ordered")) else None,
+                                       "sssp": 32 * bf_tile if bf_rd.startswith(("warp", "ordered")) else None},
                    "autotune_ms": {"pagerank": {_cand(c): round(c["ms"], 3) for c in tune_pr["candidates"]
                                                 if "ms" in c},
                                    "sssp": {_cand(c): round(c["ms"], 3) for c in tune_bf["candidates"]
@@ -384,6 +386,8 @@ def run_gpu(args):
 def kernel_name(mode, variant, delta, reads, warp_tile=7):
     """The sweep kernel a solve runs (for the roofline's kernel and the ncu launch list)."""
     var = "ASYNC" if variant == "async" or (variant == "delayed" and delta == 0) else variant.upper()
+    if reads.startswith("warp") and "frontier" in reads:
+        return f"sweep_warp_frontier_kernel<{mode},{warp_tile}>"
     if reads.startswith("warp"):
         return f"sweep_warp_kernel<{mode},{var},{warp_tile}>"
     if reads.startswith("ordered"):
@@ -509,6 +513,9 @@ def _variant_rows(dag, torch, plan, g, src, w_d, variants, trials=3):
 VARIANT_ROWS = [("sync", "sync", 0, "refresh"), ("async", "async", 0, "refresh"),
                 ("async_own_l1", "async", 0, "own_l1"), ("sync_frontier", "sync", 0, "frontier"),
                 ("async_frontier", "async", 0, "frontier"), ("async_own_l1_frontier", "async", 0, "own_l1+frontier"),
+                ("async_cached", "async", 0, "cached"), ("async_cached_frontier", "async", 0, "cached+frontier"),
+                ("warp_async_frontier", "async", 0, "warp+frontier"),
+                ("warp_async_cached_frontier", "async", 0, "warp+cached+frontier"),
                 ("delayed32", "delayed", 32, "refresh"), ("delayed256", "delayed", 256, "refresh"),
                 ("delayed4096", "delayed", 4096, "refresh"), ("delayed4096_local", "delayed", 4096, "local"),
                 ("warp_sync", "sync", 0, "warp"), ("warp_async_cached", "async", 0, "warp+cached"),

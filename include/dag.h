@@ -120,7 +120,11 @@ int dag_plan_set_worker_cap(dag_plan* plan, int32_t max_workers);
  * sets both how often a worker publishes and how often it takes in others'
  * values. DAG_READ_COHERENT: every read goes to L2, the point where all CTAs'
  * stores meet (as fresh as the asynchronous form). DAG_READ_CACHED: ordinary
- * loads refreshed only by the grid barrier between sweeps.
+ * loads refreshed only by the grid barrier between sweeps. The asynchronous
+ * form takes DAG_READ_CACHED too: its gathers then become ordinary loads (L1)
+ * refreshed by the grid barrier instead of L2 loads, so a value read is at
+ * most one sweep old (still as fresh as the synchronous form's) while its own
+ * stores stay in place; with DAG_SSSP_FRONTIER as well.
  */
 #define DAG_READ_COHERENT 2
 #define DAG_READ_CACHED 4
@@ -164,8 +168,13 @@ int dag_plan_set_worker_cap(dag_plan* plan, int32_t max_workers);
  * the earlier runs' partial sums at the end of the sweep. delta counts rows
  * per warp (each warp has its own buffer). No CTA-wide barrier inside a sweep.
  * The asynchronous form reads through L2 (DAG_READ_CACHED: ordinary loads,
- * refreshed by the barrier between sweeps). DAG_ERR_INVALID with
- * DAG_SSSP_FRONTIER, DAG_READ_LOCAL or DAG_READ_OWN_L1.
+ * refreshed by the barrier between sweeps). With DAG_SSSP_FRONTIER
+ * (asynchronous Bellman-Ford only) each warp also lists its rows that got a
+ * smaller distance; after a sweep whose changed rows have few out-edges (at
+ * most dag_plan_set_warp_frontier_marks per warp tile, 1 by default) only the
+ * warp tiles holding those out-edges run, claimed by any warp, each row they
+ * touch relaxed with an atomic minimum. DAG_ERR_INVALID with DAG_READ_LOCAL,
+ * DAG_READ_OWN_L1, or DAG_SSSP_FRONTIER in another form.
  */
 #define DAG_WARP_WORKERS 64
 /*
@@ -188,6 +197,14 @@ int dag_plan_set_worker_cap(dag_plan* plan, int32_t max_workers);
 int dag_plan_set_warp_tile(dag_plan* plan, int32_t items_per_lane);
 /* Items (rows + in-edges) per warp tile of the plan's warp-worker sweeps (the default shape's for NULL). */
 int32_t dag_warp_tile_items(const dag_plan* plan);
+/*
+ * Warp-tile frontier (DAG_WARP_WORKERS | DAG_SSSP_FRONTIER): the next sweep
+ * runs only the stamped warp tiles when the out-degree sum of the rows the
+ * sweep lowered is at most marks_per_tile x the warp tiles; 1 when a plan is
+ * created, 0 keeps every sweep dense. A tuning choice. DAG_ERR_INVALID for a
+ * value outside [0, 1e6] or a null plan.
+ */
+int dag_plan_set_warp_frontier_marks(dag_plan* plan, float marks_per_tile);
 
 /*
  * PageRank (Sec. IV-A; stopping rule Sec. IV):
@@ -201,7 +218,8 @@ int32_t dag_warp_tile_items(const dag_plan* plan);
  * values, Sec. III-B; delta >= rows per CTA flushes once per sweep). d_rank
  * (device, float [n]) receives r; with DAG_PR_WARM_START it also gives r^0.
  * Without it r^0 = t. FP32 values, FP64 residual and dangling sums.
- * flags: DAG_PR_WARM_START | one DAG_READ_* (delayed form only) | DAG_READ_OWN_L1 (async form only).
+ * flags: DAG_PR_WARM_START | one DAG_READ_* (delayed form; the async form takes DAG_READ_CACHED) |
+ * DAG_READ_OWN_L1 (async form only).
  * A delayed sweep with 0 < delta < dag_tile_items() cuts its tiles so that
  * none completes more than delta rows, so the buffer is flushed after about
  * every delta rows (a tile's rows are computed together and flushed at its end).
@@ -215,7 +233,7 @@ int dag_pagerank(dag_plan* plan, float d, double tol, dag_variant variant, int32
  * dist_u finite of dist_u + w_uv), every value stored every sweep, changed
  * or not (Sec. IV); stops after a sweep that lowered no value. d_w: uint32 weight per in-edge (device, [m]); d_dist (device,
  * uint32 [n]) receives the distances, 0xFFFFFFFF for unreachable vertices.
- * flags: DAG_READ_* (delayed form only) | DAG_READ_OWN_L1 (async form only) |
+ * flags: DAG_READ_* (delayed form; the async form takes DAG_READ_CACHED) | DAG_READ_OWN_L1 (async form only) |
  * DAG_SSSP_FRONTIER (sync and async forms).
  */
 int dag_sssp(dag_plan* plan, uint32_t src, dag_variant variant, int32_t delta, int32_t max_iters,

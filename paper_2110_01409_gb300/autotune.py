@@ -30,13 +30,14 @@ _lock = threading.Lock()
 
 # (variant, delta[, reads[, warp tile items per lane]]); reads defaults to "refresh" (see
 # dag.READ_MODES), the warp tile to 7 items per lane (used by the "warp..." and "ordered..." read paths only)
-SINGLE_CANDIDATES = [("sync", 0), ("async", 0), ("async", 0, "own_l1"), ("delayed", 32), ("delayed", 256),
-                     ("delayed", 4096), ("delayed", 4096, "local"),
+SINGLE_CANDIDATES = [("sync", 0), ("async", 0), ("async", 0, "own_l1"), ("async", 0, "cached"), ("delayed", 32),
+                     ("delayed", 256), ("delayed", 4096), ("delayed", 4096, "local"),
                      ("sync", 0, "warp"), ("async", 0, "warp+cached"), ("async", 0, "warp+cached", 5),
                      ("async", 0, "warp+cached", 11), ("delayed", 16, "warp"), ("delayed", 256, "warp+cached"),
                      ("async", 0, "ordered+cached", 7), ("async", 0, "ordered+cached", 11)]
 WARP_TILES = (5, 7, 11)
-SSSP_EXTRA = [("async", 0, "frontier"), ("async", 0, "own_l1+frontier")]  # Bellman-Ford only
+SSSP_EXTRA = [("async", 0, "frontier"), ("async", 0, "own_l1+frontier"), ("async", 0, "cached+frontier"),
+              ("async", 0, "warp+frontier"), ("async", 0, "warp+cached+frontier")]  # Bellman-Ford only
 BATCH_CANDIDATES = [("sync", 0), ("async", 0), ("delayed", 4), ("delayed", 16)]
 WORKER_FRACTIONS = [1.0, 0.5]
 
@@ -121,7 +122,7 @@ def tune(plan: dag.Plan, algo: str, candidates=None, worker_fractions=None, tria
         hit = _load(cache).get(key)
         if hit:
             plan.set_worker_cap(hit["workers"])
-            if str(hit.get("reads", "")).startswith("warp"):
+            if dag.uses_warp_tile(str(hit.get("reads", ""))):
                 plan.set_warp_tile(hit.get("warp_tile", 7))
             return hit
     plan.set_worker_cap(0)
@@ -138,7 +139,7 @@ def tune(plan: dag.Plan, algo: str, candidates=None, worker_fractions=None, tria
         for variant, delta, reads, ipt in cands:
             times, sweeps = [], []
             try:
-                if reads.startswith("warp"):
+                if dag.uses_warp_tile(reads):
                     plan.set_warp_tile(ipt)
                 for _ in range(trials):
                     ms, st = _run(plan, algo, variant, delta, reads, kw)
@@ -157,7 +158,7 @@ def tune(plan: dag.Plan, algo: str, candidates=None, worker_fractions=None, tria
     if signal is not None:
         choice["locality"] = signal
     plan.set_worker_cap(best["workers"])
-    if best["reads"].startswith("warp"):
+    if dag.uses_warp_tile(best["reads"]):
         plan.set_warp_tile(best["warp_tile"])
     if cache:
         _store(cache, key, choice)

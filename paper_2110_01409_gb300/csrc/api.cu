@@ -202,14 +202,19 @@ int sssp_impl(dag_plan* plan, uint32_t src, int variant, int delta, int max_iter
     p.frontier = (flags & DAG_SSSP_FRONTIER) ? 1 : 0;
     p.warp = (flags & (DAG_WARP_WORKERS | DAG_WARP_ORDERED)) ? 1 : 0;
     p.ordered = (flags & DAG_WARP_ORDERED) ? 1 : 0;
-    if (p.warp && p.frontier) return set_error(DAG_ERR_INVALID, "the frontier runs the CTA-tile sweeps");
     if (p.frontier && var == DAG_DELAYED)
         return set_error(DAG_ERR_INVALID, "the frontier runs the synchronous and asynchronous forms (delta 0)");
+    if (p.frontier && p.warp && (var != DAG_ASYNC || p.ordered))
+        return set_error(DAG_ERR_INVALID, "the warp-tile frontier runs the asynchronous form on warp runs");
     if (p.frontier) {  // the frontier maps of this launch shape are built (once) outside the timed solve
-        int nb0 = 0, cap0 = 0;
-        Partition* part = nullptr;
-        rc = sweep_shape(plan, w8 ? MODE_BF8 : MODE_BF, var, delta, &nb0, &cap0, &part, s);
-        if (rc == DAG_OK) rc = frontier_maps(plan, part, s);
+        if (p.warp) {
+            rc = warp_frontier_maps(plan, w8 ? MODE_BF8 : MODE_BF, s);
+        } else {
+            int nb0 = 0, cap0 = 0;
+            Partition* part = nullptr;
+            rc = sweep_shape(plan, w8 ? MODE_BF8 : MODE_BF, var, delta, &nb0, &cap0, &part, s);
+            if (rc == DAG_OK) rc = frontier_maps(plan, part, s);
+        }
         if (rc) return rc;
     }
     Timer tm;

@@ -119,6 +119,7 @@ struct SweepParams {
     int* fr_chg;            // [n] the CTAs' rows that changed in the current sweep
     int* fr_glist;          // [tiles] shared sweeps: the tiles any CTA may claim
     int* fr_gchg;           // [n + tiles] shared sweeps: rows logged as changed (a row may repeat)
+    float fr_sparse;        // warp-tile frontier: a sweep is sparse after one whose marks <= fr_sparse per tile
     // warp workers (sweep_warp.cu): cta_row / cta_tile hold each warp's first row / tile
     int warp;                     // 1: one worker per warp
     int ordered;                  // 1: warps take the tiles of the whole merge path in turn (async form)
@@ -169,6 +170,7 @@ struct dag_plan {
     long long skip_timeout_ns = 0;
     int worker_cap = 0;       // > 0: at most this many CTAs per solve (more rows per CTA)
     int warp_ipt = 7;         // items per lane of the warp-worker tiles (5, 7 or 11)
+    float fr_sparse_warp = 1.0f;  // warp-tile frontier: marks per tile at or below which the next sweep is sparse
     // per-vertex data
     int* outdeg = nullptr;    // [n]
     float* degf = nullptr;    // [n]
@@ -241,6 +243,8 @@ int sweep_rows(dag_plan* plan, int mode, int lo, int hi, SweepParams& p, double*
 // sweep_warp.cu
 const void* sweep_warp_kernel_ptr(int mode, int variant, int ipt);
 const void* sweep_ordered_kernel_ptr(int mode, int ipt);
+const void* sweep_warp_frontier_kernel_ptr(int mode, int ipt);
+int warp_frontier_maps(dag_plan* plan, int mode, cudaStream_t s);
 int launch_warp_sweep(dag_plan* plan, int mode, int variant, int delta, SweepParams& p, cudaStream_t s,
                       int* out_nblocks);
 

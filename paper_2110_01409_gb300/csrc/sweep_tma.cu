@@ -287,7 +287,11 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
     double adj_sum = sh.gprev;  // adjoint: sum lambda as the sweep starts
     const double tol = (MODE == MODE_ADJ) ? p.tol * T : p.tol;
 
-    const int own_lo = row_lo, own_n = p.own_l1 ? row_hi - row_lo : 0;
+    // Gathers that take ordinary loads (L1): the CTA's own block with DAG_READ_OWN_L1 (as fresh as L2: only
+    // this CTA writes it), every vertex with DAG_READ_CACHED (a view refreshed by the grid barrier, so a value
+    // is at most one sweep old, which the stopping rule tolerates: a sweep that changes nothing read fresh values)
+    const bool cached = p.read_mode == READ_CACHED;
+    const int own_lo = cached ? 0 : row_lo, own_n = cached ? p.n : p.own_l1 ? row_hi - row_lo : 0;
     const uint64_t pol_edge = policy_evict_first();
     const uint64_t pol_vertex = policy_evict_last();
     int it = 0;
@@ -311,7 +315,7 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
         // write is then an atomicMin (a partial row is as valid a relaxation as a
         // whole one) and own-block L1 reads are off (any CTA may write any row).
         const bool shared = FRONTIER && !dense;
-        const int own_n_sweep = shared ? 0 : own_n;
+        const int own_n_sweep = (shared && !cached) ? 0 : own_n;
         int next_own = tile_lo;  // own sweeps: the next tile to hand out
         const int list_cnt = shared ? ld_relaxed_i32(&sb->fr_cnt[slot]) : 0;
         if constexpr (FRONTIER) {

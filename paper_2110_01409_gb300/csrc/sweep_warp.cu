@@ -38,167 +38,9 @@
 #include <climits>
 #include <cstdint>
 
-#include "sweep_common.cuh"
+#include "sweep_warp.cuh"
 
 namespace dag {
-
-// Warp tile shapes: items per lane (odd: fewer bank conflicts in the walk);
-// the plan picks one (dag_plan_set_warp_tile), WIPT_DEFAULT unless told.
-constexpr int WIPT_DEFAULT = 7;
-constexpr int WWARPS = NWARP;        // warps per CTA (block reductions and the grid barrier are per CTA)
-constexpr int WMINBLOCKS = 4;        // CTAs per SM the register budget is sized for
-constexpr int LIVE_EVERY = 8;        // async / delayed PageRank: a warp reads and adds to the live sum every 8
-                                     // tiles (1,792 items, the CTA-tile kernels' tile), not every tile
-
-template <int WTILE>
-struct WarpShared {
-    int end[WWARPS][WTILE + 1];      // tile-relative row ends (+ sentinel)
-    uint32_t val[WWARPS][WTILE];     // edge terms of the tile
-    uint32_t sum[WWARPS][WTILE];     // per-row reduction of the tile
-    double red0[NWARP];
-    double red1[NWARP];
-    double res, gprev, T;
-};
-
-// Inputs of the next warp tile, loaded while the current one is walked.
-template <int WIPT>
-struct WStage {
-    int a0, b0, NA, NB;
-    int rp0;              // rowptr[a0]: the tile starts inside row a0 when b0 > rp0
-    uint32_t term[WIPT];  // edge terms: gathered value, combined with the edge's weight / value
-    uint32_t xo;          // old value of row a0 + lane
-    float dg;             // its out-degree (PageRank)
-    long long gs;         // one stripe of the live global sum (async / delayed PageRank)
-};
-
-template <int MODE, int WIPT>
-__device__ __forceinline__ void wfetch(WStage<WIPT>& st, const SweepParams& p, const uint32_t* xin, int t, int lane, int rmode,
-                                       bool live, uint64_t pol_edge, uint64_t pol_vertex)
-{
-    constexpr bool BF = MODE == MODE_BF || MODE == MODE_BF8;
-    st.a0 = p.tile_row[t];
-    st.b0 = p.tile_nz[t];
-    st.NA = p.tile_row[t + 1] - st.a0;
-    st.NB = p.tile_nz[t + 1] - st.b0;
-    st.rp0 = (int)ld_vertex_b32(p.rowptr + st.a0, pol_vertex);
-    int col[WIPT];
-    uint32_t aux[WIPT];
-#pragma unroll
-    for (int q = 0; q < WIPT; ++q) {
-        const int j = lane + 32 * q;
-        col[q] = -1;
-        aux[q] = 0u;
-        if (j < st.NB) {
-            col[q] = (int)ld_edge_b32(p.colidx + st.b0 + j, pol_edge);
-            if constexpr (MODE == MODE_BF) aux[q] = ld_edge_b32(p.w + st.b0 + j, pol_edge);
-            if constexpr (MODE == MODE_BF8) aux[q] = ld_edge_u8(p.w8 + st.b0 + j, pol_edge);
-            if constexpr (MODE == MODE_PRW || MODE == MODE_ADJ) aux[q] = ld_edge_b32(p.val + st.b0 + j, pol_edge);
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < WIPT; ++q) {
-        uint32_t term = Op<MODE>::identity();
-        if (col[q] >= 0) {
-            const uint32_t xv = rmode == READ_COHERENT ? ld_relaxed_keep_b32(xin + col[q], pol_vertex)
-                                                       : ld_weak_keep_b32(xin + col[q], pol_vertex);
-            if constexpr (BF) term = relax(xv, aux[q]);
-            else if constexpr (MODE == MODE_PR) term = xv;
-            else term = __float_as_uint(__uint_as_float(aux[q]) * __uint_as_float(xv));
-        }
-        st.term[q] = term;
-    }
-    st.xo = 0u;
-    st.dg = 0.0f;
-    if (lane < st.NA) {  // only this warp writes its rows, so a value loaded ahead is still the current one
-        st.xo = ld_weak_keep_b32(xin + st.a0 + lane, pol_vertex);
-        if constexpr (!BF) st.dg = __uint_as_float(ld_vertex_b32(p.degf + st.a0 + lane, pol_vertex));
-    }
-    if (live) st.gs = ld_relaxed_i64(&p.sync->stripe[lane * GSTRIDE]);
-}
-
-// One warp tile's merge path, warp segmented scan and per-row sums into
-// sum[0 .. NA). carry: the partial of the row continuing from the previous
-// tile; returns the partial of row NA (continuing into the next tile).
-template <int MODE, int WIPT>
-__device__ __forceinline__ uint32_t wwalk(const int* end, const uint32_t* val, uint32_t* sum, int NA, int NB,
-                                          uint32_t carry, int lane)
-{
-    using O = Op<MODE>;
-    const int L = NA + NB;
-    const int k0 = min(lane * WIPT, L);
-    int lo = max(0, k0 - NB), hi = min(k0, NA);
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (end[mid] <= k0 - 1 - mid) lo = mid + 1;
-        else hi = mid;
-    }
-    int i = lo, j = k0 - lo;
-    const int i_start = i;
-    bool emitted = false;
-    uint32_t acc = lane == 0 ? carry : O::identity();
-    int re = end[i];
-#pragma unroll
-    for (int q = 0; q < WIPT; ++q) {
-        if (k0 + q < L) {
-            if (re <= j) {
-                sum[i] = acc;
-                emitted = true;
-                acc = O::identity();
-                ++i;
-                re = end[i];
-            } else {
-                acc = O::combine(acc, val[j]);
-                ++j;
-            }
-        }
-    }
-    // inclusive segmented scan of (row in progress, partial) over the lanes
-    const int key = i;
-    uint32_t sv = acc;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t ov = __shfl_up_sync(0xffffffffu, sv, o);
-        const int ok = __shfl_up_sync(0xffffffffu, key, o);
-        if (lane >= o && ok == key) sv = O::combine(sv, ov);
-    }
-    const uint32_t cin = __shfl_up_sync(0xffffffffu, sv, 1);
-    const int kprev = __shfl_up_sync(0xffffffffu, key, 1);
-    if (lane > 0 && emitted && kprev == i_start) sum[i_start] = O::combine(sum[i_start], cin);
-    return __shfl_sync(0xffffffffu, sv, 31);
-}
-
-__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p)
-{
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v)
-{
-    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-// The partial that warp k published for sweep `stamp` (waits, bounded); false
-// when the wait ran out or another CTA recorded an error.
-__device__ __forceinline__ bool wait_published(const unsigned long long* pub, int k, unsigned stamp, SyncBlock* sb,
-                                               long long timeout_ns, uint32_t* out)
-{
-    const unsigned long long t0 = globaltimer_ns();
-    unsigned spins = 0;
-    for (;;) {
-        const unsigned long long v = ld_relaxed_u64(pub + k);
-        if ((unsigned)(v >> 32) == stamp) {
-            *out = (uint32_t)v;
-            return true;
-        }
-        if (ld_relaxed_i32(&sb->err) != 0) return false;
-        if ((++spins & 15u) == 0 && (long long)(globaltimer_ns() - t0) > timeout_ns) {
-            atomicCAS(&sb->err, 0, DAG_ERR_BARRIER_TIMEOUT);
-            return false;
-        }
-        __nanosleep(64);
-    }
-}
 
 template <int MODE, int VAR, int WIPT>
 __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_warp_kernel(const SweepParams p)
@@ -789,12 +631,20 @@ const void* sweep_warp_kernel_ptr(int mode, int variant, int ipt)
 // launch), warps = CTAs * WWARPS workers, and the delayed form's buffer of
 // min(delta - 1 + WTILE, rows of the longest run) values per warp, clamped to
 // what fits in shared memory (flushed when the next tile might not fit).
+enum WarpKind { WARP_RUNS = 0, WARP_ORDERED = 1, WARP_FRONTIER = 2 };
+
+static const void* warp_kernel(int kind, int mode, int variant, int ipt)
+{
+    if (kind == WARP_ORDERED) return sweep_ordered_kernel_ptr(mode, ipt);
+    if (kind == WARP_FRONTIER) return sweep_warp_frontier_kernel_ptr(mode, ipt);
+    return sweep_warp_kernel_ptr(mode, variant, ipt);
+}
+
 static int warp_shape(dag_plan* plan, int mode, int variant, int delta, int* nb_out, int* cap_out, int* clamped_out,
-                      Partition** part_out, cudaStream_t s, bool ordered)
+                      Partition** part_out, cudaStream_t s, int kind)
 {
     const int WTILE = 32 * plan->warp_ipt;
-    const void* k = ordered ? sweep_ordered_kernel_ptr(mode, plan->warp_ipt)
-                            : sweep_warp_kernel_ptr(mode, variant, plan->warp_ipt);
+    const void* k = warp_kernel(kind, mode, variant, plan->warp_ipt);
     if (!k) return set_error(DAG_ERR_INVALID, "no warp tile of that shape");
     cudaFuncAttributes fa{};
     DAG_CUDA(cudaFuncGetAttributes(&fa, k));
@@ -846,19 +696,46 @@ static int warp_shape(dag_plan* plan, int mode, int variant, int delta, int* nb_
     return DAG_OK;
 }
 
+// The frontier maps of the warp partition a frontier solve of this plan would use (built once, outside the
+// timed solve, as the CTA-tile frontier's are).
+int warp_frontier_maps(dag_plan* plan, int mode, cudaStream_t s)
+{
+    int nb = 0, cap = 0, clamped = 0;
+    Partition* part = nullptr;
+    int rc = warp_shape(plan, mode, DAG_ASYNC, 0, &nb, &cap, &clamped, &part, s, WARP_FRONTIER);
+    if (rc) return rc;
+    return frontier_maps(plan, part, s);
+}
+
 int launch_warp_sweep(dag_plan* plan, int mode, int variant, int delta, SweepParams& p, cudaStream_t s,
                       int* out_nblocks)
 {
-    if (p.frontier) return set_error(DAG_ERR_INVALID, "the frontier runs the CTA-tile sweeps");
     if (p.local_read || p.own_l1) return set_error(DAG_ERR_INVALID, "local and own-block reads run the CTA-tile sweeps");
     const bool ordered = p.ordered != 0;
     if (ordered && variant != DAG_ASYNC)
         return set_error(DAG_ERR_INVALID, "ordered warp sweeps run the asynchronous form (delta 0)");
+    if (p.frontier && (ordered || variant != DAG_ASYNC || (mode != MODE_BF && mode != MODE_BF8)))
+        return set_error(DAG_ERR_INVALID, "the warp-tile frontier runs the asynchronous Bellman-Ford form");
+    const int kind = p.frontier ? WARP_FRONTIER : ordered ? WARP_ORDERED : WARP_RUNS;
     int nb = 0, cap = 0, clamped = 0;
     Partition* part = nullptr;
-    int rc = warp_shape(plan, mode, variant, delta, &nb, &cap, &clamped, &part, s, ordered);
+    int rc = warp_shape(plan, mode, variant, delta, &nb, &cap, &clamped, &part, s, kind);
     if (rc) return rc;
     if (ordered && !part->tpub) DAG_CUDA(cudaMalloc(&part->tpub, (size_t)part->tiles * sizeof(unsigned long long)));
+    if (p.frontier) {
+        rc = frontier_maps(plan, part, s);
+        if (rc) return rc;
+        p.fr_orow = plan->fr_orow;
+        p.fr_otile = part->fr_otile;
+        p.fr_oend = part->fr_oend;
+        p.fr_act = part->fr_act;
+        p.fr_alist = part->fr_alist;
+        p.fr_chg = part->fr_chg;
+        p.fr_glist = part->fr_glist;
+        p.fr_gchg = part->fr_gchg;
+        p.fr_sparse = plan->fr_sparse_warp;
+        DAG_CUDA(cudaMemsetAsync(part->fr_act, 0, (size_t)std::max(part->tiles, 1) * sizeof(int), s));
+    }
     p.nblocks = nb;
     p.delta = (variant == DAG_DELAYED) ? delta : 0;
     p.buf_cap = cap;
@@ -882,8 +759,7 @@ int launch_warp_sweep(dag_plan* plan, int mode, int variant, int delta, SweepPar
     // stamps of an earlier solve must not pass for this one's
     DAG_CUDA(cudaMemsetAsync(p.wpub, 0, (size_t)(ordered ? part->tiles : part->nblocks) * sizeof(unsigned long long),
                              s));
-    const void* k = ordered ? sweep_ordered_kernel_ptr(mode, plan->warp_ipt)
-                            : sweep_warp_kernel_ptr(mode, variant, plan->warp_ipt);
+    const void* k = warp_kernel(kind, mode, variant, plan->warp_ipt);
     const size_t dyn = (size_t)WWARPS * (size_t)cap * 4;
     DAG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     void* args[] = {(void*)&p};
@@ -956,4 +832,13 @@ extern "C" int dag_plan_set_warp_tile(dag_plan* plan, int32_t items_per_lane)
 extern "C" int32_t dag_warp_tile_items(const dag_plan* plan)
 {
     return 32 * (plan ? plan->warp_ipt : dag::WIPT_DEFAULT);
+}
+
+extern "C" int dag_plan_set_warp_frontier_marks(dag_plan* plan, float marks_per_tile)
+{
+    if (!plan) return dag::set_error(DAG_ERR_INVALID, "null plan");
+    if (!(marks_per_tile >= 0.0f) || !(marks_per_tile <= 1.0e6f))
+        return dag::set_error(DAG_ERR_INVALID, "marks per tile must lie in [0, 1e6]");
+    plan->fr_sparse_warp = marks_per_tile;
+    return DAG_OK;
 }

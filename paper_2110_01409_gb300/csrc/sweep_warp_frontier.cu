@@ -1,0 +1,323 @@
+// Frontier Bellman-Ford on warp tiles: the asynchronous sweep of Sec. I with
+// the conditionally written updates of Sec. V (DAG_WARP_WORKERS together with
+// DAG_SSSP_FRONTIER, dag_sssp / dag_sssp_u8).
+//
+// Dense sweeps are the warp-worker sweep (sweep_warp.cu): every warp walks
+// its run of warp tiles, owns the rows that end in it and finishes a row that
+// straddles runs with the bounded look-back over published partials. Each
+// warp also keeps the list of its rows that got a smaller distance, and the
+// sweep's total of their out-degrees (the tile marks they would cause) goes
+// through the grid reduction with the residual. When that total is at most
+// FRW_SPARSE marks per warp tile, the next sweep is sparse: the changed rows
+// stamp the warp tiles holding their out-edges (fr_otile, in-CSR position of
+// each out-edge), the stamped tiles are gathered into one list, and the warps
+// claim that list a few tiles at a time. A tile of a sparse sweep relaxes its
+// rows with atomicMin: a row that the tile holds only part of (its first or
+// last one) gets the minimum over that part, which is as valid a relaxation as
+// the whole row's (every other in-edge's source kept its value since its tile
+// last ran). A sweep that lowers no distance ends the solve, as in Sec. IV.
+//
+// Gathers read the live array through L2 (relaxed loads) or, with
+// DAG_READ_CACHED, with ordinary loads refreshed by every grid barrier; either
+// way a tile that read a value older than a change made in the same sweep is
+// stamped again by that change for the next sweep.
+#include <algorithm>
+#include <climits>
+#include <cstdint>
+
+#include "sweep_warp.cuh"
+
+namespace dag {
+
+constexpr int FRW_CLAIM = 8;  // warp tiles a warp claims from a sparse sweep's list at once (1,792 items at 7 per lane)
+
+// Stamps s + 1 on the warp tile of every out-edge of the rows list[first], list[first + stride], ...
+// (one warp per row, its lanes over the row's out-edges).
+__device__ __forceinline__ void stamp_edge_tiles(const int* list, int cnt, const int* orow, const int* otile, int* act,
+                                                 int s, int first, int stride, int lane)
+{
+    for (int k = first; k < cnt; k += stride) {
+        const int v = list[k];
+        const int e1 = orow[v + 1];
+        for (int e = orow[v] + lane; e < e1; e += 32) act[otile[e]] = s + 1;
+    }
+}
+
+// Appends `v` of every lane with `changed` to list[*cnt ...] (one atomic per warp; order free). All lanes call it.
+__device__ __forceinline__ void log_rows(int* list, int* cnt, bool changed, int v, int lane)
+{
+    const unsigned bal = __ballot_sync(0xffffffffu, changed);
+    if (bal == 0u) return;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(cnt, __popc(bal));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (changed) list[base + __popc(bal & ((1u << lane) - 1u))] = v;
+}
+
+template <int MODE, int WIPT>
+__global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_warp_frontier_kernel(const SweepParams p)
+{
+    static_assert(MODE == MODE_BF || MODE == MODE_BF8, "frontier: Bellman-Ford only");
+    constexpr int WTILE = 32 * WIPT;
+    using O = Op<MODE>;
+    constexpr unsigned FULL = 0xffffffffu;
+    (void)WTILE;
+
+    __shared__ WarpShared<32 * WIPT> sh;
+    const int c = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wl = tid >> 5;
+    const int w = c * WWARPS + wl;
+    const int W = p.nblocks * WWARPS;
+    SyncBlock* sb = p.sync;
+    unsigned long long bar_target = 0;
+    uint32_t* X = (uint32_t*)p.x0;
+    const int row_lo = p.cta_row[w], row_hi = p.cta_row[w + 1];
+    const int t_lo = p.cta_tile[w], t_hi = p.cta_tile[w + 1];
+    int* end = sh.end[wl];
+    uint32_t* val = sh.val[wl];
+    uint32_t* sum = sh.sum[wl];
+    int* own_chg = p.fr_chg + row_lo;  // dense sweeps: this warp's changed rows (its own, so at most row_hi - row_lo)
+    const bool mid0 = t_lo < t_hi && p.tile_nz[t_lo] > p.rowptr[p.tile_row[t_lo]];
+    const bool head = mid0 && row_hi > row_lo;
+
+    for (int v = row_lo + lane; v < row_hi; v += 32) X[v] = (v == (int)p.src) ? 0u : INF;
+    if (p.skip_barrier_cta0 && c == 0) return;  // test hook: the others' waits must run out
+    if (!grid_barrier(sb, p.nblocks, bar_target, p.timeout_ns)) return;
+
+    const int rmode = p.read_mode == READ_CACHED ? READ_CACHED : READ_COHERENT;
+    const uint64_t pol_edge = policy_evict_first();
+    const uint64_t pol_vertex = policy_evict_last();
+    const double sparse_marks = (double)p.fr_sparse * (double)p.ntiles;
+    int it = 0;
+    bool converged = false, dense = true;
+    double last_res = 0.0;
+    int own_cnt = 0;  // rows on own_chg after a dense sweep (warp-uniform)
+
+    for (; it < p.max_iters; ++it) {
+        const int slot = it % 3;
+        const unsigned stamp = (unsigned)it + 1u;
+        float res_part = 0.0f, unused_g = 0.0f, unused_dg = 0.0f;
+        long long marks = 0;  // this lane's share of the out-degree sum of the rows lowered in the sweep
+        long long edges = 0;  // lane 0: edges of the tiles this warp ran
+        bool ok = true;
+
+        if (dense) {
+            // ---------------- dense sweep: the warp's run, in order ----------------
+            own_cnt = 0;
+            uint32_t carry = O::identity();
+            bool head_pending = head;
+            uint32_t head_part = O::identity();
+            WStage<WIPT> nx;
+            if (t_lo < t_hi) wfetch<MODE, WIPT>(nx, p, X, t_lo, lane, rmode, false, pol_edge, pol_vertex);
+            for (int t = t_lo; t < t_hi; ++t) {
+                const int a0 = nx.a0, b0 = nx.b0, NA = nx.NA, NB = nx.NB;
+                const uint32_t pf_xo = nx.xo;
+                __syncwarp();
+#pragma unroll
+                for (int q = 0; q < WIPT; ++q) {
+                    const int j = lane + 32 * q;
+                    if (j < NB) val[j] = nx.term[q];
+                }
+                for (int i = lane; i < NA; i += 32) end[i] = (int)ld_vertex_b32(p.rowptr + a0 + i + 1, pol_vertex) - b0;
+                if (lane == 0) end[NA] = INT_MAX;
+                if (t + 1 < t_hi) wfetch<MODE, WIPT>(nx, p, X, t + 1, lane, rmode, false, pol_edge, pol_vertex);
+                __syncwarp();
+                carry = wwalk<MODE, WIPT>(end, val, sum, NA, NB, carry, lane);
+                __syncwarp();
+                const int skip = (head_pending && NA > 0) ? 1 : 0;  // the run's first row waits for the look-back
+                if (skip && lane == 0) head_part = sum[0];
+                head_pending = head_pending && NA == 0;
+                uint32_t xo_k[WIPT];
+                xo_k[0] = pf_xo;
+#pragma unroll
+                for (int k = 1; k < WIPT; ++k) {
+                    const int r = lane + 32 * k;
+                    xo_k[k] = r < NA ? ld_weak_b32(X + a0 + r) : 0u;
+                }
+#pragma unroll
+                for (int k = 0; k < WIPT; ++k) {
+                    const int r = lane + 32 * k;
+                    if (32 * k >= NA) break;  // warp-uniform: no lane has a row in this or a later slot
+                    bool changed = false;
+                    if (r < NA && !(k == 0 && lane == 0 && skip)) {
+                        const uint32_t xnew =
+                            row_update<MODE>(p, a0 + r, sum[r], xo_k[k], 0.0f, 0.0f, res_part, unused_g, unused_dg);
+                        changed = xnew < xo_k[k];
+                        st_relaxed_b32(X + a0 + r, xnew);
+                    }
+                    const unsigned bal = __ballot_sync(FULL, changed);
+                    if (changed) own_chg[own_cnt + __popc(bal & ((1u << lane) - 1u))] = a0 + r;
+                    own_cnt += __popc(bal);
+                }
+            }
+            if (lane == 0) edges += (long long)(p.tile_nz[t_hi] - p.tile_nz[t_lo]);
+            // the row this run leaves unfinished, and the one it started inside (as in the warp-worker sweep)
+            if (lane == 0) st_relaxed_u64(p.wpub + w, ((unsigned long long)stamp << 32) | carry);
+            if (head) {
+                uint32_t s = __shfl_sync(FULL, head_part, 0);
+                for (int k = w - 1; k >= 0; --k) {
+                    uint32_t pk = 0u;
+                    if (lane == 0) ok = wait_published(p.wpub, k, stamp, sb, p.timeout_ns, &pk);
+                    ok = __shfl_sync(FULL, ok, 0) != 0;
+                    pk = __shfl_sync(FULL, pk, 0);
+                    if (!ok) break;
+                    s = O::combine(s, pk);
+                    const int tk0 = p.cta_tile[k], tk1 = p.cta_tile[k + 1];
+                    const bool k_emits = p.cta_row[k + 1] > p.cta_row[k];
+                    const bool k_mid = tk0 >= tk1 || p.tile_nz[tk0] > p.rowptr[p.tile_row[tk0]];
+                    if (k_emits || !k_mid) break;
+                }
+                if (ok) {
+                    bool changed = false;
+                    if (lane == 0) {
+                        const uint32_t xo = ld_weak_b32(X + row_lo);
+                        const uint32_t xnew = row_update<MODE>(p, row_lo, s, xo, 0.0f, 0.0f, res_part, unused_g,
+                                                               unused_dg);
+                        changed = xnew < xo;
+                        st_relaxed_b32(X + row_lo, xnew);
+                    }
+                    changed = __shfl_sync(FULL, changed, 0) != 0;
+                    if (changed && lane == 0) own_chg[own_cnt] = row_lo;
+                    own_cnt += changed ? 1 : 0;
+                }
+            }
+            __syncwarp();  // the list's entries before the lanes read them
+            for (int k = lane; k < own_cnt; k += 32) {
+                const int v = own_chg[k];
+                marks += p.fr_orow[v + 1] - p.fr_orow[v];
+            }
+        } else {
+            // ---------------- sparse sweep: the stamped tiles, claimed FRW_CLAIM at a time ----------------
+            const int cnt = ld_relaxed_i32(&sb->fr_cnt[slot]);
+            int kq = 0, kq_end = 0;  // this warp's claimed list positions [kq, kq_end)
+            auto next_tile = [&]() -> int {
+                if (kq >= kq_end) {
+                    int base = 0;
+                    if (lane == 0) base = atomicAdd(&sb->fr_head[slot], FRW_CLAIM);
+                    base = __shfl_sync(FULL, base, 0);
+                    kq = base;
+                    kq_end = min(base + FRW_CLAIM, cnt);
+                }
+                return kq < kq_end ? p.fr_glist[kq++] : -1;
+            };
+            int t = next_tile();
+            WStage<WIPT> nx;
+            if (t >= 0) wfetch<MODE, WIPT>(nx, p, X, t, lane, rmode, false, pol_edge, pol_vertex);
+            while (t >= 0) {
+                const int a0 = nx.a0, b0 = nx.b0, NA = nx.NA, NB = nx.NB;
+                const uint32_t pf_xo = nx.xo;
+                const int tn = next_tile();
+                __syncwarp();
+#pragma unroll
+                for (int q = 0; q < WIPT; ++q) {
+                    const int j = lane + 32 * q;
+                    if (j < NB) val[j] = nx.term[q];
+                }
+                for (int i = lane; i < NA; i += 32) end[i] = (int)ld_vertex_b32(p.rowptr + a0 + i + 1, pol_vertex) - b0;
+                if (lane == 0) end[NA] = INT_MAX;
+                if (tn >= 0) wfetch<MODE, WIPT>(nx, p, X, tn, lane, rmode, false, pol_edge, pol_vertex);
+                __syncwarp();
+                const uint32_t trail = wwalk<MODE, WIPT>(end, val, sum, NA, NB, O::identity(), lane);
+                __syncwarp();
+                if (lane == 0) edges += NB;
+                // rows of the tile (the first may be partial), then the partial of the row it leaves unfinished;
+                // a value read here may be older than the latest (never lower), so only a smaller sum is sent
+#pragma unroll
+                for (int k = 0; k <= WIPT; ++k) {
+                    const int r = lane + 32 * k;
+                    if (32 * k > NA) break;  // warp-uniform
+                    bool changed = false;
+                    const int v = a0 + r;
+                    uint32_t cand = INF, seen = 0u;
+                    if (r < NA) {
+                        cand = sum[r];
+                        seen = k == 0 ? pf_xo : ld_weak_b32(X + v);
+                    } else if (r == NA && v < p.n) {  // the row continuing into the next tile
+                        cand = trail;
+                        seen = ld_weak_b32(X + v);
+                    }
+                    if (cand != INF && cand < seen) {
+                        const uint32_t old = atomicMin(X + v, cand);
+                        changed = cand < old;
+                    }
+                    if (changed) {
+                        res_part += 1.0f;
+                        marks += p.fr_orow[v + 1] - p.fr_orow[v];
+                    }
+                    log_rows(p.fr_gchg, &sb->fr_nchg[slot], changed, v, lane);
+                }
+                t = tn;
+            }
+        }
+
+        // ---------------- end of sweep: rows lowered, marks, edges; barrier; stopping rule ----------------
+        double res_d = (double)res_part, g_d = (double)marks;  // marks: exact in FP64
+        block_sum2(sh, res_d, g_d);
+        if (lane == 0 && edges) atomicAdd((unsigned long long*)&sb->edges, (unsigned long long)edges);
+        if (tid == 0) {
+            if (res_d != 0.0) atomicAdd(&sb->acc_res[slot], res_d);
+            if (g_d != 0.0) atomicAdd(&sb->acc_g[slot], g_d);
+        }
+        if (!grid_barrier(sb, p.nblocks, bar_target, p.timeout_ns)) return;
+        if (tid == 0) {
+            sh.res = ld_relaxed_f64(&sb->acc_res[slot]);
+            sh.gprev = ld_relaxed_f64(&sb->acc_g[slot]);
+            sh.T = (double)ld_relaxed_i32(&sb->fr_nchg[slot]);  // (sh.T: free here) rows on the grid's list
+            if (c == 0) {
+                const int dead = (it + 2) % 3;  // read by everyone before this barrier
+                sb->acc_res[dead] = 0.0;
+                sb->acc_g[dead] = 0.0;
+                sb->fr_cnt[dead] = 0;
+                sb->fr_head[dead] = 0;
+                sb->fr_nchg[dead] = 0;
+            }
+        }
+        __syncthreads();
+        last_res = sh.res;
+        if (last_res <= 0.0) {
+            converged = true;
+            ++it;
+            break;
+        }
+        const bool was_dense = dense;
+        const int g_cnt = (int)sh.T;
+        dense = sh.gprev > sparse_marks;
+        if (!dense) {
+            // stamp the next sweep's tiles: a dense sweep's rows from each warp's own list, a sparse one's from
+            // the grid's list (shared out over all warps)
+            if (was_dense)
+                stamp_edge_tiles(own_chg, own_cnt, p.fr_orow, p.fr_otile, p.fr_act, it, 0, 1, lane);
+            else
+                stamp_edge_tiles(p.fr_gchg, g_cnt, p.fr_orow, p.fr_otile, p.fr_act, it, w, W, lane);
+            if (!grid_barrier(sb, p.nblocks, bar_target, p.timeout_ns)) return;
+            // this warp's run of tiles stamped for the next sweep goes on the grid's list
+            for (int base = t_lo; base < t_hi; base += 32) {
+                const int t = base + lane;
+                const bool on = t < t_hi && p.fr_act[t] == it + 1;
+                log_rows(p.fr_glist, &sb->fr_cnt[(it + 1) % 3], on, t, lane);
+            }
+            if (!grid_barrier(sb, p.nblocks, bar_target, p.timeout_ns)) return;
+        }
+    }
+
+    for (int v = row_lo + lane; v < row_hi; v += 32) ((uint32_t*)p.out)[v] = ld_relaxed_b32(X + v);
+    if (tid == 0 && c == 0) {
+        sb->iters = it;
+        sb->residual = last_res;
+        sb->converged = converged ? 1 : 0;
+    }
+}
+
+const void* sweep_warp_frontier_kernel_ptr(int mode, int ipt)
+{
+    if (mode != MODE_BF && mode != MODE_BF8) return nullptr;
+    const bool b8 = mode == MODE_BF8;
+    switch (ipt) {
+    case 5: return b8 ? (const void*)sweep_warp_frontier_kernel<MODE_BF8, 5> : (const void*)sweep_warp_frontier_kernel<MODE_BF, 5>;
+    case 7: return b8 ? (const void*)sweep_warp_frontier_kernel<MODE_BF8, 7> : (const void*)sweep_warp_frontier_kernel<MODE_BF, 7>;
+    case 11:
+        return b8 ? (const void*)sweep_warp_frontier_kernel<MODE_BF8, 11> : (const void*)sweep_warp_frontier_kernel<MODE_BF, 11>;
+    default: return nullptr;
+    }
+}
+
+}  // namespace dag

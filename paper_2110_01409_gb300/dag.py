@@ -21,12 +21,19 @@ OK, ERR_INVALID, ERR_NOT_CONVERGED, ERR_BARRIER_TIMEOUT, ERR_CUDA, ERR_NOMEM = 0
 SYNC, ASYNC, DELAYED = 0, 1, 2
 VARIANTS = {"sync": SYNC, "async": ASYNC, "delayed": DELAYED}
 WARM_START = 1
-READ_MODES = {"refresh": 0, "coherent": 2, "cached": 4,  # delayed form's reads (DAG_READ_*)
+READ_MODES = {"refresh": 0, "coherent": 2, "cached": 4,  # delayed form's reads (DAG_READ_*); async: cached gathers
               "local": 8, "local+coherent": 10, "local+cached": 12,
               "own_l1": 16,  # async form: own block through L1 (DAG_READ_OWN_L1)
               "frontier": 32, "own_l1+frontier": 48,  # Bellman-Ford: run only changed tiles (DAG_SSSP_FRONTIER)
+              "cached+frontier": 36,
               "warp": 64, "warp+coherent": 66, "warp+cached": 68,  # one worker per warp (DAG_WARP_WORKERS)
+              "warp+frontier": 96, "warp+cached+frontier": 100,  # async Bellman-Ford: warp-tile frontier
               "ordered": 128, "ordered+cached": 132}  # async: warps take the path's tiles in turn (DAG_WARP_ORDERED)
+
+
+def uses_warp_tile(reads: str) -> bool:
+    """True for the read paths that run warp tiles (Plan.set_warp_tile selects their shape)."""
+    return reads.startswith(("warp", "ordered"))
 
 EXPORTS = (
     "dag_plan_create", "dag_plan_destroy", "dag_plan_out_degree", "dag_partition", "dag_workers",
@@ -35,7 +42,7 @@ EXPORTS = (
     "dag_debug_skip_barrier_once", "dag_debug_stall_staging_once", "dag_tile_items", "dag_pagerank_noalloc", "dag_gather_f32", "dag_plan_set_worker_cap",
     "dag_sssp_u8", "dag_probe_gather", "dag_access_matrix", "dag_plan_set_batched_graph", "dag_warp_tile_items",
     "dag_plan_set_warp_tile", "dag_plan_last_status", "dag_sssp_batched_u8", "dag_rank_to_state",
-    "dag_state_to_rank", "dag_pagerank_sweep_rows", "dag_sssp_sweep_rows",
+    "dag_state_to_rank", "dag_pagerank_sweep_rows", "dag_sssp_sweep_rows", "dag_plan_set_warp_frontier_marks",
 )
 
 
@@ -104,6 +111,7 @@ def lib():
             L.dag_warp_tile_items.restype = _i32
             L.dag_warp_tile_items.argtypes = [_vp]
             L.dag_plan_set_warp_tile.argtypes = [_vp, _i32]
+            L.dag_plan_set_warp_frontier_marks.argtypes = [_vp, _f32]
             L.dag_plan_last_status.argtypes = [_vp, _vp, _vp]
             L.dag_rank_to_state.argtypes = [_vp, _vp, _vp, _vp, _vp]
             L.dag_state_to_rank.argtypes = [_vp, _vp, _vp, _vp]
@@ -214,6 +222,10 @@ class Plan:
     def set_warp_tile(self, items_per_lane: int):
         """Warp tile shape (32 x items_per_lane items, 5, 7 or 11) of warp-worker solves."""
         _raise(lib().dag_plan_set_warp_tile(self.h, items_per_lane), False)
+
+    def set_warp_frontier_marks(self, marks_per_tile: float):
+        """Warp-tile frontier: marks per warp tile at or below which the next sweep runs only stamped tiles."""
+        _raise(lib().dag_plan_set_warp_frontier_marks(self.h, float(marks_per_tile)), False)
 
     def warp_tile_items(self) -> int:
         return int(lib().dag_warp_tile_items(self.h))

@@ -131,3 +131,21 @@ def test_warp_candidates_set_their_tile_and_the_choice_keeps_it(monkeypatch):
     ch = A.tune(plan, "pagerank", candidates=cands, worker_fractions=[1.0], trials=1, cache=None)
     assert ("warp+cached", 5) in seen and ("warp+cached", 11) in seen
     assert (ch["reads"], ch["warp_tile"]) == ("warp+cached", 11) and plan.tiles[-1] == 11
+
+
+def test_ordered_candidates_set_their_tile_too(monkeypatch):
+    # ordered warp sweeps run warp tiles: each candidate must run at its own shape, even after a
+    # warp-worker candidate left the plan at another one
+    plan = FakePlan()
+    cands = [("async", 0, "warp+cached", 11), ("async", 0, "ordered+cached", 7), ("async", 0, "ordered+cached", 11)]
+    seen = []
+
+    def run(plan_, algo, variant, delta, reads, kw):
+        seen.append((reads, plan_.tiles[-1]))
+        return {("ordered+cached", 7): 1.0}.get((reads, plan_.tiles[-1]), 2.0), {"iters": 3}
+
+    monkeypatch.setattr(A, "_run", run)
+    ch = A.tune(plan, "pagerank", candidates=cands, worker_fractions=[1.0], trials=1, cache=None)
+    assert seen == [("warp+cached", 11), ("ordered+cached", 7), ("ordered+cached", 11)]
+    assert (ch["reads"], ch["warp_tile"]) == ("ordered+cached", 7) and plan.tiles[-1] == 7
+    assert dag.uses_warp_tile("ordered") and dag.uses_warp_tile("warp+cached") and not dag.uses_warp_tile("own_l1")

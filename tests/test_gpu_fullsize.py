@@ -82,8 +82,11 @@ PR_FULL = [("sync", 0, "refresh", 7), ("async", 0, "refresh", 7), ("async", 0, "
            ("delayed", 32, "refresh", 7), ("delayed", 256, "refresh", 7), ("delayed", 4096, "refresh", 7),
            ("delayed", 4096, "local", 7), ("sync", 0, "warp", 7), ("async", 0, "warp+cached", 5),
            ("async", 0, "warp+cached", 7), ("async", 0, "warp+cached", 11), ("delayed", 16, "warp", 7),
-           ("delayed", 256, "warp+cached", 7), ("async", 0, "ordered+cached", 7), ("async", 0, "ordered+cached", 11)]
-SSSP_FULL = PR_FULL + [("sync", 0, "frontier", 7), ("async", 0, "frontier", 7), ("async", 0, "own_l1+frontier", 7)]
+           ("delayed", 256, "warp+cached", 7), ("async", 0, "ordered+cached", 7), ("async", 0, "ordered+cached", 11),
+           ("async", 0, "cached", 7)]
+SSSP_FULL = PR_FULL + [("sync", 0, "frontier", 7), ("async", 0, "frontier", 7), ("async", 0, "own_l1+frontier", 7),
+                       ("async", 0, "cached+frontier", 7), ("async", 0, "warp+frontier", 7),
+                       ("async", 0, "warp+cached+frontier", 7), ("async", 0, "warp+cached+frontier", 5)]
 
 
 @pytest.mark.parametrize("variant,delta,reads,ipt", PR_FULL)
@@ -100,13 +103,13 @@ def test_pagerank_full_size_against_fixed_point(big, big_rstar, variant, delta, 
 def test_sssp_full_size_optimal(big, variant, delta, reads, ipt):
     dag, g, w, srcs, plan, w8, src_e, dst_e = big
     plan.set_warp_tile(ipt)
-    sources = srcs if reads == "own_l1+frontier" else srcs[:2]
+    sources = srcs if reads in ("own_l1+frontier", "warp+cached+frontier") and ipt == 7 else srcs[:2]
     for k, s in enumerate(sources):
         d, st = dag.sssp(plan, int(s), w8, variant, delta, g.n + 1, reads=reads)
         assert st["converged"], st
         got = d.cpu().numpy().view(np.uint32)
         _check_optimal(got, int(s), w, src_e, dst_e, g.n)
-        if k == 0 and reads == "own_l1+frontier":
+        if k == 0 and reads in ("own_l1+frontier", "warp+cached+frontier"):
             assert np.array_equal(got, oracle.dijkstra(g, w, int(s)))
 
 
@@ -126,7 +129,8 @@ BENCH_ROWS = [("sync", 0, "refresh"), ("async", 0, "refresh"), ("async", 0, "own
               ("async", 0, "frontier"), ("async", 0, "own_l1+frontier"), ("delayed", 32, "refresh"),
               ("delayed", 256, "refresh"), ("delayed", 4096, "refresh"), ("delayed", 4096, "local"),
               ("sync", 0, "warp"), ("async", 0, "warp+cached"), ("delayed", 16, "warp"),
-              ("delayed", 256, "warp+cached"), ("async", 0, "ordered+cached")]
+              ("delayed", 256, "warp+cached"), ("async", 0, "ordered+cached"), ("async", 0, "cached+frontier"),
+              ("async", 0, "warp+frontier"), ("async", 0, "warp+cached+frontier")]
 
 
 @pytest.fixture(scope="module", params=[c[0] for c in CONFIG3])

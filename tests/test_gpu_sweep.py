@@ -281,19 +281,22 @@ def test_local_reads_parity(dag, delta):
         assert st2["iters"] <= it_sync
 
 
+@pytest.mark.parametrize("reads", ["own_l1", "cached"])
 @pytest.mark.parametrize("algo", ["pagerank", "sssp", "sssp8"])
-def test_async_own_block_l1_parity(dag, algo):
-    # async form with the CTA's own block read through L1: same fixed point / exact distances
+def test_async_own_block_l1_parity(dag, algo, reads):
+    # async form (CTA tiles) with the CTA's own block read through L1 (own_l1), or every gather an ordinary
+    # load refreshed by the grid barrier (cached): same fixed point / exact distances, and no more
+    # Bellman-Ford sweeps than the synchronous form (every value read is at most one sweep old)
     for g in [I.rmat(14, 16, seed=8), I.banded(30011, 15, 1024, 1, seed=4), I.banded(1 << 17, 15, 16, 1, seed=4)]:
         plan = _plan(dag, g)
         if algo == "pagerank":
-            r, st = dag.pagerank(plan, 0.85, 1e-6, "async", 0, reads="own_l1")
+            r, st = dag.pagerank(plan, 0.85, 1e-6, "async", 0, reads=reads)
             assert st["converged"] and _l1(r, oracle.pagerank_fixed_point(g, 0.85)) <= 1e-5
             continue
         w = I.weights_u32(g, 2)
         ref = oracle.dijkstra(g, w, 3)
         wd = torch.from_numpy(w.astype(np.uint8)).cuda() if algo == "sssp8" else _w_dev(w)
-        d, st = dag.sssp(plan, 3, wd, "async", 0, reads="own_l1")
+        d, st = dag.sssp(plan, 3, wd, "async", 0, reads=reads)
         assert st["converged"] and np.array_equal(_u32(d), ref)
         _, it_sync, _, _ = oracle.sssp(g, w, 3, oracle.SYNC)
         assert st["iters"] <= it_sync

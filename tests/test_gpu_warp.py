@@ -107,7 +107,8 @@ def test_warp_weighted_pagerank_and_teleport(dag):
 
 
 def test_warp_flags_refused_with_frontier_and_local(dag):
-    # the frontier and local reads run the CTA-tile sweeps: combined with warp workers they are refused
+    # local reads run the CTA-tile sweeps, and the warp-tile frontier only the asynchronous Bellman-Ford:
+    # other combinations with warp workers are refused
     g = I.rmat(10, 16, seed=1)
     plan = dag.Plan.from_graph(g, "cuda")
     w = torch.from_numpy(I.weights_u32(g, 1).astype(np.uint8)).cuda()
@@ -115,8 +116,13 @@ def test_warp_flags_refused_with_frontier_and_local(dag):
     rank = torch.empty(g.n, device="cuda")
     L = dag.lib()
     warp, frontier, local = dag.READ_MODES["warp"], dag.READ_MODES["frontier"], dag.READ_MODES["local"]
-    assert L.dag_sssp_u8(plan.h, 0, dag.ASYNC, 0, 10, dag._ptr(w), dag._ptr(dist), warp | frontier, None,
-                         dag._stream()) == dag.ERR_INVALID
+    ordered = dag.READ_MODES["ordered"]
+    for var, delta, flags in ((dag.SYNC, 0, warp | frontier), (dag.DELAYED, 16, warp | frontier),
+                              (dag.ASYNC, 0, ordered | frontier)):
+        assert L.dag_sssp_u8(plan.h, 0, var, delta, 10, dag._ptr(w), dag._ptr(dist), flags, None,
+                             dag._stream()) == dag.ERR_INVALID
+    assert L.dag_pagerank(plan.h, 0.85, 1e-6, dag.ASYNC, 0, 100, None, None, dag._ptr(rank), warp | frontier, None,
+                          dag._stream()) == dag.ERR_INVALID
     assert L.dag_pagerank(plan.h, 0.85, 1e-6, dag.DELAYED, 16, 100, None, None, dag._ptr(rank), warp | local, None,
                           dag._stream()) == dag.ERR_INVALID
 
