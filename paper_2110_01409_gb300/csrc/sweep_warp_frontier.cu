@@ -6,21 +6,28 @@
 // its run of warp tiles, owns the rows that end in it and finishes a row that
 // straddles runs with the bounded look-back over published partials. Each
 // warp also keeps the list of its rows that got a smaller distance, and the
-// sweep's total of their out-degrees (the tile marks they would cause) goes
+// sweep's total of their out-degrees (the tile flags they would set) goes
 // through the grid reduction with the residual. When that total is at most
-// FRW_SPARSE marks per warp tile, the next sweep is sparse: the changed rows
-// stamp the warp tiles holding their out-edges (fr_otile, in-CSR position of
-// each out-edge), the stamped tiles are gathered into one list, and the warps
-// claim that list a few tiles at a time. A tile of a sparse sweep relaxes its
-// rows with atomicMin: a row that the tile holds only part of (its first or
-// last one) gets the minimum over that part, which is as valid a relaxation as
-// the whole row's (every other in-edge's source kept its value since its tile
-// last ran). A sweep that lowers no distance ends the solve, as in Sec. IV.
+// fr_sparse per warp tile, the sweeps turn sparse: the lowered rows set the
+// flag of every warp tile holding one of their out-edges (fr_otile, the in-CSR
+// position of each out-edge), and a sparse sweep runs only flagged tiles, in
+// tile order (warps claim the tile ids 32 at a time). A tile's flag is taken
+// (exchanged for 0) before the tile reads its inputs, and a row a sparse tile
+// lowers flags its out-edges' tiles at once, after a fence: a tile further on
+// in the same sweep then runs with the new value, and a tile already taken is
+// flagged again for the next sweep, so no lowered value goes unpropagated. A
+// sparse tile relaxes its rows with atomicMin: a row that the tile holds only
+// part of (its first or last one) gets the minimum over that part, which is as
+// valid a relaxation as the whole row's (every other in-edge's source kept
+// its value since its tile last ran). A sweep that lowers no distance ends the
+// solve, as in Sec. IV; one grid barrier per sweep, one more when the sweeps
+// turn sparse.
 //
-// Gathers read the live array through L2 (relaxed loads) or, with
-// DAG_READ_CACHED, with ordinary loads refreshed by every grid barrier; either
-// way a tile that read a value older than a change made in the same sweep is
-// stamped again by that change for the next sweep.
+// Dense sweeps gather through L2 (relaxed loads) or, with DAG_READ_CACHED,
+// with ordinary loads refreshed by every grid barrier (a tile that read a
+// value older than a change of the same sweep is flagged by that change);
+// sparse sweeps always gather through L2, after the fence that orders them
+// behind the flags they took.
 #include <algorithm>
 #include <climits>
 #include <cstdint>
@@ -29,9 +36,7 @@
 
 namespace dag {
 
-constexpr int FRW_CLAIM = 8;  // warp tiles a warp claims from a sparse sweep's list at once (1,792 items at 7 per lane)
-
-// Stamps s + 1 on the warp tile of every out-edge of the rows list[first], list[first + stride], ...
+// Sets to s + 1 the flag of the warp tile of every out-edge of the rows list[first], list[first + stride], ...
 // (one warp per row, its lanes over the row's out-edges).
 __device__ __forceinline__ void stamp_edge_tiles(const int* list, int cnt, const int* orow, const int* otile, int* act,
                                                  int s, int first, int stride, int lane)
@@ -41,17 +46,6 @@ __device__ __forceinline__ void stamp_edge_tiles(const int* list, int cnt, const
         const int e1 = orow[v + 1];
         for (int e = orow[v] + lane; e < e1; e += 32) act[otile[e]] = s + 1;
     }
-}
-
-// Appends `v` of every lane with `changed` to list[*cnt ...] (one atomic per warp; order free). All lanes call it.
-__device__ __forceinline__ void log_rows(int* list, int* cnt, bool changed, int v, int lane)
-{
-    const unsigned bal = __ballot_sync(0xffffffffu, changed);
-    if (bal == 0u) return;
-    int base = 0;
-    if (lane == 0) base = atomicAdd(cnt, __popc(bal));
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (changed) list[base + __popc(bal & ((1u << lane) - 1u))] = v;
 }
 
 template <int MODE, int WIPT>
@@ -66,7 +60,6 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_warp_frontier_kernel(con
     __shared__ WarpShared<32 * WIPT> sh;
     const int c = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wl = tid >> 5;
     const int w = c * WWARPS + wl;
-    const int W = p.nblocks * WWARPS;
     SyncBlock* sb = p.sync;
     unsigned long long bar_target = 0;
     uint32_t* X = (uint32_t*)p.x0;
@@ -186,22 +179,34 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_warp_frontier_kernel(con
                 marks += p.fr_orow[v + 1] - p.fr_orow[v];
             }
         } else {
-            // ---------------- sparse sweep: the stamped tiles, claimed FRW_CLAIM at a time ----------------
-            const int cnt = ld_relaxed_i32(&sb->fr_cnt[slot]);
-            int kq = 0, kq_end = 0;  // this warp's claimed list positions [kq, kq_end)
+            // ---------------- sparse sweep: the flagged tiles, in tile order ----------------
+            // Warps claim the tile ids 32 at a time in increasing order; a flagged tile's flag is taken
+            // (exchanged for 0) before its inputs are read, so a flag set later by a lowered input is kept for
+            // a later claim or the next sweep, and one set earlier is seen with the value that set it.
+            unsigned bits = 0u;
+            int base = 0;
             auto next_tile = [&]() -> int {
-                if (kq >= kq_end) {
-                    int base = 0;
-                    if (lane == 0) base = atomicAdd(&sb->fr_head[slot], FRW_CLAIM);
-                    base = __shfl_sync(FULL, base, 0);
-                    kq = base;
-                    kq_end = min(base + FRW_CLAIM, cnt);
+                for (;;) {
+                    if (bits) {
+                        const int b = __ffs(bits) - 1;
+                        bits &= bits - 1u;
+                        return base + b;
+                    }
+                    int b0 = 0;
+                    if (lane == 0) b0 = atomicAdd(&sb->fr_head[slot], 32);
+                    b0 = __shfl_sync(FULL, b0, 0);
+                    if (b0 >= p.ntiles) return -1;
+                    base = b0;
+                    const int t = b0 + lane;
+                    bool mine = false;
+                    if (t < p.ntiles && ld_relaxed_i32(p.fr_act + t) != 0) mine = atomicExch(p.fr_act + t, 0) != 0;
+                    bits = __ballot_sync(FULL, mine);
+                    if (bits) __threadfence();  // the flags' setters' lowered values before this warp's reads
                 }
-                return kq < kq_end ? p.fr_glist[kq++] : -1;
             };
             int t = next_tile();
             WStage<WIPT> nx;
-            if (t >= 0) wfetch<MODE, WIPT>(nx, p, X, t, lane, rmode, false, pol_edge, pol_vertex);
+            if (t >= 0) wfetch<MODE, WIPT>(nx, p, X, t, lane, READ_COHERENT, false, pol_edge, pol_vertex);
             while (t >= 0) {
                 const int a0 = nx.a0, b0 = nx.b0, NA = nx.NA, NB = nx.NB;
                 const uint32_t pf_xo = nx.xo;
@@ -214,13 +219,15 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_warp_frontier_kernel(con
                 }
                 for (int i = lane; i < NA; i += 32) end[i] = (int)ld_vertex_b32(p.rowptr + a0 + i + 1, pol_vertex) - b0;
                 if (lane == 0) end[NA] = INT_MAX;
-                if (tn >= 0) wfetch<MODE, WIPT>(nx, p, X, tn, lane, rmode, false, pol_edge, pol_vertex);
+                if (tn >= 0) wfetch<MODE, WIPT>(nx, p, X, tn, lane, READ_COHERENT, false, pol_edge, pol_vertex);
                 __syncwarp();
                 const uint32_t trail = wwalk<MODE, WIPT>(end, val, sum, NA, NB, O::identity(), lane);
                 __syncwarp();
                 if (lane == 0) edges += NB;
                 // rows of the tile (the first may be partial), then the partial of the row it leaves unfinished;
-                // a value read here may be older than the latest (never lower), so only a smaller sum is sent
+                // a value read here may be older than the latest (never lower), so only a smaller sum is sent.
+                // A lowered row flags the tiles of its out-edges at once (after a fence, so that a warp that
+                // takes the flag reads the lowered value).
 #pragma unroll
                 for (int k = 0; k <= WIPT; ++k) {
                     const int r = lane + 32 * k;
@@ -230,20 +237,29 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_warp_frontier_kernel(con
                     uint32_t cand = INF, seen = 0u;
                     if (r < NA) {
                         cand = sum[r];
-                        seen = k == 0 ? pf_xo : ld_weak_b32(X + v);
+                        seen = k == 0 ? pf_xo : ld_relaxed_b32(X + v);
                     } else if (r == NA && v < p.n) {  // the row continuing into the next tile
                         cand = trail;
-                        seen = ld_weak_b32(X + v);
+                        seen = ld_relaxed_b32(X + v);
                     }
                     if (cand != INF && cand < seen) {
                         const uint32_t old = atomicMin(X + v, cand);
                         changed = cand < old;
                     }
+                    unsigned bal = __ballot_sync(FULL, changed);
+                    if (bal == 0u) continue;
+                    __threadfence();
                     if (changed) {
                         res_part += 1.0f;
                         marks += p.fr_orow[v + 1] - p.fr_orow[v];
                     }
-                    log_rows(p.fr_gchg, &sb->fr_nchg[slot], changed, v, lane);
+                    while (bal) {
+                        const int ld = __ffs(bal) - 1;
+                        bal &= bal - 1u;
+                        const int u = __shfl_sync(FULL, v, ld);
+                        const int e1 = p.fr_orow[u + 1];
+                        for (int e = p.fr_orow[u] + lane; e < e1; e += 32) st_relaxed_b32(p.fr_act + p.fr_otile[e], 1u);
+                    }
                 }
                 t = tn;
             }
@@ -261,7 +277,6 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_warp_frontier_kernel(con
         if (tid == 0) {
             sh.res = ld_relaxed_f64(&sb->acc_res[slot]);
             sh.gprev = ld_relaxed_f64(&sb->acc_g[slot]);
-            sh.T = (double)ld_relaxed_i32(&sb->fr_nchg[slot]);  // (sh.T: free here) rows on the grid's list
             if (c == 0) {
                 const int dead = (it + 2) % 3;  // read by everyone before this barrier
                 sb->acc_res[dead] = 0.0;
@@ -279,22 +294,11 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_warp_frontier_kernel(con
             break;
         }
         const bool was_dense = dense;
-        const int g_cnt = (int)sh.T;
         dense = sh.gprev > sparse_marks;
-        if (!dense) {
-            // stamp the next sweep's tiles: a dense sweep's rows from each warp's own list, a sparse one's from
-            // the grid's list (shared out over all warps)
-            if (was_dense)
-                stamp_edge_tiles(own_chg, own_cnt, p.fr_orow, p.fr_otile, p.fr_act, it, 0, 1, lane);
-            else
-                stamp_edge_tiles(p.fr_gchg, g_cnt, p.fr_orow, p.fr_otile, p.fr_act, it, w, W, lane);
-            if (!grid_barrier(sb, p.nblocks, bar_target, p.timeout_ns)) return;
-            // this warp's run of tiles stamped for the next sweep goes on the grid's list
-            for (int base = t_lo; base < t_hi; base += 32) {
-                const int t = base + lane;
-                const bool on = t < t_hi && p.fr_act[t] == it + 1;
-                log_rows(p.fr_glist, &sb->fr_cnt[(it + 1) % 3], on, t, lane);
-            }
+        if (!dense && was_dense) {
+            // into the sparse phase: the rows the dense sweep lowered flag the tiles of their out-edges (a sparse
+            // sweep's lowered rows flagged theirs as they went)
+            stamp_edge_tiles(own_chg, own_cnt, p.fr_orow, p.fr_otile, p.fr_act, 0, 0, 1, lane);
             if (!grid_barrier(sb, p.nblocks, bar_target, p.timeout_ns)) return;
         }
     }
