@@ -301,9 +301,10 @@ def run_gpu(args):
             return None
         sweeps = statistics.mean(best["sweeps"])
         gbs = algorithmic_bytes(n, m, kind) * sweeps / (best["ms"] * 1e-3) / 1e9
-        return {"kernel": kernel_name(mode, "delayed", best["delta"], best["reads"], best["warp_tile"]),
-                "delta": best["delta"], "reads": best["reads"], "ms": round(best["ms"], 3), "sweeps": sweeps,
-                "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4)}
+        kern = kernel_name(mode, "delayed", best["delta"], best["reads"], best["warp_tile"])
+        return {"kernel": kern, "delta": best["delta"], "reads": best["reads"], "ms": round(best["ms"], 3),
+                "sweeps": sweeps, "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
+                "traffic": _recorded_traffic(kern, sweeps)}
 
     delayed_roofline = {"pagerank": delayed_roof(tune_pr, "pr", "PR"), "sssp": delayed_roof(tune_bf, "bf8", "BF8")}
 
@@ -486,10 +487,13 @@ def run_e2e(args, g, w, srcs, dev, dag, torch, pr_choice, bf_choice):
 
 
 def _variant_rows(dag, torch, plan, g, src, w_d, variants, trials=3):
-    """Median time and sweeps of each (name, variant, delta, reads) row for PageRank and
-    Bellman-Ford; frontier rows are Bellman-Ford only. Also the edges the SSSP solves ran."""
+    """Median time and sweeps of each (name, variant, delta, reads[, warp tile]) row for PageRank
+    and Bellman-Ford; frontier rows are Bellman-Ford only. Also the edges the SSSP solves ran.
+    Warp-tile rows run 32 x 7 items unless the row names another shape."""
     res = {}
-    for name, var, dl, rd in variants:
+    for row_spec in variants:
+        name, var, dl, rd = row_spec[:4]
+        plan.set_warp_tile(row_spec[4] if len(row_spec) > 4 else 7)
         pr_it, pr_ms, bf_it, bf_ms = [], [], [], []
         for _ in range(trials):
             if "frontier" not in rd:
@@ -520,7 +524,7 @@ VARIANT_ROWS = [("sync", "sync", 0, "refresh"), ("async", "async", 0, "refresh")
                 ("delayed4096", "delayed", 4096, "refresh"), ("delayed4096_local", "delayed", 4096, "local"),
                 ("warp_sync", "sync", 0, "warp"), ("warp_async_cached", "async", 0, "warp+cached"),
                 ("warp_delayed16", "delayed", 16, "warp"), ("warp_delayed256_cached", "delayed", 256, "warp+cached"),
-                ("ordered_cached", "async", 0, "ordered+cached")]
+                ("ordered_cached", "async", 0, "ordered+cached", 11)]
 
 
 def run_detail(g, w, srcs, plan, w_d, dag, torch, args):
