@@ -335,12 +335,18 @@ int dag_gather_f32(const float* d_src, const int32_t* d_idx, int64_t m, float* d
  * (with d_rank the forward result, d_s the normaliser, d_val the in-edge P):
  *   d_grad_w[e] = d r_u (lambda_v - (M^T lambda)_u) / s_u  for in-edge e = (u -> v),
  *   d_grad_t[v] = (1 - d) lambda_v.
- * d_lambda (device float [n], nullable) receives lambda.
+ * d_lambda (device float [n], nullable) receives lambda. flags: the read path
+ * of the adjoint sweep, as for dag_pagerank (one DAG_READ_* for the delayed
+ * form, DAG_READ_CACHED or DAG_READ_OWN_L1 for the asynchronous form,
+ * DAG_WARP_WORKERS, DAG_WARP_ORDERED); 0 for the default. Every form deflates
+ * the slow error mode along the all-ones vector after each sweep short of the
+ * stopping rule (the iteration operator maps 1 to d 1), which leaves the fixed
+ * point unchanged.
  */
 int dag_pagerank_adjoint(dag_plan* in_plan, dag_plan* out_plan, float d, double tol, dag_variant variant,
                          int32_t delta, int32_t max_iters, const float* d_val, const float* d_val_out,
                          const float* d_s, const float* d_rank, const float* d_c, float* d_grad_w,
-                         float* d_grad_t, float* d_lambda, dag_stats* h_stats, void* stream);
+                         float* d_grad_t, float* d_lambda, int32_t flags, dag_stats* h_stats, void* stream);
 
 /*
  * PageRank with no device allocation. This is an interface convenience with

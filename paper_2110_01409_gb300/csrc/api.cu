@@ -267,7 +267,7 @@ extern "C" int dag_pagerank_adjoint(dag_plan* in_plan, dag_plan* out_plan, float
                                     dag_variant variant, int32_t delta, int32_t max_iters, const float* d_val,
                                     const float* d_val_out, const float* d_s, const float* d_rank,
                                     const float* d_c, float* d_grad_w, float* d_grad_t, float* d_lambda,
-                                    dag_stats* h_stats, void* stream)
+                                    int32_t flags, dag_stats* h_stats, void* stream)
 {
     if (!in_plan || !out_plan || !d_c || !d_rank || !d_s) return set_error(DAG_ERR_INVALID, "null argument");
     if (in_plan->n != out_plan->n || in_plan->m != out_plan->m)
@@ -276,6 +276,8 @@ extern "C" int dag_pagerank_adjoint(dag_plan* in_plan, dag_plan* out_plan, float
         return set_error(DAG_ERR_INVALID, "null edge values");
     if (!(d > 0.0f && d < 1.0f)) return set_error(DAG_ERR_INVALID, "d must lie in (0, 1)");
     if (!(tol > 0.0)) return set_error(DAG_ERR_INVALID, "tol must be > 0");
+    if (flags & (DAG_PR_WARM_START | DAG_SSSP_FRONTIER | DAG_READ_LOCAL))
+        return set_error(DAG_ERR_INVALID, "flag not taken by the adjoint");
     int rc = check_variant(variant, delta, max_iters);
     if (rc) return rc;
     int var = variant;
@@ -303,6 +305,10 @@ extern "C" int dag_pagerank_adjoint(dag_plan* in_plan, dag_plan* out_plan, float
     p.x1 = out_plan->x1;
     p.out = lam;
     p.aux_out = in_plan->scratch_f;  // (M^T lambda)_u of the last sweep
+    p.read_mode = read_mode_of(flags);
+    p.own_l1 = (flags & DAG_READ_OWN_L1) ? 1 : 0;
+    p.warp = (flags & (DAG_WARP_WORKERS | DAG_WARP_ORDERED)) ? 1 : 0;
+    p.ordered = (flags & DAG_WARP_ORDERED) ? 1 : 0;
     Timer tm;
     tm.start(s, true);
     int nb = 0;

@@ -152,32 +152,13 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
     unsigned long long bar_target = 0;
     uint32_t* X0 = (uint32_t*)p.x0;
     uint32_t* X1 = (uint32_t*)p.x1;
-    const int row_lo = p.cta_row[c], row_hi = p.cta_row[c + 1];
+    const int row_lo = p.cta_row[c];
     const int tile_lo = p.cta_tile[c], tile_hi = p.cta_tile[c + 1];
-    const float inv_n = 1.0f / (float)p.n;
 
-    // ---------------- initial values of the owned rows ----------------
+    // ---------------- initial values (a grid-stride pass, init_values) ----------------
     {
         double gpart = 0.0, tpart = 0.0;
-        for (int v = row_lo + tid; v < row_hi; v += NT) {
-            if constexpr (BF) {
-                X0[v] = (v == (int)p.src) ? 0u : INF;
-            } else if constexpr (MODE == MODE_ADJ) {
-                float cv = p.base[v];
-                float l0 = p.init ? p.init[v] : cv;
-                X0[v] = __float_as_uint(l0);
-                gpart += (double)l0;
-                tpart += fabs((double)cv);
-            } else {
-                float t = p.base ? p.base[v] : inv_n;
-                float r0 = p.init ? p.init[v] : t;
-                float dg = p.degf[v];
-                float x = (MODE == MODE_PR && dg > 0.0f) ? r0 / dg : r0;
-                X0[v] = __float_as_uint(x);
-                if (dg > 0.0f) gpart += (double)r0;
-                tpart += (double)t;
-            }
-        }
+        init_values<MODE>(p, X0, gpart, tpart);
         if constexpr (!BF) {
             block_sum2(sh, gpart, tpart);
             if (tid == 0) {
@@ -202,7 +183,7 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
     double gprev = BF ? 0.0 : sh.gprev;
     LiveSum L{};
     if constexpr (LIVE_G) L = live_sum_setup<MODE>(p, T, gprev);
-    double adj_sum = gprev;  // adjoint: sum lambda as the sweep starts
+    AdjOffset A{gprev, 0.0, 0.0f, 0.0, 0.0, 0};  // adjoint: sum lambda, deflation offset
     const double tol = (MODE == MODE_ADJ) ? p.tol * T : p.tol;
 
     // sync reads the previous iterate with ordinary loads; async reads the live
@@ -352,7 +333,7 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
                     xo_bits = weak ? ld_weak_b32(xin + v) : ld_relaxed_b32(xin + v);
                     if constexpr (!BF) dg = ld_stream_f32(p.degf + v);
                 }
-                const uint32_t xnew = row_update<MODE>(p, v, sum, xo_bits, dg, gt, res_part, g_part, dg_part);
+                const uint32_t xnew = row_update<MODE>(p, v, sum, xo_bits, dg, gt, A.off_f, res_part, g_part, dg_part);
                 if constexpr (FRONTIER)  // the row goes on the CTA's list; its marks are counted at the sweep's end
                     log_changed(p.fr_chg + row_lo, &sh.nchg, xnew < xo_bits, v, epilogue_lanes(NA, k));
                 if constexpr (SYNC) st_weak_b32(xout + v, xnew);
@@ -382,7 +363,7 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
         block_sum2(sh, res_d, g_d);
         if (tid == 0) {
             if (res_d != 0.0) atomicAdd(&sb->acc_res[slot], res_d);
-            if ((FRONTIER || (SYNC && !BF)) && g_d != 0.0) atomicAdd(&sb->acc_g[slot], g_d);
+            if ((FRONTIER || (SYNC && !BF) || MODE == MODE_ADJ) && g_d != 0.0) atomicAdd(&sb->acc_g[slot], g_d);
             if (FRONTIER && edges_done) atomicAdd((unsigned long long*)&sb->edges, (unsigned long long)edges_done);
             edges_done = 0;
         }
@@ -404,23 +385,7 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
             ++it;
             break;
         }
-        if constexpr (MODE == MODE_ADJ) {  // deflation of the slow mode along 1 (adjoint_shift)
-            if constexpr (LIVE_G) {
-                if (tid == 0) sh.gprev = live_value(sb, L);
-                __syncthreads();
-            }
-            const double sum_new = sh.gprev;
-            const float shift = adjoint_shift(p, sum_new, adj_sum);
-            uint32_t* xs = SYNC ? xout : X0;  // the next sweep's input
-            for (int v = row_lo + tid; v < row_hi; v += NT)
-                st_relaxed_b32(xs + v, __float_as_uint(__uint_as_float(ld_relaxed_b32(xs + v)) + shift));
-            adj_sum = sum_new + (double)p.n * shift;
-            if constexpr (SYNC) gprev = adj_sum;
-            if constexpr (LIVE_G) {
-                if (c == 0 && tid == 0) live_add(sb, 0, (float)((double)p.n * shift), L.S);
-            }
-            if (!grid_barrier(sb, p.nblocks, bar_target, p.timeout_ns)) return;  // every value shifted
-        }
+        if constexpr (MODE == MODE_ADJ) adjoint_deflate(p, A, gprev, SYNC);  // the slow mode along 1, as an offset
         if constexpr (FRONTIER) {
             // sparse next sweep: stamp the tiles the changed rows feed, publish, run only those
             dense = gprev > FR_SPARSE * (double)p.cta_tile[p.nblocks];
@@ -432,18 +397,10 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_kernel(const SweepParams 
         }
     }
 
-    // ---------------- output of the owned rows ----------------
+    // ---------------- output (a grid-stride pass, write_output) ----------------
     {
         const uint32_t* xf = SYNC ? ((it & 1) ? X1 : X0) : X0;
-        for (int v = row_lo + tid; v < row_hi; v += NT) {
-            const uint32_t x = ld_relaxed_b32(xf + v);
-            if constexpr (BF || MODE == MODE_ADJ || MODE == MODE_PRW) {
-                ((uint32_t*)p.out)[v] = x;
-            } else {
-                const float dg = p.degf[v];
-                ((float*)p.out)[v] = dg > 0.0f ? __uint_as_float(x) * dg : __uint_as_float(x);
-            }
-        }
+        write_output<MODE>(p, xf, A.off_f);
     }
     if (tid == 0) {
         if (flushes) atomicAdd((unsigned long long*)&sb->flushes, (unsigned long long)flushes);

@@ -373,27 +373,172 @@ __device__ __forceinline__ float live_term(const LiveSum& L, long long G)
 // change: for the synchronous sweep this replaces B by B + 1 w^T with
 // w^T 1 = -d, which keeps B's other eigenvalues, sends the one of 1 to 0 and
 // leaves the fixed point where it was (a Wielandt deflation of the known
-// eigenpair (d, 1)); the in-place forms use the same shift.
-__device__ __forceinline__ float adjoint_shift(const SweepParams& p, double sum_new, double sum_old)
+// eigenpair (d, 1)); the in-place forms take the same step with their own
+// contraction rate (adjoint_deflate). The shift is applied as an offset
+// (AdjOffset, below), not to the array.
+
+// The adjoint keeps its deflation shifts as one offset: the array holds
+// lambda - aoff (aoff the sum of the shifts so far), so a shift is one add to
+// a scalar every CTA computes alike instead of a pass over all n values and a
+// grid barrier. A row's update from the held values: with lambda_v = x_v + aoff
+// and every out-edge value row of M^T summing to 1,
+//   lambda'_u = c_u + d (sum + aoff) = c_u + d sum + d aoff (u with out-edges),
+//   lambda'_u = c_u + d (sum x + n aoff) / n = c_u + gt + d aoff (dangling u),
+// so x'_u = lambda'_u - aoff = c_u - (1 - d) aoff + d sum (+ gt when dangling),
+// gt the global term of the held values; (M^T lambda)_u = sum + aoff for u
+// with out-edges. Changes, the residual and the live sum are those of the held
+// values; the sum of lambda is theirs plus n aoff; the output adds aoff back.
+struct AdjOffset {
+    double sum;    // sum lambda as the sweep starts (held values + n aoff)
+    double off;    // aoff
+    float off_f;   // aoff in FP32 for the row updates
+    double dprev;  // the previous sweep's mean change
+    double sprev;  // the previous shift
+    int steps;     // shifts so far
+};
+
+// After a sweep short of the stopping rule: the shift of the slow mode from the
+// sweep's sum of the held values (exact FP64 grid sum, the same in every CTA).
+// A sweep multiplies the mean error e by rho: d for the synchronous sweep, so
+// its mean change is (rho - 1) e and the shift that cancels the error after the
+// sweep is rho / (1 - rho) times the mean change. An in-place sweep reuses
+// values it has already lowered, so its rho is below d and d's shift would
+// overshoot (the mean error then alternates in sign and can grow). Its rho is
+// estimated from the response to the previous shift s: the mean changes
+// satisfy delta_k = rho (delta_{k-1} + s) - s, so rho = (delta_k + s) /
+// (delta_{k-1} + s), clamped to [0, d].
+__device__ __forceinline__ void adjoint_deflate(const SweepParams& p, AdjOffset& A, double held_sum, bool jacobi)
 {
-    return (float)((double)p.d / (1.0 - (double)p.d) * (sum_new - sum_old) / (double)p.n);
+    const double n = (double)p.n, d = (double)p.d;
+    const double sum_new = held_sum + n * A.off;
+    const double delta = (sum_new - A.sum) / n;
+    double rho = d;
+    if (!jacobi && A.steps > 0) {
+        const double den = A.dprev + A.sprev;
+        const double r = den != 0.0 ? (delta + A.sprev) / den : d;
+        rho = fmin(fmax(r, 0.0), d);
+    }
+    const double shift = rho / (1.0 - rho) * delta;
+    A.off += shift;
+    A.off_f = (float)A.off;
+    A.sum = sum_new + n * shift;
+    A.dprev = delta;
+    A.sprev = shift;
+    ++A.steps;
 }
 
-// The live sum's value (sum lambda for the adjoint) from its stripes, read
-// by one thread once every CTA has reached a grid barrier.
-__device__ __forceinline__ double live_value(const SyncBlock* sb, const LiveSum& L)
-{
-    long long G = 0;
-    for (int k = 0; k < GSTRIPES; ++k) G += ld_relaxed_i64(&sb->stripe[k * GSTRIDE]);
-    return ldexp((double)(L.base + G), -L.S);
-}
-
-// New value of row v from its pull sum and old value (PageRank: x = r/outdeg
-// with dg = outdeg; adjoint: lambda; Bellman-Ford: dist), with the residual
-// and global-sum contributions.
+// Initial values of all n rows as a grid-stride pass (any thread any row:
+// nothing reads them before the grid barrier that follows; a pass over the
+// worker's own rows would leave the grid waiting for the workers whose blocks
+// hold thousands of rows without in-edges), four rows' inputs loaded before
+// any is stored. PageRank: x = r0 / outdeg (r0 on vertices without
+// out-edges), gpart += r0 over vertices with out-edges (N(0)), tpart += t (T);
+// the adjoint: lambda0 = c (or the warm start), gpart += lambda0, tpart += |c|;
+// Bellman-Ford: 0 at the source, INF elsewhere.
 template <int MODE>
-__device__ __forceinline__ uint32_t row_update(const SweepParams& p, int v, uint32_t sum, uint32_t xo_bits, float dg,
-                                               float gt, float& res_part, float& g_part, float& dg_part)
+__device__ __forceinline__ void init_values(const SweepParams& p, uint32_t* X, double& gpart, double& tpart)
+{
+    constexpr bool BF = MODE == MODE_BF || MODE == MODE_BF8;
+    const long long stride = (long long)gridDim.x * blockDim.x, n = p.n;
+    const float inv_n = 1.0f / (float)p.n;
+    for (long long v0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; v0 < n; v0 += 4 * stride) {
+        if constexpr (BF) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const long long v = v0 + q * stride;
+                if (v < n) X[v] = (v == (long long)p.src) ? 0u : INF;
+            }
+        } else {
+            float t[4], r0[4], dg[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const long long v = v0 + q * stride;
+                t[q] = inv_n;
+                r0[q] = 0.0f;
+                dg[q] = 0.0f;
+                if (v < n) {
+                    if (MODE == MODE_ADJ || p.base) t[q] = p.base[v];
+                    r0[q] = p.init ? p.init[v] : t[q];
+                    if constexpr (MODE != MODE_ADJ) dg[q] = p.degf[v];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const long long v = v0 + q * stride;
+                if (v >= n) continue;
+                if constexpr (MODE == MODE_ADJ) {
+                    X[v] = __float_as_uint(r0[q]);
+                    gpart += (double)r0[q];
+                    tpart += fabs((double)t[q]);
+                } else {
+                    X[v] = __float_as_uint((MODE == MODE_PR && dg[q] > 0.0f) ? r0[q] / dg[q] : r0[q]);
+                    if (dg[q] > 0.0f) gpart += (double)r0[q];
+                    tpart += (double)t[q];
+                }
+            }
+        }
+    }
+}
+
+// The caller's output from the final state x as a grid-stride pass (after the
+// last grid barrier every value is final), four values in flight per thread:
+// distances, lambda and the weighted form's r as they are, PageRank's
+// x = r / outdeg back to r.
+template <int MODE>
+__device__ __forceinline__ void write_output(const SweepParams& p, const uint32_t* x, float aoff = 0.0f)
+{
+    constexpr bool RAW = MODE == MODE_BF || MODE == MODE_BF8 || MODE == MODE_ADJ || MODE == MODE_PRW;
+    const long long stride = (long long)gridDim.x * blockDim.x, n = p.n;
+    for (long long v0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; v0 < n; v0 += 4 * stride) {
+        uint32_t a[4];
+        float dg[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const long long v = v0 + q * stride;
+            a[q] = v < n ? ld_relaxed_b32(x + v) : 0u;
+            dg[q] = (!RAW && v < n) ? p.degf[v] : 0.0f;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const long long v = v0 + q * stride;
+            if (v >= n) continue;
+            if constexpr (MODE == MODE_ADJ) ((float*)p.out)[v] = __uint_as_float(a[q]) + aoff;  // AdjOffset
+            else if constexpr (RAW) ((uint32_t*)p.out)[v] = a[q];
+            else ((float*)p.out)[v] = dg[q] > 0.0f ? __uint_as_float(a[q]) * dg[q] : __uint_as_float(a[q]);
+        }
+    }
+}
+
+// Sum of the live sum's stripes read by one thread: all loads issued before
+// any is added, so the thread waits for one L2 round trip, not one per stripe.
+__device__ __forceinline__ long long stripes_total(const SyncBlock* sb)
+{
+    long long a[GSTRIPES];
+#pragma unroll
+    for (int k = 0; k < GSTRIPES; ++k) a[k] = ld_relaxed_i64(&sb->stripe[k * GSTRIDE]);
+    long long G = 0;
+#pragma unroll
+    for (int k = 0; k < GSTRIPES; ++k) G += a[k];
+    return G;
+}
+
+// The base term of row v: c_v for the adjoint, (1 - d) t_v for PageRank with a
+// teleport vector, (1 - d) / n without one (Bellman-Ford: none).
+template <int MODE>
+__device__ __forceinline__ float row_base(const SweepParams& p, int v)
+{
+    if constexpr (MODE == MODE_ADJ) return ld_stream_f32(p.base + v);
+    else if constexpr (MODE == MODE_BF || MODE == MODE_BF8) return 0.0f;
+    else return p.base ? p.base_scale * ld_stream_f32(p.base + v) : p.uniform_base;
+}
+
+// New value of row v from its pull sum, old value and base term bv (row_base;
+// PageRank: x = r/outdeg with dg = outdeg; adjoint: lambda; Bellman-Ford:
+// dist), with the residual and global-sum contributions.
+template <int MODE>
+__device__ __forceinline__ uint32_t row_update_b(const SweepParams& p, int v, uint32_t sum, uint32_t xo_bits,
+                                                 float dg, float gt, float bv, float aoff, float& res_part,
+                                                 float& g_part, float& dg_part)
 {
     constexpr bool BF = MODE == MODE_BF || MODE == MODE_BF8;
     if constexpr (BF) {
@@ -405,13 +550,13 @@ __device__ __forceinline__ uint32_t row_update(const SweepParams& p, int v, uint
         float rnew, rold;
         if constexpr (MODE == MODE_ADJ) {
             rold = xo;
-            rnew = ld_stream_f32(p.base + v) + p.d * __uint_as_float(sum) + (dg == 0.0f ? gt : 0.0f);
+            // held values (AdjOffset): x' = c - (1 - d) aoff + d sum (+ gt when dangling)
+            rnew = (bv - (1.0f - p.d) * aoff) + p.d * __uint_as_float(sum) + (dg == 0.0f ? gt : 0.0f);
             g_part += rnew;
             dg_part += rnew - rold;
-            if (p.aux_out) p.aux_out[v] = __uint_as_float(sum);
+            if (p.aux_out) p.aux_out[v] = __uint_as_float(sum) + (dg > 0.0f ? aoff : 0.0f);
         } else {
             rold = (MODE == MODE_PR && dg > 0.0f) ? xo * dg : xo;
-            const float bv = p.base ? p.base_scale * ld_stream_f32(p.base + v) : p.uniform_base;
             rnew = bv + p.d * __uint_as_float(sum) + gt;
             if (dg > 0.0f) {
                 g_part += rnew;
@@ -423,6 +568,14 @@ __device__ __forceinline__ uint32_t row_update(const SweepParams& p, int v, uint
         // quotient of a dangling row (dg = 0) is discarded by the select
         return __float_as_uint((MODE == MODE_PR && dg > 0.0f) ? __fdividef(rnew, dg) : rnew);
     }
+}
+
+// row_update_b with the base term loaded here (aoff: the adjoint's offset, 0 for the other modes).
+template <int MODE>
+__device__ __forceinline__ uint32_t row_update(const SweepParams& p, int v, uint32_t sum, uint32_t xo_bits, float dg,
+                                               float gt, float aoff, float& res_part, float& g_part, float& dg_part)
+{
+    return row_update_b<MODE>(p, v, sum, xo_bits, dg, gt, row_base<MODE>(p, v), aoff, res_part, g_part, dg_part);
 }
 
 }  // namespace dag

@@ -232,7 +232,6 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
     uint32_t* X = (uint32_t*)p.x0;
     const int row_lo = p.cta_row[c], row_hi = p.cta_row[c + 1];
     const int tile_lo = p.cta_tile[c], tile_hi = p.cta_tile[c + 1];
-    const float inv_n = 1.0f / (float)p.n;
 
     if (tid == 0) {
         for (int s = 0; s < RING; ++s) mbar_init(&sh.fill_bar[s], 1);
@@ -242,28 +241,10 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
         for (int k = 0; k < NWARP; ++k) sh.dgw[k] = 0.0f;
     }
 
-    // ---------------- initial values of the owned rows ----------------
+    // ---------------- initial values (a grid-stride pass, init_values) ----------------
     {
         double gpart = 0.0, tpart = 0.0;
-        for (int v = row_lo + tid; v < row_hi; v += NT) {
-            if constexpr (BF) {
-                X[v] = (v == (int)p.src) ? 0u : INF;
-            } else if constexpr (MODE == MODE_ADJ) {
-                float cv = p.base[v];
-                float l0 = p.init ? p.init[v] : cv;
-                X[v] = __float_as_uint(l0);
-                gpart += (double)l0;
-                tpart += fabs((double)cv);
-            } else {
-                float t = p.base ? p.base[v] : inv_n;
-                float r0 = p.init ? p.init[v] : t;
-                float dg = p.degf[v];
-                float x = (MODE == MODE_PR && dg > 0.0f) ? r0 / dg : r0;
-                X[v] = __float_as_uint(x);
-                if (dg > 0.0f) gpart += (double)r0;
-                tpart += (double)t;
-            }
-        }
+        init_values<MODE>(p, X, gpart, tpart);
         if constexpr (!BF) {
             block_sum2(sh, gpart, tpart);
             if (tid == 0) {
@@ -284,7 +265,7 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
     if constexpr (!BF) T = (MODE == MODE_ADJ || p.base) ? sh.T : 1.0;  // a uniform teleport sums to 1 exactly
     LiveSum L{};
     if constexpr (LIVE_G) L = live_sum_setup<MODE>(p, T, sh.gprev);
-    double adj_sum = sh.gprev;  // adjoint: sum lambda as the sweep starts
+    AdjOffset A{sh.gprev, 0.0, 0.0f, 0.0, 0.0, 0};  // adjoint: sum lambda, deflation offset
     const double tol = (MODE == MODE_ADJ) ? p.tol * T : p.tol;
 
     // Gathers that take ordinary loads (L1): the CTA's own block with DAG_READ_OWN_L1 (as fresh as L2: only
@@ -474,7 +455,7 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
                     xo_bits = ld_relaxed_b32(X + v);
                     if constexpr (!BF) dg = ld_stream_f32(p.degf + v);
                 }
-                const uint32_t xnew = row_update<MODE>(p, v, sh.rowsum[r], xo_bits, dg, gt, res_part, g_part,
+                const uint32_t xnew = row_update<MODE>(p, v, sh.rowsum[r], xo_bits, dg, gt, A.off_f, res_part, g_part,
                                                        dg_part);
                 if constexpr (FRONTIER)  // the row goes on the CTA's list; its marks are counted at the sweep's end
                     log_changed(p.fr_chg + row_lo, &sh.nchg, xnew < xo_bits, v, epilogue_lanes(NA, k));
@@ -503,6 +484,7 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
         marks = 0;
         block_sum2(sh, res_d, g_d);
         if (tid == 0 && res_d != 0.0) atomicAdd(&sb->acc_res[slot], res_d);
+        if (MODE == MODE_ADJ && tid == 0 && g_d != 0.0) atomicAdd(&sb->acc_g[slot], g_d);
         if (FRONTIER && tid == 0) {
             if (g_d != 0.0) atomicAdd(&sb->acc_g[slot], g_d);
             // edges of the tiles run: an own sweep runs all of the CTA's tiles
@@ -513,10 +495,8 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
         if (!grid_barrier(sb, p.nblocks, bar_target, p.timeout_ns)) return;
         if (tid == 0) {
             sh.res = ld_relaxed_f64(&sb->acc_res[slot]);
-            if (FRONTIER) {
-                sh.gprev = ld_relaxed_f64(&sb->acc_g[slot]);
-                sh.cnt[0] = ld_relaxed_i32(&sb->fr_nchg[slot]);
-            }
+            if (FRONTIER || MODE == MODE_ADJ) sh.gprev = ld_relaxed_f64(&sb->acc_g[slot]);
+            if (FRONTIER) sh.cnt[0] = ld_relaxed_i32(&sb->fr_nchg[slot]);
             if (c == 0) {
                 const int dead = (it + 2) % 3;  // read by everyone before this barrier
                 sb->acc_res[dead] = 0.0;
@@ -533,17 +513,7 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
             ++it;
             break;
         }
-        if constexpr (MODE == MODE_ADJ) {  // deflation of the slow mode along 1 (adjoint_shift)
-            if (tid == 0) sh.gprev = live_value(sb, L);
-            __syncthreads();
-            const double sum_new = sh.gprev;
-            const float shift = adjoint_shift(p, sum_new, adj_sum);
-            for (int v = row_lo + tid; v < row_hi; v += NT)
-                st_relaxed_b32(X + v, __float_as_uint(__uint_as_float(ld_relaxed_b32(X + v)) + shift));
-            adj_sum = sum_new + (double)p.n * shift;
-            if (c == 0 && tid == 0) live_add(sb, 0, (float)((double)p.n * shift), L.S);
-            if (!grid_barrier(sb, p.nblocks, bar_target, p.timeout_ns)) return;  // every value shifted
-        }
+        if constexpr (MODE == MODE_ADJ) adjoint_deflate(p, A, sh.gprev, false);  // the slow mode along 1, as an offset
         if constexpr (FRONTIER) {
             // sparse next sweep: stamp the tiles the changed rows feed, publish them in one list, run that
             const bool was_shared = shared;
@@ -563,16 +533,8 @@ __global__ void __launch_bounds__(NT, MINBLOCKS) sweep_tma_kernel(const SweepPar
         }
     }
 
-    // ---------------- output of the owned rows ----------------
-    for (int v = row_lo + tid; v < row_hi; v += NT) {
-        const uint32_t x = ld_relaxed_b32(X + v);
-        if constexpr (BF || MODE == MODE_ADJ || MODE == MODE_PRW) {
-            ((uint32_t*)p.out)[v] = x;
-        } else {
-            const float dg = p.degf[v];
-            ((float*)p.out)[v] = dg > 0.0f ? __uint_as_float(x) * dg : __uint_as_float(x);
-        }
-    }
+    // ---------------- output (a grid-stride pass, write_output) ----------------
+    write_output<MODE>(p, X, A.off_f);
     if (tid == 0 && c == 0) {
         sb->iters = it;
         sb->residual = last_res;

@@ -65,7 +65,6 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_warp_kernel(const SweepP
     uint32_t* X1 = (uint32_t*)p.x1;
     const int row_lo = p.cta_row[w], row_hi = p.cta_row[w + 1];  // rows whose end item lies in the run
     const int t_lo = p.cta_tile[w], t_hi = p.cta_tile[w + 1];
-    const float inv_n = 1.0f / (float)p.n;
     int* end = sh.end[wl];
     uint32_t* val = sh.val[wl];
     uint32_t* sum = sh.sum[wl];
@@ -74,27 +73,10 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_warp_kernel(const SweepP
     const bool mid0 = t_lo < t_hi && p.tile_nz[t_lo] > p.rowptr[p.tile_row[t_lo]];
     const bool head = mid0 && row_hi > row_lo;
 
-    // ---------------- initial values of the owned rows (a row-range sweep is given them) ----------------
+    // ---------------- initial values, a grid-stride pass (a row-range sweep is given them) ----------------
     if (!p.shard) {
         double gpart = 0.0, tpart = 0.0;
-        for (int v = row_lo + lane; v < row_hi; v += 32) {
-            if constexpr (BF) {
-                X0[v] = (v == (int)p.src) ? 0u : INF;
-            } else if constexpr (MODE == MODE_ADJ) {
-                const float cv = p.base[v];
-                const float l0 = p.init ? p.init[v] : cv;
-                X0[v] = __float_as_uint(l0);
-                gpart += (double)l0;
-                tpart += fabs((double)cv);
-            } else {
-                const float t = p.base ? p.base[v] : inv_n;
-                const float r0 = p.init ? p.init[v] : t;
-                const float dg = p.degf[v];
-                X0[v] = __float_as_uint((MODE == MODE_PR && dg > 0.0f) ? r0 / dg : r0);
-                if (dg > 0.0f) gpart += (double)r0;
-                tpart += (double)t;
-            }
-        }
+        init_values<MODE>(p, X0, gpart, tpart);
         if constexpr (!BF) {
             block_sum2(sh, gpart, tpart);
             if (tid == 0) {
@@ -114,6 +96,7 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_warp_kernel(const SweepP
     __syncthreads();
     if constexpr (!BF) T = (MODE == MODE_ADJ || p.base || p.shard) ? sh.T : 1.0;  // a uniform teleport sums to 1
     double gprev = BF ? 0.0 : sh.gprev;
+    AdjOffset A{gprev, 0.0, 0.0f, 0.0, 0.0, 0};  // adjoint: sum lambda, deflation offset
     LiveSum L{};
     if constexpr (LIVE_G) L = live_sum_setup<MODE>(p, T, gprev);
     const double tol = (MODE == MODE_ADJ) ? p.tol * T : p.tol;
@@ -158,8 +141,7 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_warp_kernel(const SweepP
                 const int j = lane + 32 * q;
                 if (j < NB) val[j] = nx.term[q];
             }
-            for (int i = lane; i < NA; i += 32) end[i] = (int)ld_vertex_b32(p.rowptr + a0 + i + 1, pol_vertex) - b0;
-            if (lane == 0) end[NA] = INT_MAX;
+            wstage_ends<WIPT>(end, nx, p, lane, pol_vertex);
             if (t + 1 < t_hi)
                 wfetch<MODE, WIPT>(nx, p, xin, t + 1, lane, rmode, LIVE_G && ((t + 1 - t_lo) & (LIVE_EVERY - 1)) == 0,
                              pol_edge, pol_vertex);
@@ -186,12 +168,21 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_warp_kernel(const SweepP
                     if constexpr (!BF) dg_k[k] = ld_stream_f32(p.degf + a0 + r);
                 }
             }
+            // the adjoint's base terms c_v: one row's load ahead of its update (a tile of many rows would
+            // otherwise wait once per row)
+            float bv_next = (MODE == MODE_ADJ && lane < NA) ? row_base<MODE>(p, a0 + lane) : 0.0f;
 #pragma unroll
             for (int k = 0; k < WIPT; ++k) {
                 const int r = lane + 32 * k;
+                float bv = bv_next;
+                if constexpr (MODE == MODE_ADJ) {
+                    if (k + 1 < WIPT && r + 32 < NA) bv_next = row_base<MODE>(p, a0 + r + 32);
+                }
                 if (r >= NA || (k == 0 && lane == 0 && skip)) continue;
                 const int v = a0 + r;
-                const uint32_t xnew = row_update<MODE>(p, v, sum[r], xo_k[k], dg_k[k], gt, res_part, g_part, dg_part);
+                if constexpr (MODE != MODE_ADJ) bv = row_base<MODE>(p, v);
+                const uint32_t xnew =
+                    row_update_b<MODE>(p, v, sum[r], xo_k[k], dg_k[k], gt, bv, A.off_f, res_part, g_part, dg_part);
                 if constexpr (SYNC) st_weak_b32(xout + v, xnew);
                 else if constexpr (ASYNC) st_relaxed_b32(X0 + v, xnew);
                 else buf[v - buf_first] = xnew;
@@ -251,12 +242,8 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_warp_kernel(const SweepP
                 const int v = row_lo;
                 const uint32_t xo = ld_weak_b32(xin + v);
                 const float dg = BF ? 0.0f : p.degf[v];
-                if constexpr (LIVE_G) {  // the live global term as the row is computed
-                    long long G = 0;
-                    for (int k = 0; k < GSTRIPES; ++k) G += ld_relaxed_i64(&sb->stripe[k * GSTRIDE]);
-                    gt = live_term<MODE>(L, G);
-                }
-                const uint32_t xnew = row_update<MODE>(p, v, s, xo, dg, gt, res_part, g_part, dg_part);
+                if constexpr (LIVE_G) gt = live_term<MODE>(L, stripes_total(sb));  // the live term as the row is computed
+                const uint32_t xnew = row_update<MODE>(p, v, s, xo, dg, gt, A.off_f, res_part, g_part, dg_part);
                 if constexpr (SYNC) st_weak_b32(xout + v, xnew);
                 else st_relaxed_b32(X0 + v, xnew);
             }
@@ -272,7 +259,7 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_warp_kernel(const SweepP
         block_sum2(sh, res_d, g_d);
         if (tid == 0) {
             if (res_d != 0.0) atomicAdd(&sb->acc_res[slot], res_d);
-            if (SYNC && !BF && g_d != 0.0) atomicAdd(&sb->acc_g[slot], g_d);
+            if ((SYNC || MODE == MODE_ADJ) && !BF && g_d != 0.0) atomicAdd(&sb->acc_g[slot], g_d);
         }
         if (!grid_barrier(sb, p.nblocks, bar_target, p.timeout_ns)) return;
         if (tid == 0) {
@@ -292,20 +279,13 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_warp_kernel(const SweepP
             ++it;
             break;
         }
+        if constexpr (MODE == MODE_ADJ) adjoint_deflate(p, A, gprev, SYNC);  // the slow mode along 1, as an offset
     }
 
-    // ---------------- output of the owned rows (a row-range sweep leaves them in x1) ----------------
+    // ---------------- output, a grid-stride pass (a row-range sweep leaves them in x1) ----------------
     if (!p.shard) {
         const uint32_t* xf = SYNC ? ((it & 1) ? X1 : X0) : X0;
-        for (int v = row_lo + lane; v < row_hi; v += 32) {
-            const uint32_t x = ld_relaxed_b32(xf + v);
-            if constexpr (BF || MODE == MODE_ADJ || MODE == MODE_PRW) {
-                ((uint32_t*)p.out)[v] = x;
-            } else {
-                const float dg = p.degf[v];
-                ((float*)p.out)[v] = dg > 0.0f ? __uint_as_float(x) * dg : __uint_as_float(x);
-            }
-        }
+        write_output<MODE>(p, xf, A.off_f);
     }
     if (lane == 0 && flushes) atomicAdd((unsigned long long*)&sb->flushes, (unsigned long long)flushes);
     if (tid == 0 && c == 0) {
@@ -375,34 +355,14 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_ordered_kernel(const Swe
     unsigned long long bar_target = 0;
     uint32_t* X = (uint32_t*)p.x0;
     unsigned long long* pub = p.wpub;  // [T]
-    const float inv_n = 1.0f / (float)p.n;
     int* end = sh.end[wl];
     uint32_t* val = sh.val[wl];
     uint32_t* sum = sh.sum[wl];
-    const long long gthreads = (long long)p.nblocks * NT, gtid = (long long)c * NT + tid;
 
     // ---------------- initial values (any thread any row: nothing reads them before the barrier) ----------------
     {
         double gpart = 0.0, tpart = 0.0;
-        for (long long vv = gtid; vv < p.n; vv += gthreads) {
-            const int v = (int)vv;
-            if constexpr (BF) {
-                X[v] = (v == (int)p.src) ? 0u : INF;
-            } else if constexpr (MODE == MODE_ADJ) {
-                const float cv = p.base[v];
-                const float l0 = p.init ? p.init[v] : cv;
-                X[v] = __float_as_uint(l0);
-                gpart += (double)l0;
-                tpart += fabs((double)cv);
-            } else {
-                const float t = p.base ? p.base[v] : inv_n;
-                const float r0 = p.init ? p.init[v] : t;
-                const float dg = p.degf[v];
-                X[v] = __float_as_uint((MODE == MODE_PR && dg > 0.0f) ? r0 / dg : r0);
-                if (dg > 0.0f) gpart += (double)r0;
-                tpart += (double)t;
-            }
-        }
+        init_values<MODE>(p, X, gpart, tpart);
         if constexpr (!BF) {
             block_sum2(sh, gpart, tpart);
             if (tid == 0) {
@@ -423,6 +383,7 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_ordered_kernel(const Swe
     if constexpr (!BF) T_tot = (MODE == MODE_ADJ || p.base) ? sh.T : 1.0;
     LiveSum L{};
     if constexpr (LIVE_G) L = live_sum_setup<MODE>(p, T_tot, sh.gprev);
+    AdjOffset A{BF ? 0.0 : sh.gprev, 0.0, 0.0f, 0.0, 0.0, 0};  // adjoint: sum lambda, deflation offset
     const double tol = (MODE == MODE_ADJ) ? p.tol * T_tot : p.tol;
     const int rmode = p.read_mode == READ_CACHED ? READ_CACHED : READ_COHERENT;
     const uint64_t pol_edge = policy_evict_first();
@@ -470,7 +431,7 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_ordered_kernel(const Swe
                 const uint32_t total = O::combine(C, pend_val);
                 if (pend_fin) {
                     const uint32_t xnew =
-                        row_update<MODE>(p, pend_row, total, pend_xo, pend_dg, gt, res_part, g_part, dg_part);
+                        row_update<MODE>(p, pend_row, total, pend_xo, pend_dg, gt, A.off_f, res_part, g_part, dg_part);
                     st_relaxed_b32(X + pend_row, xnew);
                 } else {
                     st_relaxed_u64(pub + pend_t, ((unsigned long long)(stamp | TPUB_INCL) << 32) | total);
@@ -496,8 +457,7 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_ordered_kernel(const Swe
                 const int j = lane + 32 * q;
                 if (j < NB) val[j] = nx.term[q];
             }
-            for (int i = lane; i < NA; i += 32) end[i] = (int)ld_vertex_b32(p.rowptr + a0 + i + 1, pol_vertex) - b0;
-            if (lane == 0) end[NA] = INT_MAX;
+            wstage_ends<WIPT>(end, nx, p, lane, pol_vertex);
             if (t + W < T)
                 wfetch<MODE, WIPT>(nx, p, X, t + W, lane, rmode, LIVE_G && ((k + 1) & (LIVE_EVERY - 1)) == 0,
                                    pol_edge, pol_vertex);
@@ -531,7 +491,8 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_ordered_kernel(const Swe
                 const int r = lane + 32 * q;
                 if (r >= NA || (q == 0 && lane == 0 && skip)) continue;
                 const int v = a0 + r;
-                const uint32_t xnew = row_update<MODE>(p, v, sum[r], xo_k[q], dg_k[q], gt, res_part, g_part, dg_part);
+                const uint32_t xnew =
+                    row_update<MODE>(p, v, sum[r], xo_k[q], dg_k[q], gt, A.off_f, res_part, g_part, dg_part);
                 st_relaxed_b32(X + v, xnew);
             }
             // -------- the previous tile's look-back, then this tile's becomes pending --------
@@ -563,9 +524,11 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_ordered_kernel(const Swe
         double res_d = (double)res_part, g_d = (double)g_part;
         block_sum2(sh, res_d, g_d);
         if (tid == 0 && res_d != 0.0) atomicAdd(&sb->acc_res[slot], res_d);
+        if (MODE == MODE_ADJ && tid == 0 && g_d != 0.0) atomicAdd(&sb->acc_g[slot], g_d);
         if (!grid_barrier(sb, p.nblocks, bar_target, p.timeout_ns)) return;
         if (tid == 0) {
             sh.res = ld_relaxed_f64(&sb->acc_res[slot]);
+            if (MODE == MODE_ADJ) sh.gprev = ld_relaxed_f64(&sb->acc_g[slot]);
             if (c == 0) {
                 const int dead = (it + 2) % 3;  // read by everyone before this barrier
                 sb->acc_res[dead] = 0.0;
@@ -579,19 +542,11 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_ordered_kernel(const Swe
             ++it;
             break;
         }
+        if constexpr (MODE == MODE_ADJ) adjoint_deflate(p, A, sh.gprev, false);  // the slow mode along 1, as an offset
     }
 
     // ---------------- output ----------------
-    for (long long vv = gtid; vv < p.n; vv += gthreads) {
-        const int v = (int)vv;
-        const uint32_t x = ld_relaxed_b32(X + v);
-        if constexpr (BF || MODE == MODE_ADJ || MODE == MODE_PRW) {
-            ((uint32_t*)p.out)[v] = x;
-        } else {
-            const float dg = p.degf[v];
-            ((float*)p.out)[v] = dg > 0.0f ? __uint_as_float(x) * dg : __uint_as_float(x);
-        }
-    }
+    write_output<MODE>(p, X, A.off_f);
     if (tid == 0 && c == 0) {
         sb->iters = it;
         sb->residual = last_res;

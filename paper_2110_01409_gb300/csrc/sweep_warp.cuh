@@ -35,6 +35,7 @@ template <int WIPT>
 struct WStage {
     int a0, b0, NA, NB;
     int rp0;              // rowptr[a0]: the tile starts inside row a0 when b0 > rp0
+    int re0;              // rowptr[a0 + lane + 1]: the end of the tile's row `lane` (lane < NA)
     uint32_t term[WIPT];  // edge terms: gathered value, combined with the edge's weight / value
     uint32_t xo;          // old value of row a0 + lane
     float dg;             // its out-degree (PageRank)
@@ -51,6 +52,7 @@ __device__ __forceinline__ void wfetch(WStage<WIPT>& st, const SweepParams& p, c
     st.NA = p.tile_row[t + 1] - st.a0;
     st.NB = p.tile_nz[t + 1] - st.b0;
     st.rp0 = (int)ld_vertex_b32(p.rowptr + st.a0, pol_vertex);
+    st.re0 = lane < st.NA ? (int)ld_vertex_b32(p.rowptr + st.a0 + lane + 1, pol_vertex) : 0;
     int col[WIPT];
     uint32_t aux[WIPT];
 #pragma unroll
@@ -84,6 +86,17 @@ __device__ __forceinline__ void wfetch(WStage<WIPT>& st, const SweepParams& p, c
         if constexpr (!BF) st.dg = __uint_as_float(ld_vertex_b32(p.degf + st.a0 + lane, pol_vertex));
     }
     if (live) st.gs = ld_relaxed_i64(&p.sync->stripe[lane * GSTRIDE]);
+}
+
+// Tile-relative row ends of a staged tile into end[0 .. NA] (sentinel INT_MAX at NA): the first 32 came
+// with the tile's fetch, the rest (a tile of mostly empty rows) are loaded here.
+template <int WIPT>
+__device__ __forceinline__ void wstage_ends(int* end, const WStage<WIPT>& st, const SweepParams& p, int lane,
+                                            uint64_t pol_vertex)
+{
+    if (lane < st.NA) end[lane] = st.re0 - st.b0;
+    for (int i = lane + 32; i < st.NA; i += 32) end[i] = (int)ld_vertex_b32(p.rowptr + st.a0 + i + 1, pol_vertex) - st.b0;
+    if (lane == 0) end[st.NA] = INT_MAX;
 }
 
 // One warp tile's merge path, warp segmented scan and per-row sums into

@@ -72,7 +72,10 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_warp_frontier_kernel(con
     const bool mid0 = t_lo < t_hi && p.tile_nz[t_lo] > p.rowptr[p.tile_row[t_lo]];
     const bool head = mid0 && row_hi > row_lo;
 
-    for (int v = row_lo + lane; v < row_hi; v += 32) X[v] = (v == (int)p.src) ? 0u : INF;
+    {
+        double unused_n = 0.0, unused_t = 0.0;
+        init_values<MODE>(p, X, unused_n, unused_t);
+    }
     if (p.skip_barrier_cta0 && c == 0) return;  // test hook: the others' waits must run out
     if (!grid_barrier(sb, p.nblocks, bar_target, p.timeout_ns)) return;
 
@@ -110,8 +113,7 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_warp_frontier_kernel(con
                     const int j = lane + 32 * q;
                     if (j < NB) val[j] = nx.term[q];
                 }
-                for (int i = lane; i < NA; i += 32) end[i] = (int)ld_vertex_b32(p.rowptr + a0 + i + 1, pol_vertex) - b0;
-                if (lane == 0) end[NA] = INT_MAX;
+                wstage_ends<WIPT>(end, nx, p, lane, pol_vertex);
                 if (t + 1 < t_hi) wfetch<MODE, WIPT>(nx, p, X, t + 1, lane, rmode, false, pol_edge, pol_vertex);
                 __syncwarp();
                 carry = wwalk<MODE, WIPT>(end, val, sum, NA, NB, carry, lane);
@@ -133,7 +135,7 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_warp_frontier_kernel(con
                     bool changed = false;
                     if (r < NA && !(k == 0 && lane == 0 && skip)) {
                         const uint32_t xnew =
-                            row_update<MODE>(p, a0 + r, sum[r], xo_k[k], 0.0f, 0.0f, res_part, unused_g, unused_dg);
+                            row_update<MODE>(p, a0 + r, sum[r], xo_k[k], 0.0f, 0.0f, 0.0f, res_part, unused_g, unused_dg);
                         changed = xnew < xo_k[k];
                         st_relaxed_b32(X + a0 + r, xnew);
                     }
@@ -163,7 +165,7 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_warp_frontier_kernel(con
                     bool changed = false;
                     if (lane == 0) {
                         const uint32_t xo = ld_weak_b32(X + row_lo);
-                        const uint32_t xnew = row_update<MODE>(p, row_lo, s, xo, 0.0f, 0.0f, res_part, unused_g,
+                        const uint32_t xnew = row_update<MODE>(p, row_lo, s, xo, 0.0f, 0.0f, 0.0f, res_part, unused_g,
                                                                unused_dg);
                         changed = xnew < xo;
                         st_relaxed_b32(X + row_lo, xnew);
@@ -217,8 +219,7 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_warp_frontier_kernel(con
                     const int j = lane + 32 * q;
                     if (j < NB) val[j] = nx.term[q];
                 }
-                for (int i = lane; i < NA; i += 32) end[i] = (int)ld_vertex_b32(p.rowptr + a0 + i + 1, pol_vertex) - b0;
-                if (lane == 0) end[NA] = INT_MAX;
+                wstage_ends<WIPT>(end, nx, p, lane, pol_vertex);
                 if (tn >= 0) wfetch<MODE, WIPT>(nx, p, X, tn, lane, READ_COHERENT, false, pol_edge, pol_vertex);
                 __syncwarp();
                 const uint32_t trail = wwalk<MODE, WIPT>(end, val, sum, NA, NB, O::identity(), lane);
@@ -303,7 +304,7 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_warp_frontier_kernel(con
         }
     }
 
-    for (int v = row_lo + lane; v < row_hi; v += 32) ((uint32_t*)p.out)[v] = ld_relaxed_b32(X + v);
+    write_output<MODE>(p, X);
     if (tid == 0 && c == 0) {
         sb->iters = it;
         sb->residual = last_res;

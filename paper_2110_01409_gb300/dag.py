@@ -100,7 +100,7 @@ def lib():
             L.dag_transpose.argtypes = [_vp, _vp, _vp, _vp, _vp]
             L.dag_normalize_weights.argtypes = [_vp, _vp, _vp, _vp, _vp]
             L.dag_pagerank_adjoint.argtypes = [_vp, _vp, _f32, _f64, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp,
-                                               _vp, _vp, _vp, ctypes.POINTER(_Stats), _vp]
+                                               _vp, _vp, _vp, _i32, ctypes.POINTER(_Stats), _vp]
             L.dag_strerror.argtypes = [_i32]
             L.dag_strerror.restype = ctypes.c_char_p
             L.dag_last_error_message.argtypes = []
@@ -342,8 +342,9 @@ def normalize_weights(plan: Plan, w: torch.Tensor):
 
 
 def pagerank_adjoint(in_plan: Plan, out_plan: Plan, val, val_out, s, rank, c, d=0.85, tol=1e-6,
-                     variant="delayed", delta=256, max_iters=10000, want_lambda=False, stream=None):
-    """Adjoint solve + gradients. Returns (grad_w [m], grad_t [n], lambda or None, stats)."""
+                     variant="delayed", delta=256, max_iters=10000, want_lambda=False, stream=None, reads="refresh"):
+    """Adjoint solve + gradients (reads: the adjoint sweep's read path, see READ_MODES; the warp forms run
+    on out_plan's warp tile). Returns (grad_w [m], grad_t [n], lambda or None, stats)."""
     dev = rank.device
     gw = torch.empty(in_plan.m, dtype=torch.float32, device=dev)
     gt = torch.empty(in_plan.n, dtype=torch.float32, device=dev)
@@ -351,7 +352,7 @@ def pagerank_adjoint(in_plan: Plan, out_plan: Plan, val, val_out, s, rank, c, d=
     st = _Stats()
     rc = lib().dag_pagerank_adjoint(in_plan.h, out_plan.h, d, tol, _variant(variant), delta, max_iters,
                                     _ptr(val), _ptr(val_out), _ptr(s), _ptr(rank), _ptr(c), _ptr(gw), _ptr(gt),
-                                    _ptr(lam), ctypes.byref(st), _stream(stream))
+                                    _ptr(lam), READ_MODES[reads], ctypes.byref(st), _stream(stream))
     _raise(rc)
     return gw, gt, lam, _stats(st, in_plan.m)
 
@@ -414,23 +415,27 @@ class WeightedPageRank:
     """Forward/backward of weighted PageRank over one graph: holds the in-edge
     plan, the out-edge CSR and its plan, and the in->out edge permutation."""
 
-    def __init__(self, plan: Plan, d=0.85, tol=1e-6, variant="delayed", delta=256, max_iters=10000):
+    def __init__(self, plan: Plan, d=0.85, tol=1e-6, variant="delayed", delta=256, max_iters=10000,
+                 reads="refresh", adjoint_reads=None):
         self.plan, self.d, self.tol, self.variant, self.delta, self.max_iters = plan, d, tol, variant, delta, max_iters
+        self.reads = reads
+        self.adjoint_reads = reads if adjoint_reads is None else adjoint_reads
         orow, ocol, perm = transpose(plan)
         self.perm = perm
         self.out_plan = Plan(orow, ocol)
+        self.out_plan.set_warp_tile(plan.warp_tile_items() // 32)
 
     def forward(self, w: torch.Tensor, teleport: torch.Tensor | None = None):
         val, s = normalize_weights(self.plan, w)
         r, st = pagerank(self.plan, self.d, self.tol, self.variant, self.delta, self.max_iters, teleport=teleport,
-                         val=val)
+                         val=val, reads=self.reads)
         return r, val, s, st
 
     def backward(self, val, s, r, c):
         val_out = torch.empty_like(val)
         _raise(lib().dag_gather_f32(_ptr(val), _ptr(self.perm), self.plan.m, _ptr(val_out), _stream()), False)
         return pagerank_adjoint(self.plan, self.out_plan, val, val_out, s, r, c.contiguous(), self.d, self.tol,
-                                self.variant, self.delta, self.max_iters)
+                                self.variant, self.delta, self.max_iters, reads=self.adjoint_reads)
 
 
 class PageRankFn(torch.autograd.Function):

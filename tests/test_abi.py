@@ -86,7 +86,7 @@ def test_null_arguments_are_refused_without_a_gpu(lib):
         "dag_transpose": lambda: lib.dag_transpose(N, N, N, N, N),
         "dag_normalize_weights": lambda: lib.dag_normalize_weights(N, N, N, N, N),
         "dag_pagerank_adjoint": lambda: lib.dag_pagerank_adjoint(N, N, f(0.85), d(1e-6), 1, 0, 10, N, N, N, N, N,
-                                                                 N, N, N, N, N),
+                                                                 N, N, N, 0, N, N),
         "dag_pagerank_noalloc": lambda: lib.dag_pagerank_noalloc(N, f(0.85), d(1e-6), 1, 0, 10, N, N, N, N),
         "dag_access_matrix": lambda: lib.dag_access_matrix(N, 4, N, N),
         "dag_debug_skip_barrier_once": lambda: lib.dag_debug_skip_barrier_once(N, 100),

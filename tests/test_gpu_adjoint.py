@@ -49,12 +49,16 @@ def _problem(g, seed, k):
     return w, t, c
 
 
-@pytest.mark.parametrize("variant,delta", [("sync", 0), ("delayed", 64), ("async", 0)])
-def test_adjoint_subgraph512_vs_dense_and_fd(dag, variant, delta):
+FORMS = [("sync", 0, "refresh"), ("delayed", 64, "refresh"), ("async", 0, "refresh"), ("sync", 0, "warp"),
+         ("async", 0, "warp+cached"), ("delayed", 64, "warp"), ("async", 0, "ordered+cached")]
+
+
+@pytest.mark.parametrize("variant,delta,reads", FORMS)
+def test_adjoint_subgraph512_vs_dense_and_fd(dag, variant, delta, reads):
     g = _subgraph512()
     w, t, c = _problem(g, 5, 64)
     plan = dag.Plan.from_graph(g, "cuda")
-    model = dag.WeightedPageRank(plan, d=0.85, tol=1e-6, variant=variant, delta=delta)
+    model = dag.WeightedPageRank(plan, d=0.85, tol=1e-6, variant=variant, delta=delta, reads=reads)
     wt = torch.from_numpy(w).cuda().requires_grad_(True)
     tt = torch.from_numpy(t.astype(np.float32)).cuda().requires_grad_(True)
     r = dag.PageRankFn.apply(wt, tt, model)
@@ -100,20 +104,33 @@ def scaled_case(dag):
 
 
 @pytest.mark.parametrize("alpha", [1e-6, 1e6])
-@pytest.mark.parametrize("variant,delta", [("async", 0), ("delayed", 64)])
-def test_adjoint_gradients_scale_with_c(dag, scaled_case, variant, delta, alpha):
+@pytest.mark.parametrize("variant,delta,reads", [("async", 0, "refresh"), ("delayed", 64, "refresh"),
+                                                 ("async", 0, "warp+cached"), ("async", 0, "ordered+cached")])
+def test_adjoint_gradients_scale_with_c(dag, scaled_case, variant, delta, reads, alpha):
     # The adjoint is linear in c and stops relative to ||c||_1, so c -> alpha c scales both
     # gradients by alpha. The asynchronous and delayed sweeps keep the live sum of lambda in
     # fixed point with a unit set from ||c||_1; this checks that unit far from ||c||_1 ~ 1.
     g, w, t, c, gw_ref, gt_ref = scaled_case
     plan = dag.Plan.from_graph(g, "cuda")
-    model = dag.WeightedPageRank(plan, tol=1e-7, variant=variant, delta=delta)
+    model = dag.WeightedPageRank(plan, tol=1e-7, variant=variant, delta=delta, reads=reads)
     r, val, s, st = model.forward(torch.from_numpy(w).cuda(), torch.from_numpy(t.astype(np.float32)).cuda())
     assert st["converged"]
     gw, gt, _, st2 = model.backward(val, s, r, torch.from_numpy((c * alpha).astype(np.float32)).cuda())
     assert st2["converged"]
     assert _rel(gw.double().cpu().numpy() / alpha, gw_ref) <= 1e-4
     assert _rel(gt.double().cpu().numpy() / alpha, gt_ref) <= 1e-4
+
+
+def test_adjoint_refuses_flags_it_does_not_take(dag):
+    g = I.rmat(10, 16, seed=1)
+    plan = dag.Plan.from_graph(g, "cuda")
+    model = dag.WeightedPageRank(plan, tol=1e-6, variant="async", delta=0)
+    w, t, c = _problem(g, 2, 16)
+    r, val, s, _ = model.forward(torch.from_numpy(w).cuda())
+    for reads in ("frontier", "local"):
+        model.adjoint_reads = reads
+        with pytest.raises(dag.DagError):
+            model.backward(val, s, r, torch.from_numpy(c.astype(np.float32)).cuda())
 
 
 def test_transpose_and_normalize_match_definitions(dag):
@@ -133,14 +150,14 @@ def test_transpose_and_normalize_match_definitions(dag):
     assert np.max(np.abs(s.cpu().numpy()[has] - s64[has]) / s64[has]) <= 1e-5
 
 
-@pytest.mark.parametrize("variant,delta", [("sync", 0), ("async", 0), ("delayed", 64)])
-def test_adjoint_deflation_cuts_the_slow_mode(dag, scaled_case, variant, delta):
+@pytest.mark.parametrize("variant,delta,reads", FORMS)
+def test_adjoint_deflation_cuts_the_slow_mode(dag, scaled_case, variant, delta, reads):
     # The adjoint's slow error mode along 1 (B 1 = d 1) is deflated after every sweep, so the
     # adjoint solve needs far fewer sweeps than the plain Jacobi adjoint at the same tolerance
     # (the oracle, which does not deflate), and its gradients stay within the dense bound.
     g, w, t, c, gw_ref, gt_ref = scaled_case
     plan = dag.Plan.from_graph(g, "cuda")
-    model = dag.WeightedPageRank(plan, tol=1e-6, variant=variant, delta=delta)
+    model = dag.WeightedPageRank(plan, tol=1e-6, variant=variant, delta=delta, reads=reads)
     r, val, s, st = model.forward(torch.from_numpy(w).cuda(), torch.from_numpy(t.astype(np.float32)).cuda())
     gw, gt, _, st2 = model.backward(val, s, r, torch.from_numpy(c.astype(np.float32)).cuda())
     assert st2["converged"]
