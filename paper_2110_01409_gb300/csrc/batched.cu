@@ -101,17 +101,31 @@ __global__ void batched_kernel(const BatchParams p)
     {
         float gpart = 0.0f, tpart = 0.0f;  // per-lane partials over the block; FP64 in the atomics
         uint32_t s0 = BF && colok ? p.src[col] : 0u;
-        for (int v = row_lo; v < row_hi; ++v) {
-            if (!colok) continue;
-            const size_t k = (size_t)v * B + col;
+        // four rows' inputs loaded before any is stored (the stores could alias the inputs, so the
+        // compiler would not overlap them itself)
+        for (int v0 = row_lo; colok && v0 < row_hi; v0 += 4) {
             if constexpr (BF) {
-                p.X0[k] = ((uint32_t)v == s0) ? 0u : INF;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int v = v0 + q;
+                    if (v < row_hi) p.X0[(size_t)v * B + col] = ((uint32_t)v == s0) ? 0u : INF;
+                }
             } else {
-                const float t = p.V[k];
-                const float dg = p.degf[v];
-                p.X0[k] = __float_as_uint(dg > 0.0f ? t / dg : t);
-                if (dg > 0.0f) gpart += t;
-                tpart += t;
+                float t[4], dg[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int v = v0 + q;
+                    t[q] = v < row_hi ? p.V[(size_t)v * B + col] : 0.0f;
+                    dg[q] = v < row_hi ? p.degf[v] : 0.0f;
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int v = v0 + q;
+                    if (v >= row_hi) continue;
+                    p.X0[(size_t)v * B + col] = __float_as_uint(dg[q] > 0.0f ? t[q] / dg[q] : t[q]);
+                    if (dg[q] > 0.0f) gpart += t[q];
+                    tpart += t[q];
+                }
             }
         }
         if (!BF && colok) {
@@ -161,20 +175,36 @@ __global__ void batched_kernel(const BatchParams p)
             uint32_t acc = carry;
             int i = 0;
             int re = s_end[0];
+            // the inputs of the row being accumulated (old value, teleport entry, out-degree), loaded when
+            // the row starts so that they arrive while its edges are gathered; only this lane writes the
+            // row's value in this column, so a value loaded early is still the current one
+            uint32_t pre_old = 0u;
+            float pre_v = 0.0f, pre_dg = 0.0f;
+            auto preload = [&](int r) {
+                if (r >= NA || !active) return;
+                const int v = a0 + r;
+                const size_t k = (size_t)v * B + col;
+                pre_old = SYNC ? ld_weak_b32(xin + k) : ld_relaxed_b32(xin + k);
+                if constexpr (!BF) {
+                    pre_v = ld_stream_f32(p.V + k);
+                    pre_dg = p.degf[v];
+                }
+            };
+            preload(0);
             auto finish_row = [&](int r, uint32_t sum) {
                 const int v = a0 + r;
                 if (!active) return;
                 const size_t k = (size_t)v * B + col;
                 uint32_t xnew;
                 if constexpr (BF) {
-                    const uint32_t old = SYNC ? ld_weak_b32(xin + k) : ld_relaxed_b32(xin + k);
+                    const uint32_t old = pre_old;
                     xnew = sum < old ? sum : old;
                     if (xnew < old) res += 1.0f;
                 } else {
-                    const float xo = __uint_as_float(SYNC ? ld_weak_b32(xin + k) : ld_relaxed_b32(xin + k));
-                    const float dg = p.degf[v];
+                    const float xo = __uint_as_float(pre_old);
+                    const float dg = pre_dg;
                     const float rold = dg > 0.0f ? xo * dg : xo;
-                    const float rnew = (1.0f - p.d) * ld_stream_f32(p.V + k) + p.d * __uint_as_float(sum) + gt;
+                    const float rnew = (1.0f - p.d) * pre_v + p.d * __uint_as_float(sum) + gt;
                     res += fabsf(rnew - rold);
                     if (dg > 0.0f) {
                         gsum += rnew;
@@ -225,6 +255,7 @@ __global__ void batched_kernel(const BatchParams p)
                             acc = b_ident<BF>();
                             ++i;
                             re = s_end[i];
+                            preload(i);
                         }
                         uint32_t term;
                         if constexpr (BF) term = b_relax(xv[u], s_w[j]);
@@ -238,6 +269,7 @@ __global__ void batched_kernel(const BatchParams p)
                 if constexpr (DELAYED) { ++buf_cnt; maybe_flush(false); }
                 acc = b_ident<BF>();
                 ++i;
+                preload(i);
             }
             carry = acc;
             if constexpr (DELAYED) maybe_flush(t == tile_hi - 1);
@@ -286,16 +318,23 @@ __global__ void batched_kernel(const BatchParams p)
 
     // ---------------- output: r = x * outdeg, from the buffer of each column's last sweep ----------------
     if (!colok) return;
-    for (int v = row_lo; v < row_hi; ++v) {
-        const size_t k = (size_t)v * B + col;
-        uint32_t x;
-        if constexpr (SYNC) x = (last_it & 1) ? ld_relaxed_b32(p.X1 + k) : ld_relaxed_b32(p.X0 + k);
-        else x = ld_relaxed_b32(p.X0 + k);
-        if constexpr (BF) {
-            p.X0[k] = x;
-        } else {
-            const float dg = p.degf[v];
-            p.X0[k] = __float_as_uint(dg > 0.0f ? __uint_as_float(x) * dg : __uint_as_float(x));
+    const uint32_t* xf = (SYNC && (last_it & 1)) ? p.X1 : p.X0;
+    for (int v0 = row_lo; v0 < row_hi; v0 += 4) {  // four rows in flight
+        uint32_t x[4];
+        float dg[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int v = v0 + q;
+            x[q] = v < row_hi ? ld_relaxed_b32(xf + (size_t)v * B + col) : 0u;
+            dg[q] = (!BF && v < row_hi) ? p.degf[v] : 0.0f;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int v = v0 + q;
+            if (v >= row_hi) continue;
+            if constexpr (BF) p.X0[(size_t)v * B + col] = x[q];
+            else p.X0[(size_t)v * B + col] =
+                __float_as_uint(dg[q] > 0.0f ? __uint_as_float(x[q]) * dg[q] : __uint_as_float(x[q]));
         }
     }
 }
