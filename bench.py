@@ -38,7 +38,8 @@ PR_DELTA, SSSP_DELTA = 32, 32  # fixed-delta runs of the variant table and the C
 DELTAS = (0, 32, 256, 4096)
 WORKLOAD = (f"rmat{SCALE}: pagerank d=0.85 tol=1e-6 + sssp x{N_SOURCES} sources, "
             f"delayed method, delta picked per algorithm over {list(DELTAS)} "
-            f"(delta 0 also with own-block or all L1 reads, and for sssp the tile frontier on CTA or warp tiles) "
+            f"(delta 0 also with own-block or all L1 reads, and for sssp the tile frontier on CTA tiles, warp runs "
+            f"or CTA-ordered warp tiles) "
             f"and over warp-worker sweeps (sync, delta 16 / 256, async with three warp tile shapes) "
             f"and ordered warp sweeps (async, two warp tile shapes)")
 
@@ -205,7 +206,8 @@ def run_gpu(args):
         [("delayed", 0, "ordered+cached", ipt) for ipt in (7, 11)]
     cands = [("delayed", dl) for dl in DELTAS] + [("delayed", 0, "own_l1"), ("delayed", 0, "cached")] + warp_cands
     cands_bf = cands + [("delayed", 0, "frontier"), ("delayed", 0, "own_l1+frontier"), ("delayed", 0, "cached+frontier"),
-                        ("delayed", 0, "warp+frontier"), ("delayed", 0, "warp+cached+frontier")]
+                        ("delayed", 0, "warp+frontier"), ("delayed", 0, "warp+cached+frontier"),
+                        ("delayed", 0, "ordered+frontier"), ("delayed", 0, "ordered+cached+frontier")]
     tune_pr = autotune.tune(plan, "pagerank", candidates=cands, worker_fractions=[1.0], trials=2, cache=None)
     tune_bf = autotune.tune(plan, "sssp", candidates=cands_bf, worker_fractions=[1.0], trials=2, cache=None,
                             src=int(srcs[0]), w=w8_d)
@@ -387,8 +389,8 @@ def run_gpu(args):
 def kernel_name(mode, variant, delta, reads, warp_tile=7):
     """The sweep kernel a solve runs (for the roofline's kernel and the ncu launch list)."""
     var = "ASYNC" if variant == "async" or (variant == "delayed" and delta == 0) else variant.upper()
-    if reads.startswith("warp") and "frontier" in reads:
-        return f"sweep_warp_frontier_kernel<{mode},{warp_tile}>"
+    if reads.startswith(("warp", "ordered")) and "frontier" in reads:
+        return f"sweep_warp_frontier_kernel<{mode},{warp_tile}{',ordered' if reads.startswith('ordered') else ''}>"
     if reads.startswith("warp"):
         return f"sweep_warp_kernel<{mode},{var},{warp_tile}>"
     if reads.startswith("ordered"):
@@ -520,6 +522,7 @@ VARIANT_ROWS = [("sync", "sync", 0, "refresh"), ("async", "async", 0, "refresh")
                 ("async_cached", "async", 0, "cached"), ("async_cached_frontier", "async", 0, "cached+frontier"),
                 ("warp_async_frontier", "async", 0, "warp+frontier"),
                 ("warp_async_cached_frontier", "async", 0, "warp+cached+frontier"),
+                ("ordered_cached_frontier", "async", 0, "ordered+cached+frontier"),
                 ("delayed32", "delayed", 32, "refresh"), ("delayed256", "delayed", 256, "refresh"),
                 ("delayed4096", "delayed", 4096, "refresh"), ("delayed4096_local", "delayed", 4096, "local"),
                 ("warp_sync", "sync", 0, "warp"), ("warp_async_cached", "async", 0, "warp+cached"),

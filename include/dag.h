@@ -185,7 +185,10 @@ int dag_plan_set_worker_cap(dag_plan* plan, int32_t max_workers);
  * asynchronous sweep (Sec. I) with every warp on it, instead of one stream per
  * worker; rows spanning tiles are finished by a bounded look-back over per-tile
  * published partials. DAG_READ_CACHED selects ordinary (L1) gathers, else L2.
- * DAG_ERR_INVALID with the synchronous or delayed form.
+ * With DAG_SSSP_FRONTIER (asynchronous Bellman-Ford): the warp-tile frontier
+ * whose dense sweeps give each CTA the tiles of its warps' runs (a Sec. III-A
+ * block), taken by its warps in turn, a row split over tiles relaxed by each
+ * tile's atomic minimum. DAG_ERR_INVALID with the synchronous or delayed form.
  */
 #define DAG_WARP_ORDERED 128
 /*

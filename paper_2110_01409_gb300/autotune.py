@@ -37,7 +37,8 @@ SINGLE_CANDIDATES = [("sync", 0), ("async", 0), ("async", 0, "own_l1"), ("async"
                      ("async", 0, "ordered+cached", 7), ("async", 0, "ordered+cached", 11)]
 WARP_TILES = (5, 7, 11)
 SSSP_EXTRA = [("async", 0, "frontier"), ("async", 0, "own_l1+frontier"), ("async", 0, "cached+frontier"),
-              ("async", 0, "warp+frontier"), ("async", 0, "warp+cached+frontier")]  # Bellman-Ford only
+              ("async", 0, "warp+frontier"), ("async", 0, "warp+cached+frontier"), ("async", 0, "ordered+frontier"),
+              ("async", 0, "ordered+cached+frontier")]  # Bellman-Ford only
 BATCH_CANDIDATES = [("sync", 0), ("async", 0), ("delayed", 4), ("delayed", 16)]
 WORKER_FRACTIONS = [1.0, 0.5]
 

@@ -204,8 +204,8 @@ int sssp_impl(dag_plan* plan, uint32_t src, int variant, int delta, int max_iter
     p.ordered = (flags & DAG_WARP_ORDERED) ? 1 : 0;
     if (p.frontier && var == DAG_DELAYED)
         return set_error(DAG_ERR_INVALID, "the frontier runs the synchronous and asynchronous forms (delta 0)");
-    if (p.frontier && p.warp && (var != DAG_ASYNC || p.ordered))
-        return set_error(DAG_ERR_INVALID, "the warp-tile frontier runs the asynchronous form on warp runs");
+    if (p.frontier && p.warp && var != DAG_ASYNC)
+        return set_error(DAG_ERR_INVALID, "the warp-tile frontier runs the asynchronous form");
     if (p.frontier) {  // the frontier maps of this launch shape are built (once) outside the timed solve
         if (p.warp) {
             rc = warp_frontier_maps(plan, w8 ? MODE_BF8 : MODE_BF, s);

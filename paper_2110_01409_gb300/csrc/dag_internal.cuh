@@ -243,7 +243,7 @@ int sweep_rows(dag_plan* plan, int mode, int lo, int hi, SweepParams& p, double*
 // sweep_warp.cu
 const void* sweep_warp_kernel_ptr(int mode, int variant, int ipt);
 const void* sweep_ordered_kernel_ptr(int mode, int ipt);
-const void* sweep_warp_frontier_kernel_ptr(int mode, int ipt);
+const void* sweep_warp_frontier_kernel_ptr(int mode, int ipt, bool ordered);
 int warp_frontier_maps(dag_plan* plan, int mode, cudaStream_t s);
 int launch_warp_sweep(dag_plan* plan, int mode, int variant, int delta, SweepParams& p, cudaStream_t s,
                       int* out_nblocks);

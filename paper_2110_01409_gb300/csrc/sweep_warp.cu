@@ -588,18 +588,18 @@ const void* sweep_warp_kernel_ptr(int mode, int variant, int ipt)
 // what fits in shared memory (flushed when the next tile might not fit).
 enum WarpKind { WARP_RUNS = 0, WARP_ORDERED = 1, WARP_FRONTIER = 2 };
 
-static const void* warp_kernel(int kind, int mode, int variant, int ipt)
+static const void* warp_kernel(int kind, int mode, int variant, int ipt, bool ordered = false)
 {
     if (kind == WARP_ORDERED) return sweep_ordered_kernel_ptr(mode, ipt);
-    if (kind == WARP_FRONTIER) return sweep_warp_frontier_kernel_ptr(mode, ipt);
+    if (kind == WARP_FRONTIER) return sweep_warp_frontier_kernel_ptr(mode, ipt, ordered);
     return sweep_warp_kernel_ptr(mode, variant, ipt);
 }
 
 static int warp_shape(dag_plan* plan, int mode, int variant, int delta, int* nb_out, int* cap_out, int* clamped_out,
-                      Partition** part_out, cudaStream_t s, int kind)
+                      Partition** part_out, cudaStream_t s, int kind, bool ordered = false)
 {
     const int WTILE = 32 * plan->warp_ipt;
-    const void* k = warp_kernel(kind, mode, variant, plan->warp_ipt);
+    const void* k = warp_kernel(kind, mode, variant, plan->warp_ipt, ordered);
     if (!k) return set_error(DAG_ERR_INVALID, "no warp tile of that shape");
     cudaFuncAttributes fa{};
     DAG_CUDA(cudaFuncGetAttributes(&fa, k));
@@ -669,14 +669,15 @@ int launch_warp_sweep(dag_plan* plan, int mode, int variant, int delta, SweepPar
     const bool ordered = p.ordered != 0;
     if (ordered && variant != DAG_ASYNC)
         return set_error(DAG_ERR_INVALID, "ordered warp sweeps run the asynchronous form (delta 0)");
-    if (p.frontier && (ordered || variant != DAG_ASYNC || (mode != MODE_BF && mode != MODE_BF8)))
+    if (p.frontier && (variant != DAG_ASYNC || (mode != MODE_BF && mode != MODE_BF8)))
         return set_error(DAG_ERR_INVALID, "the warp-tile frontier runs the asynchronous Bellman-Ford form");
     const int kind = p.frontier ? WARP_FRONTIER : ordered ? WARP_ORDERED : WARP_RUNS;
     int nb = 0, cap = 0, clamped = 0;
     Partition* part = nullptr;
-    int rc = warp_shape(plan, mode, variant, delta, &nb, &cap, &clamped, &part, s, kind);
+    int rc = warp_shape(plan, mode, variant, delta, &nb, &cap, &clamped, &part, s, kind, ordered);
     if (rc) return rc;
-    if (ordered && !part->tpub) DAG_CUDA(cudaMalloc(&part->tpub, (size_t)part->tiles * sizeof(unsigned long long)));
+    if (kind == WARP_ORDERED && !part->tpub)
+        DAG_CUDA(cudaMalloc(&part->tpub, (size_t)part->tiles * sizeof(unsigned long long)));
     if (p.frontier) {
         rc = frontier_maps(plan, part, s);
         if (rc) return rc;
@@ -699,7 +700,7 @@ int launch_warp_sweep(dag_plan* plan, int mode, int variant, int delta, SweepPar
     p.cta_tile = part->cta_tile;
     p.tile_row = part->tile_row;
     p.tile_nz = part->tile_nz;
-    p.wpub = ordered ? part->tpub : part->wpub;
+    p.wpub = kind == WARP_ORDERED ? part->tpub : part->wpub;
     p.ntiles = part->tiles;
     p.sync = plan->sync;
     p.timeout_ns = plan->timeout_ns;
@@ -712,9 +713,10 @@ int launch_warp_sweep(dag_plan* plan, int mode, int variant, int delta, SweepPar
     }
     DAG_CUDA(cudaMemsetAsync(plan->sync, 0, sizeof(SyncBlock), s));
     // stamps of an earlier solve must not pass for this one's
-    DAG_CUDA(cudaMemsetAsync(p.wpub, 0, (size_t)(ordered ? part->tiles : part->nblocks) * sizeof(unsigned long long),
+    DAG_CUDA(cudaMemsetAsync(p.wpub, 0,
+                             (size_t)(kind == WARP_ORDERED ? part->tiles : part->nblocks) * sizeof(unsigned long long),
                              s));
-    const void* k = warp_kernel(kind, mode, variant, plan->warp_ipt);
+    const void* k = warp_kernel(kind, mode, variant, plan->warp_ipt, ordered);
     const size_t dyn = (size_t)WWARPS * (size_t)cap * 4;
     DAG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     void* args[] = {(void*)&p};

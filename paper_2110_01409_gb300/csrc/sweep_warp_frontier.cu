@@ -48,7 +48,8 @@ __device__ __forceinline__ void stamp_edge_tiles(const int* list, int cnt, const
     }
 }
 
-template <int MODE, int WIPT>
+// ORD: dense sweeps on the CTA's tiles in turn (DAG_WARP_ORDERED), else on each warp's run.
+template <int MODE, int WIPT, bool ORD>
 __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_warp_frontier_kernel(const SweepParams p)
 {
     static_assert(MODE == MODE_BF || MODE == MODE_BF8, "frontier: Bellman-Ford only");
@@ -58,6 +59,7 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_warp_frontier_kernel(con
     (void)WTILE;
 
     __shared__ WarpShared<32 * WIPT> sh;
+    __shared__ int s_cnt;  // ordered dense sweeps: rows on the CTA's list of lowered rows
     const int c = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wl = tid >> 5;
     const int w = c * WWARPS + wl;
     SyncBlock* sb = p.sync;
@@ -69,6 +71,10 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_warp_frontier_kernel(con
     uint32_t* val = sh.val[wl];
     uint32_t* sum = sh.sum[wl];
     int* own_chg = p.fr_chg + row_lo;  // dense sweeps: this warp's changed rows (its own, so at most row_hi - row_lo)
+    // ordered dense sweeps: the CTA's tiles [T0, T1) (its warps' runs together), taken by its warps in turn, and
+    // its list of lowered rows (a row split over k of its tiles may appear k times: at most rows + tiles entries)
+    const int T0 = p.cta_tile[c * WWARPS], T1 = p.cta_tile[c * WWARPS + WWARPS];
+    int* cta_chg = p.fr_gchg + (p.cta_row[c * WWARPS] + T0);
     const bool mid0 = t_lo < t_hi && p.tile_nz[t_lo] > p.rowptr[p.tile_row[t_lo]];
     const bool head = mid0 && row_hi > row_lo;
 
@@ -96,7 +102,73 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_warp_frontier_kernel(con
         long long edges = 0;  // lane 0: edges of the tiles this warp ran
         bool ok = true;
 
-        if (dense) {
+        if (ORD && dense) {
+            // ---------------- dense sweep, ordered: the CTA's tiles, its warps taking them in turn ----------------
+            // A row whose in-edges all lie in one tile gets min(old, sum) from that tile alone; a row split over
+            // tiles gets each tile's partial with an atomic minimum (as valid a relaxation as the whole row's),
+            // so no tile waits for another.
+            if (tid == 0) s_cnt = 0;
+            __syncthreads();
+            WStage<WIPT> nx;
+            if (T0 + wl < T1) wfetch<MODE, WIPT>(nx, p, X, T0 + wl, lane, rmode, false, pol_edge, pol_vertex);
+            for (int t = T0 + wl; t < T1; t += WWARPS) {
+                const int a0 = nx.a0, b0 = nx.b0, NA = nx.NA, NB = nx.NB;
+                const bool cont = b0 > nx.rp0;  // the tile starts inside row a0
+                const uint32_t pf_xo = nx.xo;
+                __syncwarp();
+#pragma unroll
+                for (int q = 0; q < WIPT; ++q) {
+                    const int j = lane + 32 * q;
+                    if (j < NB) val[j] = nx.term[q];
+                }
+                wstage_ends<WIPT>(end, nx, p, lane, pol_vertex);
+                if (t + WWARPS < T1)
+                    wfetch<MODE, WIPT>(nx, p, X, t + WWARPS, lane, rmode, false, pol_edge, pol_vertex);
+                __syncwarp();
+                const uint32_t trail = wwalk<MODE, WIPT>(end, val, sum, NA, NB, O::identity(), lane);
+                __syncwarp();
+                if (lane == 0) edges += NB;
+                uint32_t xo_k[WIPT];
+                xo_k[0] = pf_xo;
+#pragma unroll
+                for (int k = 1; k < WIPT; ++k) {
+                    const int r = lane + 32 * k;
+                    xo_k[k] = r < NA ? ld_weak_b32(X + a0 + r) : 0u;
+                }
+#pragma unroll
+                for (int k = 0; k <= WIPT; ++k) {
+                    const int r = lane + 32 * k;
+                    if (32 * k > NA) break;  // warp-uniform
+                    bool changed = false;
+                    const int v = a0 + r;
+                    if (r < NA) {
+                        const uint32_t sv = sum[r];
+                        const uint32_t xo = xo_k[k < WIPT ? k : 0];
+                        if (r == 0 && cont) {  // the rest of a row begun in an earlier tile
+                            if (sv != INF && sv < xo) changed = sv < atomicMin(X + v, sv);
+                        } else if (sv < xo) {  // a whole row: only this tile writes it in a dense sweep
+                            st_relaxed_b32(X + v, sv);
+                            changed = true;
+                        }
+                    } else if (r == NA && v < p.n && trail != INF) {  // the start of a row ending in a later tile
+                        if (trail < ld_weak_b32(X + v)) changed = trail < atomicMin(X + v, trail);
+                    }
+                    const unsigned bal = __ballot_sync(FULL, changed);
+                    if (bal == 0u) continue;
+                    if (changed) res_part += 1.0f;
+                    int base = 0;
+                    if (lane == 0) base = atomicAdd(&s_cnt, __popc(bal));
+                    base = __shfl_sync(FULL, base, 0);
+                    if (changed) cta_chg[base + __popc(bal & ((1u << lane) - 1u))] = v;
+                }
+            }
+            __syncthreads();  // the CTA's list is complete
+            own_cnt = s_cnt;
+            for (int k = wl * 32 + lane; k < own_cnt; k += NT) {
+                const int v = cta_chg[k];
+                marks += p.fr_orow[v + 1] - p.fr_orow[v];
+            }
+        } else if (!ORD && dense) {
             // ---------------- dense sweep: the warp's run, in order ----------------
             own_cnt = 0;
             uint32_t carry = O::identity();
@@ -299,7 +371,10 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_warp_frontier_kernel(con
         if (!dense && was_dense) {
             // into the sparse phase: the rows the dense sweep lowered flag the tiles of their out-edges (a sparse
             // sweep's lowered rows flagged theirs as they went)
-            stamp_edge_tiles(own_chg, own_cnt, p.fr_orow, p.fr_otile, p.fr_act, 0, 0, 1, lane);
+            if (ORD)
+                stamp_edge_tiles(cta_chg, own_cnt, p.fr_orow, p.fr_otile, p.fr_act, 0, wl, WWARPS, lane);
+            else
+                stamp_edge_tiles(own_chg, own_cnt, p.fr_orow, p.fr_otile, p.fr_act, 0, 0, 1, lane);
             if (!grid_barrier(sb, p.nblocks, bar_target, p.timeout_ns)) return;
         }
     }
@@ -312,17 +387,16 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_warp_frontier_kernel(con
     }
 }
 
-const void* sweep_warp_frontier_kernel_ptr(int mode, int ipt)
+const void* sweep_warp_frontier_kernel_ptr(int mode, int ipt, bool ordered)
 {
     if (mode != MODE_BF && mode != MODE_BF8) return nullptr;
-    const bool b8 = mode == MODE_BF8;
-    switch (ipt) {
-    case 5: return b8 ? (const void*)sweep_warp_frontier_kernel<MODE_BF8, 5> : (const void*)sweep_warp_frontier_kernel<MODE_BF, 5>;
-    case 7: return b8 ? (const void*)sweep_warp_frontier_kernel<MODE_BF8, 7> : (const void*)sweep_warp_frontier_kernel<MODE_BF, 7>;
-    case 11:
-        return b8 ? (const void*)sweep_warp_frontier_kernel<MODE_BF8, 11> : (const void*)sweep_warp_frontier_kernel<MODE_BF, 11>;
-    default: return nullptr;
-    }
+#define DAG_WF(I) \
+    {(const void*)sweep_warp_frontier_kernel<MODE_BF, I, false>, (const void*)sweep_warp_frontier_kernel<MODE_BF, I, true>, \
+     (const void*)sweep_warp_frontier_kernel<MODE_BF8, I, false>, (const void*)sweep_warp_frontier_kernel<MODE_BF8, I, true>}
+    static const void* const table[3][4] = {DAG_WF(5), DAG_WF(7), DAG_WF(11)};
+#undef DAG_WF
+    const int k = ipt == 5 ? 0 : ipt == 7 ? 1 : ipt == 11 ? 2 : -1;
+    return k < 0 ? nullptr : table[k][(mode == MODE_BF8 ? 2 : 0) + (ordered ? 1 : 0)];
 }
 
 }  // namespace dag

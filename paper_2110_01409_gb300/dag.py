@@ -28,6 +28,7 @@ READ_MODES = {"refresh": 0, "coherent": 2, "cached": 4,  # delayed form's reads 
               "cached+frontier": 36,
               "warp": 64, "warp+coherent": 66, "warp+cached": 68,  # one worker per warp (DAG_WARP_WORKERS)
               "warp+frontier": 96, "warp+cached+frontier": 100,  # async Bellman-Ford: warp-tile frontier
+              "ordered+frontier": 160, "ordered+cached+frontier": 164,  # ... dense sweeps on CTA-ordered tiles
               "ordered": 128, "ordered+cached": 132}  # async: warps take the path's tiles in turn (DAG_WARP_ORDERED)
 
 

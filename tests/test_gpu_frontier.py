@@ -102,7 +102,7 @@ def test_frontier_edge_cases_and_rejections(dag):
 
 
 # ---- the warp-tile frontier (DAG_WARP_WORKERS | DAG_SSSP_FRONTIER, asynchronous form) ----
-WARP_READS = ["warp+frontier", "warp+cached+frontier"]
+WARP_READS = ["warp+frontier", "warp+cached+frontier", "ordered+frontier", "ordered+cached+frontier"]
 
 
 @pytest.mark.parametrize("maker", GRAPHS + [lambda: I.from_edges(200001, np.arange(1, 200001),

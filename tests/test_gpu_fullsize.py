@@ -86,7 +86,9 @@ PR_FULL = [("sync", 0, "refresh", 7), ("async", 0, "refresh", 7), ("async", 0, "
            ("async", 0, "cached", 7)]
 SSSP_FULL = PR_FULL + [("sync", 0, "frontier", 7), ("async", 0, "frontier", 7), ("async", 0, "own_l1+frontier", 7),
                        ("async", 0, "cached+frontier", 7), ("async", 0, "warp+frontier", 7),
-                       ("async", 0, "warp+cached+frontier", 7), ("async", 0, "warp+cached+frontier", 5)]
+                       ("async", 0, "warp+cached+frontier", 7), ("async", 0, "warp+cached+frontier", 5),
+                       ("async", 0, "ordered+frontier", 7), ("async", 0, "ordered+cached+frontier", 7),
+                       ("async", 0, "ordered+cached+frontier", 5)]
 
 
 @pytest.mark.parametrize("variant,delta,reads,ipt", PR_FULL)
@@ -103,13 +105,14 @@ def test_pagerank_full_size_against_fixed_point(big, big_rstar, variant, delta, 
 def test_sssp_full_size_optimal(big, variant, delta, reads, ipt):
     dag, g, w, srcs, plan, w8, src_e, dst_e = big
     plan.set_warp_tile(ipt)
-    sources = srcs if reads in ("own_l1+frontier", "warp+cached+frontier") and ipt == 7 else srcs[:2]
+    sources = srcs if reads in ("own_l1+frontier", "warp+cached+frontier", "ordered+cached+frontier") and ipt == 7 \
+        else srcs[:2]
     for k, s in enumerate(sources):
         d, st = dag.sssp(plan, int(s), w8, variant, delta, g.n + 1, reads=reads)
         assert st["converged"], st
         got = d.cpu().numpy().view(np.uint32)
         _check_optimal(got, int(s), w, src_e, dst_e, g.n)
-        if k == 0 and reads in ("own_l1+frontier", "warp+cached+frontier"):
+        if k == 0 and reads in ("own_l1+frontier", "warp+cached+frontier", "ordered+cached+frontier"):
             assert np.array_equal(got, oracle.dijkstra(g, w, int(s)))
 
 
@@ -130,7 +133,7 @@ BENCH_ROWS = [("sync", 0, "refresh"), ("async", 0, "refresh"), ("async", 0, "own
               ("delayed", 256, "refresh"), ("delayed", 4096, "refresh"), ("delayed", 4096, "local"),
               ("sync", 0, "warp"), ("async", 0, "warp+cached"), ("delayed", 16, "warp"),
               ("delayed", 256, "warp+cached"), ("async", 0, "ordered+cached"), ("async", 0, "cached+frontier"),
-              ("async", 0, "warp+frontier"), ("async", 0, "warp+cached+frontier")]
+              ("async", 0, "warp+frontier"), ("async", 0, "warp+cached+frontier"), ("async", 0, "ordered+cached+frontier")]
 
 
 @pytest.fixture(scope="module", params=[c[0] for c in CONFIG3])

@@ -116,9 +116,9 @@ def test_warp_flags_refused_with_frontier_and_local(dag):
     rank = torch.empty(g.n, device="cuda")
     L = dag.lib()
     warp, frontier, local = dag.READ_MODES["warp"], dag.READ_MODES["frontier"], dag.READ_MODES["local"]
-    ordered = dag.READ_MODES["ordered"]
+    ordered = dag.READ_MODES["ordered"]  # (with the frontier: the asynchronous form only)
     for var, delta, flags in ((dag.SYNC, 0, warp | frontier), (dag.DELAYED, 16, warp | frontier),
-                              (dag.ASYNC, 0, ordered | frontier)):
+                              (dag.SYNC, 0, ordered | frontier)):
         assert L.dag_sssp_u8(plan.h, 0, var, delta, 10, dag._ptr(w), dag._ptr(dist), flags, None,
                              dag._stream()) == dag.ERR_INVALID
     assert L.dag_pagerank(plan.h, 0.85, 1e-6, dag.ASYNC, 0, 100, None, None, dag._ptr(rank), warp | frontier, None,
