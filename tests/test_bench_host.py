@@ -57,6 +57,7 @@ def test_committed_record_parses():
     assert figures and all(v > 0 for v in figures.values())
     assert all(k.endswith((f"rmat{bench.SCALE} dram_bytes_per_sweep", f"rmat{bench.SCALE} dram_bytes_per_edge_run"))
                for k in figures)
-    assert float(keys[f"sweep_tma_kernel<BF8,frontier> rmat{bench.SCALE} dram_bytes_per_edge_run"]) > 0
+    # at least one frontier kernel has a per-edge figure (the step's Bellman-Ford runs one)
+    assert any(k.endswith(f"rmat{bench.SCALE} dram_bytes_per_edge_run") and float(v) > 0 for k, v in keys.items())
     if keys["sweep_source_sha256"] != bench.sweep_source_hash():
         pytest.skip("kernel sources changed since the capture: the bench reports traffic as null")
