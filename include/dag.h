@@ -304,6 +304,17 @@ int dag_sssp_batched_u8(dag_plan* plan, dag_variant variant, int32_t delta, int3
  * for a null plan.
  */
 int dag_plan_set_batched_graph(dag_plan* plan, int32_t on);
+/*
+ * Kernel of the plan's batched synchronous and asynchronous solves with 32,
+ * 64, 128 or 256 columns: on (1, when a plan is created) a warp owns all B
+ * columns (B / 32 per lane, one vector access each) and an eighth of each
+ * merge-path tile, so a source vertex's B values are gathered by one warp in
+ * one burst; off (0), and always for other column counts and the delayed
+ * form, each warp owns 32 columns and the CTA's warps walk every edge
+ * together. Results agree within rounding (the same sweep; sums may be added
+ * in another order). DAG_ERR_INVALID for a null plan.
+ */
+int dag_plan_set_batched_wide(dag_plan* plan, int32_t on);
 
 /*
  * Out-edge CSR of the plan's graph (for the adjoint pull). d_out_rowptr

@@ -339,7 +339,437 @@ __global__ void batched_kernel(const BatchParams p)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Wide batched sweep (synchronous and asynchronous forms, B = 32 CPL columns,
+// CPL in {1, 2, 4, 8}). The kernel above gives each warp 32 columns and walks
+// every edge of a tile with all eight warps in lock step, so a source row of
+// B values is fetched as eight 128-byte slices by eight warps and each tile
+// waits for the slowest of them. Here a warp owns all B columns (CPL per lane,
+// one vector access each) and an eighth of each merge-path tile: it gathers a
+// source's whole row as one burst and walks its share of the tile's rows and
+// edges on its own. A row split between two warps' shares is finished after
+// the tile's barrier from the shares' partials (kept in shared memory), and a
+// row continuing into the next tile carries its partial there.
+// ---------------------------------------------------------------------------
+template <int CPL>
+__device__ __forceinline__ void ld_cols(const uint32_t* a, uint32_t (&o)[CPL], bool coherent)
+{
+    if constexpr (CPL == 8) {
+        if (coherent) {
+            asm volatile("ld.relaxed.gpu.global.v4.b32 {%0, %1, %2, %3}, [%4];"
+                         : "=r"(o[0]), "=r"(o[1]), "=r"(o[2]), "=r"(o[3]) : "l"(a) : "memory");
+            asm volatile("ld.relaxed.gpu.global.v4.b32 {%0, %1, %2, %3}, [%4];"
+                         : "=r"(o[4]), "=r"(o[5]), "=r"(o[6]), "=r"(o[7]) : "l"(a + 4) : "memory");
+        } else {
+            const uint4 u = *(const uint4*)a, w = *(const uint4*)(a + 4);
+            o[0] = u.x; o[1] = u.y; o[2] = u.z; o[3] = u.w; o[4] = w.x; o[5] = w.y; o[6] = w.z; o[7] = w.w;
+        }
+    } else if constexpr (CPL == 4) {
+        if (coherent) {
+            asm volatile("ld.relaxed.gpu.global.v4.b32 {%0, %1, %2, %3}, [%4];"
+                         : "=r"(o[0]), "=r"(o[1]), "=r"(o[2]), "=r"(o[3]) : "l"(a) : "memory");
+        } else {
+            const uint4 u = *(const uint4*)a;
+            o[0] = u.x; o[1] = u.y; o[2] = u.z; o[3] = u.w;
+        }
+    } else if constexpr (CPL == 2) {
+        if (coherent) {
+            asm volatile("ld.relaxed.gpu.global.v2.b32 {%0, %1}, [%2];" : "=r"(o[0]), "=r"(o[1]) : "l"(a) : "memory");
+        } else {
+            const uint2 u = *(const uint2*)a;
+            o[0] = u.x; o[1] = u.y;
+        }
+    } else {
+        o[0] = coherent ? ld_relaxed_b32(a) : *a;
+    }
+}
+
+// Stores the lane's CPL values (all of them when every column runs, else only the running ones).
+template <int CPL>
+__device__ __forceinline__ void st_cols(uint32_t* a, const uint32_t (&v)[CPL], unsigned run, bool coherent)
+{
+    constexpr unsigned ALL = (1u << CPL) - 1u;
+    if (run == ALL && CPL >= 2) {
+        if constexpr (CPL == 8) {
+            if (coherent) {
+                asm volatile("st.relaxed.gpu.global.v4.b32 [%0], {%1, %2, %3, %4};"
+                             ::"l"(a), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]) : "memory");
+                asm volatile("st.relaxed.gpu.global.v4.b32 [%0], {%1, %2, %3, %4};"
+                             ::"l"(a + 4), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]) : "memory");
+            } else {
+                *(uint4*)a = make_uint4(v[0], v[1], v[2], v[3]);
+                *(uint4*)(a + 4) = make_uint4(v[4], v[5], v[6], v[7]);
+            }
+            return;
+        } else if constexpr (CPL == 4) {
+            if (coherent)
+                asm volatile("st.relaxed.gpu.global.v4.b32 [%0], {%1, %2, %3, %4};"
+                             ::"l"(a), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]) : "memory");
+            else *(uint4*)a = make_uint4(v[0], v[1], v[2], v[3]);
+            return;
+        } else if constexpr (CPL == 2) {
+            if (coherent) asm volatile("st.relaxed.gpu.global.v2.b32 [%0], {%1, %2};" ::"l"(a), "r"(v[0]), "r"(v[1]) : "memory");
+            else *(uint2*)a = make_uint2(v[0], v[1]);
+            return;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) {
+        if (!((run >> q) & 1u)) continue;
+        if (coherent) st_relaxed_b32(a + q, v[q]);
+        else a[q] = v[q];
+    }
+}
+
+constexpr int WIDE_WARPS = 8;  // warps per CTA of the wide kernel
+constexpr int WIDE_U = 4;      // edges whose rows a warp gathers before accumulating
+
+template <bool BF, int VAR, bool W8, int CPL>
+__global__ void __launch_bounds__(NT, 2) batched_wide_kernel(const BatchParams p)
+{
+    constexpr bool SYNC = VAR == DAG_SYNC;
+    constexpr bool LIVE = !SYNC && !BF;
+    constexpr unsigned ALL = (1u << CPL) - 1u;
+    constexpr int B = 32 * CPL;
+    static_assert(VAR != DAG_DELAYED, "the delayed form runs the column-chunk kernel");
+    extern __shared__ __align__(16) uint32_t smem[];
+    int* s_col = (int*)smem;                            // [TILE] the tile's edge sources
+    int* s_end = s_col + TILE;                          // [TILE + 4] tile-relative row ends (+ sentinel)
+    uint32_t* s_w = (uint32_t*)(s_end + TILE + 4);      // [TILE] weights (Bellman-Ford)
+    uint32_t* s_part = s_w + (BF ? TILE : 0);           // [WIDE_WARPS][B] each share's trailing partial
+    uint32_t* s_carry = s_part + WIDE_WARPS * B;        // [2][B] the partial carried into a tile
+    double* s_T = (double*)(s_carry + 2 * B);           // [B] teleport totals (PageRank)
+    double* s_g = s_T + B;                              // [B] mass on linked vertices, last sweep (synchronous)
+    float* s_red = (float*)(s_g + B);                   // [WIDE_WARPS][B] the warps' per-column sums of a sweep
+    float* s_dg = s_red + WIDE_WARPS * B;               // [B] the CTA's change of the live mass (asynchronous)
+    int* s_last = (int*)(s_dg + B);                     // [B] sweeps each column ran
+    __shared__ int s_i0[WIDE_WARPS], s_head[WIDE_WARPS], s_ends[WIDE_WARPS], s_tcont;
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tid = threadIdx.x;
+    const int cb = blockIdx.x, c0 = lane * CPL;
+    const int row_lo = p.cta_row[cb], row_hi = p.cta_row[cb + 1];
+    const int tile_lo = p.cta_tile[cb], tile_hi = p.cta_tile[cb + 1];
+    unsigned long long bar = 0;
+    uint32_t srcv[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) srcv[q] = BF ? p.src[c0 + q] : 0u;
+
+    // ---------------- initial values (the CTA's rows, a warp per row, CPL columns per lane) ----------------
+    {
+        float gpart[CPL], tpart[CPL];
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) gpart[q] = tpart[q] = 0.0f;
+        for (int v = row_lo + warp; v < row_hi; v += WIDE_WARPS) {
+            uint32_t x[CPL];
+            if constexpr (BF) {
+#pragma unroll
+                for (int q = 0; q < CPL; ++q) x[q] = ((uint32_t)v == srcv[q]) ? 0u : INF;
+            } else {
+                uint32_t t[CPL];
+                ld_cols<CPL>((const uint32_t*)p.V + (size_t)v * B + c0, t, false);
+                const float dg = p.degf[v];
+#pragma unroll
+                for (int q = 0; q < CPL; ++q) {
+                    const float tv = __uint_as_float(t[q]);
+                    x[q] = __float_as_uint(dg > 0.0f ? tv / dg : tv);
+                    if (dg > 0.0f) gpart[q] += tv;
+                    tpart[q] += tv;
+                }
+            }
+            st_cols<CPL>(p.X0 + (size_t)v * B + c0, x, ALL, false);
+        }
+        if constexpr (!BF) {
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) {
+                if (tpart[q] != 0.0f) atomicAdd(&p.T[c0 + q], (double)tpart[q]);
+                if (gpart[q] != 0.0f) {
+                    atomicAdd(&p.acc_g[2 * B + c0 + q], (double)gpart[q]);
+                    if (LIVE) atomicAdd(&p.gl[c0 + q], (double)gpart[q]);
+                }
+            }
+        }
+    }
+    if (!grid_barrier(p.sb, p.nblocks, bar, p.timeout_ns)) return;
+    for (int c = tid; c < B; c += NT) {
+        if constexpr (!BF) {
+            s_T[c] = ld_relaxed_f64(&p.T[c]);
+            s_g[c] = ld_relaxed_f64(&p.acc_g[2 * B + c]);
+        }
+        s_last[c] = 0;
+        s_dg[c] = 0.0f;
+    }
+    __syncthreads();
+    unsigned act = ALL;  // this lane's columns still running (the same in every warp and CTA)
+    int it = 0;
+    for (; it < p.max_iters; ++it) {
+        const int slot = it % 3;
+        const uint32_t* xin = SYNC ? ((it & 1) ? p.X1 : p.X0) : p.X0;
+        uint32_t* xout = SYNC ? ((it & 1) ? p.X0 : p.X1) : p.X0;
+        float res[CPL], gsum[CPL], dga[CPL], gt[CPL];
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) {
+            res[q] = gsum[q] = dga[q] = 0.0f;
+            gt[q] = (SYNC && !BF) ? (float)((double)p.g_coef * (s_T[c0 + q] - s_g[c0 + q])) : 0.0f;
+        }
+        // the new values of tile row i from its sum acc
+        auto finish_row = [&](int a0, int i, const uint32_t (&acc)[CPL]) {
+            const int v = a0 + i;
+            const size_t base = (size_t)v * B + c0;
+            uint32_t old[CPL], xn[CPL];
+            ld_cols<CPL>(xin + base, old, !SYNC);
+            if constexpr (BF) {
+#pragma unroll
+                for (int q = 0; q < CPL; ++q) {
+                    xn[q] = acc[q] < old[q] ? acc[q] : old[q];
+                    if (((act >> q) & 1u) && xn[q] < old[q]) res[q] += 1.0f;
+                }
+            } else {
+                uint32_t tv[CPL];
+                ld_cols<CPL>((const uint32_t*)p.V + base, tv, false);
+                const float dg = p.degf[v];
+#pragma unroll
+                for (int q = 0; q < CPL; ++q) {
+                    const float xo = __uint_as_float(old[q]);
+                    const float rold = dg > 0.0f ? xo * dg : xo;
+                    const float rnew = (1.0f - p.d) * __uint_as_float(tv[q]) + p.d * __uint_as_float(acc[q]) + gt[q];
+                    if ((act >> q) & 1u) {
+                        res[q] += fabsf(rnew - rold);
+                        if (dg > 0.0f) {
+                            gsum[q] += rnew;
+                            dga[q] += rnew - rold;
+                        }
+                    }
+                    xn[q] = __float_as_uint(dg > 0.0f ? __fdividef(rnew, dg) : rnew);  // 2 ulp, no special-value path
+                }
+            }
+            st_cols<CPL>(xout + base, xn, act, !SYNC);
+        };
+        const bool any = __syncthreads_or(act != 0u) != 0;  // (the same in every CTA)
+        int cbuf = 0;
+        for (int t = tile_lo; any && t < tile_hi; ++t) {
+            const int a0 = p.tile_row[t], b0 = p.tile_nz[t];
+            const int NA = p.tile_row[t + 1] - a0, NB = p.tile_nz[t + 1] - b0;
+            __syncthreads();  // the previous tile's buffers are no longer read
+            for (int i = tid; i < NA; i += NT) s_end[i] = ld_stream_i32(p.rowptr + a0 + i + 1) - b0;
+            if (tid == 0) {
+                s_end[NA] = INT_MAX;
+                s_tcont = b0 > ld_stream_i32(p.rowptr + a0) ? 1 : 0;  // the tile starts inside row a0
+            }
+            for (int j = tid; j < NB; j += NT) {
+                s_col[j] = ld_stream_i32(p.colidx + b0 + j);
+                if constexpr (BF && W8) s_w[j] = (uint32_t)p.w8[b0 + j];
+                else if constexpr (BF) s_w[j] = ld_stream_u32(p.w + b0 + j);
+            }
+            __syncthreads();
+            if constexpr (LIVE) {
+#pragma unroll
+                for (int q = 0; q < CPL; ++q)
+                    if ((act >> q) & 1u) gt[q] = (float)((double)p.g_coef * (s_T[c0 + q] - ld_relaxed_f64(&p.gl[c0 + q])));
+            }
+            // this warp's share of the tile: merge-path diagonals [d0, d1)
+            const int L = NA + NB;
+            const int d0 = (int)((long long)warp * L / WIDE_WARPS), d1 = (int)((long long)(warp + 1) * L / WIDE_WARPS);
+            auto search = [&](int d) -> int {  // rows completed before diagonal d
+                int lo = max(0, d - NB), hi = min(d, NA);
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (s_end[mid] <= d - 1 - mid) lo = mid + 1;
+                    else hi = mid;
+                }
+                return lo;
+            };
+            const int i0 = search(d0), i1 = search(d1);
+            const int j0 = d0 - i0, j1 = d1 - i1;
+            const bool head = i0 == 0 ? (s_tcont != 0 || j0 > 0) : j0 > s_end[i0 - 1];
+            bool pending = head;  // the share's first row began before it: finished after the barrier
+            uint32_t acc[CPL], headp[CPL];
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) acc[q] = headp[q] = b_ident<BF>();
+            int i = i0;
+            bool head_done = false;
+            auto row_end = [&]() {
+                if (pending) {
+#pragma unroll
+                    for (int q = 0; q < CPL; ++q) headp[q] = acc[q];
+                    pending = false;
+                    head_done = true;
+                } else {
+                    finish_row(a0, i, acc);
+                }
+#pragma unroll
+                for (int q = 0; q < CPL; ++q) acc[q] = b_ident<BF>();
+                ++i;
+            };
+            for (int jb = j0; jb < j1; jb += WIDE_U) {
+                const int nu = min(WIDE_U, j1 - jb);
+                uint32_t xv[WIDE_U][CPL];
+#pragma unroll
+                for (int u = 0; u < WIDE_U; ++u)
+                    if (u < nu) ld_cols<CPL>(xin + (size_t)s_col[jb + u] * B + c0, xv[u], !SYNC);
+#pragma unroll
+                for (int u = 0; u < WIDE_U; ++u) {
+                    if (u >= nu) break;
+                    const int e = jb + u;
+                    while (i < i1 && s_end[i] <= e) row_end();
+                    const uint32_t we = BF ? s_w[e] : 0u;
+#pragma unroll
+                    for (int q = 0; q < CPL; ++q)
+                        acc[q] = b_comb<BF>(acc[q], BF ? b_relax(xv[u][q], we) : xv[u][q]);
+                }
+            }
+            while (i < i1) row_end();
+            // the share's trailing partial, and how its first row relates to the shares before it
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) s_part[warp * B + c0 + q] = acc[q];
+            if (lane == 0) {
+                s_i0[warp] = i0;
+                s_head[warp] = head ? 1 : 0;
+                s_ends[warp] = i1 > i0 ? 1 : 0;
+            }
+            __syncthreads();
+            // a row begun in earlier shares: theirs back to the one where it starts (or the tile's carry)
+            auto gather_back = [&](int w_from, uint32_t (&tot)[CPL]) {
+                int w2 = w_from;
+                for (;; --w2) {
+                    if (w2 < 0) {
+#pragma unroll
+                        for (int q = 0; q < CPL; ++q) tot[q] = b_comb<BF>(tot[q], s_carry[cbuf * B + c0 + q]);
+                        break;
+                    }
+#pragma unroll
+                    for (int q = 0; q < CPL; ++q) tot[q] = b_comb<BF>(tot[q], s_part[w2 * B + c0 + q]);
+                    if (s_ends[w2] || !s_head[w2]) break;
+                }
+            };
+            if (head_done) {
+                uint32_t tot[CPL];
+#pragma unroll
+                for (int q = 0; q < CPL; ++q) tot[q] = headp[q];
+                gather_back(warp - 1, tot);
+                finish_row(a0, i0, tot);
+            }
+            if (warp == WIDE_WARPS - 1) {  // the partial carried into the next tile (identity when none)
+                uint32_t tot[CPL];
+#pragma unroll
+                for (int q = 0; q < CPL; ++q) tot[q] = b_ident<BF>();
+                gather_back(WIDE_WARPS - 1, tot);
+#pragma unroll
+                for (int q = 0; q < CPL; ++q) s_carry[(cbuf ^ 1) * B + c0 + q] = tot[q];
+            }
+            cbuf ^= 1;
+            if constexpr (LIVE) {  // the tile's change of the live mass: the CTA's shares, then one atomic each
+#pragma unroll
+                for (int q = 0; q < CPL; ++q) {
+                    if (dga[q] != 0.0f) atomicAdd(&s_dg[c0 + q], dga[q]);
+                    dga[q] = 0.0f;
+                }
+                __syncthreads();
+                for (int c = tid; c < B; c += NT) {
+                    const float v = s_dg[c];
+                    if (v != 0.0f) {
+                        atomicAdd(&p.gl[c], (double)v);
+                        s_dg[c] = 0.0f;
+                    }
+                }
+            }
+        }
+        // ---- end of sweep: per-column sums (the CTA's warps added in a fixed order, so that the synchronous
+        // form is deterministic; then one FP64 atomic each), barrier, stopping rules ----
+        auto cta_sum = [&](const float (&part)[CPL], double* dst) {
+            __syncthreads();  // s_red is free
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) s_red[warp * B + c0 + q] = part[q];
+            __syncthreads();
+            for (int c = tid; c < B; c += NT) {
+                float v = 0.0f;
+#pragma unroll
+                for (int w2 = 0; w2 < WIDE_WARPS; ++w2) v += s_red[w2 * B + c];
+                if (v != 0.0f) atomicAdd(&dst[c], (double)v);
+            }
+        };
+        cta_sum(res, p.acc_res + slot * B);
+        if constexpr (SYNC && !BF) cta_sum(gsum, p.acc_g + slot * B);
+        if (!grid_barrier(p.sb, p.nblocks, bar, p.timeout_ns)) return;
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) {
+            if (!((act >> q) & 1u)) continue;
+            const int c = c0 + q;
+            const double r = ld_relaxed_f64(&p.acc_res[slot * B + c]);
+            if (SYNC && !BF && warp == 0) s_g[c] = ld_relaxed_f64(&p.acc_g[slot * B + c]);
+            if (r <= p.tol) {
+                act &= ~(1u << q);
+                if (warp == 0) {
+                    s_last[c] = it + 1;
+                    if (cb == 0) p.iters[c] = it + 1;
+                }
+            }
+        }
+        if (cb == 0) {
+            const int dead = (it + 2) % 3;
+            for (int c = tid; c < B; c += NT) {
+                p.acc_res[dead * B + c] = 0.0;
+                p.acc_g[dead * B + c] = 0.0;
+            }
+        }
+        if (!__syncthreads_or(act != 0u)) {
+            ++it;
+            break;
+        }
+    }
+    if (warp == 0) {
+#pragma unroll
+        for (int q = 0; q < CPL; ++q)
+            if ((act >> q) & 1u) {  // not converged: ran them all
+                s_last[c0 + q] = it;
+                if (cb == 0) p.iters[c0 + q] = it;
+            }
+    }
+    {
+        const int any_active = __syncthreads_or(act != 0u ? 1 : 0);
+        if (cb == 0 && tid == 0) {
+            p.sb->iters = it;
+            p.sb->converged = any_active ? 0 : 1;
+        }
+    }
+
+    // ---------------- output: r = x * outdeg, from the buffer of each column's last sweep ----------------
+    for (int v = row_lo + warp; v < row_hi; v += WIDE_WARPS) {
+        uint32_t x[CPL];
+        const size_t base = (size_t)v * B + c0;
+        if constexpr (SYNC) {
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) x[q] = ld_relaxed_b32(((s_last[c0 + q] & 1) ? p.X1 : p.X0) + base + q);
+        } else {
+            ld_cols<CPL>(p.X0 + base, x, true);
+        }
+        if constexpr (!BF) {
+            const float dg = p.degf[v];
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) x[q] = __float_as_uint(dg > 0.0f ? __uint_as_float(x[q]) * dg : __uint_as_float(x[q]));
+        }
+        st_cols<CPL>(p.X0 + base, x, ALL, false);
+    }
+}
+
 using BKernel = void (*)(const BatchParams);
+
+// The wide kernel of (is_bf, variant) for B = 32 * cpl columns; nullptr when it does not apply (the delayed
+// form, or a column count that is not 32, 64, 128 or 256).
+static BKernel wide_kernel_for(int is_bf, int variant, int B)
+{
+    if (variant == DAG_DELAYED || B % 32 != 0) return nullptr;
+    const int cpl = B / 32;
+    const int ci = cpl == 1 ? 0 : cpl == 2 ? 1 : cpl == 4 ? 2 : cpl == 8 ? 3 : -1;
+    if (ci < 0) return nullptr;
+#define DAG_WIDE(BFV, W8V, VAR) \
+    {batched_wide_kernel<BFV, VAR, W8V, 1>, batched_wide_kernel<BFV, VAR, W8V, 2>, batched_wide_kernel<BFV, VAR, W8V, 4>, \
+     batched_wide_kernel<BFV, VAR, W8V, 8>}
+    static const BKernel table[3][2][4] = {{DAG_WIDE(false, false, DAG_SYNC), DAG_WIDE(false, false, DAG_ASYNC)},
+                                           {DAG_WIDE(true, false, DAG_SYNC), DAG_WIDE(true, false, DAG_ASYNC)},
+                                           {DAG_WIDE(true, true, DAG_SYNC), DAG_WIDE(true, true, DAG_ASYNC)}};
+#undef DAG_WIDE
+    return table[is_bf][variant == DAG_SYNC ? 0 : 1][ci];
+}
 
 // is_bf: 0 PPR, 1 Bellman-Ford with four-byte weights, 2 with one-byte weights
 static BKernel bkernel_for(int is_bf, int variant)
@@ -516,6 +946,16 @@ int launch_batched(dag_plan* plan, int is_bf, int variant, int delta, int max_it
     const int dl = (variant == DAG_DELAYED) ? delta : 0;
     size_t dyn = (size_t)(2 * TILE + 1 + (is_bf ? TILE : 0)) * 4 + (size_t)W * dl * 32 * 4;
     BKernel k = bkernel_for(is_bf, variant);
+    int threads_launch = threads;
+    // the wide kernel's vector accesses want 16-byte aligned column arrays (rows of B values are)
+    const bool aligned16 = ((uintptr_t)out & 15u) == 0 && (is_bf || ((uintptr_t)V_or_src & 15u) == 0);
+    if (BKernel kw = (plan->batched_wide && aligned16) ? wide_kernel_for(is_bf, variant, B) : nullptr) {
+        k = kw;
+        threads_launch = NT;
+        // s_col, s_end, s_w, the shares' partials, the carries; then FP64 T and linked mass, FP32 sums, last sweeps
+        dyn = (size_t)(2 * TILE + 4 + (is_bf ? TILE : 0) + (WIDE_WARPS + 2) * B) * 4 +
+              (size_t)B * (16 + 4 * WIDE_WARPS + 4 + 4);
+    }
     int max_dyn = 0;
     DAG_CUDA(cudaDeviceGetAttribute(&max_dyn, cudaDevAttrMaxSharedMemoryPerBlockOptin, plan->device));
     if (dyn > (size_t)max_dyn)
@@ -523,12 +963,12 @@ int launch_batched(dag_plan* plan, int is_bf, int variant, int delta, int max_it
     DAG_CUDA(cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     int per_sm = 0;
     DAG_CUDA(cudaFuncSetAttribute((const void*)k, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-    DAG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k, threads, dyn));
+    DAG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k, threads_launch, dyn));
     if (per_sm < 1) return set_error(DAG_ERR_INVALID, "batched kernel cannot be resident");
     {
         cudaFuncAttributes fa;
         DAG_CUDA(cudaFuncGetAttributes(&fa, (const void*)k));
-        const int rc = set_l1_carveout((const void*)k, plan->device, threads, fa.sharedSizeBytes, dyn, per_sm);
+        const int rc = set_l1_carveout((const void*)k, plan->device, threads_launch, fa.sharedSizeBytes, dyn, per_sm);
         if (rc) return rc;
     }
     int nb = per_sm * plan->num_sms;
@@ -599,8 +1039,8 @@ int launch_batched(dag_plan* plan, int is_bf, int variant, int delta, int max_it
     }
     void* args[] = {(void*)&p};
     bool replayed = false;
-    cudaError_t le = use_graph ? graph_launch(plan, (const void*)k, nb, threads, dyn, cbytes, args, s, &replayed)
-                               : cudaLaunchCooperativeKernel((const void*)k, dim3(nb), dim3(threads), args, dyn, s);
+    cudaError_t le = use_graph ? graph_launch(plan, (const void*)k, nb, threads_launch, dyn, cbytes, args, s, &replayed)
+                               : cudaLaunchCooperativeKernel((const void*)k, dim3(nb), dim3(threads_launch), args, dyn, s);
     if (le != cudaSuccess) {
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
@@ -634,6 +1074,13 @@ int launch_batched(dag_plan* plan, int is_bf, int variant, int delta, int max_it
 }
 
 }  // namespace dag
+
+extern "C" int dag_plan_set_batched_wide(dag_plan* plan, int32_t on)
+{
+    if (!plan) return dag::set_error(DAG_ERR_INVALID, "null plan");
+    plan->batched_wide = on != 0;
+    return DAG_OK;
+}
 
 extern "C" int dag_plan_set_batched_graph(dag_plan* plan, int32_t on)
 {

@@ -171,6 +171,7 @@ struct dag_plan {
     int worker_cap = 0;       // > 0: at most this many CTAs per solve (more rows per CTA)
     int warp_ipt = 7;         // items per lane of the warp-worker tiles (5, 7 or 11)
     float fr_sparse_warp = 1.0f;  // warp-tile frontier: marks per tile at or below which the next sweep is sparse
+    bool batched_wide = true;     // batched sync / async solves of 32, 64, 128 or 256 columns: the wide kernel
     // per-vertex data
     int* outdeg = nullptr;    // [n]
     float* degf = nullptr;    // [n]

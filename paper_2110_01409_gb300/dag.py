@@ -44,6 +44,7 @@ EXPORTS = (
     "dag_sssp_u8", "dag_probe_gather", "dag_access_matrix", "dag_plan_set_batched_graph", "dag_warp_tile_items",
     "dag_plan_set_warp_tile", "dag_plan_last_status", "dag_sssp_batched_u8", "dag_rank_to_state",
     "dag_state_to_rank", "dag_pagerank_sweep_rows", "dag_sssp_sweep_rows", "dag_plan_set_warp_frontier_marks",
+    "dag_plan_set_batched_wide",
 )
 
 
@@ -121,6 +122,7 @@ def lib():
             L.dag_gather_f32.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp]
             L.dag_plan_set_worker_cap.argtypes = [_vp, _i32]
             L.dag_plan_set_batched_graph.argtypes = [_vp, _i32]
+            L.dag_plan_set_batched_wide.argtypes = [_vp, _i32]
             L.dag_access_matrix.argtypes = [_vp, _i32, _vp, _vp]
             L.dag_probe_gather.argtypes = [_vp, ctypes.c_int64, _vp, _i32, _i32, _i32, ctypes.POINTER(_f32), _vp]
             L.dag_sssp_u8.argtypes = [_vp, ctypes.c_uint32, _i32, _i32, _i32, _vp, _vp, _i32,
@@ -216,9 +218,14 @@ class Plan:
         return w.value
 
     def set_batched_graph(self, on: bool):
-        """Batched solves on this plan through CUDA graphs captured once per launch shape (on), or
-        launched directly (off, the default)."""
+        """Batched solves on this plan through CUDA graphs captured once per launch shape (on, the
+        default), or launched directly (off)."""
         _raise(lib().dag_plan_set_batched_graph(self.h, 1 if on else 0), False)
+
+    def set_batched_wide(self, on: bool):
+        """Batched sync / async solves of 32, 64, 128 or 256 columns on the wide kernel (a warp per
+        share of a tile, all columns; on, the default) or on 32-column warps (off)."""
+        _raise(lib().dag_plan_set_batched_wide(self.h, 1 if on else 0), False)
 
     def set_warp_tile(self, items_per_lane: int):
         """Warp tile shape (32 x items_per_lane items, 5, 7 or 11) of warp-worker solves."""

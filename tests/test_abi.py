@@ -71,6 +71,7 @@ def test_null_arguments_are_refused_without_a_gpu(lib):
         "dag_plan_set_batched_graph": lambda: lib.dag_plan_set_batched_graph(N, 1),
         "dag_plan_set_warp_tile": lambda: lib.dag_plan_set_warp_tile(N, 7),
         "dag_plan_set_warp_frontier_marks": lambda: lib.dag_plan_set_warp_frontier_marks(N, ctypes.c_float(1.0)),
+        "dag_plan_set_batched_wide": lambda: lib.dag_plan_set_batched_wide(N, 1),
         "dag_plan_last_status": lambda: lib.dag_plan_last_status(N, N, N),
         "dag_rank_to_state": lambda: lib.dag_rank_to_state(N, N, N, N, N),
         "dag_state_to_rank": lambda: lib.dag_state_to_rank(N, N, N, N),

@@ -150,3 +150,71 @@ def test_sssp_batched_one_byte_weights(dag, graph, variant, delta):
     D8 = D8.cpu().numpy().view(np.uint32)
     for c in (0, 17, 39):
         assert np.array_equal(D8[:, c], oracle.dijkstra(g, w, int(srcs[c])))
+
+
+# ---- the wide kernel: 32, 64, 128 or 256 columns, synchronous and asynchronous forms ----
+@pytest.mark.parametrize("B", [32, 64, 128, 256])
+@pytest.mark.parametrize("variant", ["sync", "async"])
+def test_wide_ppr_batched_matches_oracle_and_the_narrow_kernel(dag, graph, B, variant):
+    # a warp per share of each tile over all B columns: every checked column within L1 1e-5 of its fp64
+    # fixed point; the synchronous form in as many sweeps as the 32-column kernel (within one) and equal
+    # values within rounding (a row split between shares adds its partial sums in another order)
+    g = graph
+    sets = I.ppr_seed_sets(g.n, B, seed=11)
+    V = torch.from_numpy(I.teleport_matrix(g.n, sets)).cuda()
+    plan = dag.Plan.from_graph(g, "cuda")
+    R, iters, st = dag.ppr_batched(plan, V, 0.85, 1e-6, variant, 0)
+    assert st["converged"], st
+    plan.set_batched_wide(False)
+    R2, iters2, st2 = dag.ppr_batched(plan, V, 0.85, 1e-6, variant, 0)
+    assert st2["converged"]
+    Rn = R.cpu().numpy().astype(np.float64)
+    for c in sorted({0, 1, B // 2, B - 1, int(np.argmax(iters.cpu().numpy()))}):
+        rstar = oracle.pagerank_fixed_point(g, 0.85, tele=V[:, c].cpu().numpy().astype(np.float64))
+        assert np.abs(Rn[:, c] - rstar).sum() <= 1e-5, c
+    if variant == "sync":
+        # the residual sums differ in their last bits (another summation order), so a column whose
+        # residual lands at the tolerance may take one sweep more in one kernel than in the other
+        assert int(np.abs(iters.cpu().numpy() - iters2.cpu().numpy()).max()) <= 1
+        assert float((R - R2).abs().max()) <= 1e-5
+    assert st["column_sweeps"] == int(iters.sum())
+
+
+@pytest.mark.parametrize("B", [32, 64, 256])
+@pytest.mark.parametrize("variant", ["sync", "async"])
+@pytest.mark.parametrize("u8", [True, False])
+def test_wide_sssp_batched_bit_exact(dag, B, variant, u8):
+    # hub rows longer than a tile and tiles inside one row: RMAT scale 14 with its heavy in-degree head
+    g = I.rmat(14, 16, seed=8)
+    w = I.weights_u32(g, 12)
+    srcs = I.sources(g, B, seed=13)
+    plan = dag.Plan.from_graph(g, "cuda")
+    wd = torch.from_numpy(w.astype(np.uint8) if u8 else w.view(np.int32)).cuda()
+    D, iters, st = dag.sssp_batched(plan, torch.from_numpy(srcs.view(np.int32)).cuda(), wd, variant, 0)
+    assert st["converged"]
+    D = D.cpu().numpy().view(np.uint32)
+    its = iters.cpu().numpy()
+    for c in sorted({0, 1, B // 3, B - 1}):
+        assert np.array_equal(D[:, c], oracle.dijkstra(g, w, int(srcs[c]))), c
+        if variant == "sync":
+            _, it, _, _ = oracle.sssp(g, w, int(srcs[c]), oracle.SYNC)
+            assert its[c] == it
+    plan.set_batched_wide(False)
+    D2, _, _ = dag.sssp_batched(plan, torch.from_numpy(srcs.view(np.int32)).cuda(), wd, variant, 0)
+    assert np.array_equal(D, D2.cpu().numpy().view(np.uint32))
+
+
+def test_wide_batched_tiny_graphs(dag):
+    # rows of no in-edges, a graph smaller than one tile, and the delayed form on the 32-column kernel
+    g = I.from_edges(6, [0, 1, 2, 0], [1, 2, 3, 3], "tiny")
+    plan = dag.Plan.from_graph(g, "cuda")
+    V = np.zeros((6, 32), dtype=np.float32)
+    V[np.arange(32) % 6, np.arange(32)] = 1.0
+    for variant, delta in (("sync", 0), ("async", 0), ("delayed", 4)):
+        # (tol 1e-6: with ranks near 0.2 the FP32 residual of six rows cannot fall much below 1e-7)
+        R, _, st = dag.ppr_batched(plan, torch.from_numpy(V).cuda(), 0.85, 1e-6, variant, delta)
+        assert st["converged"]
+        R = R.cpu().numpy()
+        for c in (0, 1, 5, 31):
+            rstar = oracle.pagerank_fixed_point(g, 0.85, tele=V[:, c].astype(np.float64))
+            assert np.abs(R[:, c] - rstar).sum() <= 1e-5, (variant, c)
