@@ -422,10 +422,12 @@ __device__ __forceinline__ void st_cols(uint32_t* a, const uint32_t (&v)[CPL], u
 }
 
 constexpr int WIDE_WARPS = 8;  // warps per CTA of the wide kernel
-constexpr int WIDE_U = 4;      // edges whose rows a warp gathers before accumulating
+constexpr int WIDE_U = 1;      // edges whose rows a warp gathers before accumulating: the warps in flight hide the
+                               // latency (measured at B = 256: 1 edge and 3 CTAs per SM beat 2, 4, 6 and 8 edges
+                               // at 2 CTAs, and 4 CTAs, whose 64 registers spill)
 
 template <bool BF, int VAR, bool W8, int CPL>
-__global__ void __launch_bounds__(NT, 2) batched_wide_kernel(const BatchParams p)
+__global__ void __launch_bounds__(NT, 3) batched_wide_kernel(const BatchParams p)
 {
     constexpr bool SYNC = VAR == DAG_SYNC;
     constexpr bool LIVE = !SYNC && !BF;
