@@ -321,13 +321,9 @@ def run_gpu(args):
                     "kernel": kernel_name("BF8", bf_var, bf_dl, bf_rd, bf_tile)}
 
     # ---- e2e through the public API from pinned host buffers ----
-    # e2e builds a plan per step: the frontier's maps (one out-CSR sort per plan, ~9 ms at this size)
-    # cost about what they save over one step's 8 solves, so e2e runs the tuner's fastest Bellman-Ford
-    # candidate without the frontier
-    bf_e2e = min((c for c in tune_bf["candidates"] if "ms" in c and "frontier" not in c["reads"]),
-                 key=lambda c: c["ms"], default=None)
-    bf_choice_e2e = (bf_e2e["variant"], bf_e2e["delta"], bf_e2e["reads"], bf_e2e["warp_tile"]) if bf_e2e else \
-        (bf_var, bf_dl, "refresh", bf_tile)
+    # e2e builds a plan per step and runs the device step's own choices; a frontier choice builds its
+    # out-edge maps (a counting sort of the in-CSR by source) inside the first solve of every step
+    bf_choice_e2e = (bf_var, bf_dl, bf_rd, bf_tile)
     e2e = run_e2e(args, g, w, srcs, dev, dag, torch, (pr_var, pr_dl, pr_rd, pr_tile), bf_choice_e2e) \
         if args.e2e else None
     if e2e is not None:

@@ -205,7 +205,7 @@ int cuda_check(cudaError_t e, const char* what);
 int get_partition(dag_plan* plan, int nblocks, Partition** out, cudaStream_t s, int row_cap);
 
 // The frontier maps of a partition (and the plan's out-CSR row pointers), built once.
-int frontier_maps(dag_plan* plan, Partition* part, cudaStream_t s);
+int frontier_maps(dag_plan* plan, Partition* part, cudaStream_t s, bool with_end = true);
 int max_workers(dag_plan* plan, int mode, int variant, int buf_cap_elems, int* out);
 
 // sweep.cu

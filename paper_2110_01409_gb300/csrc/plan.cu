@@ -393,15 +393,6 @@ __global__ void k_edge_dst(const int* rowptr, int n, int* dst)
     }
 }
 
-// a[x] = t for x in [lo[t], lo[t+1]), t < count: one warp per segment.
-__global__ void k_fill_segments(const int* lo, int count, int* a)
-{
-    const int lane = threadIdx.x & 31;
-    const long long t = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    if (t >= count) return;
-    const int x1 = lo[t + 1];
-    for (int x = lo[t] + lane; x < x1; x += 32) a[x] = (int)t;
-}
 __global__ void k_gather_i32(const int* src, const int* idx, int* out, long long m)
 {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < m; e += (long long)gridDim.x * blockDim.x)
@@ -450,67 +441,91 @@ int launch_transpose(dag_plan* plan, int* out_rowptr, int* out_colidx, int* perm
     return DAG_OK;
 }
 
-// Frontier maps: for every out-edge u -> v (out-CSR order), the tile holding its
-// in-CSR position and the tile holding v's row end. A change of u makes the
-// tiles between the two run again in the next sweep.
+// Frontier maps: for every out-edge u -> v, the tile holding its in-CSR
+// position and the tile holding v's row end. A change of u makes the tiles
+// between the two run again in the next sweep. The maps are read as one set
+// per source, so the order of the edges inside a source's out-list is free:
+// a counting sort by source fills them in one pass over the in-CSR.
 
-// otile[e] = etile[perm[e]], oend[e] = rtile[ocol[e]]: the tiles of every
-// out-edge's in-CSR position and of its target's row end.
-__global__ void k_frontier_maps(const int* perm, const int* ocol, long long m, const int* etile, const int* rtile,
-                                int* otile, int* oend)
+// One warp per tile t: every in-edge e = (v <- u) of the tile (edges
+// [tile_nz[t], tile_nz[t+1]) of rows [tile_row[t], tile_row[t+1]]) takes the
+// next slot of u's out-list (cursor[u], one atomic per run of equal sources
+// in the warp) and writes there t and the tile ending row v: t itself for the
+// rows that end inside t, else the tile ending row tile_row[t+1] (oend may
+// be null).
+__global__ void k_frontier_scatter(const int* rowptr, const int* colidx, int n, const int* tile_row,
+                                   const int* tile_nz, int tiles, int* cursor, int* otile, int* oend)
 {
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < m; e += (long long)gridDim.x * blockDim.x) {
-        otile[e] = etile[perm[e]];
-        oend[e] = rtile[ocol[e]];
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (int)(((long long)gridDim.x * blockDim.x) >> 5);
+    for (int t = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5); t < tiles; t += nwarps) {
+        const int r0 = tile_row[t], r1 = tile_row[t + 1];
+        const int nz0 = tile_nz[t], nz1 = tile_nz[t + 1];
+        if (nz0 >= nz1) continue;
+        // the tile ending row r1: the first t' > t whose successor starts past r1
+        int end1 = t;
+        if (r1 < n) {
+            int lo = t + 1, hi = tiles - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (tile_row[mid + 1] > r1) hi = mid; else lo = mid + 1;
+            }
+            end1 = lo;
+        }
+        const int vmax = min(r1, n - 1);
+        for (int e0 = nz0; e0 < nz1; e0 += 32) {
+            const int e = e0 + lane;
+            const bool live = e < nz1;
+            const unsigned act = __ballot_sync(0xffffffffu, live);
+            if (!live) continue;
+            // the row of e: the last row of the tile starting at or before e
+            int lo = r0, hi = vmax;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (rowptr[mid] <= e) lo = mid; else hi = mid - 1;
+            }
+            const int u = colidx[e];
+            const unsigned peers = __match_any_sync(act, u);
+            const int leader = __ffs(peers) - 1;
+            int base = 0;
+            if (lane == leader) base = atomicAdd(cursor + u, __popc(peers));
+            base = __shfl_sync(peers, base, leader);
+            const int pos = base + __popc(peers & ((1u << lane) - 1u));
+            otile[pos] = t;
+            if (oend) oend[pos] = lo < r1 ? t : end1;
+        }
     }
 }
 
-int frontier_maps(dag_plan* plan, Partition* part, cudaStream_t s)
+// fr_orow[0] = 0, fr_orow[1 ..] = inclusive prefix of out-degree. with_end
+// false leaves out fr_oend (the warp-tile frontier stamps one tile per edge).
+int frontier_maps(dag_plan* plan, Partition* part, cudaStream_t s, bool with_end)
 {
     if (part->fr_act) return DAG_OK;
     const int n = plan->n;
     const long long m = plan->m;
-    int *ocol = nullptr, *perm = nullptr;
+    size_t scan_bytes = 0;
+    DAG_CUDA(cub::DeviceScan::InclusiveSum(nullptr, scan_bytes, plan->outdeg, (int*)nullptr, n, s));
+    // fr_otile doubles as the scan's scratch before the scatter fills it
+    const size_t otile_ints = std::max((size_t)std::max(m, 1LL), (scan_bytes + sizeof(int) - 1) / sizeof(int));
     if (!plan->fr_orow) DAG_CUDA(cudaMalloc(&plan->fr_orow, (size_t)(n + 1) * sizeof(int)));
-    DAG_CUDA(cudaMalloc(&part->fr_otile, (size_t)std::max(m, 1LL) * sizeof(int)));
-    DAG_CUDA(cudaMalloc(&part->fr_oend, (size_t)std::max(m, 1LL) * sizeof(int)));
+    DAG_CUDA(cudaMalloc(&part->fr_otile, otile_ints * sizeof(int)));
+    if (with_end) DAG_CUDA(cudaMalloc(&part->fr_oend, (size_t)std::max(m, 1LL) * sizeof(int)));
     DAG_CUDA(cudaMalloc(&part->fr_alist, (size_t)std::max(part->tiles, 1) * sizeof(int)));
     DAG_CUDA(cudaMalloc(&part->fr_chg, (size_t)n * sizeof(int)));
     DAG_CUDA(cudaMalloc(&part->fr_glist, (size_t)std::max(part->tiles, 1) * sizeof(int)));
     DAG_CUDA(cudaMalloc(&part->fr_gchg, ((size_t)n + (size_t)std::max(part->tiles, 1)) * sizeof(int)));
-    DAG_CUDA(cudaMalloc(&ocol, (size_t)std::max(m, 1LL) * sizeof(int)));
-    DAG_CUDA(cudaMalloc(&perm, (size_t)std::max(m, 1LL) * sizeof(int)));
-    int rc = launch_transpose(plan, plan->fr_orow, ocol, perm, s);
-    if (rc == DAG_OK && m > 0 && part->tiles > 0) {
-        // the tile of every in-edge and of every row end (tiles cover both in order), then per out-edge
-        int *etile = nullptr, *rtile = nullptr;
-        if (cudaMalloc(&etile, (size_t)m * sizeof(int)) != cudaSuccess ||
-            cudaMalloc(&rtile, (size_t)n * sizeof(int)) != cudaSuccess) {
-            cudaFree(etile);
-            cudaGetLastError();
-            rc = set_error(DAG_ERR_NOMEM, "frontier maps");
-        } else {
-            const int blocks = (int)(((long long)part->tiles * 32 + 255) / 256);
-            k_fill_segments<<<blocks, 256, 0, s>>>(part->tile_nz, part->tiles, etile);
-            k_fill_segments<<<blocks, 256, 0, s>>>(part->tile_row, part->tiles, rtile);
-            k_frontier_maps<<<2048, 256, 0, s>>>(perm, ocol, m, etile, rtile, part->fr_otile, part->fr_oend);
-            const cudaError_t e = cudaGetLastError();
-            if (e != cudaSuccess) rc = cuda_check(e, "frontier maps");
-            if (rc == DAG_OK) {
-                const cudaError_t e2 = cudaStreamSynchronize(s);
-                if (e2 != cudaSuccess) rc = cuda_check(e2, "frontier maps");
-            }
-            cudaFree(etile);
-            cudaFree(rtile);
-        }
+    DAG_CUDA(cudaMemsetAsync(plan->fr_orow, 0, sizeof(int), s));
+    DAG_CUDA(cub::DeviceScan::InclusiveSum(part->fr_otile, scan_bytes, plan->outdeg, plan->fr_orow + 1, n, s));
+    if (m > 0 && part->tiles > 0) {
+        // fr_chg (a per-sweep list, written before it is read) serves as the cursor
+        DAG_CUDA(cudaMemcpyAsync(part->fr_chg, plan->fr_orow, (size_t)n * sizeof(int), cudaMemcpyDeviceToDevice, s));
+        const int blocks = (int)std::min(((long long)part->tiles * 32 + 255) / 256, 152LL * 64);
+        k_frontier_scatter<<<blocks, 256, 0, s>>>(plan->rowptr, plan->colidx, n, part->tile_row, part->tile_nz,
+                                                  part->tiles, part->fr_chg, part->fr_otile, part->fr_oend);
+        DAG_CUDA(cudaGetLastError());
     }
-    if (rc == DAG_OK) {
-        const cudaError_t e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) rc = cuda_check(e, "frontier maps");
-    }
-    cudaFree(ocol);
-    cudaFree(perm);
-    if (rc != DAG_OK) return rc;
+    DAG_CUDA(cudaStreamSynchronize(s));
     // allocated last: a set fr_act marks the maps complete
     DAG_CUDA(cudaMalloc(&part->fr_act, (size_t)std::max(part->tiles, 1) * sizeof(int)));
     return DAG_OK;

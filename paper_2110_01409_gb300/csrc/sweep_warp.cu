@@ -659,7 +659,7 @@ int warp_frontier_maps(dag_plan* plan, int mode, cudaStream_t s)
     Partition* part = nullptr;
     int rc = warp_shape(plan, mode, DAG_ASYNC, 0, &nb, &cap, &clamped, &part, s, WARP_FRONTIER);
     if (rc) return rc;
-    return frontier_maps(plan, part, s);
+    return frontier_maps(plan, part, s, false);
 }
 
 int launch_warp_sweep(dag_plan* plan, int mode, int variant, int delta, SweepParams& p, cudaStream_t s,
@@ -679,7 +679,7 @@ int launch_warp_sweep(dag_plan* plan, int mode, int variant, int delta, SweepPar
     if (kind == WARP_ORDERED && !part->tpub)
         DAG_CUDA(cudaMalloc(&part->tpub, (size_t)part->tiles * sizeof(unsigned long long)));
     if (p.frontier) {
-        rc = frontier_maps(plan, part, s);
+        rc = frontier_maps(plan, part, s, false);
         if (rc) return rc;
         p.fr_orow = plan->fr_orow;
         p.fr_otile = part->fr_otile;
