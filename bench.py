@@ -718,7 +718,8 @@ def run_adjoint(g, plan, dag, torch):
     """Adjoint form (RMAT scale 22, FP32 weights in (0,1], 4096 targets, w_i ~ N(0,1)):
     forward weighted PageRank and its backward pass, beside the plain sweep. The headline pair is
     the asynchronous form on warp workers with cached reads (forward and adjoint alike); the
-    synchronous warp form and the CTA-tile asynchronous form are reported beside it."""
+    synchronous warp form, the ordered warp sweep and the CTA-tile asynchronous form are reported
+    beside it."""
     from paper_2110_01409_gb300 import inputs as I
 
     w = torch.from_numpy(I.weights_f32(g, SEED)).cuda()
@@ -729,7 +730,7 @@ def run_adjoint(g, plan, dag, torch):
     forms = {}
     plan.set_warp_tile(7)
     for name, variant, reads in (("warp_async_cached", "async", "warp+cached"), ("warp_sync", "sync", "warp"),
-                                 ("cta_async", "async", "refresh")):
+                                 ("ordered_cached", "async", "ordered+cached"), ("cta_async", "async", "refresh")):
         model = dag.WeightedPageRank(plan, d=0.85, tol=1e-6, variant=variant, delta=0, reads=reads)
         for rep in range(2):
             e0, e1, e2 = ev(), ev(), ev()
@@ -739,7 +740,9 @@ def run_adjoint(g, plan, dag, torch):
             gw, gt, _, st_b = model.backward(val, s, r, c)
             e2.record()
             torch.cuda.synchronize()
-            # forward_ms includes the weight normalisation (an out-CSR sort); the solves compare directly
+            # forward_ms includes the weight normalisation (its out-CSR order is built on the plan's first
+            # call, in rep 0); backward_ms the gather of the weights into out-edge order; adjoint_solve_ms
+            # is the adjoint solve with the edge gradients, against the forward solve alone
             forms[name] = {"variant": variant, "reads": reads, "forward_ms": round(e0.elapsed_time(e1), 3),
                            "forward_solve_ms": round(st_f["ms"], 3), "forward_sweeps": st_f["iters"],
                            "backward_ms": round(e1.elapsed_time(e2), 3), "adjoint_sweeps": st_b["iters"],

@@ -329,7 +329,11 @@ int dag_transpose(dag_plan* plan, int32_t* d_out_rowptr, int32_t* d_out_colidx, 
  * Row normalisation of raw edge weights into the transition matrix: d_s[u] =
  * sum of d_w over u's out-edges (device float [n]), d_val[e] = d_w[e] /
  * d_s[src(e)] (device float [m], in-edge order). d_w > 0 expected. (M_vu of
- * dag_pagerank; no counterpart in the paper.)
+ * dag_pagerank; no counterpart in the paper.) The first call on a plan sorts
+ * its edges by source once and keeps that order in the plan (4 (n + m) bytes
+ * more, freed by dag_plan_destroy); every call then runs asynchronously on
+ * the stream. Each d_s[u] is summed in a fixed order: repeated calls on the
+ * same weights give the same bits.
  */
 int dag_normalize_weights(dag_plan* plan, const float* d_w, float* d_val, float* d_s, void* stream);
 

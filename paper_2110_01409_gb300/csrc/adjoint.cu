@@ -2,19 +2,26 @@
 // (no counterpart in the paper). With M_vu = w_uv / s_u, r the forward fixed
 // point and lambda the adjoint (lambda = c + d M^T lambda + d g sum(lambda)/n):
 //   dL/dw_uv = d r_u (lambda_v - (M^T lambda)_u) / s_u,   dL/dt_v = (1 - d) lambda_v.
-// One pass over the in-edges in the caller's (in-CSR) order; each CTA walks
-// its vertex block tile by tile and finds an edge's row by binary search over
-// the tile's row ends in shared memory.
+// A pass over the vertices packs each source's two factors, d r_u / s_u and
+// (M^T lambda)_u, into one 8-byte pair; then one pass over the in-edges in the
+// caller's (in-CSR) order, one gather per edge: each CTA walks its vertex
+// block tile by tile and finds an edge's row by binary search over the tile's
+// row ends in shared memory.
 #include <climits>
 
 #include "dag_internal.cuh"
 
 namespace dag {
 
+__global__ void k_grad_coef(const float* s_norm, const float* rank, const float* mt, float d, int n, float2* coef)
+{
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < n) coef[u] = make_float2(d * rank[u] / s_norm[u], mt[u]);  // s_u = 0: u is no edge's source
+}
+
 __global__ void __launch_bounds__(NT) k_edge_grad(const int* rowptr, const int* colidx, const int* cta_tile,
-                                                  const int* tile_row, const int* tile_nz, float d,
-                                                  const float* s_norm, const float* rank, const float* lambda,
-                                                  const float* mt, float* grad_w)
+                                                  const int* tile_row, const int* tile_nz, const float2* coef,
+                                                  const float* lambda, float* grad_w)
 {
     __shared__ int s_end[TILE + 1];
     const int c = blockIdx.x;
@@ -33,10 +40,9 @@ __global__ void __launch_bounds__(NT) k_edge_grad(const int* rowptr, const int* 
                 if (s_end[mid] > j) hi = mid;
                 else lo = mid + 1;
             }
-            const int v = a0 + lo;
             const int e = b0 + j;
-            const int u = colidx[e];
-            grad_w[e] = d * rank[u] * (lambda[v] - mt[u]) / s_norm[u];
+            const float2 cf = coef[colidx[e]];
+            grad_w[e] = cf.x * (lambda[a0 + lo] - cf.y);
         }
     }
 }
@@ -55,9 +61,12 @@ int launch_edge_grad(dag_plan* plan, float d, const float* val, const float* s_n
     Partition* part = nullptr;
     int rc = get_partition(plan, P, &part, st, 0);
     if (rc) return rc;
-    if (grad_w && plan->m > 0)
-        k_edge_grad<<<P, NT, 0, st>>>(plan->rowptr, plan->colidx, part->cta_tile, part->tile_row, part->tile_nz, d,
-                                      s_norm, rank, lambda, mt, grad_w);
+    if (grad_w && plan->m > 0) {
+        if (!plan->grad_coef) DAG_CUDA(cudaMalloc(&plan->grad_coef, (size_t)plan->n * sizeof(float2)));
+        k_grad_coef<<<(plan->n + 255) / 256, 256, 0, st>>>(s_norm, rank, mt, d, plan->n, (float2*)plan->grad_coef);
+        k_edge_grad<<<P, NT, 0, st>>>(plan->rowptr, plan->colidx, part->cta_tile, part->tile_row, part->tile_nz,
+                                      (const float2*)plan->grad_coef, lambda, grad_w);
+    }
     if (grad_t) k_teleport_grad<<<(plan->n + 255) / 256, 256, 0, st>>>(lambda, 1.0f - d, grad_t, plan->n);
     DAG_CUDA(cudaGetLastError());
     return DAG_OK;

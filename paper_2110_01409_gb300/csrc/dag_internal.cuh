@@ -181,6 +181,10 @@ struct dag_plan {
     dag::SyncBlock* sync = nullptr;
     float* scratch_f = nullptr; // [n] float scratch (adjoint aux)
     int* fr_orow = nullptr;   // [n+1] out-CSR row pointers (frontier sweeps, built on first use)
+    int* nw_perm = nullptr;   // [m] in-edge of each out-edge, targets ascending (weight normalisation, first use)
+    int* nw_hubs = nullptr;   // sources of more than NW_HUB out-edges (summed by a whole block)
+    int nw_nhubs = 0;
+    void* grad_coef = nullptr;  // [n] float2 (d r_u / s_u, (M^T lambda)_u) of the edge gradients, first use
     std::map<long long, dag::Partition> parts;  // key: nblocks | row_cap << 32
     std::map<std::tuple<int, int, int, int>, dag::Partition> range_parts;  // (warps, tile, lo, hi)
     // batched workspace (grown on demand)

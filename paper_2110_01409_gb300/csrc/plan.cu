@@ -531,15 +531,52 @@ int frontier_maps(dag_plan* plan, Partition* part, cudaStream_t s, bool with_end
     return DAG_OK;
 }
 
-// s[u] = sum of w over u's out-edges (one thread per source over the
-// out-CSR, fixed order); val[e] = w[e] / s[colidx[e]].
+// s[u] = sum of w over u's out-edges, in a fixed order whatever the launch:
+// a warp per source (lane j takes out-edges j, j + 32, ... in out-CSR order,
+// then a butterfly of the lanes' sums); sources of more than NW_HUB out-edges
+// are left to k_out_sum_hub, a whole block per source.
+constexpr int NW_HUB = 2048;
+constexpr int NW_HUB_THREADS = 256;
 __global__ void k_out_sum(const int* orow, const int* perm, const float* w, int n, float* s)
 {
-    int u = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const long long u = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     if (u >= n) return;
+    const int k0 = orow[u], k1 = orow[u + 1];
+    if (k1 - k0 > NW_HUB) return;
     float acc = 0.0f;
-    for (int k = orow[u]; k < orow[u + 1]; ++k) acc += w[perm[k]];
-    s[u] = acc;
+    for (int k = k0 + lane; k < k1; k += 32) acc += w[perm[k]];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) s[u] = acc;
+}
+__global__ void __launch_bounds__(NW_HUB_THREADS) k_out_sum_hub(const int* orow, const int* perm, const float* w,
+                                                               const int* hubs, int nhubs, float* s)
+{
+    __shared__ float part[NW_HUB_THREADS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int h = blockIdx.x; h < nhubs; h += gridDim.x) {
+        const int u = hubs[h];
+        const int k1 = orow[u + 1];
+        float acc = 0.0f;
+        for (int k = orow[u] + threadIdx.x; k < k1; k += NW_HUB_THREADS) acc += w[perm[k]];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) part[wid] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float t = 0.0f;
+            for (int j = 0; j < NW_HUB_THREADS / 32; ++j) t += part[j];
+            s[u] = t;
+        }
+        __syncthreads();
+    }
+}
+// The sources of more than NW_HUB out-edges (list order free: each is summed alone).
+__global__ void k_hub_list(const int* orow, int n, int* hubs, int* nhubs)
+{
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < n && orow[u + 1] - orow[u] > NW_HUB) hubs[atomicAdd(nhubs, 1)] = u;
 }
 __global__ void k_div(const int* colidx, const float* w, const float* s, float* val, long long m)
 {
@@ -553,23 +590,50 @@ __global__ void k_gather_f32(const float* src, const int* idx, float* out, long 
         out[e] = src[idx[e]];
 }
 
+// The out-CSR order of the plan's edges (row pointers and permutation) is
+// built on the first call and kept: only the weights change between calls.
 int launch_normalize(dag_plan* plan, const float* w, float* val, float* s_out, cudaStream_t s)
 {
     const int n = plan->n;
     const long long m = plan->m;
-    int *orow = nullptr, *ocol = nullptr, *perm = nullptr;
-    DAG_CUDA(cudaMalloc(&orow, (size_t)(n + 1) * sizeof(int)));
-    DAG_CUDA(cudaMalloc(&ocol, (size_t)std::max(m, 1LL) * sizeof(int)));
-    DAG_CUDA(cudaMalloc(&perm, (size_t)std::max(m, 1LL) * sizeof(int)));
-    int rc = launch_transpose(plan, orow, ocol, perm, s);
-    if (rc) return rc;
-    k_out_sum<<<(n + 255) / 256, 256, 0, s>>>(orow, perm, w, n, s_out);
+    if (!plan->nw_perm) {
+        int* orow = plan->fr_orow;
+        int *ocol = nullptr, *perm = nullptr, *hubs = nullptr;
+        if (!orow) DAG_CUDA(cudaMalloc(&orow, (size_t)(n + 1) * sizeof(int)));
+        plan->fr_orow = orow;
+        DAG_CUDA(cudaMalloc(&ocol, (size_t)std::max(m, 1LL) * sizeof(int)));
+        if (cudaMalloc(&perm, (size_t)std::max(m, 1LL) * sizeof(int)) != cudaSuccess) {
+            cudaFree(ocol);
+            return cuda_check(cudaGetLastError(), "normalisation out-CSR");
+        }
+        int rc = launch_transpose(plan, orow, ocol, perm, s);
+        cudaFree(ocol);
+        if (rc == DAG_OK && cudaMalloc(&hubs, (size_t)(n + 1) * sizeof(int)) != cudaSuccess)
+            rc = cuda_check(cudaGetLastError(), "normalisation hub list");
+        if (rc == DAG_OK) {
+            // hubs[n] counts the list
+            int nh = 0;
+            cudaMemsetAsync(hubs + n, 0, sizeof(int), s);
+            k_hub_list<<<(n + 255) / 256, 256, 0, s>>>(orow, n, hubs, hubs + n);
+            cudaMemcpyAsync(&nh, hubs + n, sizeof(int), cudaMemcpyDeviceToHost, s);
+            const cudaError_t e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) rc = cuda_check(e, "normalisation hub list");
+            plan->nw_nhubs = nh;
+        }
+        if (rc != DAG_OK) {
+            cudaFree(perm);
+            cudaFree(hubs);
+            return rc;
+        }
+        plan->nw_hubs = hubs;
+        plan->nw_perm = perm;  // set last: a set nw_perm marks the out-CSR order complete
+    }
+    k_out_sum<<<(unsigned)(((long long)n * 32 + 255) / 256), 256, 0, s>>>(plan->fr_orow, plan->nw_perm, w, n, s_out);
+    if (plan->nw_nhubs > 0)
+        k_out_sum_hub<<<std::min(plan->nw_nhubs, 4 * plan->num_sms), NW_HUB_THREADS, 0, s>>>(
+            plan->fr_orow, plan->nw_perm, w, plan->nw_hubs, plan->nw_nhubs, s_out);
     if (m) k_div<<<2048, 256, 0, s>>>(plan->colidx, w, s_out, val, m);
     DAG_CUDA(cudaGetLastError());
-    DAG_CUDA(cudaStreamSynchronize(s));
-    cudaFree(orow);
-    cudaFree(ocol);
-    cudaFree(perm);
     return DAG_OK;
 }
 
@@ -672,6 +736,9 @@ extern "C" int dag_plan_destroy(dag_plan* p)
         cudaFree(kv.second.wpub);
     }
     cudaFree(p->fr_orow);
+    cudaFree(p->nw_perm);
+    cudaFree(p->nw_hubs);
+    cudaFree(p->grad_coef);
     delete p;
     return DAG_OK;
 }

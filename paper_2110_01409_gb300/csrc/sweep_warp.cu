@@ -168,19 +168,21 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_warp_kernel(const SweepP
                     if constexpr (!BF) dg_k[k] = ld_stream_f32(p.degf + a0 + r);
                 }
             }
-            // the adjoint's base terms c_v: one row's load ahead of its update (a tile of many rows would
-            // otherwise wait once per row)
-            float bv_next = (MODE == MODE_ADJ && lane < NA) ? row_base<MODE>(p, a0 + lane) : 0.0f;
+            // the adjoint's base terms c_v, all of the tile's loads in flight together (a load per row
+            // ahead of its update would wait once per row)
+            float bv_k[WIPT];
+            if constexpr (MODE == MODE_ADJ) {
+#pragma unroll
+                for (int k = 0; k < WIPT; ++k) bv_k[k] = lane + 32 * k < NA ? row_base<MODE>(p, a0 + lane + 32 * k) : 0.0f;
+            }
 #pragma unroll
             for (int k = 0; k < WIPT; ++k) {
                 const int r = lane + 32 * k;
-                float bv = bv_next;
-                if constexpr (MODE == MODE_ADJ) {
-                    if (k + 1 < WIPT && r + 32 < NA) bv_next = row_base<MODE>(p, a0 + r + 32);
-                }
                 if (r >= NA || (k == 0 && lane == 0 && skip)) continue;
                 const int v = a0 + r;
-                if constexpr (MODE != MODE_ADJ) bv = row_base<MODE>(p, v);
+                float bv;
+                if constexpr (MODE == MODE_ADJ) bv = bv_k[k];
+                else bv = row_base<MODE>(p, v);
                 const uint32_t xnew =
                     row_update_b<MODE>(p, v, sum[r], xo_k[k], dg_k[k], gt, bv, A.off_f, res_part, g_part, dg_part);
                 if constexpr (SYNC) st_weak_b32(xout + v, xnew);
@@ -486,13 +488,21 @@ __global__ void __launch_bounds__(NT, WMINBLOCKS) sweep_ordered_kernel(const Swe
                     if constexpr (!BF) dg_k[q] = ld_stream_f32(p.degf + a0 + r);
                 }
             }
+            float bv_k[WIPT];  // the adjoint's base terms c_v, loaded together
+            if constexpr (MODE == MODE_ADJ) {
+#pragma unroll
+                for (int q = 0; q < WIPT; ++q) bv_k[q] = lane + 32 * q < NA ? row_base<MODE>(p, a0 + lane + 32 * q) : 0.0f;
+            }
 #pragma unroll
             for (int q = 0; q < WIPT; ++q) {
                 const int r = lane + 32 * q;
                 if (r >= NA || (q == 0 && lane == 0 && skip)) continue;
                 const int v = a0 + r;
+                float bv;
+                if constexpr (MODE == MODE_ADJ) bv = bv_k[q];
+                else bv = row_base<MODE>(p, v);
                 const uint32_t xnew =
-                    row_update<MODE>(p, v, sum[r], xo_k[q], dg_k[q], gt, A.off_f, res_part, g_part, dg_part);
+                    row_update_b<MODE>(p, v, sum[r], xo_k[q], dg_k[q], gt, bv, A.off_f, res_part, g_part, dg_part);
                 st_relaxed_b32(X + v, xnew);
             }
             // -------- the previous tile's look-back, then this tile's becomes pending --------

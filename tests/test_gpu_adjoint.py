@@ -150,6 +150,35 @@ def test_transpose_and_normalize_match_definitions(dag):
     assert np.max(np.abs(s.cpu().numpy()[has] - s64[has]) / s64[has]) <= 1e-5
 
 
+
+def test_normalize_hubs_and_repeat(dag):
+    # Sources past the warp-sized sum (one of 6000 out-edges, one of exactly 2048 and one of 2049)
+    # beside ordinary ones: every s[u] within FP32 rounding of the fp64 definition, and a second
+    # call on the same weights gives the same bits (a fixed summation order).
+    rng = np.random.default_rng(21)
+    n = 8000
+    src = [np.zeros(6000, np.int64), np.full(2048, 1), np.full(2049, 2), rng.integers(3, n, 40000)]
+    dst = [rng.choice(np.arange(1, n), 6000, replace=False), rng.choice(np.arange(3, n), 2048, replace=False),
+           rng.choice(np.arange(3, n), 2049, replace=False), rng.integers(0, n, 40000)]
+    src, dst = np.concatenate(src), np.concatenate(dst)
+    keep = src != dst
+    g = I.from_edges(n, src[keep], dst[keep], "hubs8000")
+    plan = dag.Plan.from_graph(g, "cuda")
+    w = I.weights_f32(g, 9)
+    wd = torch.from_numpy(w).cuda()
+    val, s = dag.normalize_weights(plan, wd)
+    v64, s64 = oracle.normalize(g, w.astype(np.float64))
+    has = s64 > 0
+    assert np.max(np.abs(s.cpu().numpy()[has] - s64[has]) / s64[has]) <= 1e-5
+    assert np.max(np.abs(val.cpu().numpy() - v64)) <= 1e-6
+    val2, s2 = dag.normalize_weights(plan, wd)
+    assert torch.equal(s, s2) and torch.equal(val, val2)
+    # new weights on the kept order
+    w3 = I.weights_f32(g, 10)
+    val3, s3 = dag.normalize_weights(plan, torch.from_numpy(w3).cuda())
+    v64, s64 = oracle.normalize(g, w3.astype(np.float64))
+    assert np.max(np.abs(val3.cpu().numpy() - v64)) <= 1e-6
+
 @pytest.mark.parametrize("variant,delta,reads", FORMS)
 def test_adjoint_deflation_cuts_the_slow_mode(dag, scaled_case, variant, delta, reads):
     # The adjoint's slow error mode along 1 (B 1 = d 1) is deflated after every sweep, so the
