@@ -380,7 +380,7 @@ int dag_pagerank_adjoint(dag_plan* in_plan, dag_plan* out_plan, float d, double 
  *    graph returns DAG_ERR_INVALID and changes nothing.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current and keeps it for the
- *    process. Make that first call before any stream capture. A device reset
+ *    process. A device reset
  *    (cudaDeviceReset) invalidates the kept address: after one, this entry
  *    point must not be called again in the same process.
  *  - The call checks the CSR on the device (rowptr order, colidx range) and
@@ -388,7 +388,8 @@ int dag_pagerank_adjoint(dag_plan* in_plan, dag_plan* out_plan, float d, double 
  *  - All calls share the array, and it keeps the previous call's contents
  *    (each call clears what it needs zeroed). Calls whose GPU work overlaps,
  *    for instance on two streams, race on it: serialise them.
- *  - The call waits for `stream`; h_stats->ms is left 0.
+ *  - The call waits for `stream` and reads its status back to the host, so
+ *    it cannot be captured into a CUDA graph; h_stats->ms is left 0.
  */
 #define DAG_NOALLOC_MAX_N (1 << 20)
 #define DAG_NOALLOC_MAX_M (1 << 24)
