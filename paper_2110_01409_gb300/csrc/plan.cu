@@ -499,9 +499,8 @@ __global__ void k_frontier_scatter(const int* rowptr, const int* colidx, int n, 
 
 // fr_orow[0] = 0, fr_orow[1 ..] = inclusive prefix of out-degree. with_end
 // false leaves out fr_oend (the warp-tile frontier stamps one tile per edge).
-int frontier_maps(dag_plan* plan, Partition* part, cudaStream_t s, bool with_end)
+static int build_frontier_maps(dag_plan* plan, Partition* part, cudaStream_t s, bool with_end)
 {
-    if (part->fr_act) return DAG_OK;
     const int n = plan->n;
     const long long m = plan->m;
     size_t scan_bytes = 0;
@@ -529,6 +528,21 @@ int frontier_maps(dag_plan* plan, Partition* part, cudaStream_t s, bool with_end
     // allocated last: a set fr_act marks the maps complete
     DAG_CUDA(cudaMalloc(&part->fr_act, (size_t)std::max(part->tiles, 1) * sizeof(int)));
     return DAG_OK;
+}
+
+int frontier_maps(dag_plan* plan, Partition* part, cudaStream_t s, bool with_end)
+{
+    if (part->fr_act) return DAG_OK;
+    const int rc = build_frontier_maps(plan, part, s, with_end);
+    if (rc != DAG_OK) {  // a failed build leaves nothing behind: the next frontier solve starts again
+        int** arrays[] = {&part->fr_otile, &part->fr_oend, &part->fr_alist, &part->fr_chg,
+                          &part->fr_glist, &part->fr_gchg, &part->fr_act};
+        for (int** a : arrays) {
+            cudaFree(*a);
+            *a = nullptr;
+        }
+    }
+    return rc;
 }
 
 // s[u] = sum of w over u's out-edges, in a fixed order whatever the launch:
