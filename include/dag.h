@@ -83,7 +83,11 @@ typedef struct dag_plan dag_plan; /* opaque */
  * untimed setup step: Sec. III-A's static partition is computed per launch
  * shape and cached here). d_colidx entries are checked against [0, n) on the
  * device. The plan owns its workspace and frees it in dag_plan_destroy.
- * barrier_timeout_ms <= 0 selects the default (2000 ms).
+ * barrier_timeout_ms <= 0 selects the default (2000 ms). Plans take their
+ * device memory from a pool the library keeps per device: up to 4 GiB of
+ * what destroyed plans held stays mapped for later plans (a plan built and
+ * destroyed per call maps its arrays once). dag_plan_destroy waits for the
+ * device (as cudaFree would) before it returns the plan's memory.
  */
 int dag_plan_create(const dag_csr* csr, int32_t barrier_timeout_ms, dag_plan** out);
 int dag_plan_destroy(dag_plan* plan);

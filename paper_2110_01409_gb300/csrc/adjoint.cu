@@ -10,6 +10,7 @@
 #include <climits>
 
 #include "dag_internal.cuh"
+#include "devmem.cuh"
 
 namespace dag {
 
@@ -62,7 +63,7 @@ int launch_edge_grad(dag_plan* plan, float d, const float* val, const float* s_n
     int rc = get_partition(plan, P, &part, st, 0);
     if (rc) return rc;
     if (grad_w && plan->m > 0) {
-        if (!plan->grad_coef) DAG_CUDA(cudaMalloc(&plan->grad_coef, (size_t)plan->n * sizeof(float2)));
+        if (!plan->grad_coef) DAG_CUDA(dev_alloc(&plan->grad_coef, (size_t)plan->n * sizeof(float2)));
         k_grad_coef<<<(plan->n + 255) / 256, 256, 0, st>>>(s_norm, rank, mt, d, plan->n, (float2*)plan->grad_coef);
         k_edge_grad<<<P, NT, 0, st>>>(plan->rowptr, plan->colidx, part->cta_tile, part->tile_row, part->tile_nz,
                                       (const float2*)plan->grad_coef, lambda, grad_w);

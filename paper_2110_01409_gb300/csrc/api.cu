@@ -5,6 +5,7 @@
 #include <string>
 
 #include "dag_internal.cuh"
+#include "devmem.cuh"
 
 namespace dag {
 
@@ -286,7 +287,7 @@ extern "C" int dag_pagerank_adjoint(dag_plan* in_plan, dag_plan* out_plan, float
     float* lam = d_lambda;
     float* lam_tmp = nullptr;
     if (!lam) {
-        DAG_CUDA(cudaMalloc(&lam_tmp, (size_t)in_plan->n * sizeof(float)));
+        DAG_CUDA(dev_alloc(&lam_tmp, (size_t)in_plan->n * sizeof(float)));
         lam = lam_tmp;
     }
     SweepParams p{};
@@ -314,13 +315,13 @@ extern "C" int dag_pagerank_adjoint(dag_plan* in_plan, dag_plan* out_plan, float
     int nb = 0;
     rc = launch_sweep(out_plan, MODE_ADJ, var, delta, p, s, &nb);
     if (rc) {
-        if (lam_tmp) cudaFree(lam_tmp);
+        if (lam_tmp) dev_free(lam_tmp);
         return rc;
     }
     rc = launch_edge_grad(in_plan, d, d_val, d_s, d_rank, lam, in_plan->scratch_f, d_grad_w, d_grad_t, s);
     tm.stop(s);
     int rc2 = finish_solve(out_plan, nb, var == DAG_DELAYED ? delta : 0, tm, s, h_stats);
-    if (lam_tmp) cudaFree(lam_tmp);
+    if (lam_tmp) dev_free(lam_tmp);
     return rc ? rc : rc2;
 }
 

@@ -7,6 +7,7 @@
 #include <algorithm>
 
 #include "dag_internal.cuh"
+#include "devmem.cuh"
 
 namespace dag {
 
@@ -231,9 +232,9 @@ int get_partition(dag_plan* plan, int P, Partition** out, cudaStream_t s, int ro
     part.row_cap = row_cap;
     int* mr_dev = nullptr;
     int* cnt = nullptr;
-    DAG_CUDA(cudaMalloc(&part.cta_row, (P + 1) * sizeof(int)));
-    DAG_CUDA(cudaMalloc(&part.cta_tile, (P + 1) * sizeof(int)));
-    DAG_CUDA(cudaMalloc(&mr_dev, sizeof(int)));
+    DAG_CUDA(dev_alloc(&part.cta_row, (P + 1) * sizeof(int)));
+    DAG_CUDA(dev_alloc(&part.cta_tile, (P + 1) * sizeof(int)));
+    DAG_CUDA(dev_alloc(&mr_dev, sizeof(int)));
     // Row-capped tiles cost a tile per row_cap rows even where rows have no
     // edges, so their blocks weigh each row ceil(TILE / row_cap) instead of 1:
     // a block's tile count then follows its weight, as it does uncapped.
@@ -241,7 +242,7 @@ int get_partition(dag_plan* plan, int P, Partition** out, cudaStream_t s, int ro
     long long total = (long long)row_w * plan->n + plan->m;
     k_cta_rows<<<(P + 1 + 255) / 256, 256, 0, s>>>(plan->rowptr, plan->n, total, P, part.cta_row, row_w);
     if (row_cap > 0) {
-        DAG_CUDA(cudaMalloc(&cnt, P * sizeof(int)));
+        DAG_CUDA(dev_alloc(&cnt, P * sizeof(int)));
         k_capped_tiles<<<(P + 127) / 128, 128, 0, s>>>(plan->rowptr, part.cta_row, P, row_cap, cnt, nullptr,
                                                       nullptr, nullptr);
         k_prefix_tiles<<<1, CT_THREADS, 0, s>>>(cnt, part.cta_row, P, part.cta_tile, mr_dev);
@@ -252,16 +253,16 @@ int get_partition(dag_plan* plan, int P, Partition** out, cudaStream_t s, int ro
     DAG_CUDA(cudaMemcpyAsync(&tiles, part.cta_tile + P, sizeof(int), cudaMemcpyDeviceToHost, s));
     DAG_CUDA(cudaMemcpyAsync(&part.max_rows, mr_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
     DAG_CUDA(cudaStreamSynchronize(s));
-    cudaFree(mr_dev);
+    dev_free(mr_dev);
     part.tiles = tiles;
-    DAG_CUDA(cudaMalloc(&part.tile_row, (tiles + 1) * sizeof(int)));
-    DAG_CUDA(cudaMalloc(&part.tile_nz, (tiles + 1) * sizeof(int)));
+    DAG_CUDA(dev_alloc(&part.tile_row, (tiles + 1) * sizeof(int)));
+    DAG_CUDA(dev_alloc(&part.tile_nz, (tiles + 1) * sizeof(int)));
     if (row_cap > 0) {
         k_capped_tiles<<<(P + 127) / 128, 128, 0, s>>>(plan->rowptr, part.cta_row, P, row_cap, nullptr,
                                                       part.cta_tile, part.tile_row, part.tile_nz);
         k_tile_end<<<1, 1, 0, s>>>(tiles, plan->n, plan->m, part.tile_row, part.tile_nz);
         DAG_CUDA(cudaStreamSynchronize(s));
-        cudaFree(cnt);
+        dev_free(cnt);
     } else {
         k_tile_coords<<<(tiles + 1 + 255) / 256, 256, 0, s>>>(plan->rowptr, plan->n, plan->m, part.cta_row,
                                                                part.cta_tile, P, tiles, part.tile_row,
@@ -329,11 +330,11 @@ int get_warp_partition(dag_plan* plan, int W, int tile, Partition** out, cudaStr
     const long long T = (total + tile - 1) / tile;
     if (T >= (1LL << 31)) return set_error(DAG_ERR_INVALID, "graph too large for warp tiles");
     part.tiles = (int)T;
-    DAG_CUDA(cudaMalloc(&part.cta_row, (W + 1) * sizeof(int)));
-    DAG_CUDA(cudaMalloc(&part.cta_tile, (W + 1) * sizeof(int)));
-    DAG_CUDA(cudaMalloc(&part.tile_row, (T + 1) * sizeof(int)));
-    DAG_CUDA(cudaMalloc(&part.tile_nz, (T + 1) * sizeof(int)));
-    DAG_CUDA(cudaMalloc(&part.wpub, W * sizeof(unsigned long long)));
+    DAG_CUDA(dev_alloc(&part.cta_row, (W + 1) * sizeof(int)));
+    DAG_CUDA(dev_alloc(&part.cta_tile, (W + 1) * sizeof(int)));
+    DAG_CUDA(dev_alloc(&part.tile_row, (T + 1) * sizeof(int)));
+    DAG_CUDA(dev_alloc(&part.tile_nz, (T + 1) * sizeof(int)));
+    DAG_CUDA(dev_alloc(&part.wpub, W * sizeof(unsigned long long)));
     k_warp_tile_coords<<<(unsigned)((T + 1 + 255) / 256), 256, 0, s>>>(plan->rowptr, plan->n, plan->m, tile, (int)T,
                                                                        part.tile_row, part.tile_nz);
     k_warp_runs<<<(W + 1 + 255) / 256, 256, 0, s>>>(part.tile_row, (int)T, W, part.cta_tile, part.cta_row);
@@ -360,11 +361,11 @@ int get_warp_partition_range(dag_plan* plan, int W, int tile, int lo, int hi, Pa
     Partition part;
     part.nblocks = W;
     part.tiles = (int)T;
-    DAG_CUDA(cudaMalloc(&part.cta_row, (W + 1) * sizeof(int)));
-    DAG_CUDA(cudaMalloc(&part.cta_tile, (W + 1) * sizeof(int)));
-    DAG_CUDA(cudaMalloc(&part.tile_row, (T + 1) * sizeof(int)));
-    DAG_CUDA(cudaMalloc(&part.tile_nz, (T + 1) * sizeof(int)));
-    DAG_CUDA(cudaMalloc(&part.wpub, W * sizeof(unsigned long long)));
+    DAG_CUDA(dev_alloc(&part.cta_row, (W + 1) * sizeof(int)));
+    DAG_CUDA(dev_alloc(&part.cta_tile, (W + 1) * sizeof(int)));
+    DAG_CUDA(dev_alloc(&part.tile_row, (T + 1) * sizeof(int)));
+    DAG_CUDA(dev_alloc(&part.tile_nz, (T + 1) * sizeof(int)));
+    DAG_CUDA(dev_alloc(&part.wpub, W * sizeof(unsigned long long)));
     k_range_tile_coords<<<(unsigned)((T + 1 + 255) / 256), 256, 0, s>>>(plan->rowptr, lo, hi, tile, (int)T,
                                                                         part.tile_row, part.tile_nz);
     k_warp_runs<<<(W + 1 + 255) / 256, 256, 0, s>>>(part.tile_row, (int)T, W, part.cta_tile, part.cta_row);
@@ -409,35 +410,35 @@ int launch_transpose(dag_plan* plan, int* out_rowptr, int* out_colidx, int* perm
     void* tmp = nullptr;
     int* padded = nullptr;
     size_t tmp_bytes = 0;
-    DAG_CUDA(cudaMalloc(&padded, (size_t)(n + 1) * sizeof(int)));
+    DAG_CUDA(dev_alloc(&padded, (size_t)(n + 1) * sizeof(int)));
     DAG_CUDA(cudaMemsetAsync(padded + n, 0, sizeof(int), s));
     DAG_CUDA(cudaMemcpyAsync(padded, plan->outdeg, (size_t)n * sizeof(int), cudaMemcpyDeviceToDevice, s));
     DAG_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp_bytes, padded, out_rowptr, n + 1, s));
-    DAG_CUDA(cudaMalloc(&tmp, tmp_bytes));
+    DAG_CUDA(dev_alloc(&tmp, tmp_bytes));
     DAG_CUDA(cub::DeviceScan::ExclusiveSum(tmp, tmp_bytes, padded, out_rowptr, n + 1, s));
     DAG_CUDA(cudaStreamSynchronize(s));
-    cudaFree(tmp);
-    cudaFree(padded);
+    dev_free(tmp);
+    dev_free(padded);
     if (m == 0) return DAG_OK;
     int *keys_out = nullptr, *vals_in = nullptr, *dst = nullptr;
-    DAG_CUDA(cudaMalloc(&keys_out, (size_t)m * sizeof(int)));
-    DAG_CUDA(cudaMalloc(&vals_in, (size_t)m * sizeof(int)));
-    DAG_CUDA(cudaMalloc(&dst, (size_t)m * sizeof(int)));
+    DAG_CUDA(dev_alloc(&keys_out, (size_t)m * sizeof(int)));
+    DAG_CUDA(dev_alloc(&vals_in, (size_t)m * sizeof(int)));
+    DAG_CUDA(dev_alloc(&dst, (size_t)m * sizeof(int)));
     k_iota<<<1024, 256, 0, s>>>(vals_in, m);
     k_edge_dst<<<(n + 255) / 256, 256, 0, s>>>(plan->rowptr, n, dst);
     tmp_bytes = 0;
     DAG_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, plan->colidx, keys_out, vals_in, perm, (int)m, 0,
                                              bits_for(n), s));
-    DAG_CUDA(cudaMalloc(&tmp, tmp_bytes));
+    DAG_CUDA(dev_alloc(&tmp, tmp_bytes));
     DAG_CUDA(cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, plan->colidx, keys_out, vals_in, perm, (int)m, 0,
                                              bits_for(n), s));
     k_gather_i32<<<1024, 256, 0, s>>>(dst, perm, out_colidx, m);
     DAG_CUDA(cudaGetLastError());
     DAG_CUDA(cudaStreamSynchronize(s));
-    cudaFree(tmp);
-    cudaFree(keys_out);
-    cudaFree(vals_in);
-    cudaFree(dst);
+    dev_free(tmp);
+    dev_free(keys_out);
+    dev_free(vals_in);
+    dev_free(dst);
     return DAG_OK;
 }
 
@@ -507,13 +508,13 @@ static int build_frontier_maps(dag_plan* plan, Partition* part, cudaStream_t s, 
     DAG_CUDA(cub::DeviceScan::InclusiveSum(nullptr, scan_bytes, plan->outdeg, (int*)nullptr, n, s));
     // fr_otile doubles as the scan's scratch before the scatter fills it
     const size_t otile_ints = std::max((size_t)std::max(m, 1LL), (scan_bytes + sizeof(int) - 1) / sizeof(int));
-    if (!plan->fr_orow) DAG_CUDA(cudaMalloc(&plan->fr_orow, (size_t)(n + 1) * sizeof(int)));
-    DAG_CUDA(cudaMalloc(&part->fr_otile, otile_ints * sizeof(int)));
-    if (with_end) DAG_CUDA(cudaMalloc(&part->fr_oend, (size_t)std::max(m, 1LL) * sizeof(int)));
-    DAG_CUDA(cudaMalloc(&part->fr_alist, (size_t)std::max(part->tiles, 1) * sizeof(int)));
-    DAG_CUDA(cudaMalloc(&part->fr_chg, (size_t)n * sizeof(int)));
-    DAG_CUDA(cudaMalloc(&part->fr_glist, (size_t)std::max(part->tiles, 1) * sizeof(int)));
-    DAG_CUDA(cudaMalloc(&part->fr_gchg, ((size_t)n + (size_t)std::max(part->tiles, 1)) * sizeof(int)));
+    if (!plan->fr_orow) DAG_CUDA(dev_alloc(&plan->fr_orow, (size_t)(n + 1) * sizeof(int)));
+    DAG_CUDA(dev_alloc(&part->fr_otile, otile_ints * sizeof(int)));
+    if (with_end) DAG_CUDA(dev_alloc(&part->fr_oend, (size_t)std::max(m, 1LL) * sizeof(int)));
+    DAG_CUDA(dev_alloc(&part->fr_alist, (size_t)std::max(part->tiles, 1) * sizeof(int)));
+    DAG_CUDA(dev_alloc(&part->fr_chg, (size_t)n * sizeof(int)));
+    DAG_CUDA(dev_alloc(&part->fr_glist, (size_t)std::max(part->tiles, 1) * sizeof(int)));
+    DAG_CUDA(dev_alloc(&part->fr_gchg, ((size_t)n + (size_t)std::max(part->tiles, 1)) * sizeof(int)));
     DAG_CUDA(cudaMemsetAsync(plan->fr_orow, 0, sizeof(int), s));
     DAG_CUDA(cub::DeviceScan::InclusiveSum(part->fr_otile, scan_bytes, plan->outdeg, plan->fr_orow + 1, n, s));
     if (m > 0 && part->tiles > 0) {
@@ -526,7 +527,7 @@ static int build_frontier_maps(dag_plan* plan, Partition* part, cudaStream_t s, 
     }
     DAG_CUDA(cudaStreamSynchronize(s));
     // allocated last: a set fr_act marks the maps complete
-    DAG_CUDA(cudaMalloc(&part->fr_act, (size_t)std::max(part->tiles, 1) * sizeof(int)));
+    DAG_CUDA(dev_alloc(&part->fr_act, (size_t)std::max(part->tiles, 1) * sizeof(int)));
     return DAG_OK;
 }
 
@@ -538,7 +539,7 @@ int frontier_maps(dag_plan* plan, Partition* part, cudaStream_t s, bool with_end
         int** arrays[] = {&part->fr_otile, &part->fr_oend, &part->fr_alist, &part->fr_chg,
                           &part->fr_glist, &part->fr_gchg, &part->fr_act};
         for (int** a : arrays) {
-            cudaFree(*a);
+            dev_free(*a);
             *a = nullptr;
         }
     }
@@ -613,16 +614,16 @@ int launch_normalize(dag_plan* plan, const float* w, float* val, float* s_out, c
     if (!plan->nw_perm) {
         int* orow = plan->fr_orow;
         int *ocol = nullptr, *perm = nullptr, *hubs = nullptr;
-        if (!orow) DAG_CUDA(cudaMalloc(&orow, (size_t)(n + 1) * sizeof(int)));
+        if (!orow) DAG_CUDA(dev_alloc(&orow, (size_t)(n + 1) * sizeof(int)));
         plan->fr_orow = orow;
-        DAG_CUDA(cudaMalloc(&ocol, (size_t)std::max(m, 1LL) * sizeof(int)));
-        if (cudaMalloc(&perm, (size_t)std::max(m, 1LL) * sizeof(int)) != cudaSuccess) {
-            cudaFree(ocol);
+        DAG_CUDA(dev_alloc(&ocol, (size_t)std::max(m, 1LL) * sizeof(int)));
+        if (dev_alloc(&perm, (size_t)std::max(m, 1LL) * sizeof(int)) != cudaSuccess) {
+            dev_free(ocol);
             return cuda_check(cudaGetLastError(), "normalisation out-CSR");
         }
         int rc = launch_transpose(plan, orow, ocol, perm, s);
-        cudaFree(ocol);
-        if (rc == DAG_OK && cudaMalloc(&hubs, (size_t)(n + 1) * sizeof(int)) != cudaSuccess)
+        dev_free(ocol);
+        if (rc == DAG_OK && dev_alloc(&hubs, (size_t)(n + 1) * sizeof(int)) != cudaSuccess)
             rc = cuda_check(cudaGetLastError(), "normalisation hub list");
         if (rc == DAG_OK) {
             // hubs[n] counts the list
@@ -635,8 +636,8 @@ int launch_normalize(dag_plan* plan, const float* w, float* val, float* s_out, c
             plan->nw_nhubs = nh;
         }
         if (rc != DAG_OK) {
-            cudaFree(perm);
-            cudaFree(hubs);
+            dev_free(perm);
+            dev_free(hubs);
             return rc;
         }
         plan->nw_hubs = hubs;
@@ -677,12 +678,12 @@ extern "C" int dag_plan_create(const dag_csr* csr, int32_t barrier_timeout_ms, d
     cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
     const int n = p->n;
     int* bad = nullptr;
-    if (cudaMalloc(&p->outdeg, (size_t)n * sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&p->degf, (size_t)n * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&p->x0, (size_t)n * 4) != cudaSuccess || cudaMalloc(&p->x1, (size_t)n * 4) != cudaSuccess ||
-        cudaMalloc(&p->scratch_f, (size_t)n * 4) != cudaSuccess ||
-        cudaMalloc(&p->sync, sizeof(SyncBlock)) != cudaSuccess || cudaMalloc(&bad, sizeof(int)) != cudaSuccess) {
-        cudaFree(bad);
+    if (dev_alloc(&p->outdeg, (size_t)n * sizeof(int)) != cudaSuccess ||
+        dev_alloc(&p->degf, (size_t)n * sizeof(float)) != cudaSuccess ||
+        dev_alloc(&p->x0, (size_t)n * 4) != cudaSuccess || dev_alloc(&p->x1, (size_t)n * 4) != cudaSuccess ||
+        dev_alloc(&p->scratch_f, (size_t)n * 4) != cudaSuccess ||
+        dev_alloc(&p->sync, sizeof(SyncBlock)) != cudaSuccess || dev_alloc(&bad, sizeof(int)) != cudaSuccess) {
+        dev_free(bad);
         cudaGetLastError();
         return fail(set_error(DAG_ERR_NOMEM, "plan workspace allocation failed"));
     }
@@ -693,18 +694,18 @@ extern "C" int dag_plan_create(const dag_csr* csr, int32_t barrier_timeout_ms, d
     int hbad = 0;
     cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) {
-        cudaFree(bad);
+        dev_free(bad);
         return fail(cuda_check(cudaGetLastError(), "rowptr check"));
     }
     if (hbad) {
-        cudaFree(bad);
+        dev_free(bad);
         return fail(set_error(DAG_ERR_INVALID, "rowptr must start at 0, not decrease and end at m"));
     }
     if (p->m > 0) k_out_degree<<<2048, 256, 0, s>>>(p->colidx, p->m, n, p->outdeg, bad);
     k_degf<<<(n + 255) / 256, 256, 0, s>>>(p->outdeg, p->degf, n);
     cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
     cudaError_t e = cudaStreamSynchronize(s);
-    cudaFree(bad);
+    dev_free(bad);
     if (e != cudaSuccess) return fail(cuda_check(e, "out-degree"));
     if (hbad) return fail(set_error(DAG_ERR_INVALID, "colidx entry outside [0, n)"));
     *out = p;
@@ -719,40 +720,46 @@ extern "C" int dag_plan_destroy(dag_plan* p)
 {
     if (!p) return DAG_OK;
     dag::release_batched_graphs(p);
-    cudaFree(p->outdeg);
-    cudaFree(p->degf);
-    cudaFree(p->x0);
-    cudaFree(p->x1);
-    cudaFree(p->scratch_f);
-    cudaFree(p->sync);
-    cudaFree(p->bx);
+    // the plan's memory goes back to its device's pool once every launch that may use it has finished
+    int prev = 0;
+    const bool have_prev = cudaGetDevice(&prev) == cudaSuccess;
+    if (!have_prev || prev != p->device) cudaSetDevice(p->device);
+    cudaDeviceSynchronize();
+    dev_free(p->outdeg);
+    dev_free(p->degf);
+    dev_free(p->x0);
+    dev_free(p->x1);
+    dev_free(p->scratch_f);
+    dev_free(p->sync);
+    cudaFree(p->bx);  // batched workspace: cudaMalloc (batched.cu)
     cudaFree(p->bsync);
     for (auto& kv : p->parts) {
-        cudaFree(kv.second.cta_row);
-        cudaFree(kv.second.cta_tile);
-        cudaFree(kv.second.tile_row);
-        cudaFree(kv.second.tile_nz);
-        cudaFree(kv.second.fr_otile);
-        cudaFree(kv.second.fr_oend);
-        cudaFree(kv.second.fr_act);
-        cudaFree(kv.second.fr_alist);
-        cudaFree(kv.second.fr_chg);
-        cudaFree(kv.second.fr_glist);
-        cudaFree(kv.second.fr_gchg);
-        cudaFree(kv.second.wpub);
-        cudaFree(kv.second.tpub);
+        dev_free(kv.second.cta_row);
+        dev_free(kv.second.cta_tile);
+        dev_free(kv.second.tile_row);
+        dev_free(kv.second.tile_nz);
+        dev_free(kv.second.fr_otile);
+        dev_free(kv.second.fr_oend);
+        dev_free(kv.second.fr_act);
+        dev_free(kv.second.fr_alist);
+        dev_free(kv.second.fr_chg);
+        dev_free(kv.second.fr_glist);
+        dev_free(kv.second.fr_gchg);
+        dev_free(kv.second.wpub);
+        cudaFree(kv.second.tpub);  // cudaMalloc (sweep_warp.cu)
     }
     for (auto& kv : p->range_parts) {
-        cudaFree(kv.second.cta_row);
-        cudaFree(kv.second.cta_tile);
-        cudaFree(kv.second.tile_row);
-        cudaFree(kv.second.tile_nz);
-        cudaFree(kv.second.wpub);
+        dev_free(kv.second.cta_row);
+        dev_free(kv.second.cta_tile);
+        dev_free(kv.second.tile_row);
+        dev_free(kv.second.tile_nz);
+        dev_free(kv.second.wpub);
     }
-    cudaFree(p->fr_orow);
-    cudaFree(p->nw_perm);
-    cudaFree(p->nw_hubs);
-    cudaFree(p->grad_coef);
+    dev_free(p->fr_orow);
+    dev_free(p->nw_perm);
+    dev_free(p->nw_hubs);
+    dev_free(p->grad_coef);
+    if (have_prev && prev != p->device) cudaSetDevice(prev);
     delete p;
     return DAG_OK;
 }
