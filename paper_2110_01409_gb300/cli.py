@@ -1,6 +1,8 @@
 """Run one solve on a generated graph and print its statistics as JSON.
 
     python -m paper_2110_01409_gb300.cli --graph rmat --scale 20 --algo sssp --variant delayed --delta 32
+    python -m paper_2110_01409_gb300.cli --graph rmat --scale 21 --algo adjoint --variant async --delta 0 \
+        --reads warp+cached
 
 Used for single-kernel profiling captures (a small case of the benchmark's
 kernels) and for quick experiments from the shell.
@@ -33,8 +35,9 @@ def main():
     ap.add_argument("--graph", default="rmat", choices=["rmat", "er", "banded"])
     ap.add_argument("--scale", type=int, default=20)
     ap.add_argument("--seed", type=int, default=2)
-    ap.add_argument("--algo", default="pagerank", choices=["pagerank", "sssp", "sssp8"],
-                    help="sssp8: Bellman-Ford with one-byte weights (dag_sssp_u8)")
+    ap.add_argument("--algo", default="pagerank", choices=["pagerank", "sssp", "sssp8", "adjoint"],
+                    help="sssp8: Bellman-Ford with one-byte weights (dag_sssp_u8); adjoint: weighted PageRank "
+                         "forward and backward (FP32 weights, 4,096 targets), the same form for both")
     ap.add_argument("--variant", default="delayed", choices=list(dag.VARIANTS))
     ap.add_argument("--delta", type=int, default=256)
     ap.add_argument("--reads", default="refresh", choices=list(dag.READ_MODES))
@@ -47,8 +50,20 @@ def main():
     plan = dag.Plan.from_graph(g, "cuda")
     plan.set_warp_tile(args.warp_tile)
     out = []
+    model = None
+    if args.algo == "adjoint":
+        model = dag.WeightedPageRank(plan, d=0.85, tol=args.tol, variant=args.variant, delta=args.delta,
+                                     reads=args.reads)
+        w_f = torch.from_numpy(I.weights_f32(g, args.seed)).cuda()
+        targets, wt = I.adjoint_targets(g.n, 4096, seed=5)
+        c = torch.zeros(g.n, dtype=torch.float32, device="cuda")
+        c[torch.from_numpy(targets).cuda()] = torch.from_numpy(wt.astype(np.float32)).cuda()
     for _ in range(args.repeat):
-        if args.algo == "pagerank":
+        if args.algo == "adjoint":
+            r, val, s, st_f = model.forward(w_f)
+            _, _, _, st = model.backward(val, s, r, c)
+            st = {"forward": st_f, "backward": st}
+        elif args.algo == "pagerank":
             _, st = dag.pagerank(plan, 0.85, args.tol, args.variant, args.delta, reads=args.reads)
         else:
             w32 = I.weights_u32(g, args.seed)
