@@ -61,6 +61,7 @@ cudaError_t current_pool(DevicePool** out)
 cudaError_t dev_alloc(void** p, size_t bytes)
 {
     *p = nullptr;
+    if (bytes == 0) return cudaSuccess;  // as cudaMalloc: no memory, a null pointer
     DevicePool* d = nullptr;
     cudaError_t e = current_pool(&d);
     if (e != cudaSuccess) return e;
