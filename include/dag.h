@@ -157,9 +157,10 @@ int dag_plan_set_worker_cap(dag_plan* plan, int32_t max_workers);
  * the end of its target's row); sweep 0 runs every tile. Distances are those
  * of the plain sweep (the synchronous trajectory is the same, sweep for
  * sweep); dag_stats.edges_processed counts the edges actually run. The first
- * solve with a launch shape builds the out-CSR and two int32 maps per edge
- * (about 8m + 4n bytes, kept in the plan). DAG_ERR_INVALID for PageRank or
- * the delayed form.
+ * solve with a launch shape builds the out-CSR row pointers and, per edge,
+ * the tile of its in-CSR position (CTA tiles also the tile ending its
+ * target's row): 4n + 8m bytes on CTA tiles, 4n + 4m on warp tiles, kept in
+ * the plan. DAG_ERR_INVALID for PageRank or the delayed form.
  */
 #define DAG_SSSP_FRONTIER 32
 /*
