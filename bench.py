@@ -407,11 +407,15 @@ def gathers_coherent(variant, delta, reads):
     return ("coherent" in reads) or (asynch and "cached" not in reads)  # own_l1: other blocks through L2
 
 
+SWEEP_SOURCES = ("sweep.cu", "sweep_tma.cu", "sweep_warp.cu", "sweep_warp_frontier.cu", "sweep_warp.cuh",
+                 "sweep_common.cuh", "dag_internal.cuh")
+
+
 def sweep_source_hash():
     """sha256 of the sweep kernel's sources: a recorded ncu traffic figure is
     used only while it still describes the kernel that runs."""
     h = hashlib.sha256()
-    for f in ("sweep.cu", "sweep_tma.cu", "sweep_warp.cu", "sweep_common.cuh", "dag_internal.cuh"):
+    for f in SWEEP_SOURCES:
         with open(os.path.join(ROOT, "paper_2110_01409_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()

@@ -61,3 +61,26 @@ def test_committed_record_parses():
     assert any(k.endswith(f"rmat{bench.SCALE} dram_bytes_per_edge_run") and float(v) > 0 for k, v in keys.items())
     if keys["sweep_source_sha256"] != bench.sweep_source_hash():
         pytest.skip("kernel sources changed since the capture: the bench reports traffic as null")
+
+
+def test_source_hash_covers_every_sweep_kernel_source():
+    # a recorded traffic figure must go null when any file of a timed sweep kernel changes
+    csrc = os.path.join(bench.ROOT, "paper_2110_01409_gb300", "csrc")
+    sweep_files = {f for f in os.listdir(csrc) if f.startswith("sweep") and f.endswith((".cu", ".cuh"))}
+    assert sweep_files <= set(bench.SWEEP_SOURCES)
+    assert {"sweep_common.cuh", "dag_internal.cuh"} <= set(bench.SWEEP_SOURCES)
+
+
+def test_kernel_names_of_the_steps_choices_have_recorded_keys():
+    # the tuner's choices for the step (and the delayed rows) name kernels that the record holds
+    path = os.path.join(bench.ROOT, "profiles", "sweep_traffic.txt")
+    with open(path) as f:
+        keys = {line.split(" rmat")[0] for line in f if line.strip() and not line.startswith(("#", "sweep_source"))}
+    assert bench.kernel_name("BF8", "async", 0, "ordered+cached+frontier", 7) in keys
+    assert bench.kernel_name("BF8", "delayed", 0, "warp+cached+frontier", 7) in keys
+    assert bench.kernel_name("PR", "async", 0, "ordered+cached", 11) in keys
+    assert bench.kernel_name("PR", "delayed", 256, "warp+cached", 7) in keys
+    assert bench.kernel_name("BF8", "delayed", 256, "warp+cached", 7) in keys
+    # the CTA-tile names
+    assert bench.kernel_name("BF8", "async", 0, "cached+frontier") == "sweep_tma_kernel<BF8,frontier>"
+    assert bench.kernel_name("PR", "delayed", 32, "refresh") == "sweep_kernel<PR,DELAYED>"
