@@ -353,6 +353,16 @@ def pagerank_adjoint(in_plan: Plan, out_plan: Plan, val, val_out, s, rank, c, d=
                      variant="delayed", delta=256, max_iters=10000, want_lambda=False, stream=None, reads="refresh"):
     """Adjoint solve + gradients (reads: the adjoint sweep's read path, see READ_MODES; the warp forms run
     on out_plan's warp tile). Returns (grad_w [m], grad_t [n], lambda or None, stats)."""
+    n, m = in_plan.n, in_plan.m
+    for t, nm in ((rank, "rank"), (s, "s"), (c, "c")):
+        if t is None:
+            raise ValueError(f"{nm}: required")
+        _dev(t, torch.float32, n, nm)
+    if m:
+        for t, nm in ((val, "val"), (val_out, "val_out")):
+            if t is None:
+                raise ValueError(f"{nm}: required")
+            _dev(t, torch.float32, m, nm)
     dev = rank.device
     gw = torch.empty(in_plan.m, dtype=torch.float32, device=dev)
     gt = torch.empty(in_plan.n, dtype=torch.float32, device=dev)
@@ -440,6 +450,7 @@ class WeightedPageRank:
         return r, val, s, st
 
     def backward(self, val, s, r, c):
+        _dev(val, torch.float32, self.plan.m, "val")
         val_out = torch.empty_like(val)
         _raise(lib().dag_gather_f32(_ptr(val), _ptr(self.perm), self.plan.m, _ptr(val_out), _stream()), False)
         return pagerank_adjoint(self.plan, self.out_plan, val, val_out, s, r, c.contiguous(), self.d, self.tol,

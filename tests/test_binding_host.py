@@ -70,3 +70,28 @@ def _dev_accepting(rowptr):
         return real(t, dtype, n, name)
 
     return check
+
+
+class _FakePlan:
+    def __init__(self, n, m):
+        self.n, self.m, self.h = n, m, None
+
+
+@pytest.mark.parametrize("bad", ["rank", "s", "c", "val", "val_out"])
+def test_adjoint_refuses_host_tensors_before_any_library_call(bad, monkeypatch):
+    # every array of the adjoint reaches the kernels as a device address: a host (or mis-sized) one is
+    # refused in Python first
+    calls = []
+    monkeypatch.setattr(dag, "lib", lambda: calls.append(1))
+    n, m = 8, 12
+    real = dag._dev
+
+    def check(t, dtype, k, name):  # the other arrays pass as if they were on the device
+        return real(t, dtype, k, name) if name == bad else t
+
+    monkeypatch.setattr(dag, "_dev", check)
+    args = dict(val=torch.zeros(m), val_out=torch.zeros(m), s=torch.zeros(n), rank=torch.zeros(n),
+                c=torch.zeros(n))
+    with pytest.raises(ValueError, match=bad):
+        dag.pagerank_adjoint(_FakePlan(n, m), _FakePlan(n, m), **args)
+    assert not calls
