@@ -301,6 +301,7 @@ def ppr_batched(plan: Plan, V: torch.Tensor, d=0.85, tol=1e-6, variant="async", 
     n, B = V.shape
     _dev(V, torch.float32, n * B, "V")
     out = out if out is not None else torch.empty_like(V)
+    _dev(out, torch.float32, n * B, "out")
     iters = torch.empty(B, dtype=torch.int32, device=V.device)
     st = _BStats()
     rc = lib().dag_ppr_batched(plan.h, d, tol, _variant(variant), delta, max_iters, B, _ptr(V), _ptr(out),
@@ -319,6 +320,7 @@ def sssp_batched(plan: Plan, srcs: torch.Tensor, w, variant="async", delta=0, ma
     if plan.m:
         _dev(w, torch.uint8 if u8 else torch.int32, plan.m, "w")
     out = out if out is not None else torch.empty((plan.n, B), dtype=torch.int32, device=srcs.device)
+    _dev(out, torch.int32, plan.n * B, "out")
     iters = torch.empty(B, dtype=torch.int32, device=srcs.device)
     max_iters = plan.n + 1 if max_iters is None else max_iters
     st = _BStats()

@@ -95,3 +95,20 @@ def test_adjoint_refuses_host_tensors_before_any_library_call(bad, monkeypatch):
     with pytest.raises(ValueError, match=bad):
         dag.pagerank_adjoint(_FakePlan(n, m), _FakePlan(n, m), **args)
     assert not calls
+
+
+@pytest.mark.parametrize("which", ["ppr", "sssp"])
+def test_batched_refuses_a_host_output_before_any_library_call(which, monkeypatch):
+    calls = []
+    monkeypatch.setattr(dag, "lib", lambda: calls.append(1))
+    n, m, B = 8, 12, 4
+    real = dag._dev
+    monkeypatch.setattr(dag, "_dev", lambda t, dtype, k, name: real(t, dtype, k, name) if name == "out" else t)
+    plan = _FakePlan(n, m)
+    with pytest.raises(ValueError, match="out"):
+        if which == "ppr":
+            dag.ppr_batched(plan, torch.zeros(n, B), out=torch.zeros(n, B))
+        else:
+            dag.sssp_batched(plan, torch.zeros(B, dtype=torch.int32), torch.zeros(m, dtype=torch.uint8),
+                             out=torch.zeros(n, B, dtype=torch.int32))
+    assert not calls
